@@ -1,0 +1,421 @@
+#!/usr/bin/env python3
+"""Throughput of the LOFAR station-to-beam path on GB300: station-samples/s.
+
+A step is one pass of the whole path (integer shift, 16-tap FIR + 256-point FFT, delay phase +
+bandpass + corner turn, weights + tied-array beam former, Stokes + integration) over one block of
+the workload through lbf_run_block.  Default workload: 48 stations (24 core in a 2 km disc, 24
+remote to 80 km), 244 subbands of 195312.5 Hz, 196608-sample int16 blocks, 127 hex beams, Stokes I
+integrated over 16 spectra, plain FP32 -- one 18.4 GB block per step (inputs larger than L2).
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on the host cores
+instead (bounded sample of the same workload).
+"""
+
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1105_0661_gb300 import dist  # noqa: E402
+from synth import generate as G  # noqa: E402
+
+FP32_LANES_PER_SM = 128      # FFMA lanes per SM (4 sub-partitions x 32)
+N_SM = 152
+
+
+def workload(name: str):
+    if name == "lofar":
+        return G.workload_lofar_fp32(0)
+    if name == "tiny":
+        return G.workload_tiny(0)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu), "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        rows = list(csv.reader(open(self.path)))
+        os.unlink(self.path)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- roofline
+def algorithmic_work(wl, dims):
+    """Per-launch algorithmic bytes / flops of each kernel (the units the design notes state)."""
+    S, F, T, B, M = wl.n_stations, wl.n_subbands, wl.block_samples, wl.n_beams, dims.n_spectra
+    word = 8 if wl.sample_bits == 16 else 4
+    ss = S * F * T                              # station-samples per block
+    nS = dims.n_stokes
+    out_bytes = B * max(nS, 1) * F * 256 * (M // wl.int_factor) * 4 if nS else B * F * T * 16
+    return {
+        "ppf_ct": ("hbm", ss * (word + 16)),    # read int samples, write 2 pols x cf32
+        "ppf": ("hbm", ss * (word + 16)),
+        "hist_update": ("hbm", 2 * S * F * dims.history_samples * word),
+        "delay_ct": ("hbm", ss * 32),
+        "bf_few": ("hbm", ss * 16 + out_bytes),  # read corner-turned cf32 once, write the output
+        "bf_many": ("alu", 8.0 * B * ss * 2),   # 8 flop per complex MAC, B x S x 2 pols x T per subband
+        "stokes": ("hbm", B * F * T * 16 + out_bytes),
+    }
+
+
+def traffic_from_profiles(kernel: str):
+    """DRAM bytes per launch recorded from an ncu capture, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.md")
+    if not os.path.exists(path):
+        return None
+    src = {"bf_many": "beamform.cu", "bf_few": "beamform.cu", "ppf_ct": "ppf.cu", "ppf": "ppf.cu",
+           "hist_update": "ppf.cu", "delay_ct": "delay.cu", "stokes": "stokes.cu"}.get(kernel)
+    if src is None:
+        return None
+    h = hashlib.sha256(open(os.path.join(ROOT, "paper_1105_0661_gb300", "csrc", src), "rb").read()).hexdigest()[:16]
+    for line in open(path):
+        cells = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cells) >= 4 and cells[0] == kernel and cells[2] == h:
+            try:
+                return float(cells[1])
+            except ValueError:
+                return None
+    return None
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def _oracle_worker(args):
+    os.environ["OMP_NUM_THREADS"] = "1"
+    wl, f, blk = args
+    from oracle import lbf_oracle
+    t0 = time.perf_counter()
+    out = lbf_oracle.observation_from_workload(wl.subset([f])).run_block(blk)
+    return time.perf_counter() - t0, out
+
+
+def run_oracle_sample(wl, blocks, subbands, workers):
+    """Time the oracle on the given subbands (one process per subband, BLAS single-threaded).
+    Returns (wall seconds, station-samples, per-subband outputs)."""
+    env_keys = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
+    old = {k: os.environ.get(k) for k in env_keys}
+    for k in env_keys:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(workers) as pool:
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_worker, [(wl, f, b) for f, b in zip(subbands, blocks)])
+            wall = time.perf_counter() - t0
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    ss = wl.n_stations * len(subbands) * wl.block_samples
+    return wall, ss, [r[1] for r in res]
+
+
+def host_block_slices(wl, seed, subbands):
+    """Station data of the listed subbands, [S][1][T][2][2], drawn by the same seeded device
+    generator the GPU arm uses (generated on the GPU when available, else as host noise)."""
+    import numpy as np
+    try:
+        import torch
+        if torch.cuda.is_available():
+            from synth.device import make_block_device
+            d = make_block_device(wl, seed, torch.device("cuda", torch.cuda.current_device()))
+            out = [d[:, f:f + 1].cpu().numpy() for f in subbands]
+            del d
+            torch.cuda.empty_cache()
+            return out
+    except ImportError:
+        pass
+    return [G.make_block(wl.subset([f]), seed=seed, source="noise") for f in subbands]
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world = dist.init("gloo")
+    if rank != 0:
+        return 0
+    wl = workload(args.workload)
+    nsub = args.cpu_subbands
+    subbands = list(range(nsub))
+    blocks = host_block_slices(wl, 0, subbands)
+    for _ in range(args.warmup):
+        run_oracle_sample(wl, blocks, subbands, nsub)
+    times = []
+    ss = 0
+    for _ in range(args.steps):
+        wall, ss, _ = run_oracle_sample(wl, blocks, subbands, nsub)
+        times.append(wall)
+    total = sum(times)
+    value = ss * args.steps / total
+    line = {
+        "impl": "reference", "metric": "station-samples/s", "value": value, "unit": "station-samples/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(wl, args),
+        "cpu_baseline": {"value": value, "unit": "station-samples/s", "cores": nsub, "kind": "oracle",
+                         "sample": f"{nsub} of {wl.n_subbands} subbands x {wl.n_stations} stations x "
+                                   f"{wl.block_samples} samples per step, whole path, FP64 numpy"},
+        "e2e": {"value": value, "unit": "station-samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict(wl, args):
+    return {"workload": wl.name, "stations": wl.n_stations, "subbands": wl.n_subbands,
+            "block_samples": wl.block_samples, "channels": wl.n_channels, "taps": wl.n_taps,
+            "beams": wl.n_beams, "output": wl.output, "int_factor": wl.int_factor,
+            "sample_bits": wl.sample_bits, "precision": args.precision,
+            "l2": "inputs larger than L2 (one block is %.1f GB)" % (wl.station_samples() * (8 if wl.sample_bits == 16 else 4) / 1e9),
+            "parallelism": "independent observation per GPU (no collective)"}
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+
+    from paper_1105_0661_gb300 import Plan
+    from paper_1105_0661_gb300.build_lib import build
+    from synth.device import make_block_device
+
+    rank, local, world = dist.env_rank()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist.init("nccl" if world > 1 else "gloo")
+    if rank == 0 or not os.path.exists(os.path.join(ROOT, "paper_1105_0661_gb300", "_lib", "liblbf.so")):
+        build()
+    dist.barrier(dev)
+    wl = workload(args.workload)
+    pk, pk_kind = peaks()
+
+    # cpu baseline first (spawned workers, before the large device allocations)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        subbands = list(range(args.cpu_subbands))
+        blocks = host_block_slices(wl, 0, subbands)
+        wall, ss, ref_out = run_oracle_sample(wl, blocks, subbands, args.cpu_subbands)
+        cpu = {"value": ss / wall, "unit": "station-samples/s", "cores": args.cpu_subbands, "kind": "oracle",
+               "sample": f"{args.cpu_subbands} of {wl.n_subbands} subbands x {wl.n_stations} stations x "
+                         f"{wl.block_samples} samples (one block), whole path, FP64 numpy, one process per subband"}
+    else:
+        ref_out = None
+
+    plan = Plan.from_workload(wl, precision=args.precision)
+    dims = plan.dims
+    d_in = make_block_device(wl, seed=rank, device=dev)
+    out_dtype = torch.float32 if dims.n_stokes else torch.complex64
+    d_out = torch.empty(plan.shape("stokes") if dims.n_stokes else plan.shape("vol"), dtype=out_dtype, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    # parity of the timed configuration on the oracle's sample (first block of a fresh stream)
+    parity = None
+    if ref_out is not None:
+        plan.reset_state(stream)
+        plan.run_block(d_in, d_out, stream)
+        stream.synchronize()
+        errs = []
+        for f, ref in zip(range(args.cpu_subbands), ref_out):
+            got = d_out[:, :, f:f + 1].double().cpu().numpy()
+            I = ref[:, 0]
+            errs.append(float((abs(got[:, 0] - I) / I).max()))
+        parity = {"max_rel_err_stokes_I": max(errs), "subbands": args.cpu_subbands}
+
+    for _ in range(args.warmup):
+        plan.run_block(d_in, d_out, stream)
+    stream.synchronize()
+    dist.barrier(dev)
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
+    smi_index = vis[local].strip() if len(vis) > local and vis[local].strip() else str(local)
+    with ClockSampler(smi_index) as clk:
+        plan.trace_begin(3 * args.steps + 8)
+        torch.cuda.synchronize(dev)
+        dist.barrier(dev)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            plan.run_block(d_in, d_out, stream)
+        ev1.record(stream)
+        stream.synchronize()
+        torch.cuda.synchronize(dev)
+        dist.barrier(dev)
+        trace = plan.trace_end()
+    clocks = clk.summary()
+    ms_local = ev0.elapsed_time(ev1)
+    ms = dist.reduce_scalar(ms_local, "max", dev)
+    ss_step = wl.station_samples()
+    value = world * ss_step * args.steps / (ms / 1e3)
+
+    # end to end through the host-buffer C-ABI call (pinned host memory, copies inside)
+    e2e = None
+    if not args.no_e2e:
+        h_in = torch.empty(d_in.shape, dtype=d_in.dtype, pin_memory=True)
+        h_in.copy_(d_in)
+        h_out = torch.empty(d_out.shape, dtype=d_out.dtype, pin_memory=True)
+        d_stage = torch.empty_like(d_in)
+        plan.run_block_host(h_in, h_out, d_stage, d_out, stream)
+        stream.synchronize()
+        dist.barrier(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k2 = max(1, min(args.steps, args.e2e_steps))
+        e0.record(stream)
+        for _ in range(k2):
+            plan.run_block_host(h_in, h_out, d_stage, d_out, stream)
+        e1.record(stream)
+        stream.synchronize()
+        ems = dist.reduce_scalar(e0.elapsed_time(e1), "max", dev)
+        e2e = {"value": world * ss_step * k2 / (ems / 1e3), "unit": "station-samples/s",
+               "h2d_bytes_per_step": dims.in_bytes, "d2h_bytes_per_step": dims.out_bytes,
+               "steps": k2, "ms_per_step": ems / k2}
+        del h_in, h_out, d_stage
+
+    # roofline of the dominant kernel from the live trace
+    work = algorithmic_work(wl, dims)
+    kernels = {}
+    total_ms = sum(v[1] for k, v in trace.items() if not k.startswith("_"))
+    for k, v in trace.items():
+        if k.startswith("_"):
+            continue
+        n, tms = v
+        avg_s = tms / n / 1e3
+        bound, amount = work[k]
+        kernels[k] = {"launches": n, "avg_ms": tms / n, "share": tms / total_ms, "bound": bound}
+        if bound == "alu":
+            kernels[k]["achieved_tflops"] = amount / avg_s / 1e12
+        else:
+            kernels[k]["achieved_gbs"] = amount / avg_s / 1e9
+    dom = max(kernels, key=lambda k: kernels[k]["share"])
+    bound, amount = work[dom]
+    avg_s = kernels[dom]["avg_ms"] / 1e3
+    if bound == "alu":
+        peak_tf = N_SM * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        achieved = amount / avg_s / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": achieved / peak_tf, "traffic": traffic_from_profiles(dom),
+                "peak_source": f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 flop x "
+                               f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind} max SM clock)"}
+    else:
+        peak = pk["hbm_gbs"]
+        achieved = amount / avg_s / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic_from_profiles(dom),
+                "peak_source": f"{pk_kind} hbm_gbs"}
+
+    launches = sum(v[0] for k, v in trace.items() if not k.startswith("_")) + trace.get("_dropped", 0)
+    bf_flop = 8.0 * wl.n_beams * ss_step * 2
+    line = {
+        "metric": "station-samples/s", "value": value, "unit": "station-samples/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "f16", "data": "synthetic",
+        "config": config_dict(wl, args), "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+        "cpu_baseline": cpu, "clocks": clocks, "kernels": kernels,
+        "beamform_tflops": bf_flop * args.steps / (sum(v[1] for k, v in trace.items() if k.startswith("bf_")) / 1e3) / 1e12,
+        "parity": parity,
+        "paper_context": "Blue Gene/P rack: up to 198 Gb/s = 3.1e9 station-samples/s (64 stations x 248 subbands)",
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    dist.barrier(dev)
+    dist.finalize()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="lofar", choices=["lofar", "tiny"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16tc"])
+    ap.add_argument("--cpu-subbands", type=int, default=4)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("bench: warm-up must be >= 3 steps", file=sys.stderr)
+        return 2
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

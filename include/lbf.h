@@ -1,0 +1,201 @@
+/*
+ * lbf.h -- C ABI of the GB300 LOFAR station-to-beam library.
+ *
+ * The library computes the beam-forming pipeline of Mol & Romein, "The LOFAR Beam Former:
+ * Implementation and Performance Analysis" (Sections 3 and 4): per subband a poly-phase filter
+ * bank (16-tap FIR + 256-point FFT into channels, Section 4.2), per-station delay compensation as
+ * an integer sample shift plus a per-sample phase rotation with bandpass correction (Sections 3,
+ * 4.3), the tied-array beam former -- a complex weighted sum over stations per beam, channel,
+ * polarisation and sample, with weights depending on channel frequency, station position and
+ * beam direction (Section 4.3) -- and Stokes I or IQUV with time integration (Sections 4.5, 5.1).
+ *
+ * Conventions shared by every call
+ *   - All sample/beam buffers are DEVICE pointers owned by the caller; the library never frees
+ *     them.  Every call is asynchronous on the caller's CUDA stream (a cudaStream_t passed as
+ *     void*, NULL = legacy default stream) unless stated otherwise.
+ *   - A plan owns device copies of its tables (taps, bandpass, delays) and its device-resident
+ *     state: the FIR/shift history of every (station, subband) stream and the run_block scratch.
+ *   - Every call returns lbf_status; nothing is thrown across the ABI.  Bad arguments give
+ *     LBF_EINVAL before any device work is enqueued.  A launch error, or an asynchronous error
+ *     from earlier work, gives LBF_ECUDA.
+ *   - One plan is one stream of blocks: calls on a plan must not overlap in time (use one plan
+ *     per concurrent observation / stream).
+ *
+ * Array layouts (row-major, rightmost index fastest; cf32 = interleaved complex float32):
+ *   in    [S][F][T][P][2]     int16 or int8   station samples (Section 3: each sample is two complex
+ *                                              16-bit integers, X and Y polarisation); P = 2
+ *   chan  [F][S][P][M][N]     cf32            filter-bank output, channel c (ascending frequency)
+ *   ct    [F][N][S][P][M]     cf32            delay-compensated, bandpass-corrected, corner-turned
+ *   vol   [B][F][N][P][M]     cf32            tied-array beam voltages (complex-voltages pipeline)
+ *   out   [B][nS][F][N][M/Q]  float32         Stokes I (nS = 1) or IQUV (nS = 4), integrated
+ *   with S stations, F subbands, T samples per block, N = 256 channels, M = T/N spectra,
+ *   B beams, Q the integration factor.
+ *
+ * Definitions (the readings used where the paper is silent):
+ *   tau_s(l,m) = -(x_s l + y_s m + z_s sqrt(1-l^2-m^2))/c       plane-wave geometric delay
+ *   n_s = round-half-away(tau_s(l0,m0)/Ts), d_s = max_s n_s - n_s     integer shift (Section 3)
+ *   x'_s[j] = x_s[j - d_s]                   samples before the first block are zero
+ *   v_m[p] = sum_{t<16} h[tN+p] x'[(m-15+t)N + p]                    FIR, h[0] on the oldest sample
+ *   X_m[k] = sum_p v_m[p] exp(-2 pi i p k/N),  channel c = (k + N/2) mod N,  df_c = (c-N/2) fs/N
+ *   Y = X * bp[c] * exp(+2 pi i (f0_f tau_s + df_c (tau_s - n_s Ts)))        (Sections 3, 4.3)
+ *   w[b,s] = exp(+2 pi i (f0_f + df_c)(tau_s(l0+dl_b, m0+dm_b) - tau_s(l0,m0)))  (Section 4.3)
+ *   V_b = sum_s w[b,s] Y_s;  I = |X|^2+|Y|^2, Q = |X|^2-|Y|^2, U = 2Re(X conj Y), V = 2Im(X conj Y)
+ *   (Section 4.5), each summed over Q consecutive spectra (Section 5.1).
+ */
+#ifndef LBF_H
+#define LBF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LBF_OK = 0,
+  LBF_EINVAL = 1,      /* bad argument, shape, NULL pointer or unsupported combination */
+  LBF_ENOMEM = 2,      /* device allocation failed */
+  LBF_ECUDA = 3,       /* a CUDA runtime error (launch or earlier asynchronous error) */
+  LBF_ESTATE = 4,      /* plan in an unusable state (e.g. destroyed, or device mismatch) */
+  LBF_ETIMEOUT = 5,    /* a bounded device-side wait gave up */
+  LBF_EBUSY = 6,       /* resource temporarily unavailable */
+  LBF_EUNSUPPORTED = 7 /* valid request this build does not implement */
+} lbf_status;
+
+typedef enum { LBF_I8 = 8, LBF_I16 = 16 } lbf_sample_bits;
+
+/* Pipelines of Section 3: complex voltages, Stokes I, Stokes IQUV. */
+typedef enum { LBF_VOLTAGES = 0, LBF_STOKES_I = 1, LBF_STOKES_IQUV = 4 } lbf_output;
+
+typedef enum { LBF_FP32 = 0, LBF_FP16_TC = 1 } lbf_precision;
+
+/* Beam-former kernel choice: AUTO picks the bandwidth-bound few-beam kernel for small B and the
+ * register-tiled many-beam kernel otherwise. */
+typedef enum { LBF_BF_AUTO = 0, LBF_BF_FEW = 1, LBF_BF_MANY = 2 } lbf_bf_variant;
+
+typedef struct lbf_config {
+  int32_t n_stations;     /* S >= 1 */
+  int32_t n_subbands;     /* F >= 1 */
+  int32_t n_channels;     /* N; this build supports 256 */
+  int32_t n_taps;         /* L; this build supports 16 */
+  int32_t n_beams;        /* B >= 1 */
+  int32_t block_samples;  /* T >= 0, a multiple of N (T = 0: every call is a no-op) */
+  int32_t int_factor;     /* Q in {1,2,4,8,16,32}; for Stokes outputs M = T/N must be a multiple */
+  int32_t sample_bits;    /* 16 (int16) or 8 (int8) */
+  int32_t output;         /* lbf_output */
+  int32_t precision;      /* lbf_precision */
+  int32_t bf_variant;     /* lbf_bf_variant */
+  int32_t reserved;       /* must be 0 */
+  double sample_rate_hz;  /* fs of one subband (195312.5 for LOFAR's 195 kHz subbands) */
+  double phase_centre_l;  /* direction cosines (l0, m0) of the phase centre */
+  double phase_centre_m;
+  const double *station_xyz_m;     /* HOST [S][3] station positions, metres, local ENU */
+  const double *subband_centre_hz; /* HOST [F] sky frequency of each subband's centre */
+  const double *beam_dlm;          /* HOST [B][2] beam offsets (dl, dm) from the phase centre */
+  const float *fir_taps;           /* HOST [L*N] prototype filter, h[t*N + p] */
+  const float *bandpass;           /* HOST [N] per-channel bandpass correction, NULL = all ones */
+} lbf_config;
+
+typedef struct lbf_dims {
+  int32_t n_stations, n_subbands, n_channels, n_taps, n_beams, block_samples, int_factor;
+  int32_t n_spectra;          /* M = T / N */
+  int32_t n_stokes;           /* nS: 1 (I), 4 (IQUV), 0 (voltages) */
+  int32_t d_max;              /* largest integer shift d_s, in samples */
+  int32_t history_samples;    /* H = (L-1) N + d_max samples kept per (station, subband) */
+  int32_t bf_kernel;          /* beam-former kernel the plan uses: LBF_BF_FEW or LBF_BF_MANY */
+  size_t in_bytes;            /* bytes of one input block */
+  size_t chan_bytes;          /* bytes of a chan buffer */
+  size_t ct_bytes;            /* bytes of a ct buffer */
+  size_t vol_bytes;           /* bytes of a vol buffer */
+  size_t out_bytes;           /* bytes of one run_block output (vol_bytes for voltages) */
+  size_t stokes_bytes;        /* bytes of a Stokes buffer [B][nS][F][N][M/Q] (0 for voltages) */
+  size_t workspace_bytes;     /* device scratch the plan holds for lbf_run_block */
+} lbf_dims;
+
+typedef struct lbf_plan_s *lbf_plan_t;
+
+/* Create a plan (Section 4 pipeline for one observation).  Validates `cfg`, computes the FP64
+ * geometry on the host (phase-centre delays tau_s, integer shifts n_s and d_s, beam delay
+ * differences), copies the tables to the current CUDA device, allocates the history (zeroed: the
+ * stream starts with zero samples) and the run_block scratch.  Synchronous.  The config's host
+ * arrays are copied; the caller keeps ownership.  On error *out is set to NULL.
+ * Errors: LBF_EINVAL (bad config), LBF_EUNSUPPORTED (N != 256, L != 16, FP16_TC precision),
+ * LBF_ENOMEM, LBF_ECUDA. */
+lbf_status lbf_plan(const lbf_config *cfg, lbf_plan_t *out);
+
+/* Release every device buffer of the plan (synchronises the device first). NULL is a no-op. */
+lbf_status lbf_plan_destroy(lbf_plan_t plan);
+
+/* Sizes and derived dimensions of a plan (host only, no device work). */
+lbf_status lbf_plan_dims(lbf_plan_t plan, lbf_dims *out);
+
+/* Copy the integer shifts n_s and d_s (Section 3 sample-level delay compensation) of the S
+ * stations to the HOST arrays n_shift[S] and d_shift[S] (either may be NULL). */
+lbf_status lbf_plan_shifts(lbf_plan_t plan, int32_t *n_shift, int32_t *d_shift);
+
+/* Zero the FIR/shift history on `stream`: the next block starts a new stream of samples. */
+lbf_status lbf_reset_state(lbf_plan_t plan, void *stream);
+
+/* Steps a1-a3: integer shift + int->float conversion + 16-tap FIR + 256-point FFT (Sections 3,
+ * 4.2) of one block.  d_in: device `in` layout; d_chan: device `chan` layout (written).
+ * Advances the plan's history by one block. */
+lbf_status lbf_ppf(lbf_plan_t plan, const void *d_in, void *d_chan, void *stream);
+
+/* Step a4: sub-sample delay compensation (phase rotation) + bandpass + corner turn (Sections 3,
+ * 4.3).  d_chan: device `chan` layout (read); d_ct: device `ct` layout (written).  Stateless. */
+lbf_status lbf_delay_correct(lbf_plan_t plan, const void *d_chan, void *d_ct, void *stream);
+
+/* Steps a5-a6: weights generated on the device (FP64 phase, reduced to one cycle, FP32 sincos)
+ * and the tied-array beam sum (Section 4.3).  d_ct: device `ct` (read); d_vol: device `vol`
+ * layout (written).  Stateless. */
+lbf_status lbf_beamform(lbf_plan_t plan, const void *d_ct, void *d_vol, void *stream);
+
+/* Steps a5-a7 fused: beam former with the Stokes/integration epilogue (Sections 4.3, 4.5, 5.1).
+ * d_ct: device `ct` (read); d_out: device `out` layout (written).  Requires a Stokes output. */
+lbf_status lbf_beamform_stokes(lbf_plan_t plan, const void *d_ct, float *d_out, void *stream);
+
+/* Step a7: Stokes I/IQUV (as configured) with integration over Q spectra (Sections 4.5, 5.1).
+ * d_vol: device `vol` (read); d_out: device `out` layout (written).  Requires a Stokes output. */
+lbf_status lbf_stokes(lbf_plan_t plan, const void *d_vol, float *d_out, void *stream);
+
+/* Steps a1-a7 for one block, fused: filter bank with the delay/bandpass/corner-turn epilogue into
+ * the plan's scratch, then the beam former with the Stokes epilogue (or voltages).  d_in: device
+ * `in`; d_out: device `out` (Stokes) or `vol` (voltages).  Advances the history by one block.
+ * Equal, within FP32 rounding, to lbf_ppf -> lbf_delay_correct -> lbf_beamform -> lbf_stokes. */
+lbf_status lbf_run_block(lbf_plan_t plan, const void *d_in, void *d_out, void *stream);
+
+/* lbf_run_block with HOST buffers: enqueues on `stream` the copy h_in -> d_in (in_bytes), the
+ * fused path d_in -> d_out, and the copy d_out -> h_out (out_bytes), one cudaMemcpyAsync each.
+ * h_in/h_out should be page-locked (cudaHostAlloc / pinned) for the copies to be asynchronous;
+ * d_in/d_out are caller-owned device staging buffers of the documented sizes.  Returns once the
+ * work is enqueued; synchronise the stream before reading h_out. */
+lbf_status lbf_run_block_host(lbf_plan_t plan, const void *h_in, void *h_out, void *d_in, void *d_out,
+                              void *stream);
+
+/* Kernel timing trace (CUDA events around every kernel the plan launches).
+ * lbf_trace_begin allocates event pairs for up to `max_launches` launches and starts recording;
+ * lbf_trace_end synchronises on the recorded events, writes per-kernel totals to `out` and frees
+ * the events.  While no trace is active the calls record nothing. */
+typedef struct lbf_trace {
+  int32_t n_kernels;           /* entries used in the arrays below */
+  int32_t launches[8];         /* launches per kernel */
+  double total_ms[8];          /* summed event time per kernel */
+  char names[8][32];           /* kernel names: "ppf", "ppf_ct", "hist_update", "delay_ct",
+                                  "bf_few", "bf_many", "stokes" */
+  int32_t dropped;             /* launches not recorded because max_launches was reached */
+} lbf_trace;
+lbf_status lbf_trace_begin(lbf_plan_t plan, int32_t max_launches);
+lbf_status lbf_trace_end(lbf_plan_t plan, lbf_trace *out);
+
+/* Human-readable name of a status code (static string). */
+const char *lbf_status_string(lbf_status s);
+
+/* Library version string (static). */
+const char *lbf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBF_H */

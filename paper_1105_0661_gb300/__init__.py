@@ -1,0 +1,6 @@
+"""GB300-native LOFAR station-to-beam library (Mol & Romein, "The LOFAR Beam Former").
+
+The compute path is the CUDA library built from csrc/ (sm_103a); `lbf` is its Python binding.
+"""
+
+from .lbf import LbfError, Plan, load_library  # noqa: F401

@@ -1,0 +1,278 @@
+// Tied-array beam former (Section 4.3) with on-the-fly positional weights and an optional fused
+// Stokes / time-integration epilogue (Sections 4.5, 5.1).
+//
+// Per (subband f, channel c) the work is a complex product  V[b][pol, m] = sum_s w[b,s] Y[s][pol, m]
+// with w[b,s] = exp(+2 pi i f_c dtau[b,s]), f_c = f0_f + df_c.  The weights are generated per CTA
+// into shared memory: FP64 phase in cycles, reduced to one cycle, FP32 sincos.
+//
+// Two kernels:
+//  * few-beam (bandwidth bound): one thread per spectrum m (both pols), weights broadcast from
+//    shared memory, one coalesced pass over the corner-turned input; Stokes integration over Q
+//    consecutive spectra is a warp-shuffle reduction across the lanes that hold them.
+//  * many-beam (FP32-ALU bound): 128 beams x 32 spectra per CTA pass, each thread a 4-beam x
+//    4-spectrum x 2-pol register tile (64 accumulators); the corner-turned input tile is staged in
+//    shared memory and every station step issues 128 FFMAs per 6 shared-memory vector loads.
+#include "lbf_internal.cuh"
+
+namespace lbf {
+namespace {
+
+constexpr int kFewThreads = 256;
+constexpr int kFewBeams = 8;     // beams per few-beam CTA (grid.y covers more)
+constexpr int kManyThreads = 256;
+constexpr int kBT = 128;         // beams per many-beam CTA
+constexpr int kMC = 32;          // spectra per many-beam pass
+
+__device__ __forceinline__ void cmac(float2 &acc, float2 w, float2 y) {
+  acc.x = fmaf(w.x, y.x, acc.x);
+  acc.x = fmaf(-w.y, y.y, acc.x);
+  acc.y = fmaf(w.x, y.y, acc.y);
+  acc.y = fmaf(w.y, y.x, acc.y);
+}
+
+__device__ __forceinline__ double channel_freq(const Geometry &g, int f, int c) {
+  return g.f0[f] + (double)(c - kN / 2) * (g.fs / kN);
+}
+
+// Stokes parameter `st` of the voltage pair (X, Y), Section 4.5.
+__device__ __forceinline__ float stokes_param(int st, float2 X, float2 Y) {
+  const float xx = fmaf(X.x, X.x, X.y * X.y);
+  const float yy = fmaf(Y.x, Y.x, Y.y * Y.y);
+  switch (st) {
+    case 0: return xx + yy;                                   // I
+    case 1: return xx - yy;                                   // Q
+    case 2: return 2.f * fmaf(X.x, Y.x, X.y * Y.y);           // U = 2 Re(X conj Y)
+    default: return 2.f * fmaf(X.y, Y.x, -X.x * Y.y);         // V = 2 Im(X conj Y)
+  }
+}
+
+// ------------------------------------------------------------------------------- few beams
+template <int OUT>
+__global__ void __launch_bounds__(kFewThreads)
+bf_few_kernel(Geometry g, const float2 *__restrict__ ct, void *__restrict__ out) {
+  extern __shared__ __align__(16) float2 wsm[];   // [S][kFewBeams]
+  const int fc = blockIdx.x;
+  const int f = fc / kN, c = fc - f * kN;
+  const int b0 = blockIdx.y * kFewBeams;
+  const int tid = threadIdx.x;
+  const double freq = channel_freq(g, f, c);
+  for (int i = tid; i < g.S * kFewBeams; i += kFewThreads) {
+    const int s = i / kFewBeams, b = b0 + (i - s * kFewBeams);
+    wsm[i] = (b < g.B) ? unit_phasor_cycles(freq * g.dtau[(long long)b * g.S + s]) : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const float2 *y = ct + (long long)fc * g.S * kP * g.M;
+  const int nS = (OUT == OUT_STOKES_IQUV) ? 4 : 1;
+  const int Mq = g.M / g.Q;
+  for (int mb = 0; mb < g.M; mb += kFewThreads) {
+    const int m = mb + tid;
+    const bool active = m < g.M;
+    float2 acc[kFewBeams][kP];
+#pragma unroll
+    for (int b = 0; b < kFewBeams; ++b) acc[b][0] = acc[b][1] = make_float2(0.f, 0.f);
+    if (active) {
+      for (int s = 0; s < g.S; ++s) {
+        const float2 yx = y[((long long)s * kP + 0) * g.M + m];
+        const float2 yy = y[((long long)s * kP + 1) * g.M + m];
+        const float4 *w4 = reinterpret_cast<const float4 *>(wsm + s * kFewBeams);
+#pragma unroll
+        for (int b2 = 0; b2 < kFewBeams / 2; ++b2) {
+          const float4 w = w4[b2];
+          cmac(acc[2 * b2][0], make_float2(w.x, w.y), yx);
+          cmac(acc[2 * b2][1], make_float2(w.x, w.y), yy);
+          cmac(acc[2 * b2 + 1][0], make_float2(w.z, w.w), yx);
+          cmac(acc[2 * b2 + 1][1], make_float2(w.z, w.w), yy);
+        }
+      }
+    }
+    if (OUT == OUT_VOLTAGES) {
+      if (active) {
+        float2 *vol = reinterpret_cast<float2 *>(out);
+#pragma unroll
+        for (int b = 0; b < kFewBeams; ++b)
+          if (b0 + b < g.B)
+#pragma unroll
+            for (int pol = 0; pol < kP; ++pol)
+              vol[((((long long)(b0 + b) * g.F + f) * kN + c) * kP + pol) * g.M + m] = acc[b][pol];
+      }
+    } else {
+      float *o = reinterpret_cast<float *>(out);
+#pragma unroll
+      for (int b = 0; b < kFewBeams; ++b) {
+        if (b0 + b >= g.B) break;   // uniform across the CTA
+#pragma unroll
+        for (int st = 0; st < nS; ++st) {
+          float v = stokes_param(st, acc[b][0], acc[b][1]);
+          for (int o2 = 1; o2 < g.Q; o2 <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o2);
+          if (active && (m & (g.Q - 1)) == 0)
+            o[((((long long)(b0 + b) * nS + st) * g.F + f) * kN + c) * Mq + m / g.Q] = v;
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------- many beams
+template <int OUT>
+__global__ void __launch_bounds__(kManyThreads, 2)
+bf_many_kernel(Geometry g, const float2 *__restrict__ ct, void *__restrict__ out, int nbt) {
+  extern __shared__ __align__(16) float2 smem[];
+  float2 *wsm = smem;                      // [S][kBT]
+  float2 *ysm = smem + (size_t)g.S * kBT;  // [S][kP][kMC]
+  const int tid = threadIdx.x;
+  const int fc = blockIdx.x / nbt;
+  const int bt = blockIdx.x - fc * nbt;
+  const int f = fc / kN, c = fc - f * kN;
+  const int bbase = bt * kBT;
+  const double freq = channel_freq(g, f, c);
+  for (int i = tid; i < g.S * kBT; i += kManyThreads) {
+    const int s = i / kBT, bl = i - s * kBT, b = bbase + bl;
+    wsm[i] = (b < g.B) ? unit_phasor_cycles(freq * g.dtau[(long long)b * g.S + s]) : make_float2(0.f, 0.f);
+  }
+  const int bg = tid >> 3;   // beams bbase + 4 bg .. +3
+  const int mg = tid & 7;    // spectra 4 mg .. +3 of the pass
+  const float2 *y = ct + (long long)fc * g.S * kP * g.M;
+  const int nS = (OUT == OUT_STOKES_IQUV) ? 4 : 1;
+  const int Mq = (OUT == OUT_VOLTAGES) ? 0 : g.M / g.Q;
+
+  for (int mc = 0; mc < g.M; mc += kMC) {
+    __syncthreads();   // weights ready / previous pass done with ysm
+    for (int i = tid; i < g.S * kP * kMC; i += kManyThreads) {
+      const int row = i / kMC, col = i - row * kMC;
+      const int m = mc + col;
+      ysm[i] = (m < g.M) ? y[(long long)row * g.M + m] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    float2 acc[4][kP][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int pol = 0; pol < kP; ++pol)
+#pragma unroll
+        for (int jm = 0; jm < 4; ++jm) acc[i][pol][jm] = make_float2(0.f, 0.f);
+
+#pragma unroll 2
+    for (int s = 0; s < g.S; ++s) {
+      const float4 *wp = reinterpret_cast<const float4 *>(wsm + s * kBT + bg * 4);
+      const float4 w01 = wp[0], w23 = wp[1];
+      const float2 w[4] = {make_float2(w01.x, w01.y), make_float2(w01.z, w01.w),
+                           make_float2(w23.x, w23.y), make_float2(w23.z, w23.w)};
+#pragma unroll
+      for (int pol = 0; pol < kP; ++pol) {
+        const float4 *yp = reinterpret_cast<const float4 *>(ysm + (s * kP + pol) * kMC + mg * 4);
+        const float4 y01 = yp[0], y23 = yp[1];
+        const float2 yv[4] = {make_float2(y01.x, y01.y), make_float2(y01.z, y01.w),
+                              make_float2(y23.x, y23.y), make_float2(y23.z, y23.w)};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int jm = 0; jm < 4; ++jm) cmac(acc[i][pol][jm], w[i], yv[jm]);
+      }
+    }
+
+    if (OUT == OUT_VOLTAGES) {
+      float2 *vol = reinterpret_cast<float2 *>(out);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int b = bbase + bg * 4 + i;
+        if (b >= g.B) continue;
+#pragma unroll
+        for (int pol = 0; pol < kP; ++pol)
+#pragma unroll
+          for (int jm = 0; jm < 4; ++jm) {
+            const int m = mc + mg * 4 + jm;
+            if (m < g.M) vol[((((long long)b * g.F + f) * kN + c) * kP + pol) * g.M + m] = acc[i][pol][jm];
+          }
+      }
+    } else {
+      float *o = reinterpret_cast<float *>(out);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int b = bbase + bg * 4 + i;
+#pragma unroll
+        for (int st = 0; st < nS; ++st) {
+          float v[4];
+#pragma unroll
+          for (int jm = 0; jm < 4; ++jm) v[jm] = stokes_param(st, acc[i][0][jm], acc[i][1][jm]);
+          if (g.Q == 1) {
+#pragma unroll
+            for (int jm = 0; jm < 4; ++jm) {
+              const int m = mc + mg * 4 + jm;
+              if (b < g.B && m < g.M) o[((((long long)b * nS + st) * g.F + f) * kN + c) * Mq + m] = v[jm];
+            }
+          } else if (g.Q == 2) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int m = mc + mg * 4 + 2 * h;
+              if (b < g.B && m < g.M)
+                o[((((long long)b * nS + st) * g.F + f) * kN + c) * Mq + m / 2] = v[2 * h] + v[2 * h + 1];
+            }
+          } else {
+            float sum = (v[0] + v[1]) + (v[2] + v[3]);
+            for (int o2 = 1; o2 < g.Q / 4; o2 <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o2);
+            const int m = mc + mg * 4;
+            if (b < g.B && m < g.M && (m & (g.Q - 1)) == 0)
+              o[((((long long)b * nS + st) * g.F + f) * kN + c) * Mq + m / g.Q] = sum;
+          }
+        }
+      }
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_beamform(const Geometry &g, int variant, int out_kind, const float2 *ct, void *out,
+                            cudaStream_t st) {
+  if ((long long)g.F * kN == 0 || g.M == 0 || g.B == 0) return cudaSuccess;
+  if (variant == 1) {
+    dim3 grid((unsigned)(g.F * kN), (unsigned)((g.B + kFewBeams - 1) / kFewBeams));
+    const size_t smem = (size_t)g.S * kFewBeams * sizeof(float2);
+    cudaError_t e;
+    switch (out_kind) {
+      case OUT_VOLTAGES:
+        e = cudaFuncSetAttribute(bf_few_kernel<OUT_VOLTAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        bf_few_kernel<OUT_VOLTAGES><<<grid, kFewThreads, smem, st>>>(g, ct, out);
+        break;
+      case OUT_STOKES_I:
+        e = cudaFuncSetAttribute(bf_few_kernel<OUT_STOKES_I>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        bf_few_kernel<OUT_STOKES_I><<<grid, kFewThreads, smem, st>>>(g, ct, out);
+        break;
+      default:
+        e = cudaFuncSetAttribute(bf_few_kernel<OUT_STOKES_IQUV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        bf_few_kernel<OUT_STOKES_IQUV><<<grid, kFewThreads, smem, st>>>(g, ct, out);
+        break;
+    }
+    return cudaGetLastError();
+  }
+  const int nbt = (g.B + kBT - 1) / kBT;
+  const long long ctas = (long long)g.F * kN * nbt;
+  const size_t smem = (size_t)g.S * (kBT + kP * kMC) * sizeof(float2);
+  cudaError_t e;
+  switch (out_kind) {
+    case OUT_VOLTAGES:
+      e = cudaFuncSetAttribute(bf_many_kernel<OUT_VOLTAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      bf_many_kernel<OUT_VOLTAGES><<<(unsigned)ctas, kManyThreads, smem, st>>>(g, ct, out, nbt);
+      break;
+    case OUT_STOKES_I:
+      e = cudaFuncSetAttribute(bf_many_kernel<OUT_STOKES_I>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      bf_many_kernel<OUT_STOKES_I><<<(unsigned)ctas, kManyThreads, smem, st>>>(g, ct, out, nbt);
+      break;
+    default:
+      e = cudaFuncSetAttribute(bf_many_kernel<OUT_STOKES_IQUV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      bf_many_kernel<OUT_STOKES_IQUV><<<(unsigned)ctas, kManyThreads, smem, st>>>(g, ct, out, nbt);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+// Largest station count the many-beam kernel accepts (its shared memory holds S x (128 + 64) cf32).
+int many_beam_max_stations() { return (227 * 1024) / ((kBT + kP * kMC) * (int)sizeof(float2)); }
+
+}  // namespace lbf

@@ -1,0 +1,450 @@
+// C-ABI layer: plan creation (host FP64 geometry, device tables and state) and the entry points
+// declared in include/lbf.h.  No compute happens here; every step of the path is a kernel.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lbf.h"
+#include "lbf_internal.cuh"
+
+namespace {
+
+constexpr uint32_t kMagic = 0x4c424650u;   // "LBFP"
+constexpr double kC = 299792458.0;         // m/s
+
+}  // namespace
+
+struct lbf_plan_s {
+  uint32_t magic = kMagic;
+  int device = 0;
+  int S = 0, F = 0, N = 0, L = 0, B = 0, T = 0, M = 0, Q = 1, nS = 0, bits = 16;
+  int out_kind = 0, variant = 1, d_max = 0, H = 0;
+  double fs = 0.0;
+  std::vector<int32_t> n_shift, d_shift;
+  float *taps = nullptr;
+  float2 *twiddle = nullptr;
+  float *bandpass = nullptr;
+  int *dshift = nullptr;
+  double *tau = nullptr, *resid = nullptr, *f0 = nullptr, *dtau = nullptr;
+  void *hist[2] = {nullptr, nullptr};
+  int cur = 0;
+  float2 *ws = nullptr;
+  size_t word = 8, hist_bytes = 0, ws_bytes = 0;
+
+  // kernel timing trace (lbf_trace_begin / lbf_trace_end)
+  struct TraceSlot { int kernel; cudaEvent_t a, b; };
+  std::vector<TraceSlot> trace;
+  size_t trace_used = 0;
+  int trace_dropped = 0;
+  bool tracing = false;
+
+  lbf::Geometry geometry() const {
+    lbf::Geometry g;
+    g.S = S; g.F = F; g.B = B; g.T = T; g.M = M; g.Q = Q; g.nS = nS; g.H = H; g.fs = fs;
+    g.taps = taps; g.twiddle = twiddle; g.bandpass = bandpass; g.dshift = dshift;
+    g.tau = tau; g.resid = resid; g.f0 = f0; g.dtau = dtau;
+    return g;
+  }
+};
+
+namespace {
+
+// Plane-wave geometric delay, evaluated left to right with no contraction so that the integer
+// shift decisions are reproducible: -(x l + y m + z n) / c with n = sqrt(max(0, 1 - l^2 - m^2)).
+double plane_wave_delay(const double *xyz, double l, double m) {
+  double nn = 1.0 - l * l - m * m;
+  const double n = std::sqrt(nn > 0.0 ? nn : 0.0);
+  const double dot = xyz[0] * l + xyz[1] * m + xyz[2] * n;
+  return -dot / kC;
+}
+
+double round_half_away(double x) {
+  const double a = std::floor(std::fabs(x) + 0.5);
+  return x < 0 ? -a : (x > 0 ? a : 0.0);
+}
+
+bool is_pow2_upto32(int q) { return q == 1 || q == 2 || q == 4 || q == 8 || q == 16 || q == 32; }
+
+lbf_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return LBF_OK;
+  if (e == cudaErrorMemoryAllocation) return LBF_ENOMEM;
+  return LBF_ECUDA;
+}
+
+template <typename T>
+cudaError_t upload(T **dst, const T *src, size_t n) {
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void **)dst, n * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return src ? cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice) : cudaSuccess;
+}
+
+void release(lbf_plan_s *p) {
+  cudaFree(p->taps); cudaFree(p->twiddle); cudaFree(p->bandpass); cudaFree(p->dshift);
+  cudaFree(p->tau); cudaFree(p->resid); cudaFree(p->f0); cudaFree(p->dtau);
+  cudaFree(p->hist[0]); cudaFree(p->hist[1]); cudaFree(p->ws);
+}
+
+lbf_status validate(const lbf_config *c) {
+  if (!c) return LBF_EINVAL;
+  if (c->n_stations < 1 || c->n_subbands < 1 || c->n_beams < 1) return LBF_EINVAL;
+  if (c->n_channels < 1 || c->n_taps < 1) return LBF_EINVAL;
+  if (c->block_samples < 0 || c->block_samples % c->n_channels != 0) return LBF_EINVAL;
+  if (c->sample_bits != 16 && c->sample_bits != 8) return LBF_EINVAL;
+  if (c->output != LBF_VOLTAGES && c->output != LBF_STOKES_I && c->output != LBF_STOKES_IQUV) return LBF_EINVAL;
+  if (c->precision != LBF_FP32 && c->precision != LBF_FP16_TC) return LBF_EINVAL;
+  if (c->bf_variant < LBF_BF_AUTO || c->bf_variant > LBF_BF_MANY) return LBF_EINVAL;
+  if (c->reserved != 0) return LBF_EINVAL;
+  if (!is_pow2_upto32(c->int_factor)) return LBF_EINVAL;
+  const int M = c->block_samples / c->n_channels;
+  if (c->output != LBF_VOLTAGES && M % c->int_factor != 0) return LBF_EINVAL;
+  if (!(c->sample_rate_hz > 0.0) || !std::isfinite(c->sample_rate_hz)) return LBF_EINVAL;
+  if (!std::isfinite(c->phase_centre_l) || !std::isfinite(c->phase_centre_m)) return LBF_EINVAL;
+  if (!c->station_xyz_m || !c->subband_centre_hz || !c->beam_dlm || !c->fir_taps) return LBF_EINVAL;
+  for (int i = 0; i < 3 * c->n_stations; ++i) if (!std::isfinite(c->station_xyz_m[i])) return LBF_EINVAL;
+  for (int i = 0; i < c->n_subbands; ++i) if (!std::isfinite(c->subband_centre_hz[i])) return LBF_EINVAL;
+  for (int i = 0; i < 2 * c->n_beams; ++i) if (!std::isfinite(c->beam_dlm[i])) return LBF_EINVAL;
+  if (c->n_channels != lbf::kN || c->n_taps != lbf::kL) return LBF_EUNSUPPORTED;
+  if (c->precision == LBF_FP16_TC) return LBF_EUNSUPPORTED;
+  if (c->bf_variant == LBF_BF_MANY && c->n_stations > lbf::many_beam_max_stations()) return LBF_EUNSUPPORTED;
+  // index arithmetic: per-plan sizes must keep grid dimensions in range
+  const long long ctas = (long long)c->n_subbands * lbf::kN * ((c->n_beams + 7) / 8);
+  if (ctas >= (1LL << 31)) return LBF_EUNSUPPORTED;
+  return LBF_OK;
+}
+
+bool valid_plan(lbf_plan_t p) { return p && p->magic == kMagic; }
+
+// Device pointer check (host-only query): rejects host pointers before any launch.
+bool device_ptr(const void *p, size_t align) {
+  if (!p || (reinterpret_cast<uintptr_t>(p) % align) != 0) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+lbf_status check_call(lbf_plan_t p) {
+  if (!valid_plan(p)) return LBF_ESTATE;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return LBF_ECUDA;
+  if (dev != p->device) return LBF_ESTATE;
+  return LBF_OK;
+}
+
+enum KernelId { K_PPF = 0, K_PPF_CT, K_HIST, K_DELAY, K_BF_FEW, K_BF_MANY, K_STOKES, K_COUNT };
+const char *const kKernelNames[K_COUNT] = {"ppf", "ppf_ct", "hist_update", "delay_ct", "bf_few",
+                                           "bf_many", "stokes"};
+
+// Launch through `fn`, bracketed by trace events when a trace is active.
+template <typename Fn>
+cudaError_t traced(lbf_plan_t p, int kernel, cudaStream_t st, Fn &&fn) {
+  if (!p->tracing) return fn();
+  if (p->trace_used >= p->trace.size()) {
+    ++p->trace_dropped;
+    return fn();
+  }
+  auto &slot = p->trace[p->trace_used++];
+  slot.kernel = kernel;
+  cudaError_t e = cudaEventRecord(slot.a, st);
+  if (e != cudaSuccess) return e;
+  e = fn();
+  if (e != cudaSuccess) return e;
+  return cudaEventRecord(slot.b, st);
+}
+
+void trace_free(lbf_plan_t p) {
+  for (auto &s : p->trace) { cudaEventDestroy(s.a); cudaEventDestroy(s.b); }
+  p->trace.clear();
+  p->trace_used = 0;
+  p->trace_dropped = 0;
+  p->tracing = false;
+}
+
+int bf_kernel_id(lbf_plan_t p) { return p->variant == 1 ? K_BF_FEW : K_BF_MANY; }
+
+// The fused path on device buffers (a1-a7).
+cudaError_t run_block_device(lbf_plan_t p, const void *d_in, void *d_out, cudaStream_t st) {
+  const lbf::Geometry g = p->geometry();
+  const void *h = p->hist[p->cur];
+  void *nh = p->hist[p->cur ^ 1];
+  cudaError_t e = traced(p, K_PPF_CT, st, [&] { return lbf::launch_ppf(g, p->bits, d_in, h, nullptr, p->ws, st); });
+  if (e == cudaSuccess) e = traced(p, K_HIST, st, [&] { return lbf::launch_hist_update(g, p->bits, d_in, h, nh, st); });
+  if (e != cudaSuccess) return e;
+  p->cur ^= 1;
+  return traced(p, bf_kernel_id(p), st,
+                [&] { return lbf::launch_beamform(g, p->variant, p->out_kind, p->ws, d_out, st); });
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lbf_status_string(lbf_status s) {
+  switch (s) {
+    case LBF_OK: return "LBF_OK";
+    case LBF_EINVAL: return "LBF_EINVAL: invalid argument";
+    case LBF_ENOMEM: return "LBF_ENOMEM: device allocation failed";
+    case LBF_ECUDA: return "LBF_ECUDA: CUDA runtime error";
+    case LBF_ESTATE: return "LBF_ESTATE: plan in an unusable state";
+    case LBF_ETIMEOUT: return "LBF_ETIMEOUT: device wait timed out";
+    case LBF_EBUSY: return "LBF_EBUSY: resource busy";
+    case LBF_EUNSUPPORTED: return "LBF_EUNSUPPORTED: not supported by this build";
+  }
+  return "LBF_?: unknown status";
+}
+
+const char *lbf_version(void) { return "lbf 0.1 (sm_103a)"; }
+
+lbf_status lbf_plan(const lbf_config *cfg, lbf_plan_t *out) {
+  if (!out) return LBF_EINVAL;
+  *out = nullptr;
+  lbf_status v = validate(cfg);
+  if (v != LBF_OK) return v;
+  lbf_plan_s *p = new (std::nothrow) lbf_plan_s();
+  if (!p) return LBF_ENOMEM;
+  p->S = cfg->n_stations; p->F = cfg->n_subbands; p->N = cfg->n_channels; p->L = cfg->n_taps;
+  p->B = cfg->n_beams; p->T = cfg->block_samples; p->M = p->T / p->N; p->Q = cfg->int_factor;
+  p->bits = cfg->sample_bits; p->fs = cfg->sample_rate_hz; p->word = p->bits == 16 ? 8 : 4;
+  p->out_kind = cfg->output == LBF_STOKES_I ? lbf::OUT_STOKES_I
+              : cfg->output == LBF_STOKES_IQUV ? lbf::OUT_STOKES_IQUV : lbf::OUT_VOLTAGES;
+  p->nS = cfg->output == LBF_STOKES_I ? 1 : cfg->output == LBF_STOKES_IQUV ? 4 : 0;
+  if (cfg->bf_variant == LBF_BF_AUTO)
+    p->variant = (p->B <= 8 || p->S > lbf::many_beam_max_stations()) ? 1 : 2;
+  else
+    p->variant = cfg->bf_variant;
+
+  // ---- FP64 geometry on the host (Section 3: delays, integer shifts, beam delay differences)
+  const double ts = 1.0 / p->fs;
+  const double l0 = cfg->phase_centre_l, m0 = cfg->phase_centre_m;
+  std::vector<double> tau(p->S), resid(p->S), dtau((size_t)p->B * p->S);
+  p->n_shift.resize(p->S);
+  p->d_shift.resize(p->S);
+  long long nmax = 0;
+  for (int s = 0; s < p->S; ++s) {
+    tau[s] = plane_wave_delay(cfg->station_xyz_m + 3 * s, l0, m0);
+    const double n = round_half_away(tau[s] / ts);
+    if (!(std::fabs(n) < 1e6)) { delete p; return LBF_EUNSUPPORTED; }
+    p->n_shift[s] = (int32_t)n;
+    nmax = (s == 0 || p->n_shift[s] > nmax) ? p->n_shift[s] : nmax;
+  }
+  for (int s = 0; s < p->S; ++s) {
+    p->d_shift[s] = (int32_t)(nmax - p->n_shift[s]);
+    p->d_max = p->d_shift[s] > p->d_max ? p->d_shift[s] : p->d_max;
+    resid[s] = tau[s] - (double)p->n_shift[s] * ts;
+  }
+  for (int b = 0; b < p->B; ++b)
+    for (int s = 0; s < p->S; ++s)
+      dtau[(size_t)b * p->S + s] =
+          plane_wave_delay(cfg->station_xyz_m + 3 * s, l0 + cfg->beam_dlm[2 * b], m0 + cfg->beam_dlm[2 * b + 1]) - tau[s];
+  p->H = (p->L - 1) * p->N + p->d_max;
+
+  std::vector<float2> tw(p->N);
+  for (int n = 0; n < p->N; ++n) {
+    const double a = 2.0 * M_PI * (double)n / (double)p->N;
+    tw[n] = make_float2((float)std::cos(a), (float)-std::sin(a));
+  }
+  std::vector<float> bp(p->N, 1.0f);
+  if (cfg->bandpass) std::memcpy(bp.data(), cfg->bandpass, sizeof(float) * p->N);
+
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e == cudaSuccess) e = upload(&p->taps, cfg->fir_taps, (size_t)p->L * p->N);
+  if (e == cudaSuccess) e = upload(&p->twiddle, tw.data(), tw.size());
+  if (e == cudaSuccess) e = upload(&p->bandpass, bp.data(), bp.size());
+  if (e == cudaSuccess) e = upload(&p->dshift, (const int *)p->d_shift.data(), (size_t)p->S);
+  if (e == cudaSuccess) e = upload(&p->tau, tau.data(), tau.size());
+  if (e == cudaSuccess) e = upload(&p->resid, resid.data(), resid.size());
+  if (e == cudaSuccess) e = upload(&p->f0, cfg->subband_centre_hz, (size_t)p->F);
+  if (e == cudaSuccess) e = upload(&p->dtau, dtau.data(), dtau.size());
+  p->hist_bytes = (size_t)p->S * p->F * p->H * p->word;
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = cudaMalloc(&p->hist[i], p->hist_bytes ? p->hist_bytes : 16);
+    if (e == cudaSuccess) e = cudaMemset(p->hist[i], 0, p->hist_bytes ? p->hist_bytes : 16);
+  }
+  p->ws_bytes = (size_t)p->F * p->N * p->S * lbf::kP * p->M * sizeof(float2);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&p->ws, p->ws_bytes ? p->ws_bytes : 16);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    release(p);
+    delete p;
+    cudaGetLastError();
+    return cuda_status(e);
+  }
+  *out = p;
+  return LBF_OK;
+}
+
+lbf_status lbf_plan_destroy(lbf_plan_t p) {
+  if (!p) return LBF_OK;
+  if (!valid_plan(p)) return LBF_ESTATE;
+  cudaDeviceSynchronize();
+  trace_free(p);
+  release(p);
+  p->magic = 0;
+  delete p;
+  return LBF_OK;
+}
+
+lbf_status lbf_plan_dims(lbf_plan_t p, lbf_dims *d) {
+  if (!valid_plan(p)) return LBF_ESTATE;
+  if (!d) return LBF_EINVAL;
+  std::memset(d, 0, sizeof(*d));
+  d->n_stations = p->S; d->n_subbands = p->F; d->n_channels = p->N; d->n_taps = p->L;
+  d->n_beams = p->B; d->block_samples = p->T; d->int_factor = p->Q; d->n_spectra = p->M;
+  d->n_stokes = p->nS; d->d_max = p->d_max; d->history_samples = p->H; d->bf_kernel = p->variant;
+  const size_t cplx = (size_t)p->S * p->F * lbf::kP * p->T * sizeof(float2);
+  d->in_bytes = (size_t)p->S * p->F * p->T * p->word;
+  d->chan_bytes = cplx;
+  d->ct_bytes = cplx;
+  d->vol_bytes = (size_t)p->B * p->F * lbf::kP * p->T * sizeof(float2);
+  d->stokes_bytes = p->nS ? (size_t)p->B * p->nS * p->F * p->N * (p->M / p->Q) * sizeof(float) : 0;
+  d->out_bytes = p->nS ? d->stokes_bytes : d->vol_bytes;
+  d->workspace_bytes = p->ws_bytes;
+  return LBF_OK;
+}
+
+lbf_status lbf_plan_shifts(lbf_plan_t p, int32_t *n_shift, int32_t *d_shift) {
+  if (!valid_plan(p)) return LBF_ESTATE;
+  if (n_shift) std::memcpy(n_shift, p->n_shift.data(), sizeof(int32_t) * p->S);
+  if (d_shift) std::memcpy(d_shift, p->d_shift.data(), sizeof(int32_t) * p->S);
+  return LBF_OK;
+}
+
+lbf_status lbf_reset_state(lbf_plan_t p, void *stream) {
+  lbf_status s = check_call(p);
+  if (s != LBF_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int i = 0; i < 2; ++i) {
+    cudaError_t e = cudaMemsetAsync(p->hist[i], 0, p->hist_bytes ? p->hist_bytes : 16, st);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  p->cur = 0;
+  return LBF_OK;
+}
+
+lbf_status lbf_ppf(lbf_plan_t p, const void *d_in, void *d_chan, void *stream) {
+  lbf_status s = check_call(p);
+  if (s != LBF_OK) return s;
+  if (p->M == 0) return LBF_OK;
+  if (!device_ptr(d_in, p->word) || !device_ptr(d_chan, 8)) return LBF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const lbf::Geometry g = p->geometry();
+  const void *h = p->hist[p->cur];
+  void *nh = p->hist[p->cur ^ 1];
+  cudaError_t e = traced(p, K_PPF, st, [&] { return lbf::launch_ppf(g, p->bits, d_in, h, (float2 *)d_chan, nullptr, st); });
+  if (e == cudaSuccess) e = traced(p, K_HIST, st, [&] { return lbf::launch_hist_update(g, p->bits, d_in, h, nh, st); });
+  if (e != cudaSuccess) return cuda_status(e);
+  p->cur ^= 1;
+  return LBF_OK;
+}
+
+lbf_status lbf_delay_correct(lbf_plan_t p, const void *d_chan, void *d_ct, void *stream) {
+  lbf_status s = check_call(p);
+  if (s != LBF_OK) return s;
+  if (p->M == 0) return LBF_OK;
+  if (!device_ptr(d_chan, 8) || !device_ptr(d_ct, 8)) return LBF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const lbf::Geometry g = p->geometry();
+  return cuda_status(traced(p, K_DELAY, st, [&] { return lbf::launch_delay_ct(g, (const float2 *)d_chan, (float2 *)d_ct, st); }));
+}
+
+lbf_status lbf_beamform(lbf_plan_t p, const void *d_ct, void *d_vol, void *stream) {
+  lbf_status s = check_call(p);
+  if (s != LBF_OK) return s;
+  if (p->M == 0) return LBF_OK;
+  if (!device_ptr(d_ct, 8) || !device_ptr(d_vol, 8)) return LBF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const lbf::Geometry g = p->geometry();
+  return cuda_status(traced(p, bf_kernel_id(p), st, [&] {
+    return lbf::launch_beamform(g, p->variant, lbf::OUT_VOLTAGES, (const float2 *)d_ct, d_vol, st); }));
+}
+
+lbf_status lbf_beamform_stokes(lbf_plan_t p, const void *d_ct, float *d_out, void *stream) {
+  lbf_status s = check_call(p);
+  if (s != LBF_OK) return s;
+  if (p->nS == 0) return LBF_EINVAL;
+  if (p->M == 0) return LBF_OK;
+  if (!device_ptr(d_ct, 8) || !device_ptr(d_out, 4)) return LBF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const lbf::Geometry g = p->geometry();
+  return cuda_status(traced(p, bf_kernel_id(p), st, [&] {
+    return lbf::launch_beamform(g, p->variant, p->out_kind, (const float2 *)d_ct, d_out, st); }));
+}
+
+lbf_status lbf_stokes(lbf_plan_t p, const void *d_vol, float *d_out, void *stream) {
+  lbf_status s = check_call(p);
+  if (s != LBF_OK) return s;
+  if (p->nS == 0) return LBF_EINVAL;
+  if (p->M == 0) return LBF_OK;
+  if (!device_ptr(d_vol, 8) || !device_ptr(d_out, 4)) return LBF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const lbf::Geometry g = p->geometry();
+  return cuda_status(traced(p, K_STOKES, st, [&] { return lbf::launch_stokes(g, p->out_kind, (const float2 *)d_vol, d_out, st); }));
+}
+
+lbf_status lbf_run_block(lbf_plan_t p, const void *d_in, void *d_out, void *stream) {
+  lbf_status s = check_call(p);
+  if (s != LBF_OK) return s;
+  if (p->M == 0) return LBF_OK;
+  if (!device_ptr(d_in, p->word) || !device_ptr(d_out, p->nS ? 4 : 8)) return LBF_EINVAL;
+  return cuda_status(run_block_device(p, d_in, d_out, (cudaStream_t)stream));
+}
+
+lbf_status lbf_run_block_host(lbf_plan_t p, const void *h_in, void *h_out, void *d_in, void *d_out,
+                              void *stream) {
+  lbf_status s = check_call(p);
+  if (s != LBF_OK) return s;
+  if (p->M == 0) return LBF_OK;
+  if (!h_in || !h_out) return LBF_EINVAL;
+  if (!device_ptr(d_in, p->word) || !device_ptr(d_out, p->nS ? 4 : 8)) return LBF_EINVAL;
+  lbf_dims d;
+  lbf_plan_dims(p, &d);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(d_in, h_in, d.in_bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = run_block_device(p, d_in, d_out, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_out, d_out, d.out_bytes, cudaMemcpyDeviceToHost, st);
+  return cuda_status(e);
+}
+
+lbf_status lbf_trace_begin(lbf_plan_t p, int32_t max_launches) {
+  if (!valid_plan(p)) return LBF_ESTATE;
+  if (max_launches < 1 || max_launches > (1 << 20)) return LBF_EINVAL;
+  trace_free(p);
+  p->trace.resize((size_t)max_launches);
+  for (auto &slot : p->trace) {
+    slot.kernel = -1;
+    if (cudaEventCreate(&slot.a) != cudaSuccess || cudaEventCreate(&slot.b) != cudaSuccess) {
+      cudaGetLastError();
+      p->trace.clear();
+      return LBF_ECUDA;
+    }
+  }
+  p->tracing = true;
+  return LBF_OK;
+}
+
+lbf_status lbf_trace_end(lbf_plan_t p, lbf_trace *out) {
+  if (!valid_plan(p)) return LBF_ESTATE;
+  if (!p->tracing) return LBF_ESTATE;
+  lbf_trace t;
+  std::memset(&t, 0, sizeof(t));
+  t.n_kernels = K_COUNT;
+  for (int k = 0; k < K_COUNT; ++k) std::strncpy(t.names[k], kKernelNames[k], sizeof(t.names[k]) - 1);
+  cudaError_t e = cudaSuccess;
+  for (size_t i = 0; i < p->trace_used && e == cudaSuccess; ++i) {
+    auto &slot = p->trace[i];
+    e = cudaEventSynchronize(slot.b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, slot.a, slot.b);
+    if (e == cudaSuccess && slot.kernel >= 0) {
+      t.launches[slot.kernel] += 1;
+      t.total_ms[slot.kernel] += ms;
+    }
+  }
+  t.dropped = p->trace_dropped;
+  trace_free(p);
+  if (out) *out = t;
+  return cuda_status(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,294 @@
+"""Python binding of the C-ABI in include/lbf.h (argument marshalling only).
+
+Every step of the path runs in the CUDA library liblbf.so; this module only converts a plan's
+configuration to the C struct, torch tensors to device pointers and torch streams to cudaStream_t.
+Importing it without the built library raises: there is no fallback path.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblbf.so")
+
+LBF_OK, LBF_EINVAL, LBF_ENOMEM, LBF_ECUDA, LBF_ESTATE, LBF_ETIMEOUT, LBF_EBUSY, LBF_EUNSUPPORTED = range(8)
+OUTPUTS = {"V": 0, "I": 1, "IQUV": 4}
+PRECISIONS = {"fp32": 0, "fp16tc": 1}
+BF_VARIANTS = {"auto": 0, "few": 1, "many": 2}
+
+# Every symbol include/lbf.h declares; the test suite checks the library exports all of them.
+EXPORTED = ("lbf_plan", "lbf_plan_destroy", "lbf_plan_dims", "lbf_plan_shifts", "lbf_reset_state",
+            "lbf_ppf", "lbf_delay_correct", "lbf_beamform", "lbf_beamform_stokes", "lbf_stokes",
+            "lbf_run_block", "lbf_run_block_host", "lbf_trace_begin", "lbf_trace_end",
+            "lbf_status_string", "lbf_version")
+
+
+class LbfError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)}")
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [
+        ("n_stations", ctypes.c_int32), ("n_subbands", ctypes.c_int32), ("n_channels", ctypes.c_int32),
+        ("n_taps", ctypes.c_int32), ("n_beams", ctypes.c_int32), ("block_samples", ctypes.c_int32),
+        ("int_factor", ctypes.c_int32), ("sample_bits", ctypes.c_int32), ("output", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("bf_variant", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("sample_rate_hz", ctypes.c_double), ("phase_centre_l", ctypes.c_double),
+        ("phase_centre_m", ctypes.c_double),
+        ("station_xyz_m", ctypes.POINTER(ctypes.c_double)),
+        ("subband_centre_hz", ctypes.POINTER(ctypes.c_double)),
+        ("beam_dlm", ctypes.POINTER(ctypes.c_double)),
+        ("fir_taps", ctypes.POINTER(ctypes.c_float)),
+        ("bandpass", ctypes.POINTER(ctypes.c_float)),
+    ]
+
+
+class _Trace(ctypes.Structure):
+    _fields_ = [("n_kernels", ctypes.c_int32), ("launches", ctypes.c_int32 * 8),
+                ("total_ms", ctypes.c_double * 8), ("names", (ctypes.c_char * 32) * 8),
+                ("dropped", ctypes.c_int32)]
+
+
+class _Dims(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in (
+        "n_stations", "n_subbands", "n_channels", "n_taps", "n_beams", "block_samples", "int_factor",
+        "n_spectra", "n_stokes", "d_max", "history_samples", "bf_kernel")] + \
+        [(n, ctypes.c_size_t) for n in (
+            "in_bytes", "chan_bytes", "ct_bytes", "vol_bytes", "out_bytes", "stokes_bytes",
+            "workspace_bytes")]
+
+
+_lib = None
+
+
+def load_library() -> ctypes.CDLL:
+    """Load liblbf.so (built in-tree by build_lib.build()); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"liblbf.so not built at {LIB_PATH}; run paper_1105_0661_gb300.build_lib.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, i32p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)
+        sig = {
+            "lbf_plan": ([ctypes.POINTER(_Config), ctypes.POINTER(vp)], ctypes.c_int),
+            "lbf_plan_destroy": ([vp], ctypes.c_int),
+            "lbf_plan_dims": ([vp, ctypes.POINTER(_Dims)], ctypes.c_int),
+            "lbf_plan_shifts": ([vp, i32p, i32p], ctypes.c_int),
+            "lbf_reset_state": ([vp, vp], ctypes.c_int),
+            "lbf_ppf": ([vp, vp, vp, vp], ctypes.c_int),
+            "lbf_delay_correct": ([vp, vp, vp, vp], ctypes.c_int),
+            "lbf_beamform": ([vp, vp, vp, vp], ctypes.c_int),
+            "lbf_beamform_stokes": ([vp, vp, vp, vp], ctypes.c_int),
+            "lbf_stokes": ([vp, vp, vp, vp], ctypes.c_int),
+            "lbf_run_block": ([vp, vp, vp, vp], ctypes.c_int),
+            "lbf_run_block_host": ([vp, vp, vp, vp, vp, vp], ctypes.c_int),
+            "lbf_trace_begin": ([vp, ctypes.c_int32], ctypes.c_int),
+            "lbf_trace_end": ([vp, ctypes.POINTER(_Trace)], ctypes.c_int),
+            "lbf_status_string": ([ctypes.c_int], ctypes.c_char_p),
+            "lbf_version": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes, fn.restype = args, res
+        _lib = lib
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return load_library().lbf_status_string(int(status)).decode()
+
+
+def _check(status: int, where: str):
+    if status != LBF_OK:
+        raise LbfError(status, where)
+
+
+def _ptr(t, need: int = 0) -> int:
+    """Address of a contiguous torch tensor holding at least `need` bytes (or an int address,
+    taken as is).  The size check keeps a short buffer from reaching a kernel."""
+    if isinstance(t, int):
+        return t
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    nbytes = t.numel() * t.element_size()
+    if nbytes < need:
+        raise ValueError(f"buffer holds {nbytes} bytes, the call needs {need}")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+@dataclass
+class Dims:
+    n_stations: int
+    n_subbands: int
+    n_channels: int
+    n_taps: int
+    n_beams: int
+    block_samples: int
+    int_factor: int
+    n_spectra: int
+    n_stokes: int
+    d_max: int
+    history_samples: int
+    bf_kernel: int
+    in_bytes: int
+    chan_bytes: int
+    ct_bytes: int
+    vol_bytes: int
+    out_bytes: int
+    stokes_bytes: int
+    workspace_bytes: int
+
+
+class Plan:
+    """One observation: tables, device-resident FIR/shift history and run_block scratch."""
+
+    def __init__(self, station_xyz, subband_hz, beam_dlm, phase_centre, taps, block_samples,
+                 int_factor=1, output="I", sample_bits=16, bandpass=None, n_channels=256, n_taps=16,
+                 sample_rate_hz=195312.5, precision="fp32", bf_variant="auto"):
+        lib = load_library()
+        self._keep = [np.ascontiguousarray(station_xyz, dtype=np.float64).reshape(-1, 3),
+                      np.ascontiguousarray(subband_hz, dtype=np.float64).reshape(-1),
+                      np.ascontiguousarray(beam_dlm, dtype=np.float64).reshape(-1, 2),
+                      np.ascontiguousarray(taps, dtype=np.float32).reshape(-1),
+                      None if bandpass is None else np.ascontiguousarray(bandpass, dtype=np.float32).reshape(-1)]
+        xyz, f0, dlm, h, bp = self._keep
+        cfg = _Config()
+        cfg.n_stations, cfg.n_subbands, cfg.n_beams = xyz.shape[0], f0.shape[0], dlm.shape[0]
+        cfg.n_channels, cfg.n_taps = n_channels, n_taps
+        cfg.block_samples, cfg.int_factor, cfg.sample_bits = block_samples, int_factor, sample_bits
+        cfg.output = OUTPUTS[output]
+        cfg.precision = PRECISIONS[precision]
+        cfg.bf_variant = BF_VARIANTS[bf_variant]
+        cfg.reserved = 0
+        cfg.sample_rate_hz = sample_rate_hz
+        cfg.phase_centre_l, cfg.phase_centre_m = float(phase_centre[0]), float(phase_centre[1])
+        dp = ctypes.POINTER(ctypes.c_double)
+        fp = ctypes.POINTER(ctypes.c_float)
+        cfg.station_xyz_m = xyz.ctypes.data_as(dp)
+        cfg.subband_centre_hz = f0.ctypes.data_as(dp)
+        cfg.beam_dlm = dlm.ctypes.data_as(dp)
+        cfg.fir_taps = h.ctypes.data_as(fp)
+        cfg.bandpass = bp.ctypes.data_as(fp) if bp is not None else ctypes.cast(None, fp)
+        self.output = output
+        self.sample_bits = sample_bits
+        handle = ctypes.c_void_p()
+        _check(lib.lbf_plan(ctypes.byref(cfg), ctypes.byref(handle)), "lbf_plan")
+        self._h = handle
+        self._lib = lib
+        d = _Dims()
+        _check(lib.lbf_plan_dims(self._h, ctypes.byref(d)), "lbf_plan_dims")
+        self.dims = Dims(**{n: getattr(d, n) for n, _ in _Dims._fields_})
+
+    @classmethod
+    def from_workload(cls, wl, **over):
+        kw = dict(station_xyz=wl.station_xyz, subband_hz=wl.subband_hz, beam_dlm=wl.beam_dlm,
+                  phase_centre=wl.phase_centre, taps=wl.taps, block_samples=wl.block_samples,
+                  int_factor=wl.int_factor, output=wl.output, sample_bits=wl.sample_bits,
+                  bandpass=wl.bandpass, n_channels=wl.n_channels, n_taps=wl.n_taps,
+                  sample_rate_hz=wl.sample_rate_hz)
+        kw.update(over)
+        return cls(**kw)
+
+    # -- shapes of the documented layouts
+    def shape(self, which: str):
+        d = self.dims
+        S, F, T, N, M, B = d.n_stations, d.n_subbands, d.block_samples, d.n_channels, d.n_spectra, d.n_beams
+        return {"in": (S, F, T, 2, 2), "chan": (F, S, 2, M, N), "ct": (F, N, S, 2, M),
+                "vol": (B, F, N, 2, M),
+                "stokes": (B, d.n_stokes, F, N, M // d.int_factor if d.n_stokes else 0)}[which]
+
+    def shifts(self):
+        S = self.dims.n_stations
+        n = (ctypes.c_int32 * S)()
+        dd = (ctypes.c_int32 * S)()
+        _check(self._lib.lbf_plan_shifts(self._h, n, dd), "lbf_plan_shifts")
+        return np.array(n[:], dtype=np.int64), np.array(dd[:], dtype=np.int64)
+
+    # -- entry points (device pointers / torch CUDA tensors)
+    def reset_state(self, stream=None):
+        _check(self._lib.lbf_reset_state(self._h, _stream(stream)), "lbf_reset_state")
+
+    def ppf(self, d_in, d_chan, stream=None):
+        d = self.dims
+        _check(self._lib.lbf_ppf(self._h, _ptr(d_in, d.in_bytes), _ptr(d_chan, d.chan_bytes),
+                                 _stream(stream)), "lbf_ppf")
+
+    def delay_correct(self, d_chan, d_ct, stream=None):
+        d = self.dims
+        _check(self._lib.lbf_delay_correct(self._h, _ptr(d_chan, d.chan_bytes), _ptr(d_ct, d.ct_bytes),
+                                           _stream(stream)), "lbf_delay_correct")
+
+    def beamform(self, d_ct, d_vol, stream=None):
+        d = self.dims
+        _check(self._lib.lbf_beamform(self._h, _ptr(d_ct, d.ct_bytes), _ptr(d_vol, d.vol_bytes),
+                                      _stream(stream)), "lbf_beamform")
+
+    def beamform_stokes(self, d_ct, d_out, stream=None):
+        d = self.dims
+        _check(self._lib.lbf_beamform_stokes(self._h, _ptr(d_ct, d.ct_bytes), _ptr(d_out, d.stokes_bytes),
+                                             _stream(stream)), "lbf_beamform_stokes")
+
+    def stokes(self, d_vol, d_out, stream=None):
+        d = self.dims
+        _check(self._lib.lbf_stokes(self._h, _ptr(d_vol, d.vol_bytes), _ptr(d_out, d.stokes_bytes),
+                                    _stream(stream)), "lbf_stokes")
+
+    def run_block(self, d_in, d_out, stream=None):
+        d = self.dims
+        _check(self._lib.lbf_run_block(self._h, _ptr(d_in, d.in_bytes), _ptr(d_out, d.out_bytes),
+                                       _stream(stream)), "lbf_run_block")
+
+    def run_block_host(self, h_in, h_out, d_in, d_out, stream=None):
+        """H2D copy of h_in, the fused path, D2H copy into h_out, all enqueued on `stream`."""
+        d = self.dims
+        _check(self._lib.lbf_run_block_host(self._h, _ptr(h_in, d.in_bytes), _ptr(h_out, d.out_bytes),
+                                            _ptr(d_in, d.in_bytes), _ptr(d_out, d.out_bytes),
+                                            _stream(stream)), "lbf_run_block_host")
+
+    def trace_begin(self, max_launches: int = 4096):
+        _check(self._lib.lbf_trace_begin(self._h, int(max_launches)), "lbf_trace_begin")
+
+    def trace_end(self) -> dict:
+        """Per-kernel {name: (launches, total_ms)} of the launches since trace_begin."""
+        t = _Trace()
+        _check(self._lib.lbf_trace_end(self._h, ctypes.byref(t)), "lbf_trace_end")
+        out = {}
+        for k in range(t.n_kernels):
+            if t.launches[k]:
+                out[t.names[k].value.decode()] = (int(t.launches[k]), float(t.total_ms[k]))
+        out["_dropped"] = int(t.dropped)
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbf_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plan_status(cfg_kwargs) -> int:
+    """Status lbf_plan returns for a configuration (validation only; LBF_OK needs a GPU)."""
+    try:
+        Plan(**cfg_kwargs).close()
+        return LBF_OK
+    except LbfError as e:
+        return e.status

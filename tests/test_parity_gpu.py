@@ -1,0 +1,307 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle on the same seeded inputs.
+
+Tolerances (FP32 path):
+  * corner turn / transposes: exact;
+  * integer shift decisions: exact;
+  * filter-bank output, delay-compensated channels and beam voltages: relative RMS error
+    ||got - ref|| / ||ref|| <= 1e-5 per (subband, station) or (beam, subband);
+  * Stokes I: |got - ref| <= 1e-5 * ref per element (I > 0);
+  * Stokes Q, U, V (they cross zero): |got - ref| <= 1e-5 * I_ref per element.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import lbf_oracle as O
+from synth import generate as G
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+N = 256
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def dev():
+    from paper_1105_0661_gb300 import build_lib
+    build_lib.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    d = torch.device("cuda:0")
+    torch.cuda.set_device(d)
+    return d
+
+
+def _plan(wl, **over):
+    from paper_1105_0661_gb300 import Plan
+    return Plan.from_workload(wl, **over)
+
+
+def _wl(S=8, F=2, T=40 * N, B=5, Q=4, out="I", bits=16, seed=0, long_baselines=True, bp=True):
+    """A small observation that spans several CTA tiles with a ragged tail (M = 40 spectra)."""
+    rng = np.random.default_rng(seed)
+    xyz = G.lofar_positions(rng, S // 2, S - S // 2) if long_baselines else G.disc_positions(rng, S, 1000.0)
+    wl = G.Workload("parity", xyz, G.subband_centres(F, 120e6), G.hex_beam_grid(B, 0.05), (0.3, 0.4), T, Q, out,
+                    sample_bits=bits, sigma=32.0 if bits == 16 else 8.0, source="tone")
+    if bp:
+        wl.bandpass = G.bandpass_ripple(N)
+    return wl
+
+
+def _rel_rms(got, ref, axes):
+    num = np.sqrt(np.sum(np.abs(got - ref) ** 2, axis=axes))
+    den = np.sqrt(np.sum(np.abs(ref) ** 2, axis=axes))
+    return num / den
+
+
+def _to_dev(x, dev):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+
+
+def _check_stokes(got, ref, tol=TOL):
+    """got/ref [B][nS][F][N][Mq]."""
+    I = ref[:, 0]
+    assert np.all(I > 0)
+    eI = np.abs(got[:, 0] - I) / I
+    assert eI.max() <= tol, f"Stokes I max rel err {eI.max():.3e}"
+    if ref.shape[1] == 4:
+        eq = np.abs(got[:, 1:] - ref[:, 1:]) / I[:, None]
+        assert eq.max() <= tol, f"Stokes QUV max err/I {eq.max():.3e}"
+
+
+# ----------------------------------------------------------------------------- geometry
+def test_integer_shifts_match_oracle(dev):
+    for wl in (G.workload_tiny(0), G.workload_lofar_fp32(0), _wl(S=12, seed=3)):
+        p = _plan(wl.subset([0]) if wl.n_subbands > 1 else wl, block_samples=N)
+        n, d = p.shifts()
+        ob = O.observation_from_workload(wl)
+        assert np.array_equal(n, ob.n_shift) and np.array_equal(d, ob.d_shift)
+        assert p.dims.d_max == ob.d_max and p.dims.history_samples == ob.H
+        p.close()
+
+
+# ----------------------------------------------------------------------------- a1-a3 filter bank
+@pytest.mark.parametrize("bits", [16, 8])
+def test_ppf_matches_oracle_over_two_blocks(dev, bits):
+    wl = _wl(bits=bits)
+    p = _plan(wl)
+    ob = O.observation_from_workload(wl)
+    assert ob.d_max > 3
+    chan = torch.empty(p.shape("chan"), dtype=torch.complex64, device=dev)
+    for bi in range(2):
+        blk = G.make_block(wl, seed=1, block_index=bi)
+        p.ppf(_to_dev(blk, dev), chan)
+        ref = ob.ppf(blk)
+        got = chan.cpu().numpy().astype(np.complex128)
+        err = _rel_rms(got, ref, (2, 3, 4))
+        assert err.max() <= TOL, (bi, err.max())
+    p.close()
+
+
+def test_ppf_streaming_equals_one_long_block(dev):
+    """Three blocks with device-resident history equal one block three times as long."""
+    wl = _wl(T=16 * N, F=1)
+    wl3 = _wl(T=48 * N, F=1)
+    p1, p3 = _plan(wl), _plan(wl3)
+    big = G.make_block(wl3, seed=2)
+    c3 = torch.empty(p3.shape("chan"), dtype=torch.complex64, device=dev)
+    p3.ppf(_to_dev(big, dev), c3)
+    c1 = torch.empty(p1.shape("chan"), dtype=torch.complex64, device=dev)
+    parts = []
+    for i in range(3):
+        p1.ppf(_to_dev(big[:, :, i * 16 * N:(i + 1) * 16 * N], dev), c1)
+        parts.append(c1.cpu().numpy())
+    assert np.array_equal(np.concatenate(parts, axis=3), c3.cpu().numpy())
+    p1.close(); p3.close()
+
+
+def test_reset_state_restarts_the_stream(dev):
+    wl = _wl(F=1, T=16 * N)
+    p = _plan(wl)
+    blk = _to_dev(G.make_block(wl, seed=4), dev)
+    chan = torch.empty(p.shape("chan"), dtype=torch.complex64, device=dev)
+    p.ppf(blk, chan)
+    first = chan.clone()
+    p.ppf(blk, chan)
+    assert not torch.equal(first, chan)
+    p.reset_state()
+    p.ppf(blk, chan)
+    assert torch.equal(first, chan)
+    p.close()
+
+
+# ----------------------------------------------------------------------------- a4 delay + corner turn
+def test_delay_correct_matches_oracle(dev):
+    wl = _wl()
+    p = _plan(wl)
+    ob = O.observation_from_workload(wl)
+    rng = np.random.default_rng(5)
+    shp = p.shape("chan")
+    chan = (rng.standard_normal(shp) + 1j * rng.standard_normal(shp)).astype(np.complex64)
+    ct = torch.empty(p.shape("ct"), dtype=torch.complex64, device=dev)
+    p.delay_correct(_to_dev(chan, dev), ct)
+    ref = ob.delay_correct(chan.astype(np.complex128))
+    got = ct.cpu().numpy().astype(np.complex128)
+    assert np.max(np.abs(got - ref)) <= 2e-6 * np.max(np.abs(ref))
+    p.close()
+
+
+def test_corner_turn_is_exact_transpose(dev):
+    """With no delays (phase centre at zenith, stations in the ground plane) and a unit bandpass,
+    delay_correct is a pure transpose [F][S][P][M][N] -> [F][N][S][P][M]: exact."""
+    wl = _wl(bp=False)
+    wl.phase_centre = (0.0, 0.0)
+    p = _plan(wl)
+    rng = np.random.default_rng(6)
+    shp = p.shape("chan")
+    chan = (rng.standard_normal(shp) + 1j * rng.standard_normal(shp)).astype(np.complex64)
+    ct = torch.empty(p.shape("ct"), dtype=torch.complex64, device=dev)
+    p.delay_correct(_to_dev(chan, dev), ct)
+    assert np.array_equal(ct.cpu().numpy(), np.ascontiguousarray(np.transpose(chan, (0, 4, 1, 2, 3))))
+    p.close()
+
+
+# ----------------------------------------------------------------------------- a5-a6 beam former
+@pytest.mark.parametrize("variant,B", [("few", 5), ("many", 5), ("many", 133), ("few", 19)])
+def test_beamform_voltages_match_oracle(dev, variant, B):
+    wl = _wl(B=B, out="V")
+    p = _plan(wl, bf_variant=variant)
+    ob = O.observation_from_workload(wl)
+    rng = np.random.default_rng(7)
+    shp = p.shape("ct")
+    ct = (rng.standard_normal(shp) + 1j * rng.standard_normal(shp)).astype(np.complex64)
+    vol = torch.empty(p.shape("vol"), dtype=torch.complex64, device=dev)
+    p.beamform(_to_dev(ct, dev), vol)
+    ref = ob.beamform(ct.astype(np.complex128))
+    err = _rel_rms(vol.cpu().numpy().astype(np.complex128), ref, (2, 3, 4))
+    assert err.max() <= TOL, err.max()
+    p.close()
+
+
+# ----------------------------------------------------------------------------- a7 Stokes
+@pytest.mark.parametrize("out,Q", [("I", 1), ("I", 8), ("IQUV", 4), ("IQUV", 32), ("I", 2)])
+def test_stokes_matches_oracle(dev, out, Q):
+    wl = _wl(T=64 * N, out=out, Q=Q, B=3)
+    p = _plan(wl)
+    ob = O.observation_from_workload(wl)
+    rng = np.random.default_rng(8)
+    shp = p.shape("vol")
+    vol = (rng.standard_normal(shp) + 1j * rng.standard_normal(shp)).astype(np.complex64)
+    o = torch.empty(p.shape("stokes"), dtype=torch.float32, device=dev)
+    p.stokes(_to_dev(vol, dev), o)
+    _check_stokes(o.cpu().numpy().astype(np.float64), ob.stokes(vol.astype(np.complex128)))
+    p.close()
+
+
+@pytest.mark.parametrize("variant", ["few", "many"])
+@pytest.mark.parametrize("out,Q", [("I", 4), ("IQUV", 16), ("I", 1), ("IQUV", 2)])
+def test_beamform_stokes_epilogue_matches_oracle(dev, variant, out, Q):
+    wl = _wl(T=64 * N, out=out, Q=Q, B=6)
+    p = _plan(wl, bf_variant=variant)
+    ob = O.observation_from_workload(wl)
+    rng = np.random.default_rng(9)
+    shp = p.shape("ct")
+    ct = (rng.standard_normal(shp) + 1j * rng.standard_normal(shp)).astype(np.complex64)
+    o = torch.empty(p.shape("stokes"), dtype=torch.float32, device=dev)
+    p.beamform_stokes(_to_dev(ct, dev), o)
+    _check_stokes(o.cpu().numpy().astype(np.float64), ob.stokes(ob.beamform(ct.astype(np.complex128))))
+    p.close()
+
+
+# ----------------------------------------------------------------------------- a1-a7 fused
+@pytest.mark.parametrize("variant", ["few", "many"])
+@pytest.mark.parametrize("out,bits", [("I", 16), ("IQUV", 16), ("V", 16), ("I", 8)])
+def test_run_block_matches_oracle(dev, variant, out, bits):
+    wl = _wl(out=out, bits=bits, Q=4 if out != "V" else 1)
+    p = _plan(wl, bf_variant=variant)
+    ob = O.observation_from_workload(wl)
+    shape = p.shape("stokes") if out != "V" else p.shape("vol")
+    o = torch.empty(shape, dtype=torch.float32 if out != "V" else torch.complex64, device=dev)
+    for bi in range(2):
+        blk = G.make_block(wl, seed=10, block_index=bi)
+        p.run_block(_to_dev(blk, dev), o)
+        ref = ob.run_block(blk)
+        got = o.cpu().numpy().astype(np.float64 if out != "V" else np.complex128)
+        if out == "V":
+            assert _rel_rms(got, ref, (2, 3, 4)).max() <= TOL
+        else:
+            _check_stokes(got, ref)
+    p.close()
+
+
+def test_fused_equals_split_chain(dev):
+    """run_block == ppf -> delay_correct -> beamform_stokes bit for bit (same arithmetic), and
+    == ppf -> delay_correct -> beamform -> stokes within FP32 rounding."""
+    wl = _wl(out="IQUV", Q=4)
+    pf, ps = _plan(wl), _plan(wl)
+    blk = _to_dev(G.make_block(wl, seed=11), dev)
+    o1 = torch.empty(pf.shape("stokes"), dtype=torch.float32, device=dev)
+    pf.run_block(blk, o1)
+    chan = torch.empty(ps.shape("chan"), dtype=torch.complex64, device=dev)
+    ct = torch.empty(ps.shape("ct"), dtype=torch.complex64, device=dev)
+    o2 = torch.empty_like(o1)
+    ps.ppf(blk, chan)
+    ps.delay_correct(chan, ct)
+    ps.beamform_stokes(ct, o2)
+    assert torch.equal(o1, o2)
+    vol = torch.empty(ps.shape("vol"), dtype=torch.complex64, device=dev)
+    o3 = torch.empty_like(o1)
+    ps.beamform(ct, vol)
+    ps.stokes(vol, o3)
+    I = o1[:, 0]
+    assert ((o3[:, 0] - I).abs() / I).max().item() < 1e-5
+    pf.close(); ps.close()
+
+
+# ----------------------------------------------------------------------------- edge cases
+def test_degenerate_single_everything(dev):
+    """S = 1, B = 1, one spectrum per block (T = N), Q = 1."""
+    wl = _wl(S=1, F=1, T=N, B=1, Q=1, long_baselines=False)
+    for variant in ("few", "many"):
+        p = _plan(wl, bf_variant=variant)
+        ob = O.observation_from_workload(wl)
+        o = torch.empty(p.shape("stokes"), dtype=torch.float32, device=dev)
+        for bi in range(3):
+            blk = G.make_block(wl, seed=12, block_index=bi)
+            p.run_block(_to_dev(blk, dev), o)
+            ref = ob.run_block(blk)
+            _check_stokes(o.cpu().numpy().astype(np.float64), ref)
+        p.close()
+
+
+def test_empty_block_is_a_no_op(dev):
+    wl = _wl(T=0, F=1)
+    p = _plan(wl)
+    assert p.dims.n_spectra == 0 and p.dims.out_bytes == 0
+    x = torch.zeros(16, dtype=torch.int16, device=dev)
+    o = torch.zeros(4, dtype=torch.float32, device=dev)
+    p.run_block(x, o)
+    p.ppf(x, o)
+    assert torch.count_nonzero(o).item() == 0
+    p.close()
+
+
+def test_host_pointer_rejected(dev):
+    from paper_1105_0661_gb300 import LbfError
+    wl = _wl(F=1, T=16 * N)
+    p = _plan(wl)
+    host = torch.zeros(p.shape("in"), dtype=torch.int16)
+    o = torch.empty(p.shape("stokes"), dtype=torch.float32, device=dev)
+    with pytest.raises(LbfError) as ei:
+        p.run_block(host, o)
+    assert ei.value.status == 1
+    with pytest.raises(ValueError):
+        p.stokes(o, o)   # a Stokes-sized buffer is far too short to be read as voltages
+    p.close()
+
+
+def test_maximum_paper_geometry(dev):
+    """64 stations (the paper's maximum, Section 3) x 8 beams x Q 16, int8, many-beam kernel."""
+    wl = _wl(S=64, F=1, T=32 * N, B=8, Q=16, bits=8)
+    p = _plan(wl, bf_variant="many")
+    ob = O.observation_from_workload(wl)
+    blk = G.make_block(wl, seed=13)
+    o = torch.empty(p.shape("stokes"), dtype=torch.float32, device=dev)
+    p.run_block(_to_dev(blk, dev), o)
+    _check_stokes(o.cpu().numpy().astype(np.float64), ob.run_block(blk))
+    p.close()
