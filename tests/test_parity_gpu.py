@@ -72,7 +72,7 @@ def _check_stokes(got, ref, tol=TOL):
 # ----------------------------------------------------------------------------- geometry
 def test_integer_shifts_match_oracle(dev):
     for wl in (G.workload_tiny(0), G.workload_lofar_fp32(0), _wl(S=12, seed=3)):
-        p = _plan(wl.subset([0]) if wl.n_subbands > 1 else wl, block_samples=N)
+        p = _plan(wl.subset([0]) if wl.n_subbands > 1 else wl, block_samples=N, int_factor=1)
         n, d = p.shifts()
         ob = O.observation_from_workload(wl)
         assert np.array_equal(n, ob.n_shift) and np.array_equal(d, ob.d_shift)
