@@ -103,7 +103,7 @@ typedef struct lbf_dims {
   int32_t n_stokes;           /* nS: 1 (I), 4 (IQUV), 0 (voltages) */
   int32_t d_max;              /* largest integer shift d_s, in samples */
   int32_t history_samples;    /* H = (L-1) N + d_max samples kept per (station, subband) */
-  int32_t bf_kernel;          /* beam-former kernel the plan uses: LBF_BF_FEW or LBF_BF_MANY */
+  int32_t bf_kernel;          /* beam former the plan uses: 1 few-beam, 2 many-beam FP32, 3 tensor core */
   size_t in_bytes;            /* bytes of one input block */
   size_t chan_bytes;          /* bytes of a chan buffer */
   size_t ct_bytes;            /* bytes of a ct buffer */
@@ -120,8 +120,12 @@ typedef struct lbf_plan_s *lbf_plan_t;
  * differences), copies the tables to the current CUDA device, allocates the history (zeroed: the
  * stream starts with zero samples) and the run_block scratch.  Synchronous.  The config's host
  * arrays are copied; the caller keeps ownership.  On error *out is set to NULL.
- * Errors: LBF_EINVAL (bad config), LBF_EUNSUPPORTED (N != 256, L != 16, FP16_TC precision),
- * LBF_ENOMEM, LBF_ECUDA. */
+ * With precision LBF_FP16_TC the many-beam beam former runs on the tensor cores (tcgen05, FP16
+ * operands, FP32 accumulation): 16-bit samples feed it as two FP16 planes (hi = fp16(Y),
+ * lo = fp16(Y - hi), two products), 8-bit samples as one plane; it needs S <= 64 and a Stokes
+ * output.
+ * Errors: LBF_EINVAL (bad config), LBF_EUNSUPPORTED (N != 256, L != 16, or an FP16_TC plan with
+ * S > 64 or voltage output), LBF_ENOMEM, LBF_ECUDA. */
 lbf_status lbf_plan(const lbf_config *cfg, lbf_plan_t *out);
 
 /* Release every device buffer of the plan (synchronises the device first). NULL is a no-op. */
@@ -179,14 +183,20 @@ lbf_status lbf_run_block_host(lbf_plan_t plan, const void *h_in, void *h_out, vo
  * the events.  While no trace is active the calls record nothing. */
 typedef struct lbf_trace {
   int32_t n_kernels;           /* entries used in the arrays below */
-  int32_t launches[8];         /* launches per kernel */
-  double total_ms[8];          /* summed event time per kernel */
-  char names[8][32];           /* kernel names: "ppf", "ppf_ct", "hist_update", "delay_ct",
-                                  "bf_few", "bf_many", "stokes" */
+  int32_t launches[16];        /* launches per kernel */
+  double total_ms[16];         /* summed event time per kernel */
+  char names[16][32];          /* kernel names: ppf, ppf_ct, hist_update, delay_ct, bf_few, bf_many,
+                                  stokes, ppf_ct16, bf_tc, ct_to_ct16 */
   int32_t dropped;             /* launches not recorded because max_launches was reached */
 } lbf_trace;
 lbf_status lbf_trace_begin(lbf_plan_t plan, int32_t max_launches);
 lbf_status lbf_trace_end(lbf_plan_t plan, lbf_trace *out);
+
+/* Synchronises the device and reports whether a bounded device-side wait (tensor-core pipeline
+ * barriers) gave up since the last call: LBF_ETIMEOUT (the results of the affected launch are
+ * invalid; *code, if given, receives the role that gave up: 1 loads, 2 MMA, 3 epilogue), else
+ * LBF_OK.  The error word is cleared. */
+lbf_status lbf_device_status(lbf_plan_t plan, int32_t *code);
 
 /* Human-readable name of a status code (static string). */
 const char *lbf_status_string(lbf_status s);

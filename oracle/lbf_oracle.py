@@ -193,11 +193,13 @@ class Observation:
         return np.exp(2j * np.pi * fc[:, None, None] * self.beam_delays()[None])
 
     # -- a6: tied-array beam former (Section 4.3)
-    def beamform(self, ct: np.ndarray) -> np.ndarray:
+    def beamform(self, ct: np.ndarray, channels=None) -> np.ndarray:
+        """V = sum_s w Y for the corner-turned block ct [F][n][S][P][M]; `channels` lists the
+        channel index of each of the n rows (default: all N channels)."""
         F, N, S, P, M = ct.shape
         vol = np.empty((self.B, F, N, P, M), dtype=np.complex128)
         for f in range(F):
-            w = self.weights(f)                                            # [N, B, S]
+            w = self.weights(f, channels)                                  # [n, B, S]
             v = w @ ct[f].reshape(N, S, P * M)                             # [N, B, P*M]
             vol[:, f] = np.transpose(v.reshape(N, self.B, P, M), (1, 0, 2, 3))
         return vol
@@ -214,9 +216,16 @@ class Observation:
         return np.ascontiguousarray(np.moveaxis(integrate(p, self.Q), 0, 1))      # [B, nS, F, N, M/Q]
 
     # -- the whole path for one block
-    def run_block(self, block: np.ndarray) -> np.ndarray:
-        vol = self.beamform(self.delay_correct(self.ppf(block)))
-        return vol if self.output == "V" else self.stokes(vol)
+    def run_block(self, block: np.ndarray, channel_group: int = 32) -> np.ndarray:
+        ct = self.delay_correct(self.ppf(block))
+        if self.output == "V":
+            return self.beamform(ct)
+        # channels are independent; evaluating them in groups only bounds the memory of the
+        # intermediate voltages (B x group x P x M) for many-beam observations
+        parts = [self.stokes(self.beamform(ct[:, c0:c0 + channel_group],
+                                           np.arange(c0, min(c0 + channel_group, self.N))))
+                 for c0 in range(0, self.N, channel_group)]
+        return np.concatenate(parts, axis=3)
 
     # -- selected (subband, channel) outputs of one block from zero history, computed one by one
     def run_block_sampled(self, block_f: np.ndarray, f: int, channels) -> np.ndarray:

@@ -3,7 +3,7 @@
 //
 // Per (subband f, channel c) the work is a complex product  V[b][pol, m] = sum_s w[b,s] Y[s][pol, m]
 // with w[b,s] = exp(+2 pi i f_c dtau[b,s]), f_c = f0_f + df_c.  The weights are generated per CTA
-// into shared memory: FP64 phase in cycles, reduced to one cycle, FP32 sincos.
+// into shared memory from the plan's FP64-reduced phase tables (tables.cu) and an FP32 sincos.
 //
 // Two kernels:
 //  * few-beam (bandwidth bound): one thread per spectrum m (both pols), weights broadcast from
@@ -30,10 +30,6 @@ __device__ __forceinline__ void cmac(float2 &acc, float2 w, float2 y) {
   acc.y = fmaf(w.y, y.x, acc.y);
 }
 
-__device__ __forceinline__ double channel_freq(const Geometry &g, int f, int c) {
-  return g.f0[f] + (double)(c - kN / 2) * (g.fs / kN);
-}
-
 // Stokes parameter `st` of the voltage pair (X, Y), Section 4.5.
 __device__ __forceinline__ float stokes_param(int st, float2 X, float2 Y) {
   const float xx = fmaf(X.x, X.x, X.y * X.y);
@@ -55,10 +51,9 @@ bf_few_kernel(Geometry g, const float2 *__restrict__ ct, void *__restrict__ out)
   const int f = fc / kN, c = fc - f * kN;
   const int b0 = blockIdx.y * kFewBeams;
   const int tid = threadIdx.x;
-  const double freq = channel_freq(g, f, c);
   for (int i = tid; i < g.S * kFewBeams; i += kFewThreads) {
     const int s = i / kFewBeams, b = b0 + (i - s * kFewBeams);
-    wsm[i] = (b < g.B) ? unit_phasor_cycles(freq * g.dtau[(long long)b * g.S + s]) : make_float2(0.f, 0.f);
+    wsm[i] = (b < g.B) ? beam_weight(g, f, c, (long long)b * g.S + s) : make_float2(0.f, 0.f);
   }
   __syncthreads();
   const float2 *y = ct + (long long)fc * g.S * kP * g.M;
@@ -124,10 +119,9 @@ bf_many_kernel(Geometry g, const float2 *__restrict__ ct, void *__restrict__ out
   const int bt = blockIdx.x - fc * nbt;
   const int f = fc / kN, c = fc - f * kN;
   const int bbase = bt * kBT;
-  const double freq = channel_freq(g, f, c);
   for (int i = tid; i < g.S * kBT; i += kManyThreads) {
     const int s = i / kBT, bl = i - s * kBT, b = bbase + bl;
-    wsm[i] = (b < g.B) ? unit_phasor_cycles(freq * g.dtau[(long long)b * g.S + s]) : make_float2(0.f, 0.f);
+    wsm[i] = (b < g.B) ? beam_weight(g, f, c, (long long)b * g.S + s) : make_float2(0.f, 0.f);
   }
   const int bg = tid >> 3;   // beams bbase + 4 bg .. +3
   const int mg = tid & 7;    // spectra 4 mg .. +3 of the pass

@@ -3,6 +3,8 @@
 // The phase is formed in FP64 cycles per (s, f, c) and reduced before the FP32 sine/cosine; the
 // transpose goes through an XOR-swizzled shared-memory tile so that both the 2 KB channel rows read
 // and the 128-byte spectrum runs written are coalesced and bank-conflict free.
+#include <cuda_fp16.h>
+
 #include "lbf_internal.cuh"
 
 namespace lbf {
@@ -48,7 +50,49 @@ delay_ct_kernel(Geometry g, const float2 *__restrict__ chan, float2 *__restrict_
   }
 }
 
+// ct [F][N][S][P][M] cf32 -> [F][N][P][M][kpad] fp16 planes (station slot 2s, 2s+1).  One CTA per
+// (f, c, pol, 64-spectrum tile): stations are gathered through shared memory so that each thread
+// writes one whole 4-station (16-byte) group of a spectrum's row.
+__global__ void __launch_bounds__(256)
+ct_to_ct16_kernel(Geometry g, const float2 *__restrict__ ct, Ct16Out o, int tiles) {
+  __shared__ float2 tile[64][65];
+  long long idx = blockIdx.x;
+  const int t = (int)(idx % tiles);
+  idx /= tiles;
+  const int pol = (int)(idx % kP);
+  const long long fc = idx / kP;
+  const int m0 = t * 64;
+  __half *hi = reinterpret_cast<__half *>(o.hi);
+  __half *lo = reinterpret_cast<__half *>(o.lo);
+  for (int s0 = 0; s0 < g.S; s0 += 64) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
+      const int sl = i >> 6, ml = i & 63, s = s0 + sl, m = m0 + ml;
+      tile[ml][sl] = (s < g.S && m < g.M) ? ct[((fc * g.S + s) * kP + pol) * g.M + m] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
+      const int ml = i >> 6, sl = i & 63, s = s0 + sl, m = m0 + ml;
+      if (s < g.S && m < g.M) {
+        const float2 v = tile[ml][sl];
+        const long long d = (((fc * kP + pol) * g.M) + m) * o.kpad + 2 * s;
+        const __half2 h = __floats2half2_rn(v.x, v.y);
+        *reinterpret_cast<__half2 *>(hi + d) = h;
+        if (lo) *reinterpret_cast<__half2 *>(lo + d) = __floats2half2_rn(v.x - __low2float(h), v.y - __high2float(h));
+      }
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_ct_to_ct16(const Geometry &g, const float2 *ct, const Ct16Out &o, cudaStream_t st) {
+  const int tiles = (g.M + 63) / 64;
+  const long long ctas = (long long)g.F * kN * kP * tiles;
+  if (ctas == 0) return cudaSuccess;
+  ct_to_ct16_kernel<<<(unsigned)ctas, 256, 0, st>>>(g, ct, o, tiles);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_delay_ct(const Geometry &g, const float2 *chan, float2 *ct, cudaStream_t st) {
   const int tiles = (g.M + kTile - 1) / kTile;

@@ -1,5 +1,8 @@
 // C-ABI layer: plan creation (host FP64 geometry, device tables and state) and the entry points
 // declared in include/lbf.h.  No compute happens here; every step of the path is a kernel.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -27,6 +30,14 @@ struct lbf_plan_s {
   float *bandpass = nullptr;
   int *dshift = nullptr;
   double *tau = nullptr, *resid = nullptr, *f0 = nullptr, *dtau = nullptr;
+  float *phase0 = nullptr, *step = nullptr;
+  // tensor-core precision: FP16 corner-turned planes and their TMA descriptors
+  bool tc = false;
+  int kpad = 0, planes = 0;
+  void *ct16[2] = {nullptr, nullptr};
+  alignas(64) CUtensorMap tmap[2];
+  size_t ct16_bytes = 0;
+  int *d_err = nullptr;   // device error word set by bounded waits that gave up
   void *hist[2] = {nullptr, nullptr};
   int cur = 0;
   float2 *ws = nullptr;
@@ -43,7 +54,7 @@ struct lbf_plan_s {
     lbf::Geometry g;
     g.S = S; g.F = F; g.B = B; g.T = T; g.M = M; g.Q = Q; g.nS = nS; g.H = H; g.fs = fs;
     g.taps = taps; g.twiddle = twiddle; g.bandpass = bandpass; g.dshift = dshift;
-    g.tau = tau; g.resid = resid; g.f0 = f0; g.dtau = dtau;
+    g.tau = tau; g.resid = resid; g.f0 = f0; g.dtau = dtau; g.phase0 = phase0; g.step = step;
     return g;
   }
 };
@@ -84,6 +95,8 @@ void release(lbf_plan_s *p) {
   cudaFree(p->taps); cudaFree(p->twiddle); cudaFree(p->bandpass); cudaFree(p->dshift);
   cudaFree(p->tau); cudaFree(p->resid); cudaFree(p->f0); cudaFree(p->dtau);
   cudaFree(p->hist[0]); cudaFree(p->hist[1]); cudaFree(p->ws);
+  cudaFree(p->phase0); cudaFree(p->step);
+  cudaFree(p->ct16[0]); cudaFree(p->ct16[1]); cudaFree(p->d_err);
 }
 
 lbf_status validate(const lbf_config *c) {
@@ -106,7 +119,9 @@ lbf_status validate(const lbf_config *c) {
   for (int i = 0; i < c->n_subbands; ++i) if (!std::isfinite(c->subband_centre_hz[i])) return LBF_EINVAL;
   for (int i = 0; i < 2 * c->n_beams; ++i) if (!std::isfinite(c->beam_dlm[i])) return LBF_EINVAL;
   if (c->n_channels != lbf::kN || c->n_taps != lbf::kL) return LBF_EUNSUPPORTED;
-  if (c->precision == LBF_FP16_TC) return LBF_EUNSUPPORTED;
+  if (c->precision == LBF_FP16_TC &&
+      (c->output == LBF_VOLTAGES || c->n_stations > lbf::tc_max_stations()))
+    return LBF_EUNSUPPORTED;
   if (c->bf_variant == LBF_BF_MANY && c->n_stations > lbf::many_beam_max_stations()) return LBF_EUNSUPPORTED;
   // index arithmetic: per-plan sizes must keep grid dimensions in range
   const long long ctas = (long long)c->n_subbands * lbf::kN * ((c->n_beams + 7) / 8);
@@ -115,6 +130,35 @@ lbf_status validate(const lbf_config *c) {
 }
 
 bool valid_plan(lbf_plan_t p) { return p && p->magic == kMagic; }
+
+// TMA descriptor of one FP16 plane [F*N*P rows][M][kpad] with 64 x 64 x 2 boxes, 128-byte swizzle.
+cudaError_t encode_ct16_map(CUtensorMap *map, void *base, int kpad, int M, long long rows) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return cudaErrorNotSupported;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[3] = {(cuuint64_t)kpad, (cuuint64_t)M, (cuuint64_t)rows};
+  const cuuint64_t strides[2] = {(cuuint64_t)kpad * 2, (cuuint64_t)M * kpad * 2};
+  const cuuint32_t box[3] = {64, 64, 2};
+  const cuuint32_t elem[3] = {1, 1, 1};
+  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, base, dims, strides, box, elem,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+lbf::Ct16Out ct16_out(lbf_plan_t p) {
+  lbf::Ct16Out o;
+  o.hi = p->ct16[0];
+  o.lo = p->planes > 1 ? p->ct16[1] : nullptr;
+  o.kpad = p->kpad;
+  return o;
+}
 
 // Device pointer check (host-only query): rejects host pointers before any launch.
 bool device_ptr(const void *p, size_t align) {
@@ -132,9 +176,11 @@ lbf_status check_call(lbf_plan_t p) {
   return LBF_OK;
 }
 
-enum KernelId { K_PPF = 0, K_PPF_CT, K_HIST, K_DELAY, K_BF_FEW, K_BF_MANY, K_STOKES, K_COUNT };
-const char *const kKernelNames[K_COUNT] = {"ppf", "ppf_ct", "hist_update", "delay_ct", "bf_few",
-                                           "bf_many", "stokes"};
+enum KernelId { K_PPF = 0, K_PPF_CT, K_HIST, K_DELAY, K_BF_FEW, K_BF_MANY, K_STOKES, K_PPF_CT16, K_BF_TC,
+                K_CT16, K_COUNT };
+static_assert(K_COUNT <= 16, "lbf_trace holds 16 kernels");
+const char *const kKernelNames[K_COUNT] = {"ppf", "ppf_ct", "hist_update", "delay_ct", "bf_few", "bf_many",
+                                           "stokes", "ppf_ct16", "bf_tc", "ct_to_ct16"};
 
 // Launch through `fn`, bracketed by trace events when a trace is active.
 template <typename Fn>
@@ -168,6 +214,16 @@ cudaError_t run_block_device(lbf_plan_t p, const void *d_in, void *d_out, cudaSt
   const lbf::Geometry g = p->geometry();
   const void *h = p->hist[p->cur];
   void *nh = p->hist[p->cur ^ 1];
+  if (p->tc) {
+    const lbf::Ct16Out o = ct16_out(p);
+    cudaError_t e = traced(p, K_PPF_CT16, st, [&] { return lbf::launch_ppf(g, p->bits, d_in, h, nullptr, nullptr, st, &o); });
+    if (e == cudaSuccess) e = traced(p, K_HIST, st, [&] { return lbf::launch_hist_update(g, p->bits, d_in, h, nh, st); });
+    if (e != cudaSuccess) return e;
+    p->cur ^= 1;
+    return traced(p, K_BF_TC, st, [&] {
+      return lbf::launch_bf_tc(g, p->out_kind, &p->tmap[0], p->planes > 1 ? &p->tmap[1] : nullptr, p->planes,
+                               (float *)d_out, p->d_err, st); });
+  }
   cudaError_t e = traced(p, K_PPF_CT, st, [&] { return lbf::launch_ppf(g, p->bits, d_in, h, nullptr, p->ws, st); });
   if (e == cudaSuccess) e = traced(p, K_HIST, st, [&] { return lbf::launch_hist_update(g, p->bits, d_in, h, nh, st); });
   if (e != cudaSuccess) return e;
@@ -256,12 +312,31 @@ lbf_status lbf_plan(const lbf_config *cfg, lbf_plan_t *out) {
   if (e == cudaSuccess) e = upload(&p->resid, resid.data(), resid.size());
   if (e == cudaSuccess) e = upload(&p->f0, cfg->subband_centre_hz, (size_t)p->F);
   if (e == cudaSuccess) e = upload(&p->dtau, dtau.data(), dtau.size());
+  if (e == cudaSuccess) e = upload<float>(&p->phase0, nullptr, (size_t)p->F * p->B * p->S);
+  if (e == cudaSuccess) e = upload<float>(&p->step, nullptr, (size_t)p->B * p->S);
+  if (e == cudaSuccess) e = lbf::launch_phase_tables(p->F, p->B, p->S, p->fs, p->f0, p->dtau, p->phase0, p->step, 0);
   p->hist_bytes = (size_t)p->S * p->F * p->H * p->word;
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
     e = cudaMalloc(&p->hist[i], p->hist_bytes ? p->hist_bytes : 16);
     if (e == cudaSuccess) e = cudaMemset(p->hist[i], 0, p->hist_bytes ? p->hist_bytes : 16);
   }
-  p->ws_bytes = (size_t)p->F * p->N * p->S * lbf::kP * p->M * sizeof(float2);
+  p->tc = cfg->precision == LBF_FP16_TC;
+  if (e == cudaSuccess) e = cudaMalloc((void **)&p->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
+  if (p->tc) {
+    // FP16 planes [F][N][P][M][kpad]; the station pad slots stay zero for the plan's lifetime
+    p->kpad = lbf::tc_kpad(p->S);
+    p->planes = p->bits == 16 ? 2 : 1;
+    p->ct16_bytes = (size_t)p->F * p->N * lbf::kP * p->M * p->kpad * 2;
+    for (int i = 0; i < p->planes && e == cudaSuccess; ++i) {
+      e = cudaMalloc(&p->ct16[i], p->ct16_bytes ? p->ct16_bytes : 16);
+      if (e == cudaSuccess) e = cudaMemset(p->ct16[i], 0, p->ct16_bytes ? p->ct16_bytes : 16);
+      if (e == cudaSuccess && p->M > 0)
+        e = encode_ct16_map(&p->tmap[i], p->ct16[i], p->kpad, p->M, (long long)p->F * p->N * lbf::kP);
+    }
+  }
+  // FP32 corner-turned scratch: run_block of FP32 plans, and the split calls of TC plans
+  p->ws_bytes = p->tc ? 0 : (size_t)p->F * p->N * p->S * lbf::kP * p->M * sizeof(float2);
   if (e == cudaSuccess) e = cudaMalloc((void **)&p->ws, p->ws_bytes ? p->ws_bytes : 16);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -291,7 +366,7 @@ lbf_status lbf_plan_dims(lbf_plan_t p, lbf_dims *d) {
   std::memset(d, 0, sizeof(*d));
   d->n_stations = p->S; d->n_subbands = p->F; d->n_channels = p->N; d->n_taps = p->L;
   d->n_beams = p->B; d->block_samples = p->T; d->int_factor = p->Q; d->n_spectra = p->M;
-  d->n_stokes = p->nS; d->d_max = p->d_max; d->history_samples = p->H; d->bf_kernel = p->variant;
+  d->n_stokes = p->nS; d->d_max = p->d_max; d->history_samples = p->H; d->bf_kernel = p->tc ? 3 : p->variant;
   const size_t cplx = (size_t)p->S * p->F * lbf::kP * p->T * sizeof(float2);
   d->in_bytes = (size_t)p->S * p->F * p->T * p->word;
   d->chan_bytes = cplx;
@@ -299,7 +374,7 @@ lbf_status lbf_plan_dims(lbf_plan_t p, lbf_dims *d) {
   d->vol_bytes = (size_t)p->B * p->F * lbf::kP * p->T * sizeof(float2);
   d->stokes_bytes = p->nS ? (size_t)p->B * p->nS * p->F * p->N * (p->M / p->Q) * sizeof(float) : 0;
   d->out_bytes = p->nS ? d->stokes_bytes : d->vol_bytes;
-  d->workspace_bytes = p->ws_bytes;
+  d->workspace_bytes = p->ws_bytes + p->planes * p->ct16_bytes;
   return LBF_OK;
 }
 
@@ -353,6 +428,7 @@ lbf_status lbf_beamform(lbf_plan_t p, const void *d_ct, void *d_vol, void *strea
   if (s != LBF_OK) return s;
   if (p->M == 0) return LBF_OK;
   if (!device_ptr(d_ct, 8) || !device_ptr(d_vol, 8)) return LBF_EINVAL;
+  if (p->tc) return LBF_EUNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   const lbf::Geometry g = p->geometry();
   return cuda_status(traced(p, bf_kernel_id(p), st, [&] {
@@ -367,6 +443,14 @@ lbf_status lbf_beamform_stokes(lbf_plan_t p, const void *d_ct, float *d_out, voi
   if (!device_ptr(d_ct, 8) || !device_ptr(d_out, 4)) return LBF_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   const lbf::Geometry g = p->geometry();
+  if (p->tc) {
+    const lbf::Ct16Out o = ct16_out(p);
+    cudaError_t e = traced(p, K_CT16, st, [&] { return lbf::launch_ct_to_ct16(g, (const float2 *)d_ct, o, st); });
+    if (e != cudaSuccess) return cuda_status(e);
+    return cuda_status(traced(p, K_BF_TC, st, [&] {
+      return lbf::launch_bf_tc(g, p->out_kind, &p->tmap[0], p->planes > 1 ? &p->tmap[1] : nullptr, p->planes, d_out,
+                               p->d_err, st); }));
+  }
   return cuda_status(traced(p, bf_kernel_id(p), st, [&] {
     return lbf::launch_beamform(g, p->variant, p->out_kind, (const float2 *)d_ct, d_out, st); }));
 }
@@ -404,6 +488,21 @@ lbf_status lbf_run_block_host(lbf_plan_t p, const void *h_in, void *h_out, void 
   if (e == cudaSuccess) e = run_block_device(p, d_in, d_out, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h_out, d_out, d.out_bytes, cudaMemcpyDeviceToHost, st);
   return cuda_status(e);
+}
+
+lbf_status lbf_device_status(lbf_plan_t p, int32_t *code) {
+  lbf_status s = check_call(p);
+  if (s != LBF_OK) return s;
+  int h = 0;
+  cudaError_t e = cudaMemcpy(&h, p->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (code) *code = h;
+  if (h != 0) {
+    e = cudaMemset(p->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_status(e);
+    return LBF_ETIMEOUT;
+  }
+  return LBF_OK;
 }
 
 lbf_status lbf_trace_begin(lbf_plan_t p, int32_t max_launches) {

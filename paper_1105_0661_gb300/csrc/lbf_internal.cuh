@@ -23,14 +23,29 @@ struct Geometry {
   const double *resid;        // [S] tau_s - n_s Ts
   const double *f0;           // [F] subband centre frequency
   const double *dtau;         // [B][S] beam delay difference
+  const float *phase0;        // [F][B][S] f0_f dtau[b,s] reduced to [-1/2, 1/2] cycle (FP64 -> FP32)
+  const float *step;          // [B][S] fs/N * dtau[b,s], cycles per channel
 };
 
 enum OutKind { OUT_VOLTAGES = 0, OUT_STOKES_I = 1, OUT_STOKES_IQUV = 4 };
 
+// FP16 corner-turned scratch of the tensor-core beam former: [F][N][P][M][kpad] halves per plane.
+struct Ct16Out {
+  void *hi, *lo;   // lo may be null (single-product form)
+  int kpad;        // 2 S rounded up to a multiple of 16
+};
+
 // --- launchers (return cudaGetLastError() of the launch) ---
-// a1-a3 (+ a4 when ct != nullptr): filter bank; reads history `hist`, block `in`.
+// a1-a3 (+ a4 when ct or ct16 is given): filter bank; reads history `hist`, block `in`.
 cudaError_t launch_ppf(const Geometry &g, int bits, const void *in, const void *hist,
-                       float2 *chan, float2 *ct, cudaStream_t st);
+                       float2 *chan, float2 *ct, cudaStream_t st, const Ct16Out *ct16 = nullptr);
+// FP32 corner-turned [F][N][S][P][M] -> FP16 [F][N][P][M][kpad] hi/lo planes (split-call TC path)
+cudaError_t launch_ct_to_ct16(const Geometry &g, const float2 *ct, const Ct16Out &o, cudaStream_t st);
+// tcgen05 beam former with fused Stokes epilogue (bf_tc.cu); tm_hi/tm_lo are CUtensorMap*
+cudaError_t launch_bf_tc(const Geometry &g, int out_kind, const void *tm_hi, const void *tm_lo, int planes,
+                         float *out, int *err, cudaStream_t st);
+int tc_max_stations();
+int tc_kpad(int S);
 // history update: new_hist = last H samples of [hist | in]
 cudaError_t launch_hist_update(const Geometry &g, int bits, const void *in, const void *hist,
                                void *new_hist, cudaStream_t st);
@@ -39,6 +54,9 @@ cudaError_t launch_delay_ct(const Geometry &g, const float2 *chan, float2 *ct, c
 // a5-a6 (+ a7): beam former; out_kind selects voltages or fused Stokes; variant 1 few, 2 many
 cudaError_t launch_beamform(const Geometry &g, int variant, int out_kind, const float2 *ct,
                             void *out, cudaStream_t st);
+// plan-time FP64 tables of the weight phases (tables.cu)
+cudaError_t launch_phase_tables(int F, int B, int S, double fs, const double *f0, const double *dtau,
+                                float *phase0, float *step, cudaStream_t st);
 // largest S the many-beam kernel accepts (shared-memory bound)
 int many_beam_max_stations();
 // a7 standalone: vol -> Stokes
@@ -57,6 +75,15 @@ __device__ __forceinline__ float2 unit_phasor_cycles(double phi) {
   float s, c;
   sincospif(2.0f * (float)r, &s, &c);
   return make_float2(c, s);
+}
+
+// Weight w[b,s] of channel c (Section 4.3) from the plan's phase tables: the FP64-reduced carrier
+// phase of (f, b, s) plus the FP32 channel term, through an FP32 sincos.
+__device__ __forceinline__ float2 beam_weight(const Geometry &g, int f, int c, long long bs) {
+  const float phi = fmaf((float)(c - kN / 2), g.step[bs], g.phase0[(long long)f * g.B * g.S + bs]);
+  float s, co;
+  sincospif(2.0f * phi, &s, &co);
+  return make_float2(co, s);
 }
 
 }  // namespace lbf

@@ -9,6 +9,8 @@
 // pols) then run as 16x16 decompositions, 16 threads per transform: a 16-point DFT in registers,
 // a twiddle from a shared table, a swizzled in-place shared-memory transpose, and a second
 // 16-point DFT.
+#include <cuda_fp16.h>
+
 #include "lbf_internal.cuh"
 
 namespace lbf {
@@ -85,19 +87,41 @@ struct PpfSmem {
   float2 gain[kN];           // bandpass * delay phasor per channel (fused epilogue)
 };
 
-template <int BITS, bool CT>
+// Output modes: the channelised layout, the FP32 corner-turned layout, or the FP16 corner-turned
+// layout of the tensor-core beam former ([F][N][P][M][Kpad] with station s at k = 2s (re), 2s+1
+// (im); a hi plane fp16(Y) and optionally a lo plane fp16(Y - hi)).
+enum PpfMode { MODE_CHAN = 0, MODE_CT32 = 1, MODE_CT16 = 2 };
+
+struct PpfOut {
+  float2 *f32;
+  __half *hi, *lo;
+  int kpad;
+};
+
+template <int BITS, int MODE>
 __global__ void __launch_bounds__(kThreads, 2)
 ppf_kernel(Geometry g, const typename SampleIO<BITS>::word *__restrict__ in,
-           const typename SampleIO<BITS>::word *__restrict__ hist, float2 *__restrict__ out,
-           int chunks) {
+           const typename SampleIO<BITS>::word *__restrict__ hist, PpfOut po, int chunks) {
   using word = typename SampleIO<BITS>::word;
+  constexpr bool CT = MODE != MODE_CHAN;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   PpfSmem &sm = *reinterpret_cast<PpfSmem *>(smem_raw);
+  float2 *__restrict__ out = po.f32;
 
   const int tid = threadIdx.x;
-  const long long sf = blockIdx.x / chunks;            // stream index s * F + f
-  const int chunk = blockIdx.x - (int)(sf * chunks);
-  const int s = (int)(sf / g.F), f = (int)(sf - (long long)s * g.F);
+  int s, f, chunk;
+  if (MODE == MODE_CT16) {   // stations fastest: the scattered 4-byte station slots of one
+    s = (int)(blockIdx.x % g.S);                 // (channel, pol, spectrum) row are written by
+    const long long rest = blockIdx.x / g.S;     // neighbouring CTAs and merge in L2
+    chunk = (int)(rest % chunks);
+    f = (int)(rest / chunks);
+  } else {
+    const long long sf = blockIdx.x / chunks;    // stream index s * F + f
+    chunk = (int)(blockIdx.x - sf * chunks);
+    s = (int)(sf / g.F);
+    f = (int)(sf - (long long)s * g.F);
+  }
+  const long long sf = (long long)s * g.F + f;
   const int m0 = chunk * kSpectraPerCta;
   const int m_end = min(g.M, m0 + kSpectraPerCta);
 
@@ -171,7 +195,22 @@ ppf_kernel(Geometry g, const typename SampleIO<BITS>::word *__restrict__ in,
       for (int p2 = 0; p2 < 16; ++p2) a[p2] = row[j * 16 + (p2 ^ j)];   // thread j = k1
       dft16(a);   // a[k2] = X[j + 16 k2]
       const int m = mt + grp;
-      if (!CT) {
+      if (MODE == MODE_CT16) {
+        if (m < m_end) {
+          const long long rowbase = (((long long)f * kN) * kP + pol) * g.M + m;
+#pragma unroll
+          for (int k2 = 0; k2 < 16; ++k2) {
+            const int c = j + 16 * ((k2 + 8) & 15);
+            const float2 v = cmul(a[k2], sm.gain[c]);
+            const long long idx = (rowbase + (long long)c * kP * g.M) * po.kpad + 2 * s;
+            const __half2 hi = __floats2half2_rn(v.x, v.y);
+            *reinterpret_cast<__half2 *>(po.hi + idx) = hi;
+            if (po.lo)
+              *reinterpret_cast<__half2 *>(po.lo + idx) =
+                  __floats2half2_rn(v.x - __low2float(hi), v.y - __high2float(hi));
+          }
+        }
+      } else if (!CT) {
         if (m < m_end) {
           float2 *dst = out + ((((long long)f * g.S + s) * kP + pol) * g.M + m) * kN;
 #pragma unroll
@@ -217,28 +256,44 @@ __global__ void hist_update_kernel(long long total, int H, int T,
   }
 }
 
-template <int BITS, bool CT>
-cudaError_t launch_ppf_t(const Geometry &g, const void *in, const void *hist, float2 *out,
-                         cudaStream_t st) {
+template <int BITS, int MODE>
+cudaError_t launch_ppf_t(const Geometry &g, const void *in, const void *hist, PpfOut po, cudaStream_t st) {
   using word = typename SampleIO<BITS>::word;
   const int chunks = (g.M + kSpectraPerCta - 1) / kSpectraPerCta;
   const long long ctas = (long long)g.S * g.F * chunks;
   if (ctas == 0) return cudaSuccess;
   const size_t smem = sizeof(PpfSmem);
-  auto kern = ppf_kernel<BITS, CT>;
+  auto kern = ppf_kernel<BITS, MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<(unsigned)ctas, kThreads, smem, st>>>(g, (const word *)in, (const word *)hist, out, chunks);
+  kern<<<(unsigned)ctas, kThreads, smem, st>>>(g, (const word *)in, (const word *)hist, po, chunks);
   return cudaGetLastError();
+}
+
+template <int BITS>
+cudaError_t launch_ppf_bits(const Geometry &g, const void *in, const void *hist, float2 *chan, float2 *ct,
+                            const Ct16Out *ct16, cudaStream_t st) {
+  PpfOut po{nullptr, nullptr, nullptr, 0};
+  if (ct16) {
+    po.hi = reinterpret_cast<__half *>(ct16->hi);
+    po.lo = reinterpret_cast<__half *>(ct16->lo);
+    po.kpad = ct16->kpad;
+    return launch_ppf_t<BITS, MODE_CT16>(g, in, hist, po, st);
+  }
+  if (ct) {
+    po.f32 = ct;
+    return launch_ppf_t<BITS, MODE_CT32>(g, in, hist, po, st);
+  }
+  po.f32 = chan;
+  return launch_ppf_t<BITS, MODE_CHAN>(g, in, hist, po, st);
 }
 
 }  // namespace
 
 cudaError_t launch_ppf(const Geometry &g, int bits, const void *in, const void *hist, float2 *chan,
-                       float2 *ct, cudaStream_t st) {
-  if (bits == 16)
-    return ct ? launch_ppf_t<16, true>(g, in, hist, ct, st) : launch_ppf_t<16, false>(g, in, hist, chan, st);
-  return ct ? launch_ppf_t<8, true>(g, in, hist, ct, st) : launch_ppf_t<8, false>(g, in, hist, chan, st);
+                       float2 *ct, cudaStream_t st, const Ct16Out *ct16) {
+  return bits == 16 ? launch_ppf_bits<16>(g, in, hist, chan, ct, ct16, st)
+                    : launch_ppf_bits<8>(g, in, hist, chan, ct, ct16, st);
 }
 
 cudaError_t launch_hist_update(const Geometry &g, int bits, const void *in, const void *hist,

@@ -1,0 +1,41 @@
+// Plan-time device tables for the positional weights (Section 4.3) in FP64.
+//
+// The weight phase of beam b, station s in channel c of subband f is, in cycles,
+//     phi = f_c * dtau[b,s] = f0_f * dtau[b,s] + (c - N/2) * df * dtau[b,s],
+// with |(c - N/2) df dtau| well below one cycle for any tied-array beam inside a station beam.
+// The large carrier term is formed and reduced to [-1/2, 1/2] cycle here, in FP64, once per
+// (subband, beam, station); the beam formers then add the small per-channel term in FP32 and take
+// an FP32 sincos.  The reduced value is exact to FP32 rounding (<= 3e-8 cycle), the channel term
+// to < 1e-7 cycle, so a weight is accurate to ~1e-6 relative -- without any per-sample FP64 work.
+#include "lbf_internal.cuh"
+
+namespace lbf {
+namespace {
+
+__global__ void phase_table_kernel(int F, int B, int S, double fs, const double *__restrict__ f0,
+                                   const double *__restrict__ dtau, float *__restrict__ phase0,
+                                   float *__restrict__ step) {
+  const long long n = (long long)F * B * S;
+  const double df = fs / kN;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long bs = i % ((long long)B * S);
+    const int f = (int)(i / ((long long)B * S));
+    const double phi = f0[f] * dtau[bs];
+    phase0[i] = (float)(phi - rint(phi));
+    if (f == 0) step[bs] = (float)(df * dtau[bs]);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_phase_tables(int F, int B, int S, double fs, const double *f0, const double *dtau,
+                                float *phase0, float *step, cudaStream_t st) {
+  const long long n = (long long)F * B * S;
+  if (n == 0) return cudaSuccess;
+  const long long want = (n + 255) / 256;
+  phase_table_kernel<<<(unsigned)(want < 4096 ? want : 4096), 256, 0, st>>>(F, B, S, fs, f0, dtau, phase0, step);
+  return cudaGetLastError();
+}
+
+}  // namespace lbf

@@ -25,7 +25,7 @@ BF_VARIANTS = {"auto": 0, "few": 1, "many": 2}
 EXPORTED = ("lbf_plan", "lbf_plan_destroy", "lbf_plan_dims", "lbf_plan_shifts", "lbf_reset_state",
             "lbf_ppf", "lbf_delay_correct", "lbf_beamform", "lbf_beamform_stokes", "lbf_stokes",
             "lbf_run_block", "lbf_run_block_host", "lbf_trace_begin", "lbf_trace_end",
-            "lbf_status_string", "lbf_version")
+            "lbf_device_status", "lbf_status_string", "lbf_version")
 
 
 class LbfError(RuntimeError):
@@ -51,8 +51,8 @@ class _Config(ctypes.Structure):
 
 
 class _Trace(ctypes.Structure):
-    _fields_ = [("n_kernels", ctypes.c_int32), ("launches", ctypes.c_int32 * 8),
-                ("total_ms", ctypes.c_double * 8), ("names", (ctypes.c_char * 32) * 8),
+    _fields_ = [("n_kernels", ctypes.c_int32), ("launches", ctypes.c_int32 * 16),
+                ("total_ms", ctypes.c_double * 16), ("names", (ctypes.c_char * 32) * 16),
                 ("dropped", ctypes.c_int32)]
 
 
@@ -91,6 +91,7 @@ def load_library() -> ctypes.CDLL:
             "lbf_run_block_host": ([vp, vp, vp, vp, vp, vp], ctypes.c_int),
             "lbf_trace_begin": ([vp, ctypes.c_int32], ctypes.c_int),
             "lbf_trace_end": ([vp, ctypes.POINTER(_Trace)], ctypes.c_int),
+            "lbf_device_status": ([vp, i32p], ctypes.c_int),
             "lbf_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "lbf_version": ([], ctypes.c_char_p),
         }
@@ -258,6 +259,13 @@ class Plan:
         _check(self._lib.lbf_run_block_host(self._h, _ptr(h_in, d.in_bytes), _ptr(h_out, d.out_bytes),
                                             _ptr(d_in, d.in_bytes), _ptr(d_out, d.out_bytes),
                                             _stream(stream)), "lbf_run_block_host")
+
+    def device_status(self) -> int:
+        """Synchronise and return the role code of a device-side wait that gave up (0 = none);
+        raises LbfError(LBF_ETIMEOUT) when one did."""
+        code = ctypes.c_int32(0)
+        _check(self._lib.lbf_device_status(self._h, ctypes.byref(code)), "lbf_device_status")
+        return code.value
 
     def trace_begin(self, max_launches: int = 4096):
         _check(self._lib.lbf_trace_begin(self._h, int(max_launches)), "lbf_trace_begin")

@@ -1,0 +1,99 @@
+"""Tensor-core (tcgen05, FP16 operands, FP32 accumulation) beam former against the FP64 oracle.
+
+Bar (precision form): Stokes I within 1e-3 relative per element; Q, U, V within 1e-3 of I.
+16-bit samples use two FP16 planes (hi + lo), 8-bit samples one plane.  The maximum errors seen are
+printed so that the error of each output is reported.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import lbf_oracle as O
+from synth import generate as G
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+N = 256
+TOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def dev():
+    from paper_1105_0661_gb300 import build_lib
+    build_lib.build()
+    d = torch.device("cuda:0")
+    torch.cuda.set_device(d)
+    return d
+
+
+def _wl(S=48, F=2, T=64 * N, B=130, Q=16, out="I", bits=16, seed=0):
+    rng = np.random.default_rng(seed)
+    wl = G.Workload("tc", G.lofar_positions(rng, S // 2, S - S // 2), G.subband_centres(F, 120e6),
+                    G.hex_beam_grid(B, 0.05), (0.3, 0.4), T, Q, out, sample_bits=bits,
+                    sigma=32.0 if bits == 16 else 8.0, source="tone")
+    wl.bandpass = G.bandpass_ripple(N)
+    return wl
+
+
+def _errors(got, ref):
+    I = ref[:, 0]
+    assert np.all(I > 0)
+    eI = float((np.abs(got[:, 0] - I) / I).max())
+    eq = float((np.abs(got[:, 1:] - ref[:, 1:]) / I[:, None]).max()) if ref.shape[1] == 4 else 0.0
+    return eI, eq
+
+
+@pytest.mark.parametrize("S,bits,out,B,M", [(48, 16, "I", 130, 64), (48, 8, "IQUV", 127, 80),
+                                            (16, 16, "IQUV", 64, 64), (64, 16, "I", 256, 48),
+                                            (8, 8, "I", 5, 64)])
+def test_tc_beamform_stokes_matches_oracle(dev, S, bits, out, B, M):
+    from paper_1105_0661_gb300 import Plan
+    Q = 16
+    wl = _wl(S=S, B=B, out=out, bits=bits, T=M * N, Q=Q)
+    p = Plan.from_workload(wl, precision="fp16tc")
+    assert p.dims.bf_kernel == 3
+    ob = O.observation_from_workload(wl)
+    rng = np.random.default_rng(1)
+    shp = p.shape("ct")
+    ct = (rng.standard_normal(shp) + 1j * rng.standard_normal(shp)).astype(np.complex64)
+    o = torch.empty(p.shape("stokes"), dtype=torch.float32, device=dev)
+    p.beamform_stokes(torch.from_numpy(ct).to(dev), o)
+    assert p.device_status() == 0
+    ref = ob.stokes(ob.beamform(ct.astype(np.complex128)))
+    eI, eq = _errors(o.cpu().numpy().astype(np.float64), ref)
+    print(f"TC S={S} bits={bits} {out} B={B} M={M}: Stokes I max rel err {eI:.2e}, QUV/I {eq:.2e}")
+    assert eI <= TOL and eq <= TOL
+    p.close()
+
+
+@pytest.mark.parametrize("bits,out", [(16, "I"), (8, "IQUV")])
+def test_tc_run_block_matches_oracle(dev, bits, out):
+    from paper_1105_0661_gb300 import Plan
+    wl = _wl(bits=bits, out=out, T=96 * N)
+    p = Plan.from_workload(wl, precision="fp16tc")
+    ob = O.observation_from_workload(wl)
+    o = torch.empty(p.shape("stokes"), dtype=torch.float32, device=dev)
+    for bi in range(2):
+        blk = G.make_block(wl, seed=2, block_index=bi)
+        p.run_block(torch.from_numpy(blk).to(dev), o)
+        assert p.device_status() == 0
+        eI, eq = _errors(o.cpu().numpy().astype(np.float64), ob.run_block(blk))
+        print(f"TC run_block bits={bits} {out} block {bi}: I {eI:.2e} QUV/I {eq:.2e}")
+        assert eI <= TOL and eq <= TOL
+    p.close()
+
+
+def test_tc_equals_fp32_path_within_precision_bar(dev):
+    from paper_1105_0661_gb300 import Plan
+    wl = _wl(out="IQUV", T=64 * N)
+    blk = torch.from_numpy(G.make_block(wl, seed=3)).to(dev)
+    outs = []
+    for prec in ("fp32", "fp16tc"):
+        p = Plan.from_workload(wl, precision=prec)
+        o = torch.empty(p.shape("stokes"), dtype=torch.float32, device=dev)
+        p.run_block(blk, o)
+        outs.append(o.double().cpu().numpy())
+        p.close()
+    eI, eq = _errors(outs[1], outs[0])
+    assert eI <= TOL and eq <= TOL
