@@ -131,7 +131,8 @@ lbf_status validate(const lbf_config *c) {
 
 bool valid_plan(lbf_plan_t p) { return p && p->magic == kMagic; }
 
-// TMA descriptor of one FP16 plane [F*N*P rows][M][kpad] with 64 x 64 x 2 boxes, 128-byte swizzle.
+// TMA descriptor of one FP16 plane [F*N*P rows][M][kpad]: boxes of 64 halves (one 128-byte
+// swizzle row) x the beam former's spectra per tile x 2 pols, 128-byte swizzle.
 cudaError_t encode_ct16_map(CUtensorMap *map, void *base, int kpad, int M, long long rows) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
@@ -144,7 +145,7 @@ cudaError_t encode_ct16_map(CUtensorMap *map, void *base, int kpad, int M, long 
   }
   const cuuint64_t dims[3] = {(cuuint64_t)kpad, (cuuint64_t)M, (cuuint64_t)rows};
   const cuuint64_t strides[2] = {(cuuint64_t)kpad * 2, (cuuint64_t)M * kpad * 2};
-  const cuuint32_t box[3] = {64, 64, 2};
+  const cuuint32_t box[3] = {64, (cuuint32_t)lbf::tc_spectra_per_tile(), 2};
   const cuuint32_t elem[3] = {1, 1, 1};
   CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, base, dims, strides, box, elem,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,

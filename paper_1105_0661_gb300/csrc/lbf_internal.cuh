@@ -45,6 +45,7 @@ cudaError_t launch_ct_to_ct16(const Geometry &g, const float2 *ct, const Ct16Out
 cudaError_t launch_bf_tc(const Geometry &g, int out_kind, const void *tm_hi, const void *tm_lo, int planes,
                          float *out, int *err, cudaStream_t st);
 int tc_max_stations();
+int tc_spectra_per_tile();   // TMA box height of the FP16 scratch (spectra per N tile)
 int tc_kpad(int S);
 // history update: new_hist = last H samples of [hist | in]
 cudaError_t launch_hist_update(const Geometry &g, int bits, const void *in, const void *hist,
