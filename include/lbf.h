@@ -60,7 +60,8 @@ typedef enum {
   LBF_ESTATE = 4,      /* plan in an unusable state (e.g. destroyed, or device mismatch) */
   LBF_ETIMEOUT = 5,    /* a bounded device-side wait gave up */
   LBF_EBUSY = 6,       /* resource temporarily unavailable */
-  LBF_EUNSUPPORTED = 7 /* valid request this build does not implement */
+  LBF_EUNSUPPORTED = 7, /* valid request this build does not implement */
+  LBF_ETOOBIG = 8       /* request exceeds the fixed scratch of lbf_run_block_static */
 } lbf_status;
 
 typedef enum { LBF_I8 = 8, LBF_I16 = 16 } lbf_sample_bits;
@@ -197,6 +198,27 @@ lbf_status lbf_trace_end(lbf_plan_t plan, lbf_trace *out);
  * invalid; *code, if given, receives the role that gave up: 1 loads, 2 MMA, 3 epilogue), else
  * LBF_OK.  The error word is cleared. */
 lbf_status lbf_device_status(lbf_plan_t plan, int32_t *code);
+
+/* lbf_run_block without any device allocation, for callers that cannot call cudaMalloc (for
+ * example a plugin whose host framework owns the device-memory budget, or a real-time ingest
+ * thread that must not take the allocator's locks mid-observation).  The paper has no
+ * counterpart: it is a deployment variant of the fused FP32 path.
+ *
+ * Processes ONE block of `cfg` as the first block of a new stream (zero history), exactly as a
+ * fresh plan's lbf_run_block would (FP32 precision only): d_in is the device `in` block, d_out
+ * the device `out` (Stokes) or `vol` (voltages) buffer, both caller-owned; the call enqueues its
+ * work on `stream` and returns.  All other device memory -- tables, zero history and the
+ * corner-turned scratch -- lives in one file-scope device array of 32 MiB that every GPU loading
+ * the library holds until the process exits; the call allocates nothing (no cudaMalloc/cudaFree,
+ * no allocating library routine).  Limits: S*F*T*16 bytes <= 24 MiB (e.g. S*F*T <= 1572864
+ * station-samples), S*F*((L-1)N + d_max)*sample-bytes <= 4 MiB, and the weight tables
+ * (about 4*F*B*S + 12*B*S bytes) <= 4 MiB; beyond them it returns LBF_ETOOBIG before touching the
+ * device.  The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  Every call shares
+ * the array and overwrites the previous call's contents (the zero history is cleared on each
+ * call); calls whose device work overlaps in time race on it.  Other errors as lbf_plan/
+ * lbf_run_block: LBF_EINVAL, LBF_EUNSUPPORTED, LBF_ECUDA. */
+lbf_status lbf_run_block_static(const lbf_config *cfg, const void *d_in, void *d_out, void *stream);
 
 /* Human-readable name of a status code (static string). */
 const char *lbf_status_string(lbf_status s);

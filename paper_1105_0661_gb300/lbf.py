@@ -16,7 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "liblbf.so")
 
-LBF_OK, LBF_EINVAL, LBF_ENOMEM, LBF_ECUDA, LBF_ESTATE, LBF_ETIMEOUT, LBF_EBUSY, LBF_EUNSUPPORTED = range(8)
+LBF_OK, LBF_EINVAL, LBF_ENOMEM, LBF_ECUDA, LBF_ESTATE, LBF_ETIMEOUT, LBF_EBUSY, LBF_EUNSUPPORTED, LBF_ETOOBIG = range(9)
 OUTPUTS = {"V": 0, "I": 1, "IQUV": 4}
 PRECISIONS = {"fp32": 0, "fp16tc": 1}
 BF_VARIANTS = {"auto": 0, "few": 1, "many": 2}
@@ -25,7 +25,7 @@ BF_VARIANTS = {"auto": 0, "few": 1, "many": 2}
 EXPORTED = ("lbf_plan", "lbf_plan_destroy", "lbf_plan_dims", "lbf_plan_shifts", "lbf_reset_state",
             "lbf_ppf", "lbf_delay_correct", "lbf_beamform", "lbf_beamform_stokes", "lbf_stokes",
             "lbf_run_block", "lbf_run_block_host", "lbf_trace_begin", "lbf_trace_end",
-            "lbf_device_status", "lbf_status_string", "lbf_version")
+            "lbf_device_status", "lbf_run_block_static", "lbf_status_string", "lbf_version")
 
 
 class LbfError(RuntimeError):
@@ -92,6 +92,7 @@ def load_library() -> ctypes.CDLL:
             "lbf_trace_begin": ([vp, ctypes.c_int32], ctypes.c_int),
             "lbf_trace_end": ([vp, ctypes.POINTER(_Trace)], ctypes.c_int),
             "lbf_device_status": ([vp, i32p], ctypes.c_int),
+            "lbf_run_block_static": ([ctypes.POINTER(_Config), vp, vp, vp], ctypes.c_int),
             "lbf_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "lbf_version": ([], ctypes.c_char_p),
         }
@@ -300,3 +301,36 @@ def plan_status(cfg_kwargs) -> int:
         return LBF_OK
     except LbfError as e:
         return e.status
+
+
+def run_block_static(station_xyz, subband_hz, beam_dlm, phase_centre, taps, block_samples, d_in, d_out,
+                     int_factor=1, output="I", sample_bits=16, bandpass=None, sample_rate_hz=195312.5,
+                     bf_variant="auto", stream=None):
+    """One block through lbf_run_block_static, the entry point that allocates no device memory:
+    for callers that cannot call cudaMalloc (a host framework that owns the device-memory budget,
+    a real-time thread that must not take the allocator's locks).  The block is processed as the
+    first block of a new stream; its scratch is a fixed 32 MiB device array shared by all calls,
+    so calls whose device work overlaps must not be issued.  Raises LbfError(LBF_ETOOBIG) when the
+    observation exceeds that scratch."""
+    lib = load_library()
+    keep = [np.ascontiguousarray(station_xyz, dtype=np.float64).reshape(-1, 3),
+            np.ascontiguousarray(subband_hz, dtype=np.float64).reshape(-1),
+            np.ascontiguousarray(beam_dlm, dtype=np.float64).reshape(-1, 2),
+            np.ascontiguousarray(taps, dtype=np.float32).reshape(-1),
+            None if bandpass is None else np.ascontiguousarray(bandpass, dtype=np.float32).reshape(-1)]
+    xyz, f0, dlm, h, bp = keep
+    cfg = _Config()
+    cfg.n_stations, cfg.n_subbands, cfg.n_beams = xyz.shape[0], f0.shape[0], dlm.shape[0]
+    cfg.n_channels, cfg.n_taps = 256, 16
+    cfg.block_samples, cfg.int_factor, cfg.sample_bits = block_samples, int_factor, sample_bits
+    cfg.output, cfg.precision, cfg.bf_variant, cfg.reserved = OUTPUTS[output], 0, BF_VARIANTS[bf_variant], 0
+    cfg.sample_rate_hz = sample_rate_hz
+    cfg.phase_centre_l, cfg.phase_centre_m = float(phase_centre[0]), float(phase_centre[1])
+    dp, fp = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float)
+    cfg.station_xyz_m = xyz.ctypes.data_as(dp)
+    cfg.subband_centre_hz = f0.ctypes.data_as(dp)
+    cfg.beam_dlm = dlm.ctypes.data_as(dp)
+    cfg.fir_taps = h.ctypes.data_as(fp)
+    cfg.bandpass = bp.ctypes.data_as(fp) if bp is not None else ctypes.cast(None, fp)
+    _check(lib.lbf_run_block_static(ctypes.byref(cfg), _ptr(d_in), _ptr(d_out), _stream(stream)),
+           "lbf_run_block_static")
