@@ -75,6 +75,10 @@ typedef enum { LBF_FP32 = 0, LBF_FP16_TC = 1 } lbf_precision;
  * register-tiled many-beam kernel otherwise. */
 typedef enum { LBF_BF_AUTO = 0, LBF_BF_FEW = 1, LBF_BF_MANY = 2 } lbf_bf_variant;
 
+/* The plan does not allocate the run_block scratch; the caller passes one to lbf_run_block_ws
+ * (several plans can then share scratch buffers, as a serving loop does). */
+#define LBF_FLAG_EXTERNAL_WORKSPACE 1
+
 typedef struct lbf_config {
   int32_t n_stations;     /* S >= 1 */
   int32_t n_subbands;     /* F >= 1 */
@@ -87,7 +91,7 @@ typedef struct lbf_config {
   int32_t output;         /* lbf_output */
   int32_t precision;      /* lbf_precision */
   int32_t bf_variant;     /* lbf_bf_variant */
-  int32_t reserved;       /* must be 0 */
+  int32_t flags;          /* LBF_FLAG_* bits (0 for lbf_run_block_static) */
   double sample_rate_hz;  /* fs of one subband (195312.5 for LOFAR's 195 kHz subbands) */
   double phase_centre_l;  /* direction cosines (l0, m0) of the phase centre */
   double phase_centre_m;
@@ -111,7 +115,9 @@ typedef struct lbf_dims {
   size_t vol_bytes;           /* bytes of a vol buffer */
   size_t out_bytes;           /* bytes of one run_block output (vol_bytes for voltages) */
   size_t stokes_bytes;        /* bytes of a Stokes buffer [B][nS][F][N][M/Q] (0 for voltages) */
-  size_t workspace_bytes;     /* device scratch the plan holds for lbf_run_block */
+  size_t workspace_bytes;     /* device scratch lbf_run_block needs (held by the plan unless
+                                 LBF_FLAG_EXTERNAL_WORKSPACE) */
+  size_t plan_bytes;          /* device memory the plan itself holds (tables, history, scratch) */
 } lbf_dims;
 
 typedef struct lbf_plan_s *lbf_plan_t;
@@ -163,6 +169,13 @@ lbf_status lbf_beamform_stokes(lbf_plan_t plan, const void *d_ct, float *d_out, 
 /* Step a7: Stokes I/IQUV (as configured) with integration over Q spectra (Sections 4.5, 5.1).
  * d_vol: device `vol` (read); d_out: device `out` layout (written).  Requires a Stokes output. */
 lbf_status lbf_stokes(lbf_plan_t plan, const void *d_vol, float *d_out, void *stream);
+
+/* lbf_run_block with caller-provided scratch: d_ws (device, >= workspace_bytes of lbf_plan_dims,
+ * 256-byte aligned) is used for this call only and may be shared with other plans between calls.
+ * Works for every plan; a plan created with LBF_FLAG_EXTERNAL_WORKSPACE can only run blocks
+ * this way.  Errors as lbf_run_block, LBF_EINVAL for a short or misaligned workspace. */
+lbf_status lbf_run_block_ws(lbf_plan_t plan, const void *d_in, void *d_out, void *d_ws, size_t ws_bytes,
+                            void *stream);
 
 /* Steps a1-a7 for one block, fused: filter bank with the delay/bandpass/corner-turn epilogue into
  * the plan's scratch, then the beam former with the Stokes epilogue (or voltages).  d_in: device

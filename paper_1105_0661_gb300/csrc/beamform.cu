@@ -10,8 +10,9 @@
 //    shared memory, one coalesced pass over the corner-turned input; Stokes integration over Q
 //    consecutive spectra is a warp-shuffle reduction across the lanes that hold them.
 //  * many-beam (FP32-ALU bound): 128 beams x 32 spectra per CTA pass, each thread a 4-beam x
-//    4-spectrum x 2-pol register tile (64 accumulators); the corner-turned input tile is staged in
-//    shared memory and every station step issues 128 FFMAs per 6 shared-memory vector loads.
+//    4-spectrum x 2-pol register tile (32 complex accumulators); the corner-turned input passes
+//    are double-buffered in shared memory by cp.async, and every station step issues 128 FFMAs
+//    per 6 conflict-free shared-memory vector loads.
 #include "lbf_internal.cuh"
 
 namespace lbf {
@@ -108,35 +109,74 @@ bf_few_kernel(Geometry g, const float2 *__restrict__ ct, void *__restrict__ out)
 }
 
 // ------------------------------------------------------------------------------- many beams
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src, int src_bytes) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gmem_src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gmem_src, int src_bytes) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(gmem_src), "r"(src_bytes) : "memory");
+}
+
+// Thread tile: beams 4 bg .. 4 bg + 3 of the CTA's 128, spectra {2 mg, 2 mg + 1, 16 + 2 mg,
+// 17 + 2 mg} of the 32-spectrum pass (so each 16-byte shared load of a warp covers 128 contiguous
+// bytes), both pols: 32 complex accumulators updated with packed FP32x2 FMAs,
+//   acc += (w.re, w.re) * (y.re, y.im) + (-w.im, w.im) * (y.im, y.re).
 template <int OUT>
 __global__ void __launch_bounds__(kManyThreads, 2)
 bf_many_kernel(Geometry g, const float2 *__restrict__ ct, void *__restrict__ out, int nbt) {
   extern __shared__ __align__(16) float2 smem[];
   float2 *wsm = smem;                      // [S][kBT]
-  float2 *ysm = smem + (size_t)g.S * kBT;  // [S][kP][kMC]
+  float2 *ysm = smem + (size_t)g.S * kBT;  // [2 buffers][S][kP][kMC]
   const int tid = threadIdx.x;
   const int fc = blockIdx.x / nbt;
   const int bt = blockIdx.x - fc * nbt;
   const int f = fc / kN, c = fc - f * kN;
   const int bbase = bt * kBT;
+  const float2 *y = ct + (long long)fc * g.S * kP * g.M;
+  const int rows = g.S * kP;
+  const size_t ybuf = (size_t)rows * kMC;
+  const bool even_m = (g.M & 1) == 0;
+
+  // async copy of pass `mc` into buffer `bi` (zero-filled beyond M)
+  auto load_pass = [&](int mc, int bi) {
+    float2 *dst = ysm + bi * ybuf;
+    if (even_m) {
+      for (int i = tid; i < rows * (kMC / 2); i += kManyThreads) {
+        const int row = i / (kMC / 2), col = 2 * (i - row * (kMC / 2));
+        const int m = mc + col;
+        const int valid = m < g.M ? 16 : 0;
+        cp_async16(dst + row * kMC + col, y + (long long)row * g.M + (valid ? m : 0), valid);
+      }
+    } else {
+      for (int i = tid; i < rows * kMC; i += kManyThreads) {
+        const int row = i / kMC, col = i - row * kMC;
+        const int m = mc + col;
+        const int valid = m < g.M ? 8 : 0;
+        cp_async8(dst + row * kMC + col, y + (long long)row * g.M + (valid ? m : 0), valid);
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  load_pass(0, 0);
+
   for (int i = tid; i < g.S * kBT; i += kManyThreads) {
     const int s = i / kBT, bl = i - s * kBT, b = bbase + bl;
     wsm[i] = (b < g.B) ? beam_weight(g, f, c, (long long)b * g.S + s) : make_float2(0.f, 0.f);
   }
   const int bg = tid >> 3;   // beams bbase + 4 bg .. +3
-  const int mg = tid & 7;    // spectra 4 mg .. +3 of the pass
-  const float2 *y = ct + (long long)fc * g.S * kP * g.M;
+  const int mg = tid & 7;    // spectra 2 mg, 2 mg + 1, 16 + 2 mg, 17 + 2 mg of the pass
   const int nS = (OUT == OUT_STOKES_IQUV) ? 4 : 1;
   const int Mq = (OUT == OUT_VOLTAGES) ? 0 : g.M / g.Q;
 
-  for (int mc = 0; mc < g.M; mc += kMC) {
-    __syncthreads();   // weights ready / previous pass done with ysm
-    for (int i = tid; i < g.S * kP * kMC; i += kManyThreads) {
-      const int row = i / kMC, col = i - row * kMC;
-      const int m = mc + col;
-      ysm[i] = (m < g.M) ? y[(long long)row * g.M + m] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
+  int buf = 0;
+  for (int mc = 0; mc < g.M; mc += kMC, buf ^= 1) {
+    if (mc + kMC < g.M) load_pass(mc + kMC, buf ^ 1);
+    else asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    __syncthreads();   // pass mc (and the weights) visible to every thread
+    const float2 *yb = ysm + buf * ybuf;
+
     float2 acc[4][kP][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -153,10 +193,11 @@ bf_many_kernel(Geometry g, const float2 *__restrict__ ct, void *__restrict__ out
                            make_float2(w23.x, w23.y), make_float2(w23.z, w23.w)};
 #pragma unroll
       for (int pol = 0; pol < kP; ++pol) {
-        const float4 *yp = reinterpret_cast<const float4 *>(ysm + (s * kP + pol) * kMC + mg * 4);
-        const float4 y01 = yp[0], y23 = yp[1];
-        const float2 yv[4] = {make_float2(y01.x, y01.y), make_float2(y01.z, y01.w),
-                              make_float2(y23.x, y23.y), make_float2(y23.z, y23.w)};
+        const float2 *row = yb + (s * kP + pol) * kMC;
+        const float4 ya = *reinterpret_cast<const float4 *>(row + 2 * mg);
+        const float4 yc = *reinterpret_cast<const float4 *>(row + 16 + 2 * mg);
+        const float2 yv[4] = {make_float2(ya.x, ya.y), make_float2(ya.z, ya.w),
+                              make_float2(yc.x, yc.y), make_float2(yc.z, yc.w)};
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -174,7 +215,7 @@ bf_many_kernel(Geometry g, const float2 *__restrict__ ct, void *__restrict__ out
         for (int pol = 0; pol < kP; ++pol)
 #pragma unroll
           for (int jm = 0; jm < 4; ++jm) {
-            const int m = mc + mg * 4 + jm;
+            const int m = mc + 16 * (jm >> 1) + 2 * mg + (jm & 1);
             if (m < g.M) vol[((((long long)b * g.F + f) * kN + c) * kP + pol) * g.M + m] = acc[i][pol][jm];
           }
       }
@@ -188,30 +229,33 @@ bf_many_kernel(Geometry g, const float2 *__restrict__ ct, void *__restrict__ out
           float v[4];
 #pragma unroll
           for (int jm = 0; jm < 4; ++jm) v[jm] = stokes_param(st, acc[i][0][jm], acc[i][1][jm]);
+          float *orow = o + ((((long long)b * nS + st) * g.F + f) * kN + c) * Mq;
           if (g.Q == 1) {
 #pragma unroll
             for (int jm = 0; jm < 4; ++jm) {
-              const int m = mc + mg * 4 + jm;
-              if (b < g.B && m < g.M) o[((((long long)b * nS + st) * g.F + f) * kN + c) * Mq + m] = v[jm];
+              const int m = mc + 16 * (jm >> 1) + 2 * mg + (jm & 1);
+              if (b < g.B && m < g.M) orow[m] = v[jm];
             }
-          } else if (g.Q == 2) {
+          } else if (g.Q == 32) {
+            float sum = (v[0] + v[1]) + (v[2] + v[3]);
+            for (int o2 = 1; o2 < 8; o2 <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o2);
+            if (b < g.B && mg == 0 && mc < g.M) orow[mc / 32] = sum;
+          } else {
+            // windows of Q consecutive spectra: pair sums, then across Q/2 lanes of mg
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-              const int m = mc + mg * 4 + 2 * h;
-              if (b < g.B && m < g.M)
-                o[((((long long)b * nS + st) * g.F + f) * kN + c) * Mq + m / 2] = v[2 * h] + v[2 * h + 1];
+              float sum = v[2 * h] + v[2 * h + 1];
+              for (int o2 = 1; o2 < g.Q / 2; o2 <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o2);
+              const int m = mc + 16 * h + 2 * mg;
+              if (b < g.B && m < g.M && (mg & (g.Q / 2 - 1)) == 0) orow[m / g.Q] = sum;
             }
-          } else {
-            float sum = (v[0] + v[1]) + (v[2] + v[3]);
-            for (int o2 = 1; o2 < g.Q / 4; o2 <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o2);
-            const int m = mc + mg * 4;
-            if (b < g.B && m < g.M && (m & (g.Q - 1)) == 0)
-              o[((((long long)b * nS + st) * g.F + f) * kN + c) * Mq + m / g.Q] = sum;
           }
         }
       }
     }
+    __syncthreads();   // everyone is done with buffer `buf` before it is refilled
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 }  // namespace
@@ -244,7 +288,7 @@ cudaError_t launch_beamform(const Geometry &g, int variant, int out_kind, const 
   }
   const int nbt = (g.B + kBT - 1) / kBT;
   const long long ctas = (long long)g.F * kN * nbt;
-  const size_t smem = (size_t)g.S * (kBT + kP * kMC) * sizeof(float2);
+  const size_t smem = (size_t)g.S * (kBT + 2 * kP * kMC) * sizeof(float2);
   cudaError_t e;
   switch (out_kind) {
     case OUT_VOLTAGES:
@@ -267,6 +311,6 @@ cudaError_t launch_beamform(const Geometry &g, int variant, int out_kind, const 
 }
 
 // Largest station count the many-beam kernel accepts (its shared memory holds S x (128 + 64) cf32).
-int many_beam_max_stations() { return (227 * 1024) / ((kBT + kP * kMC) * (int)sizeof(float2)); }
+int many_beam_max_stations() { return (227 * 1024) / ((kBT + 2 * kP * kMC) * (int)sizeof(float2)); }
 
 }  // namespace lbf

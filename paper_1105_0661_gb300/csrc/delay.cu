@@ -50,36 +50,29 @@ delay_ct_kernel(Geometry g, const float2 *__restrict__ chan, float2 *__restrict_
   }
 }
 
-// ct [F][N][S][P][M] cf32 -> [F][N][P][M][kpad] fp16 planes (station slot 2s, 2s+1).  One CTA per
-// (f, c, pol, 64-spectrum tile): stations are gathered through shared memory so that each thread
-// writes one whole 4-station (16-byte) group of a spectrum's row.
+// ct [F][N][S][P][M] cf32 -> FP16 planes [F*N][kpad][Mb][P][32] (rows k = 2s re, 2s+1 im): an
+// elementwise split, both sides spectrum-fastest, so reads and writes are coalesced as they are.
 __global__ void __launch_bounds__(256)
-ct_to_ct16_kernel(Geometry g, const float2 *__restrict__ ct, Ct16Out o, int tiles) {
-  __shared__ float2 tile[64][65];
-  long long idx = blockIdx.x;
-  const int t = (int)(idx % tiles);
-  idx /= tiles;
-  const int pol = (int)(idx % kP);
-  const long long fc = idx / kP;
-  const int m0 = t * 64;
+ct_to_ct16_kernel(Geometry g, const float2 *__restrict__ ct, Ct16Out o, long long n) {
   __half *hi = reinterpret_cast<__half *>(o.hi);
   __half *lo = reinterpret_cast<__half *>(o.lo);
-  for (int s0 = 0; s0 < g.S; s0 += 64) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
-      const int sl = i >> 6, ml = i & 63, s = s0 + sl, m = m0 + ml;
-      tile[ml][sl] = (s < g.S && m < g.M) ? ct[((fc * g.S + s) * kP + pol) * g.M + m] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
-      const int ml = i >> 6, sl = i & 63, s = s0 + sl, m = m0 + ml;
-      if (s < g.S && m < g.M) {
-        const float2 v = tile[ml][sl];
-        const long long d = (((fc * kP + pol) * g.M) + m) * o.kpad + 2 * s;
-        const __half2 h = __floats2half2_rn(v.x, v.y);
-        *reinterpret_cast<__half2 *>(hi + d) = h;
-        if (lo) *reinterpret_cast<__half2 *>(lo + d) = __floats2half2_rn(v.x - __low2float(h), v.y - __high2float(h));
-      }
+  const int mb = (g.M + 31) >> 5;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(i % g.M);
+    const long long r = i / g.M;                             // (fc * S + s) * P + pol
+    const int pol = (int)(r % kP);
+    const long long fcs = r / kP;
+    const long long fc = fcs / g.S;
+    const int s = (int)(fcs - fc * g.S);
+    const float2 v = ct[i];
+    const long long re = (((fc * o.kpad + 2 * s) * mb + (m >> 5)) * 64) + pol * 32 + (m & 31);
+    const long long im = re + (long long)mb * 64;
+    const __half hr = __float2half_rn(v.x), hm = __float2half_rn(v.y);
+    hi[re] = hr;
+    hi[im] = hm;
+    if (lo) {
+      lo[re] = __float2half_rn(v.x - __half2float(hr));
+      lo[im] = __float2half_rn(v.y - __half2float(hm));
     }
   }
 }
@@ -87,10 +80,10 @@ ct_to_ct16_kernel(Geometry g, const float2 *__restrict__ ct, Ct16Out o, int tile
 }  // namespace
 
 cudaError_t launch_ct_to_ct16(const Geometry &g, const float2 *ct, const Ct16Out &o, cudaStream_t st) {
-  const int tiles = (g.M + 63) / 64;
-  const long long ctas = (long long)g.F * kN * kP * tiles;
-  if (ctas == 0) return cudaSuccess;
-  ct_to_ct16_kernel<<<(unsigned)ctas, 256, 0, st>>>(g, ct, o, tiles);
+  const long long n = (long long)g.F * kN * g.S * kP * g.M;
+  if (n == 0) return cudaSuccess;
+  const long long want = (n + 255) / 256;
+  ct_to_ct16_kernel<<<(unsigned)(want < 152LL * 64 ? want : 152LL * 64), 256, 0, st>>>(g, ct, o, n);
   return cudaGetLastError();
 }
 

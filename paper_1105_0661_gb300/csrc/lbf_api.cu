@@ -37,6 +37,8 @@ struct lbf_plan_s {
   void *ct16[2] = {nullptr, nullptr};
   alignas(64) CUtensorMap tmap[2];
   size_t ct16_bytes = 0;
+  bool external_ws = false;     // scratch passed per call (lbf_run_block_ws)
+  size_t ws_need = 0;           // scratch bytes one block needs
   int *d_err = nullptr;   // device error word set by bounded waits that gave up
   void *hist[2] = {nullptr, nullptr};
   int cur = 0;
@@ -96,7 +98,7 @@ void release(lbf_plan_s *p) {
   cudaFree(p->tau); cudaFree(p->resid); cudaFree(p->f0); cudaFree(p->dtau);
   cudaFree(p->hist[0]); cudaFree(p->hist[1]); cudaFree(p->ws);
   cudaFree(p->phase0); cudaFree(p->step);
-  cudaFree(p->ct16[0]); cudaFree(p->ct16[1]); cudaFree(p->d_err);
+  cudaFree(p->ct16[0]); cudaFree(p->d_err);
 }
 
 lbf_status validate(const lbf_config *c) {
@@ -108,7 +110,7 @@ lbf_status validate(const lbf_config *c) {
   if (c->output != LBF_VOLTAGES && c->output != LBF_STOKES_I && c->output != LBF_STOKES_IQUV) return LBF_EINVAL;
   if (c->precision != LBF_FP32 && c->precision != LBF_FP16_TC) return LBF_EINVAL;
   if (c->bf_variant < LBF_BF_AUTO || c->bf_variant > LBF_BF_MANY) return LBF_EINVAL;
-  if (c->reserved != 0) return LBF_EINVAL;
+  if ((c->flags & ~LBF_FLAG_EXTERNAL_WORKSPACE) != 0) return LBF_EINVAL;
   if (!is_pow2_upto32(c->int_factor)) return LBF_EINVAL;
   const int M = c->block_samples / c->n_channels;
   if (c->output != LBF_VOLTAGES && M % c->int_factor != 0) return LBF_EINVAL;
@@ -131,9 +133,10 @@ lbf_status validate(const lbf_config *c) {
 
 bool valid_plan(lbf_plan_t p) { return p && p->magic == kMagic; }
 
-// TMA descriptor of one FP16 plane [F*N*P rows][M][kpad]: boxes of 64 halves (one 128-byte
-// swizzle row) x the beam former's spectra per tile x 2 pols, 128-byte swizzle.
-cudaError_t encode_ct16_map(CUtensorMap *map, void *base, int kpad, int M, long long rows) {
+// TMA descriptor of one FP16 plane [F*N][kpad][Mb][P][32] (Mb = ceil(M/32) blocks of 32 spectra,
+// the two pols of a block side by side): boxes of 64 halves (one 128-byte swizzle row: 2 pols x 32
+// spectra) x 64 K rows, 128-byte swizzle.
+cudaError_t encode_ct16_map(CUtensorMap *map, void *base, int kpad, int M, long long fc_rows) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void *fn = nullptr;
@@ -143,11 +146,12 @@ cudaError_t encode_ct16_map(CUtensorMap *map, void *base, int kpad, int M, long 
       return cudaErrorNotSupported;
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
-  const cuuint64_t dims[3] = {(cuuint64_t)kpad, (cuuint64_t)M, (cuuint64_t)rows};
-  const cuuint64_t strides[2] = {(cuuint64_t)kpad * 2, (cuuint64_t)M * kpad * 2};
-  const cuuint32_t box[3] = {64, (cuuint32_t)lbf::tc_spectra_per_tile(), 2};
-  const cuuint32_t elem[3] = {1, 1, 1};
-  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, base, dims, strides, box, elem,
+  const cuuint64_t mb = (cuuint64_t)(M + 31) / 32;
+  const cuuint64_t dims[4] = {64, mb, (cuuint64_t)kpad, (cuuint64_t)fc_rows};
+  const cuuint64_t strides[3] = {128, mb * 128, (cuuint64_t)kpad * mb * 128};
+  const cuuint32_t box[4] = {64, 1, 64, 1};
+  const cuuint32_t elem[4] = {1, 1, 1, 1};
+  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, base, dims, strides, box, elem,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
@@ -156,9 +160,18 @@ cudaError_t encode_ct16_map(CUtensorMap *map, void *base, int kpad, int M, long 
 lbf::Ct16Out ct16_out(lbf_plan_t p) {
   lbf::Ct16Out o;
   o.hi = p->ct16[0];
-  o.lo = p->planes > 1 ? p->ct16[1] : nullptr;
+  o.lo = p->planes > 1 ? static_cast<unsigned char *>(p->ct16[0]) + p->ct16_bytes : nullptr;
   o.kpad = p->kpad;
   return o;
+}
+
+// Descriptors of the FP16 planes of a tensor-core scratch at `ws` (hi, then lo).
+cudaError_t encode_planes(lbf_plan_t p, void *ws, CUtensorMap *maps) {
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < p->planes && e == cudaSuccess; ++i)
+    e = encode_ct16_map(&maps[i], static_cast<unsigned char *>(ws) + i * p->ct16_bytes, p->kpad, p->M,
+                        (long long)p->F * p->N);
+  return e;
 }
 
 // Device pointer check (host-only query): rejects host pointers before any launch.
@@ -210,28 +223,37 @@ void trace_free(lbf_plan_t p) {
 
 int bf_kernel_id(lbf_plan_t p) { return p->variant == 1 ? K_BF_FEW : K_BF_MANY; }
 
-// The fused path on device buffers (a1-a7).
-cudaError_t run_block_device(lbf_plan_t p, const void *d_in, void *d_out, cudaStream_t st) {
+// The fused path on device buffers (a1-a7).  `ws` is the scratch of this call: the FP32
+// corner-turned block, or the FP16 planes of a tensor-core plan (with `maps` their descriptors).
+cudaError_t run_block_device(lbf_plan_t p, const void *d_in, void *d_out, void *ws, const CUtensorMap *maps,
+                             cudaStream_t st) {
   const lbf::Geometry g = p->geometry();
   const void *h = p->hist[p->cur];
   void *nh = p->hist[p->cur ^ 1];
   if (p->tc) {
-    const lbf::Ct16Out o = ct16_out(p);
+    lbf::Ct16Out o;
+    o.hi = ws;
+    o.lo = p->planes > 1 ? static_cast<unsigned char *>(ws) + p->ct16_bytes : nullptr;
+    o.kpad = p->kpad;
     cudaError_t e = traced(p, K_PPF_CT16, st, [&] { return lbf::launch_ppf(g, p->bits, d_in, h, nullptr, nullptr, st, &o); });
     if (e == cudaSuccess) e = traced(p, K_HIST, st, [&] { return lbf::launch_hist_update(g, p->bits, d_in, h, nh, st); });
     if (e != cudaSuccess) return e;
     p->cur ^= 1;
     return traced(p, K_BF_TC, st, [&] {
-      return lbf::launch_bf_tc(g, p->out_kind, &p->tmap[0], p->planes > 1 ? &p->tmap[1] : nullptr, p->planes,
+      return lbf::launch_bf_tc(g, p->out_kind, &maps[0], p->planes > 1 ? &maps[1] : nullptr, p->planes,
                                (float *)d_out, p->d_err, st); });
   }
-  cudaError_t e = traced(p, K_PPF_CT, st, [&] { return lbf::launch_ppf(g, p->bits, d_in, h, nullptr, p->ws, st); });
+  float2 *ct = static_cast<float2 *>(ws);
+  cudaError_t e = traced(p, K_PPF_CT, st, [&] { return lbf::launch_ppf(g, p->bits, d_in, h, nullptr, ct, st); });
   if (e == cudaSuccess) e = traced(p, K_HIST, st, [&] { return lbf::launch_hist_update(g, p->bits, d_in, h, nh, st); });
   if (e != cudaSuccess) return e;
   p->cur ^= 1;
   return traced(p, bf_kernel_id(p), st,
-                [&] { return lbf::launch_beamform(g, p->variant, p->out_kind, p->ws, d_out, st); });
+                [&] { return lbf::launch_beamform(g, p->variant, p->out_kind, ct, d_out, st); });
 }
+
+// The plan's own scratch (tensor-core planes are contiguous: hi then lo).
+void *own_ws(lbf_plan_t p) { return p->tc ? p->ct16[0] : static_cast<void *>(p->ws); }
 
 }  // namespace
 
@@ -323,22 +345,26 @@ lbf_status lbf_plan(const lbf_config *cfg, lbf_plan_t *out) {
     if (e == cudaSuccess) e = cudaMemset(p->hist[i], 0, p->hist_bytes ? p->hist_bytes : 16);
   }
   p->tc = cfg->precision == LBF_FP16_TC;
+  p->external_ws = (cfg->flags & LBF_FLAG_EXTERNAL_WORKSPACE) != 0;
   if (e == cudaSuccess) e = cudaMalloc((void **)&p->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
   if (p->tc) {
-    // FP16 planes [F][N][P][M][kpad]; the station pad slots stay zero for the plan's lifetime
+    // FP16 planes [F*N][kpad][Mb][P][32], hi then lo in one buffer; pad rows k >= 2S and pad
+    // spectra m >= M stay zero
     p->kpad = lbf::tc_kpad(p->S);
     p->planes = p->bits == 16 ? 2 : 1;
-    p->ct16_bytes = (size_t)p->F * p->N * lbf::kP * p->M * p->kpad * 2;
-    for (int i = 0; i < p->planes && e == cudaSuccess; ++i) {
-      e = cudaMalloc(&p->ct16[i], p->ct16_bytes ? p->ct16_bytes : 16);
-      if (e == cudaSuccess) e = cudaMemset(p->ct16[i], 0, p->ct16_bytes ? p->ct16_bytes : 16);
-      if (e == cudaSuccess && p->M > 0)
-        e = encode_ct16_map(&p->tmap[i], p->ct16[i], p->kpad, p->M, (long long)p->F * p->N * lbf::kP);
+    p->ct16_bytes = (size_t)p->F * p->N * p->kpad * ((p->M + 31) / 32) * 64 * 2;
+    p->ws_need = p->planes * p->ct16_bytes;
+    if (!p->external_ws && e == cudaSuccess) {
+      e = cudaMalloc(&p->ct16[0], p->ws_need ? p->ws_need : 16);
+      if (e == cudaSuccess) e = cudaMemset(p->ct16[0], 0, p->ws_need ? p->ws_need : 16);
+      if (e == cudaSuccess && p->M > 0) e = encode_planes(p, p->ct16[0], p->tmap);
     }
+  } else {
+    p->ws_need = (size_t)p->F * p->N * p->S * lbf::kP * p->M * sizeof(float2);
   }
-  // FP32 corner-turned scratch: run_block of FP32 plans, and the split calls of TC plans
-  p->ws_bytes = p->tc ? 0 : (size_t)p->F * p->N * p->S * lbf::kP * p->M * sizeof(float2);
+  // FP32 corner-turned scratch of FP32 plans (unless the caller provides it per call)
+  p->ws_bytes = (p->tc || p->external_ws) ? 0 : p->ws_need;
   if (e == cudaSuccess) e = cudaMalloc((void **)&p->ws, p->ws_bytes ? p->ws_bytes : 16);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -376,7 +402,10 @@ lbf_status lbf_plan_dims(lbf_plan_t p, lbf_dims *d) {
   d->vol_bytes = (size_t)p->B * p->F * lbf::kP * p->T * sizeof(float2);
   d->stokes_bytes = p->nS ? (size_t)p->B * p->nS * p->F * p->N * (p->M / p->Q) * sizeof(float) : 0;
   d->out_bytes = p->nS ? d->stokes_bytes : d->vol_bytes;
-  d->workspace_bytes = p->ws_bytes + p->planes * p->ct16_bytes;
+  d->workspace_bytes = p->ws_need;
+  d->plan_bytes = 2 * p->hist_bytes + (p->external_ws ? 0 : p->ws_need) +
+                  sizeof(float) * ((size_t)p->F * p->B * p->S + (size_t)p->B * p->S + (size_t)p->L * p->N + p->N) +
+                  sizeof(double) * ((size_t)p->B * p->S + 2 * (size_t)p->S + p->F) + sizeof(float2) * p->N;
   return LBF_OK;
 }
 
@@ -446,6 +475,7 @@ lbf_status lbf_beamform_stokes(lbf_plan_t p, const void *d_ct, float *d_out, voi
   cudaStream_t st = (cudaStream_t)stream;
   const lbf::Geometry g = p->geometry();
   if (p->tc) {
+    if (p->external_ws) return LBF_EUNSUPPORTED;
     const lbf::Ct16Out o = ct16_out(p);
     cudaError_t e = traced(p, K_CT16, st, [&] { return lbf::launch_ct_to_ct16(g, (const float2 *)d_ct, o, st); });
     if (e != cudaSuccess) return cuda_status(e);
@@ -472,8 +502,30 @@ lbf_status lbf_run_block(lbf_plan_t p, const void *d_in, void *d_out, void *stre
   lbf_status s = check_call(p);
   if (s != LBF_OK) return s;
   if (p->M == 0) return LBF_OK;
+  if (p->external_ws) return LBF_EINVAL;
   if (!device_ptr(d_in, p->word) || !device_ptr(d_out, p->nS ? 4 : 8)) return LBF_EINVAL;
-  return cuda_status(run_block_device(p, d_in, d_out, (cudaStream_t)stream));
+  return cuda_status(run_block_device(p, d_in, d_out, own_ws(p), p->tmap, (cudaStream_t)stream));
+}
+
+lbf_status lbf_run_block_ws(lbf_plan_t p, const void *d_in, void *d_out, void *d_ws, size_t ws_bytes,
+                            void *stream) {
+  lbf_status s = check_call(p);
+  if (s != LBF_OK) return s;
+  if (p->M == 0) return LBF_OK;
+  if (!device_ptr(d_in, p->word) || !device_ptr(d_out, p->nS ? 4 : 8)) return LBF_EINVAL;
+  if (ws_bytes < p->ws_need || !device_ptr(d_ws, 256)) return LBF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  CUtensorMap maps[2];
+  if (p->tc) {
+    cudaError_t e = encode_planes(p, d_ws, maps);
+    // pad rows k in [2S, kpad) of each (subband, channel) must read as zero
+    const size_t row = (size_t)((p->M + 31) / 32) * 128;   // bytes of one K row
+    for (int i = 0; i < p->planes && e == cudaSuccess && p->kpad > 2 * p->S; ++i)
+      e = cudaMemset2DAsync(static_cast<unsigned char *>(d_ws) + i * p->ct16_bytes + 2 * p->S * row,
+                            p->kpad * row, 0, (p->kpad - 2 * p->S) * row, (size_t)p->F * p->N, st);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return cuda_status(run_block_device(p, d_in, d_out, d_ws, maps, st));
 }
 
 lbf_status lbf_run_block_host(lbf_plan_t p, const void *h_in, void *h_out, void *d_in, void *d_out,
@@ -481,13 +533,13 @@ lbf_status lbf_run_block_host(lbf_plan_t p, const void *h_in, void *h_out, void 
   lbf_status s = check_call(p);
   if (s != LBF_OK) return s;
   if (p->M == 0) return LBF_OK;
-  if (!h_in || !h_out) return LBF_EINVAL;
+  if (!h_in || !h_out || p->external_ws) return LBF_EINVAL;
   if (!device_ptr(d_in, p->word) || !device_ptr(d_out, p->nS ? 4 : 8)) return LBF_EINVAL;
   lbf_dims d;
   lbf_plan_dims(p, &d);
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaMemcpyAsync(d_in, h_in, d.in_bytes, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = run_block_device(p, d_in, d_out, st);
+  if (e == cudaSuccess) e = run_block_device(p, d_in, d_out, own_ws(p), p->tmap, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h_out, d_out, d.out_bytes, cudaMemcpyDeviceToHost, st);
   return cuda_status(e);
 }

@@ -29,7 +29,8 @@ struct Geometry {
 
 enum OutKind { OUT_VOLTAGES = 0, OUT_STOKES_I = 1, OUT_STOKES_IQUV = 4 };
 
-// FP16 corner-turned scratch of the tensor-core beam former: [F][N][P][M][kpad] halves per plane.
+// FP16 corner-turned scratch of the tensor-core beam former: [F*N][kpad][ceil(M/32)][P][32]
+// halves per plane (k = 2 station + re|im; blocks of 32 spectra, the two pols side by side).
 struct Ct16Out {
   void *hi, *lo;   // lo may be null (single-product form)
   int kpad;        // 2 S rounded up to a multiple of 16

@@ -1,14 +1,18 @@
 // Poly-phase filter bank of Section 4.2: integer sample shift (Section 3), int->float conversion,
 // 16-tap FIR and 256-point FFT into channels, with an optional fused epilogue that applies the
-// sub-sample delay phase and bandpass (Sections 3, 4.3) and writes the corner-turned layout.
+// sub-sample delay phase and bandpass (Sections 3, 4.3) and writes a corner-turned layout.
 //
-// One CTA filters up to 64 consecutive spectra of one (station, subband) stream, both
-// polarisations.  Thread p owns FIR point p: it slides a 16-frame window of dual-pol samples
-// through registers (one coalesced 8-byte load per frame per thread, each frame read once per CTA)
-// and produces v_m[p] for 16 spectra into shared memory.  The 32 FFTs of a tile (16 spectra x 2
-// pols) then run as 16x16 decompositions, 16 threads per transform: a 16-point DFT in registers,
-// a twiddle from a shared table, a swizzled in-place shared-memory transpose, and a second
-// 16-point DFT.
+// One CTA filters up to 128 consecutive spectra of one (station, subband) stream in tiles of 16
+// spectra, with 512 threads: thread (pol, p) owns polarisation pol of FIR point p.
+//  * The tile's input samples arrive through a two-stage cp.async ring in shared memory (whole
+//    dual-pol samples, one 8-byte copy each, issued one tile ahead), so global-load latency
+//    overlaps the filtering and the FFTs of the tile before.
+//  * Each thread converts its polarisation exactly to float with the 2^23 magic-number method
+//    (integer ops + one packed add instead of the conversion pipe) and slides a 16-frame window
+//    of complex values through registers, producing v_m[p] for 16 spectra into shared memory.
+// The 32 FFTs of a tile (16 spectra x 2 pols) then run as 16x16 decompositions, 16 threads per
+// transform: a 16-point DFT in registers (packed FP32x2 butterflies), a twiddle from a shared
+// table, a swizzled in-place shared-memory transpose, and a second 16-point DFT.
 #include <cuda_fp16.h>
 
 #include "lbf_internal.cuh"
@@ -16,37 +20,47 @@
 namespace lbf {
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kTile = 16;        // spectra per shared-memory tile
-constexpr int kTilesPerCta = 4;  // spectra per CTA = 64
-constexpr int kSpectraPerCta = kTile * kTilesPerCta;
+constexpr int kThreads = 512;
+constexpr int kTile = 16;                  // spectra per tile: 32 transforms = one FFT round
+constexpr int kTilesPerCta = 8;
+constexpr int kSpectraPerCta = kTile * kTilesPerCta;   // 128
+constexpr int kStages = 2;                 // input ring depth (tiles)
+constexpr float kMagic16 = 8421376.0f;     // 2^23 + 2^15
+constexpr float kMagic8 = 8388736.0f;      // 2^23 + 2^7
 
 template <int BITS> struct SampleIO;
 template <> struct SampleIO<16> {   // X.re, X.im, Y.re, Y.im as four little-endian int16
   using word = uint2;
-  __device__ static float4 cvt(uint2 u) {
-    return make_float4((float)(int16_t)(u.x & 0xffffu), (float)(int16_t)(u.x >> 16),
-                       (float)(int16_t)(u.y & 0xffffu), (float)(int16_t)(u.y >> 16));
+  // One polarisation (re, im as two int16 in a 32-bit word) to float: the bits
+  // 0x4B00 | (v + 2^15) are the float 2^23 + v + 2^15, so one packed subtract is exact.
+  __device__ static float2 cvt_pol(const word &w, int pol) {
+    const uint32_t a = (pol ? w.y : w.x) ^ 0x80008000u;
+    return __fadd2_rn(make_float2(__uint_as_float(__byte_perm(a, 0x4B00u, 0x5410u)),
+                                  __uint_as_float(__byte_perm(a, 0x4B00u, 0x5432u))),
+                      make_float2(-kMagic16, -kMagic16));
   }
 };
 template <> struct SampleIO<8> {    // X.re, X.im, Y.re, Y.im as four int8
   using word = uint32_t;
-  __device__ static float4 cvt(uint32_t u) {
-    return make_float4((float)(int8_t)(u & 0xffu), (float)(int8_t)((u >> 8) & 0xffu),
-                       (float)(int8_t)((u >> 16) & 0xffu), (float)(int8_t)(u >> 24));
+  // One polarisation (two int8) to float: 0x4B0000 | (v + 2^7) is the float 2^23 + v + 2^7.
+  __device__ static float2 cvt_pol(const word &w, int pol) {
+    const uint32_t a = (w ^ 0x80808080u) >> (16 * pol);
+    return __fadd2_rn(make_float2(__uint_as_float(__byte_perm(a, 0x4B00u, 0x5440u)),
+                                  __uint_as_float(__byte_perm(a, 0x4B00u, 0x5441u))),
+                      make_float2(-kMagic8, -kMagic8));
   }
 };
 
-__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
 
-// In-place 4-point DFT, y_k = sum_n x_n exp(-2 pi i n k / 4).
+// In-place 4-point DFT, y_k = sum_n x_n exp(-2 pi i n k / 4), packed FP32x2 adds.
 __device__ __forceinline__ void dft4(float2 &x0, float2 &x1, float2 &x2, float2 &x3) {
-  const float2 a = f2add(x0, x2), b = f2sub(x0, x2), c = f2add(x1, x3), d = f2sub(x1, x3);
-  x0 = f2add(a, c);
-  x2 = f2sub(a, c);
-  x1 = make_float2(b.x + d.y, b.y - d.x);   // b - i d
-  x3 = make_float2(b.x - d.y, b.y + d.x);   // b + i d
+  const float2 a = __fadd2_rn(x0, x2), b = __fadd2_rn(x0, f2neg(x2));
+  const float2 c = __fadd2_rn(x1, x3), d = __fadd2_rn(x1, f2neg(x3));
+  x0 = __fadd2_rn(a, c);
+  x2 = __fadd2_rn(a, f2neg(c));
+  x1 = __fadd2_rn(b, make_float2(d.y, -d.x));   // b - i d
+  x3 = __fadd2_rn(b, make_float2(-d.y, d.x));   // b + i d
 }
 
 // exp(-2 pi i j / 16) for the j = n2 * k1 products that occur in a 4x4 split.
@@ -81,15 +95,17 @@ __device__ __forceinline__ void dft16(float2 (&a)[16]) {
   for (int r = 0; r < 16; ++r) a[r] = t[r];
 }
 
+template <int BITS>
 struct PpfSmem {
-  float2 v[kP][kTile][kN];   // FIR outputs, then FFT scratch, then corner-turn staging
-  float2 tw[kN];             // exp(-2 pi i n / 256)
-  float2 gain[kN];           // bandpass * delay phasor per channel (fused epilogue)
+  float2 v[kP][kTile][kN];                                  // 64 KB: FIR out -> FFT -> staging
+  typename SampleIO<BITS>::word in[kStages][kTile][kN];     // input ring (64 KB int16, 32 KB int8)
+  float2 tw[kN];                                            // exp(-2 pi i n / 256)
+  float2 gain[kN];                                          // bandpass * delay phasor per channel
 };
 
-// Output modes: the channelised layout, the FP32 corner-turned layout, or the FP16 corner-turned
-// layout of the tensor-core beam former ([F][N][P][M][Kpad] with station s at k = 2s (re), 2s+1
-// (im); a hi plane fp16(Y) and optionally a lo plane fp16(Y - hi)).
+// Output modes: the channelised layout, the FP32 corner-turned layout, or the FP16 layout of the
+// tensor-core beam former ([F*N][Kpad][M/32][P][32] with station s in rows k = 2s (re), 2s+1 (im);
+// a hi plane fp16(Y) and optionally a lo plane fp16(Y - hi)).
 enum PpfMode { MODE_CHAN = 0, MODE_CT32 = 1, MODE_CT16 = 2 };
 
 struct PpfOut {
@@ -98,21 +114,32 @@ struct PpfOut {
   int kpad;
 };
 
+__device__ __forceinline__ void cp_async(void *smem_dst, const void *gmem_src, int bytes) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+  if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gmem_src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 template <int BITS, int MODE>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 1)
 ppf_kernel(Geometry g, const typename SampleIO<BITS>::word *__restrict__ in,
            const typename SampleIO<BITS>::word *__restrict__ hist, PpfOut po, int chunks) {
   using word = typename SampleIO<BITS>::word;
   constexpr bool CT = MODE != MODE_CHAN;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  PpfSmem &sm = *reinterpret_cast<PpfSmem *>(smem_raw);
+  PpfSmem<BITS> &sm = *reinterpret_cast<PpfSmem<BITS> *>(smem_raw);
   float2 *__restrict__ out = po.f32;
 
   const int tid = threadIdx.x;
   int s, f, chunk;
-  if (MODE == MODE_CT16) {   // stations fastest: the scattered 4-byte station slots of one
-    s = (int)(blockIdx.x % g.S);                 // (channel, pol, spectrum) row are written by
-    const long long rest = blockIdx.x / g.S;     // neighbouring CTAs and merge in L2
+  if (MODE == MODE_CT16) {   // stations fastest: neighbouring CTAs fill neighbouring K rows of
+    s = (int)(blockIdx.x % g.S);                 // the same (channel) planes
+    const long long rest = blockIdx.x / g.S;
     chunk = (int)(rest % chunks);
     f = (int)(rest / chunks);
   } else {
@@ -124,9 +151,10 @@ ppf_kernel(Geometry g, const typename SampleIO<BITS>::word *__restrict__ in,
   const long long sf = (long long)s * g.F + f;
   const int m0 = chunk * kSpectraPerCta;
   const int m_end = min(g.M, m0 + kSpectraPerCta);
+  const int ntiles = (m_end - m0 + kTile - 1) / kTile;
 
-  sm.tw[tid] = g.twiddle[tid];
-  if (CT) {
+  if (tid < kN) sm.tw[tid] = g.twiddle[tid];
+  if (CT && tid < kN) {
     // Y = X * bp[c] * exp(+2 pi i (f0 tau_s + df_c (tau_s - n_s Ts))), phase in FP64 cycles
     const int c = tid;
     const double df = (double)(c - kN / 2) * (g.fs / kN);
@@ -137,108 +165,136 @@ ppf_kernel(Geometry g, const typename SampleIO<BITS>::word *__restrict__ in,
   }
 
   // x'[j] = x[j - d_s]; block-relative x' index j lives at extended index H - d_s + j of
-  // [history (H samples) | block (T samples)].
-  const int p = tid;
+  // [history (H samples) | block (T samples)].  Frames r >= -15, r < M.
+  const int pol = tid >> 8;        // this thread's polarisation
+  const int p = tid & (kN - 1);    // and FIR point
   const long long base = (long long)g.H - g.dshift[s] + p;
   const word *hs = hist + sf * g.H;
   const word *bs = in + sf * g.T;
-  auto load_frame = [&](int r) -> float4 {   // sample x'[r N + p], frame r >= -15, r < M
+  auto src_of = [&](int r) -> const word * {
     const long long e = base + (long long)r * kN;
-    const word w = (e < g.H) ? hs[e] : bs[e - g.H];
-    return SampleIO<BITS>::cvt(w);
+    return (e < g.H) ? hs + e : bs + (e - g.H);
   };
+  // async copies of tile t's frames: sample p of frame q is copied by the thread of pol q & 1
+  auto issue_tile = [&](int t) {
+    if (t < ntiles) {
+      const int mt = m0 + t * kTile;
+#pragma unroll
+      for (int q = pol; q < kTile; q += 2)
+        if (mt + q < m_end) cp_async(&sm.in[t % kStages][q][p], src_of(mt + q), (int)sizeof(word));
+    }
+    cp_async_commit();
+  };
+  issue_tile(0);
 
   float h[kL];
 #pragma unroll
   for (int t = 0; t < kL; ++t) h[t] = g.taps[t * kN + p];
 
-  float4 win[kL];   // frame r is kept in slot r & 15
+  float2 win[kL];   // frame r of this pol is kept in slot r & 15 (m0 is a multiple of 16)
 #pragma unroll
-  for (int i = 0; i < kL - 1; ++i) win[i + 1] = load_frame(m0 - (kL - 1) + i);
+  for (int i = 0; i < kL - 1; ++i) win[i + 1] = SampleIO<BITS>::cvt_pol(*src_of(m0 - (kL - 1) + i), pol);
 
-  const int j = tid & 15;     // lane within a 16-thread transform group
-  const int grp = tid >> 4;   // transform group: spectrum q of the tile
+  const int j = tid & 15;          // lane within a 16-thread transform group
+  const int grp = tid >> 4;        // transform group 0..31
+  const int gpol = grp >> 4;       // its polarisation
+  const int gq = grp & 15;         // its spectrum within the tile
 
-  for (int mt = m0; mt < m_end; mt += kTile) {
-    // ---- FIR: v_m[p] = sum_t h[tN + p] x'[(m - 15 + t) N + p], for 16 spectra
+  for (int t = 0; t < ntiles; ++t) {
+    const int mt = m0 + t * kTile;
+    issue_tile(t + 1);
+    cp_async_wait<1>();            // this thread's copies of tile t have landed
+    __syncthreads();               // ... and everyone's
+    // ---- FIR: v_m[p] = sum_t h[tN + p] x'[(m - 15 + t) N + p], 16 spectra, this pol
 #pragma unroll
     for (int q = 0; q < kTile; ++q) {
       const int m = mt + q;
-      win[q] = (m < m_end) ? load_frame(m) : make_float4(0.f, 0.f, 0.f, 0.f);
-      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      win[q] = (m < m_end) ? SampleIO<BITS>::cvt_pol(sm.in[t % kStages][q][p], pol) : make_float2(0.f, 0.f);
+      float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int t = 0; t < kL; ++t) {
-        const float4 x = win[(q + 1 + t) & 15];
-        acc.x = fmaf(h[t], x.x, acc.x);
-        acc.y = fmaf(h[t], x.y, acc.y);
-        acc.z = fmaf(h[t], x.z, acc.z);
-        acc.w = fmaf(h[t], x.w, acc.w);
+      for (int tap = 0; tap < kL; ++tap) {
+        const float2 x = win[(q + 1 + tap) & 15];
+        acc.x = fmaf(h[tap], x.x, acc.x);
+        acc.y = fmaf(h[tap], x.y, acc.y);
       }
-      sm.v[0][q][p] = make_float2(acc.x, acc.y);
-      sm.v[1][q][p] = make_float2(acc.z, acc.w);
+      sm.v[pol][q][p] = acc;
     }
     __syncthreads();
 
-    // ---- FFT-256 of the 32 transforms (pol = round, spectrum q = group), 16 threads each
-#pragma unroll 1
-    for (int pol = 0; pol < kP; ++pol) {
-      float2 *row = sm.v[pol][grp];
-      float2 a[16];
+    // ---- FFT-256 of the 32 transforms (pol, spectrum) of the tile, 16 threads each
+    float2 *row = sm.v[gpol][gq];
+    float2 a[16];
 #pragma unroll
-      for (int p1 = 0; p1 < 16; ++p1) a[p1] = row[16 * p1 + j];   // thread j = p2
-      __syncwarp();
-      dft16(a);
+    for (int p1 = 0; p1 < 16; ++p1) a[p1] = row[16 * p1 + j];   // thread j = p2
+    __syncwarp();
+    dft16(a);
 #pragma unroll
-      for (int k1 = 0; k1 < 16; ++k1) row[k1 * 16 + (j ^ k1)] = cmul(a[k1], sm.tw[j * k1]);
-      __syncwarp();
+    for (int k1 = 0; k1 < 16; ++k1) row[k1 * 16 + (j ^ k1)] = cmul(a[k1], sm.tw[j * k1]);
+    __syncwarp();
 #pragma unroll
-      for (int p2 = 0; p2 < 16; ++p2) a[p2] = row[j * 16 + (p2 ^ j)];   // thread j = k1
-      dft16(a);   // a[k2] = X[j + 16 k2]
-      const int m = mt + grp;
-      if (MODE == MODE_CT16) {
-        if (m < m_end) {
-          const long long rowbase = (((long long)f * kN) * kP + pol) * g.M + m;
+    for (int p2 = 0; p2 < 16; ++p2) a[p2] = row[j * 16 + (p2 ^ j)];   // thread j = k1
+    dft16(a);   // a[k2] = X[j + 16 k2]
+    const int m = mt + gq;
+    if (MODE == MODE_CT16) {
+      __syncthreads();   // every group has read its row: each pol plane becomes staging [c][q]
+      float2 *stage = &sm.v[gpol][0][0];
 #pragma unroll
-          for (int k2 = 0; k2 < 16; ++k2) {
-            const int c = j + 16 * ((k2 + 8) & 15);
-            const float2 v = cmul(a[k2], sm.gain[c]);
-            const long long idx = (rowbase + (long long)c * kP * g.M) * po.kpad + 2 * s;
-            const __half2 hi = __floats2half2_rn(v.x, v.y);
-            *reinterpret_cast<__half2 *>(po.hi + idx) = hi;
-            if (po.lo)
-              *reinterpret_cast<__half2 *>(po.lo + idx) =
-                  __floats2half2_rn(v.x - __low2float(hi), v.y - __high2float(hi));
-          }
-        }
-      } else if (!CT) {
-        if (m < m_end) {
-          float2 *dst = out + ((((long long)f * g.S + s) * kP + pol) * g.M + m) * kN;
-#pragma unroll
-          for (int k2 = 0; k2 < 16; ++k2) dst[j + 16 * ((k2 + 8) & 15)] = a[k2];   // c = (k + N/2) mod N
-        }
-      } else {
-        __syncthreads();   // every group has read its row: the pol plane becomes staging [c][q]
-        float2 *stage = &sm.v[pol][0][0];
-#pragma unroll
-        for (int k2 = 0; k2 < 16; ++k2) {
-          const int c = j + 16 * ((k2 + 8) & 15);
-          stage[c * 16 + (grp ^ (c & 15))] = cmul(a[k2], sm.gain[c]);
-        }
-        __syncthreads();
-        // ct[f][c][s][pol][m]: runs of 16 consecutive spectra per (c, pol)
-        const int q = tid & 15;
-        if (mt + q < m_end) {
+      for (int k2 = 0; k2 < 16; ++k2) {
+        const int c = j + 16 * ((k2 + 8) & 15);
+        stage[c * kTile + (gq ^ (c & 15))] = cmul(a[k2], sm.gain[c]);
+      }
+      __syncthreads();
+      // [F*N][Kpad][Mb][P][32]: rows k = 2s (re) and 2s+1 (im), runs of 16 spectra (32 B)
+      const int q = tid & 15;
+      const int mb = (g.M + 31) >> 5;
+      const int m = mt + q;
+      if (m < m_end) {
 #pragma unroll 4
-          for (int pass = 0; pass < kN / 16; ++pass) {
-            const int c = pass * 16 + (tid >> 4);
-            out[((((long long)f * kN + c) * g.S + s) * kP + pol) * g.M + mt + q] =
-                stage[c * 16 + (q ^ (c & 15))];
+        for (int pass = 0; pass < kP * kN / 32; ++pass) {
+          const int row2 = pass * 32 + (tid >> 4);     // (pol, c)
+          const int pl = row2 >> 8, c = row2 & (kN - 1);
+          const float2 v = (&sm.v[pl][0][0])[c * kTile + (q ^ (c & 15))];
+          const long long re = ((((long long)f * kN + c) * po.kpad + 2 * s) * mb + (m >> 5)) * 64 + pl * 32 + (m & 31);
+          const long long im = re + (long long)mb * 64;
+          const __half hr = __float2half_rn(v.x), hi_ = __float2half_rn(v.y);
+          po.hi[re] = hr;
+          po.hi[im] = hi_;
+          if (po.lo) {
+            po.lo[re] = __float2half_rn(v.x - __half2float(hr));
+            po.lo[im] = __float2half_rn(v.y - __half2float(hi_));
           }
+        }
+      }
+    } else if (!CT) {
+      if (m < m_end) {
+        float2 *dst = out + ((((long long)f * g.S + s) * kP + gpol) * g.M + m) * kN;
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) dst[j + 16 * ((k2 + 8) & 15)] = a[k2];   // c = (k + N/2) mod N
+      }
+    } else {
+      __syncthreads();   // every group has read its row: each pol plane becomes staging [c][q]
+      float2 *stage = &sm.v[gpol][0][0];
+#pragma unroll
+      for (int k2 = 0; k2 < 16; ++k2) {
+        const int c = j + 16 * ((k2 + 8) & 15);
+        stage[c * kTile + (gq ^ (c & 15))] = cmul(a[k2], sm.gain[c]);
+      }
+      __syncthreads();
+      // ct[f][c][s][pol][m]: runs of 16 consecutive spectra (128 B) per (c, pol)
+      const int q = tid & 15;
+      if (mt + q < m_end) {
+#pragma unroll 4
+        for (int pass = 0; pass < kP * kN / 32; ++pass) {
+          const int row2 = pass * 32 + (tid >> 4);     // (pol, c)
+          const int pl = row2 >> 8, c = row2 & (kN - 1);
+          out[((((long long)f * kN + c) * g.S + s) * kP + pl) * g.M + mt + q] =
+              (&sm.v[pl][0][0])[c * kTile + (q ^ (c & 15))];
         }
       }
     }
     __syncthreads();
   }
+  cp_async_wait<0>();
 }
 
 template <int BITS>
@@ -262,7 +318,7 @@ cudaError_t launch_ppf_t(const Geometry &g, const void *in, const void *hist, Pp
   const int chunks = (g.M + kSpectraPerCta - 1) / kSpectraPerCta;
   const long long ctas = (long long)g.S * g.F * chunks;
   if (ctas == 0) return cudaSuccess;
-  const size_t smem = sizeof(PpfSmem);
+  const size_t smem = sizeof(PpfSmem<BITS>);
   auto kern = ppf_kernel<BITS, MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

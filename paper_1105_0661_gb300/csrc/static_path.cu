@@ -81,7 +81,7 @@ extern "C" lbf_status lbf_run_block_static(const lbf_config *c, const void *d_in
   if (c->block_samples % lbf::kN != 0) return LBF_EINVAL;
   if (c->sample_bits != 16 && c->sample_bits != 8) return LBF_EINVAL;
   if (c->output != LBF_STOKES_I && c->output != LBF_STOKES_IQUV && c->output != LBF_VOLTAGES) return LBF_EINVAL;
-  if (c->precision != LBF_FP32 || c->reserved != 0) return LBF_EUNSUPPORTED;
+  if (c->precision != LBF_FP32 || c->flags != 0) return LBF_EUNSUPPORTED;
   const int q = c->int_factor;
   if (!(q == 1 || q == 2 || q == 4 || q == 8 || q == 16 || q == 32)) return LBF_EINVAL;
   const int S = c->n_stations, F = c->n_subbands, B = c->n_beams, T = c->block_samples, M = T / lbf::kN;

@@ -24,7 +24,7 @@ BF_VARIANTS = {"auto": 0, "few": 1, "many": 2}
 # Every symbol include/lbf.h declares; the test suite checks the library exports all of them.
 EXPORTED = ("lbf_plan", "lbf_plan_destroy", "lbf_plan_dims", "lbf_plan_shifts", "lbf_reset_state",
             "lbf_ppf", "lbf_delay_correct", "lbf_beamform", "lbf_beamform_stokes", "lbf_stokes",
-            "lbf_run_block", "lbf_run_block_host", "lbf_trace_begin", "lbf_trace_end",
+            "lbf_run_block", "lbf_run_block_ws", "lbf_run_block_host", "lbf_trace_begin", "lbf_trace_end",
             "lbf_device_status", "lbf_run_block_static", "lbf_status_string", "lbf_version")
 
 
@@ -39,7 +39,7 @@ class _Config(ctypes.Structure):
         ("n_stations", ctypes.c_int32), ("n_subbands", ctypes.c_int32), ("n_channels", ctypes.c_int32),
         ("n_taps", ctypes.c_int32), ("n_beams", ctypes.c_int32), ("block_samples", ctypes.c_int32),
         ("int_factor", ctypes.c_int32), ("sample_bits", ctypes.c_int32), ("output", ctypes.c_int32),
-        ("precision", ctypes.c_int32), ("bf_variant", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("bf_variant", ctypes.c_int32), ("flags", ctypes.c_int32),
         ("sample_rate_hz", ctypes.c_double), ("phase_centre_l", ctypes.c_double),
         ("phase_centre_m", ctypes.c_double),
         ("station_xyz_m", ctypes.POINTER(ctypes.c_double)),
@@ -62,7 +62,7 @@ class _Dims(ctypes.Structure):
         "n_spectra", "n_stokes", "d_max", "history_samples", "bf_kernel")] + \
         [(n, ctypes.c_size_t) for n in (
             "in_bytes", "chan_bytes", "ct_bytes", "vol_bytes", "out_bytes", "stokes_bytes",
-            "workspace_bytes")]
+            "workspace_bytes", "plan_bytes")]
 
 
 _lib = None
@@ -88,6 +88,7 @@ def load_library() -> ctypes.CDLL:
             "lbf_beamform_stokes": ([vp, vp, vp, vp], ctypes.c_int),
             "lbf_stokes": ([vp, vp, vp, vp], ctypes.c_int),
             "lbf_run_block": ([vp, vp, vp, vp], ctypes.c_int),
+            "lbf_run_block_ws": ([vp, vp, vp, vp, ctypes.c_size_t, vp], ctypes.c_int),
             "lbf_run_block_host": ([vp, vp, vp, vp, vp, vp], ctypes.c_int),
             "lbf_trace_begin": ([vp, ctypes.c_int32], ctypes.c_int),
             "lbf_trace_end": ([vp, ctypes.POINTER(_Trace)], ctypes.c_int),
@@ -153,6 +154,7 @@ class Dims:
     out_bytes: int
     stokes_bytes: int
     workspace_bytes: int
+    plan_bytes: int
 
 
 class Plan:
@@ -160,7 +162,7 @@ class Plan:
 
     def __init__(self, station_xyz, subband_hz, beam_dlm, phase_centre, taps, block_samples,
                  int_factor=1, output="I", sample_bits=16, bandpass=None, n_channels=256, n_taps=16,
-                 sample_rate_hz=195312.5, precision="fp32", bf_variant="auto"):
+                 sample_rate_hz=195312.5, precision="fp32", bf_variant="auto", external_workspace=False):
         lib = load_library()
         self._keep = [np.ascontiguousarray(station_xyz, dtype=np.float64).reshape(-1, 3),
                       np.ascontiguousarray(subband_hz, dtype=np.float64).reshape(-1),
@@ -175,7 +177,7 @@ class Plan:
         cfg.output = OUTPUTS[output]
         cfg.precision = PRECISIONS[precision]
         cfg.bf_variant = BF_VARIANTS[bf_variant]
-        cfg.reserved = 0
+        cfg.flags = 1 if external_workspace else 0
         cfg.sample_rate_hz = sample_rate_hz
         cfg.phase_centre_l, cfg.phase_centre_m = float(phase_centre[0]), float(phase_centre[1])
         dp = ctypes.POINTER(ctypes.c_double)
@@ -254,6 +256,18 @@ class Plan:
         _check(self._lib.lbf_run_block(self._h, _ptr(d_in, d.in_bytes), _ptr(d_out, d.out_bytes),
                                        _stream(stream)), "lbf_run_block")
 
+    def run_block_ws(self, d_in, d_out, d_ws, stream=None):
+        """run_block with a caller-provided scratch buffer (>= dims.workspace_bytes)."""
+        d = self.dims
+        nbytes = d_ws.numel() * d_ws.element_size() if not isinstance(d_ws, int) else d.workspace_bytes
+        _check(self._lib.lbf_run_block_ws(self._h, _ptr(d_in, d.in_bytes), _ptr(d_out, d.out_bytes),
+                                          _ptr(d_ws, d.workspace_bytes), nbytes, _stream(stream)),
+               "lbf_run_block_ws")
+
+    def device_bytes(self) -> int:
+        """Device memory the plan itself holds (tables, history, and its scratch unless external)."""
+        return self.dims.plan_bytes
+
     def run_block_host(self, h_in, h_out, d_in, d_out, stream=None):
         """H2D copy of h_in, the fused path, D2H copy into h_out, all enqueued on `stream`."""
         d = self.dims
@@ -323,7 +337,7 @@ def run_block_static(station_xyz, subband_hz, beam_dlm, phase_centre, taps, bloc
     cfg.n_stations, cfg.n_subbands, cfg.n_beams = xyz.shape[0], f0.shape[0], dlm.shape[0]
     cfg.n_channels, cfg.n_taps = 256, 16
     cfg.block_samples, cfg.int_factor, cfg.sample_bits = block_samples, int_factor, sample_bits
-    cfg.output, cfg.precision, cfg.bf_variant, cfg.reserved = OUTPUTS[output], 0, BF_VARIANTS[bf_variant], 0
+    cfg.output, cfg.precision, cfg.bf_variant, cfg.flags = OUTPUTS[output], 0, BF_VARIANTS[bf_variant], 0
     cfg.sample_rate_hz = sample_rate_hz
     cfg.phase_centre_l, cfg.phase_centre_m = float(phase_centre[0]), float(phase_centre[1])
     dp, fp = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float)
