@@ -78,6 +78,11 @@ typedef enum { LBF_BF_AUTO = 0, LBF_BF_FEW = 1, LBF_BF_MANY = 2 } lbf_bf_variant
 /* The plan does not allocate the run_block scratch; the caller passes one to lbf_run_block_ws
  * (several plans can then share scratch buffers, as a serving loop does). */
 #define LBF_FLAG_EXTERNAL_WORKSPACE 1
+/* The Stokes output gains one beam, index B: the incoherent beam (Section 3) -- the Stokes
+ * parameters of the unweighted station signals summed over stations as powers, i.e. the wide
+ * field of view of the stations -- formed by lbf_run_block, lbf_run_block_ws and
+ * lbf_beamform_stokes (not by lbf_stokes, which has no station data).  Stokes outputs only. */
+#define LBF_FLAG_INCOHERENT_BEAM 2
 
 typedef struct lbf_config {
   int32_t n_stations;     /* S >= 1 */
@@ -114,7 +119,8 @@ typedef struct lbf_dims {
   size_t ct_bytes;            /* bytes of a ct buffer */
   size_t vol_bytes;           /* bytes of a vol buffer */
   size_t out_bytes;           /* bytes of one run_block output (vol_bytes for voltages) */
-  size_t stokes_bytes;        /* bytes of a Stokes buffer [B][nS][F][N][M/Q] (0 for voltages) */
+  size_t stokes_bytes;        /* bytes of a Stokes buffer [B (+1 incoherent)][nS][F][N][M/Q]
+                                 (0 for voltages) */
   size_t workspace_bytes;     /* device scratch lbf_run_block needs (held by the plan unless
                                  LBF_FLAG_EXTERNAL_WORKSPACE) */
   size_t plan_bytes;          /* device memory the plan itself holds (tables, history, scratch) */
@@ -128,9 +134,9 @@ typedef struct lbf_plan_s *lbf_plan_t;
  * stream starts with zero samples) and the run_block scratch.  Synchronous.  The config's host
  * arrays are copied; the caller keeps ownership.  On error *out is set to NULL.
  * With precision LBF_FP16_TC the many-beam beam former runs on the tensor cores (tcgen05, FP16
- * operands, FP32 accumulation): 16-bit samples feed it as two FP16 planes (hi = fp16(Y),
- * lo = fp16(Y - hi), two products), 8-bit samples as one plane; it needs S <= 64 and a Stokes
- * output.
+ * operands, FP32 accumulation): the filtered spectrum Y of either sample width feeds it as two
+ * FP16 planes (hi = fp16(Y), lo = fp16(Y - hi)) and the weights are split the same way, three
+ * products per tile; it needs S <= 64 and a Stokes output.
  * Errors: LBF_EINVAL (bad config), LBF_EUNSUPPORTED (N != 256, L != 16, or an FP16_TC plan with
  * S > 64 or voltage output), LBF_ENOMEM, LBF_ECUDA. */
 lbf_status lbf_plan(const lbf_config *cfg, lbf_plan_t *out);
@@ -183,6 +189,14 @@ lbf_status lbf_run_block_ws(lbf_plan_t plan, const void *d_in, void *d_out, void
  * Equal, within FP32 rounding, to lbf_ppf -> lbf_delay_correct -> lbf_beamform -> lbf_stokes. */
 lbf_status lbf_run_block(lbf_plan_t plan, const void *d_in, void *d_out, void *stream);
 
+/* Superstation beam former (Section 4.2: combine several stations as if they were one): the
+ * delay-compensated signals of the stations of each group summed with unit weight.
+ * group_of_station: HOST [S], values in [0, n_groups); d_ct: device `ct` [F][N][S][P][M];
+ * d_ss: device [F][N][n_groups][P][M] cf32 (the corner-turned layout with groups in place of
+ * stations).  Synchronises `stream` while the group table is uploaded.  Stateless. */
+lbf_status lbf_superstation(lbf_plan_t plan, const int32_t *group_of_station, int32_t n_groups, const void *d_ct,
+                            void *d_ss, void *stream);
+
 /* lbf_run_block with HOST buffers: enqueues on `stream` the copy h_in -> d_in (in_bytes), the
  * fused path d_in -> d_out, and the copy d_out -> h_out (out_bytes), one cudaMemcpyAsync each.
  * h_in/h_out should be page-locked (cudaHostAlloc / pinned) for the copies to be asynchronous;
@@ -232,6 +246,46 @@ lbf_status lbf_device_status(lbf_plan_t plan, int32_t *code);
  * call); calls whose device work overlaps in time race on it.  Other errors as lbf_plan/
  * lbf_run_block: LBF_EINVAL, LBF_EUNSUPPORTED, LBF_ECUDA. */
 lbf_status lbf_run_block_static(const lbf_config *cfg, const void *d_in, void *d_out, void *stream);
+
+/* ---- Batches: several observations processed together (Section 7: independent observations can
+ * run in parallel as long as resources allow).  One block of every plan of
+ * a batch runs as ONE persistent grouped launch per stage -- filter bank (with the delay / bandpass
+ * / corner-turn epilogue), history update, beam former with its Stokes epilogue -- instead of
+ * three launches per plan; CTAs take work items from a shared counter, so uneven observations
+ * load-balance.  Plans of a batch must be FP32 plans with their own scratch (no
+ * LBF_FLAG_EXTERNAL_WORKSPACE), on the current device, each in at most one active batch; their
+ * history advances exactly as with lbf_run_block.  d_in[i] / d_out[i] are plan i's device `in`
+ * and `out` (or `vol`) buffers. */
+typedef struct lbf_batch_s *lbf_batch_t;
+
+typedef struct lbf_batch_tuning {
+  int32_t n_candidates;         /* candidates timed (3 or 6) */
+  int32_t spc[6];               /* spectra per filter-bank work item of each candidate */
+  int32_t mid_variant[6];       /* 1: plans with 9..64 beams switched to the other beam former */
+  double ms[6];                 /* mean time of one batch block per candidate */
+  int32_t best_spc, best_mid_variant;
+  double best_ms;
+} lbf_batch_tuning;
+
+lbf_status lbf_batch_create(const lbf_plan_t *plans, int32_t n, lbf_batch_t *out);
+lbf_status lbf_batch_destroy(lbf_batch_t batch);
+
+/* One block of every plan: grouped launches on `stream`.  Synchronises `stream` first (the
+ * launch tables are staged in pinned host memory). */
+lbf_status lbf_batch_run(lbf_batch_t batch, const void *const *d_in, void *const *d_out, void *stream);
+
+/* Capture the batch block for these buffers as CUDA graphs (one per history parity) and make
+ * lbf_batch_launch replay them: a whole batch block becomes a single graph launch.  Any
+ * lbf_batch_run or lbf_batch_tune call drops the graphs. */
+lbf_status lbf_batch_capture(lbf_batch_t batch, const void *const *d_in, void *const *d_out, void *stream);
+lbf_status lbf_batch_launch(lbf_batch_t batch, void *stream);
+
+/* Autotune the batch's tile shapes on these buffers: spectra per filter-bank work item (64, 128,
+ * 256) and, for plans with 9..64 beams, the few- or many-beam beam former; each candidate is timed
+ * over `reps` blocks with CUDA events, the fastest is kept.  The candidate runs use the plans'
+ * histories, so every plan's stream is restarted (history zeroed) afterwards.  `out` may be NULL. */
+lbf_status lbf_batch_tune(lbf_batch_t batch, const void *const *d_in, void *const *d_out, void *stream,
+                          int32_t reps, lbf_batch_tuning *out);
 
 /* Human-readable name of a status code (static string). */
 const char *lbf_status_string(lbf_status s);

@@ -112,7 +112,8 @@ class Observation:
     """
 
     def __init__(self, station_xyz, subband_hz, beam_dlm, phase_centre, taps, bandpass=None,
-                 n_channels=256, n_taps=16, sample_rate_hz=195312.5, int_factor=1, output="I"):
+                 n_channels=256, n_taps=16, sample_rate_hz=195312.5, int_factor=1, output="I",
+                 incoherent_beam=False):
         self.xyz = np.asarray(station_xyz, dtype=np.float64).reshape(-1, 3)
         self.f0 = np.asarray(subband_hz, dtype=np.float64).reshape(-1)
         self.beam_dlm = np.asarray(beam_dlm, dtype=np.float64).reshape(-1, 2)
@@ -125,6 +126,7 @@ class Observation:
         self.ts = 1.0 / self.fs
         self.Q = int(int_factor)
         self.output = output
+        self.incoherent_beam = bool(incoherent_beam)   # Stokes output gains beam B: incoherent
         self.S, self.F, self.B = self.xyz.shape[0], self.f0.shape[0], self.beam_dlm.shape[0]
         # geometry for the phase centre (sample shift + sub-sample phase) and for each beam
         self.tau = plane_wave_delay(self.xyz, self.l0, self.m0)
@@ -210,6 +212,17 @@ class Observation:
         p = stokes_from_voltages(ct[:, :, :, 0], ct[:, :, :, 1], "IQUV" if self.output == "IQUV" else "I")
         return integrate(p.sum(axis=3), self.Q)
 
+    def superstation(self, ct: np.ndarray, group_of_station) -> np.ndarray:
+        """Superstation beam former (Section 4.2): the delay-compensated signals of the stations of
+        each group summed with unit weight, as if the group were one station.
+        ct [F][N][S][P][M] -> [F][N][G][P][M], G = max(group) + 1."""
+        grp = np.asarray(group_of_station)
+        G = int(grp.max()) + 1
+        out = np.zeros(ct.shape[:2] + (G,) + ct.shape[3:], dtype=np.complex128)
+        for s in range(ct.shape[2]):
+            out[:, :, grp[s]] += ct[:, :, s]
+        return out
+
     # -- a7: Stokes + integration (Sections 4.5, 5.1)
     def stokes(self, vol: np.ndarray) -> np.ndarray:
         p = stokes_from_voltages(vol[:, :, :, 0], vol[:, :, :, 1], self.output)   # [nS, B, F, N, M]
@@ -225,7 +238,10 @@ class Observation:
         parts = [self.stokes(self.beamform(ct[:, c0:c0 + channel_group],
                                            np.arange(c0, min(c0 + channel_group, self.N))))
                  for c0 in range(0, self.N, channel_group)]
-        return np.concatenate(parts, axis=3)
+        out = np.concatenate(parts, axis=3)
+        if self.incoherent_beam:
+            out = np.concatenate([out, self.incoherent(ct)[None]], axis=0)
+        return out
 
     # -- selected (subband, channel) outputs of one block from zero history, computed one by one
     def run_block_sampled(self, block_f: np.ndarray, f: int, channels) -> np.ndarray:
@@ -265,6 +281,11 @@ class Observation:
 
 
 def observation_from_workload(wl, **over) -> Observation:
+    """(`over` may also set incoherent_beam.)"""
+    return _observation_from_workload(wl, **over)
+
+
+def _observation_from_workload(wl, **over) -> Observation:
     """Build an Observation from a synth.Workload-like object (attributes only, no import)."""
     kw = dict(station_xyz=wl.station_xyz, subband_hz=wl.subband_hz, beam_dlm=wl.beam_dlm,
               phase_centre=wl.phase_centre, taps=wl.taps, bandpass=wl.bandpass,

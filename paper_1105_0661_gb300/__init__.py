@@ -3,4 +3,4 @@
 The compute path is the CUDA library built from csrc/ (sm_103a); `lbf` is its Python binding.
 """
 
-from .lbf import LbfError, Plan, load_library  # noqa: F401
+from .lbf import Batch, LbfError, Plan, load_library  # noqa: F401

@@ -1,0 +1,334 @@
+// Batches: several observations (plans) processed together, one block each, by persistent grouped
+// kernels -- one filter-bank launch, one history launch and one beam-former launch for the whole
+// batch -- instead of three launches per observation.  Uneven observations share the GPU through a
+// work counter: CTAs (one or two per SM) take (observation, stream, spectrum chunk) and
+// (observation, subband-channel, beam group) items until all are done, so small observations do
+// not leave the GPU idle and large ones do not serialise the batch.
+//
+// A batch can be captured as CUDA graphs (one per history parity: each block flips every plan's
+// history ping-pong) and replayed with a single graph launch per block, and its tile shapes --
+// spectra per filter-bank item and, for observations with 9..64 beams, the few- or many-beam
+// beam former -- can be tuned by timing the candidates on the batch itself.
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lbf.h"
+#include "lbf_internal.cuh"
+#include "plan.h"
+
+namespace {
+
+constexpr uint32_t kBatchMagic = 0x4c424642u;   // "LBFB"
+constexpr size_t kTwoPerSm = 113 * 1024;        // beam-former shared memory that still fits twice per SM
+
+bool plan_ok(lbf_plan_t p) { return p && p->magic == lbf::kPlanMagic; }
+
+bool dev_ptr(const void *p, size_t align) {
+  if (!p || (reinterpret_cast<uintptr_t>(p) % align) != 0) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+lbf_status status_of(cudaError_t e) {
+  if (e == cudaSuccess) return LBF_OK;
+  return e == cudaErrorMemoryAllocation ? LBF_ENOMEM : LBF_ECUDA;
+}
+
+}  // namespace
+
+struct lbf_batch_s {
+  uint32_t magic = kBatchMagic;
+  int device = 0;
+  std::vector<lbf_plan_t> plans;
+  int spc = 128;                       // spectra per filter-bank item
+  std::vector<int> variant;            // beam-former kernel per plan
+  // group tables: [parity][plan]; parity p describes the plans' history state after p blocks
+  lbf::PpfGroup *h_ppf = nullptr, *d_ppf = nullptr;   // pinned host / device, 2 * n
+  lbf::BfGroup *h_bf = nullptr, *d_bf = nullptr;     // plans of shared-memory class 0, then class 1
+  unsigned long long *d_counter = nullptr;            // [3] work counters
+  long long ppf_items = 0, hist_items = 0;
+  // beam-former classes: 0 fits two CTAs per SM, 1 needs one (large station counts)
+  int bf_n[2] = {0, 0};
+  long long bf_items[2] = {0, 0};
+  size_t bf_smem[2] = {0, 0};
+  int ppf_ctas = 0, sms = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int graph_parity = 0;                // which graph describes the current state
+};
+
+namespace {
+
+void free_graphs(lbf_batch_t b) {
+  for (auto &g : b->graph) {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
+  }
+}
+
+// Fill the group tables of parity `par` (par = 1: every plan's history one block ahead) for the
+// given block buffers.
+void fill_tables(lbf_batch_t b, int par, const void *const *d_in, void *const *d_out) {
+  const int n = (int)b->plans.size();
+  long long pi = 0, hi = 0;
+  for (int i = 0; i < n; ++i) {
+    lbf_plan_t p = b->plans[i];
+    const int cur = p->cur ^ par;
+    lbf::PpfGroup &G = b->h_ppf[par * n + i];
+    G.g = p->geometry();
+    G.in = d_in[i];
+    G.hist = p->hist[cur];
+    G.new_hist = p->hist[cur ^ 1];
+    G.ct = p->ws;
+    G.bits = p->bits;
+    G.spc = b->spc;
+    G.chunks = (p->M + b->spc - 1) / b->spc;
+    G.first_item = pi;
+    G.first_hist = hi;
+    pi += (long long)p->S * p->F * G.chunks;
+    hi += (long long)p->S * p->F * p->H;
+  }
+  b->ppf_items = pi;
+  b->hist_items = hi;
+  // beam former: class 0 (two CTAs per SM fit) first, then class 1
+  int slot = par * n;
+  for (int cls = 0; cls < 2; ++cls) {
+    long long items = 0;
+    size_t smem = 0;
+    int cnt = 0;
+    for (int i = 0; i < n; ++i) {
+      lbf_plan_t p = b->plans[i];
+      const size_t sm = lbf::bf_smem_bytes(b->variant[i], p->S);
+      if ((sm > kTwoPerSm) != (cls == 1)) continue;
+      lbf::BfGroup &Bg = b->h_bf[slot++];
+      Bg.g = p->geometry();
+      Bg.ct = p->ws;
+      Bg.out = d_out[i];
+      Bg.variant = b->variant[i];
+      Bg.out_kind = p->out_kind;
+      const int per = b->variant[i] == 1 ? lbf::few_beams_per_item() : lbf::many_beams_per_item();
+      Bg.per_fc = (p->B + per - 1) / per;
+      Bg.first_item = items;
+      items += (long long)p->F * lbf::kN * Bg.per_fc;
+      smem = sm > smem ? sm : smem;
+      ++cnt;
+    }
+    b->bf_n[cls] = cnt;
+    b->bf_items[cls] = items;
+    b->bf_smem[cls] = smem;
+  }
+}
+
+// Enqueue one batch block with the tables of parity `par` (already filled).
+cudaError_t enqueue(lbf_batch_t b, int par, cudaStream_t st) {
+  const int n = (int)b->plans.size();
+  cudaError_t e = cudaMemcpyAsync(b->d_ppf + par * n, b->h_ppf + par * n, sizeof(lbf::PpfGroup) * n,
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_bf + par * n, b->h_bf + par * n, sizeof(lbf::BfGroup) * n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = lbf::launch_ppf_group(b->d_ppf + par * n, n, b->ppf_items, b->d_counter, b->ppf_ctas, st);
+  if (e == cudaSuccess) e = lbf::launch_hist_group(b->d_ppf + par * n, n, b->hist_items, st);
+  if (e == cudaSuccess && b->bf_n[0])
+    e = lbf::launch_bf_group(b->d_bf + par * n, b->bf_n[0], b->bf_items[0], b->d_counter + 1, 2 * b->sms,
+                             b->bf_smem[0], st);
+  if (e == cudaSuccess && b->bf_n[1])
+    e = lbf::launch_bf_group(b->d_bf + par * n + b->bf_n[0], b->bf_n[1], b->bf_items[1], b->d_counter + 2, b->sms,
+                             b->bf_smem[1], st);
+  return e;
+}
+
+void advance(lbf_batch_t b) {
+  for (lbf_plan_t p : b->plans) p->cur ^= 1;
+}
+
+lbf_status check_buffers(lbf_batch_t b, const void *const *d_in, void *const *d_out) {
+  if (!d_in || !d_out) return LBF_EINVAL;
+  for (size_t i = 0; i < b->plans.size(); ++i) {
+    lbf_plan_t p = b->plans[i];
+    if (!dev_ptr(d_in[i], p->word) || !dev_ptr(d_out[i], p->nS ? 4 : 8)) return LBF_EINVAL;
+  }
+  return LBF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbf_status lbf_batch_create(const lbf_plan_t *plans, int32_t n, lbf_batch_t *out) {
+  if (!out) return LBF_EINVAL;
+  *out = nullptr;
+  if (!plans || n < 1 || n > 4096) return LBF_EINVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return LBF_ECUDA;
+  for (int i = 0; i < n; ++i) {
+    lbf_plan_t p = plans[i];
+    if (!plan_ok(p)) return LBF_ESTATE;
+    if (p->device != dev) return LBF_ESTATE;
+    if (p->tc || p->external_ws) return LBF_EUNSUPPORTED;   // batches run the FP32 path on plan scratch
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == p) return LBF_EINVAL;
+  }
+  lbf_batch_s *b = new (std::nothrow) lbf_batch_s();
+  if (!b) return LBF_ENOMEM;
+  b->device = dev;
+  b->plans.assign(plans, plans + n);
+  b->variant.resize(n);
+  for (int i = 0; i < n; ++i) b->variant[i] = plans[i]->variant;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  b->sms = sms > 0 ? sms : 152;
+  b->ppf_ctas = b->sms;                       // one 512-thread filter-bank CTA per SM
+  cudaError_t e = cudaMallocHost((void **)&b->h_ppf, sizeof(lbf::PpfGroup) * 2 * n);
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_bf, sizeof(lbf::BfGroup) * 2 * n);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_ppf, sizeof(lbf::PpfGroup) * 2 * n);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_bf, sizeof(lbf::BfGroup) * 2 * n);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_counter, 3 * sizeof(unsigned long long));
+  if (e != cudaSuccess) {
+    cudaFreeHost(b->h_ppf); cudaFreeHost(b->h_bf); cudaFree(b->d_ppf); cudaFree(b->d_bf); cudaFree(b->d_counter);
+    delete b;
+    cudaGetLastError();
+    return status_of(e);
+  }
+  *out = b;
+  return LBF_OK;
+}
+
+lbf_status lbf_batch_destroy(lbf_batch_t b) {
+  if (!b) return LBF_OK;
+  if (b->magic != kBatchMagic) return LBF_ESTATE;
+  cudaDeviceSynchronize();
+  free_graphs(b);
+  cudaFreeHost(b->h_ppf); cudaFreeHost(b->h_bf); cudaFree(b->d_ppf); cudaFree(b->d_bf); cudaFree(b->d_counter);
+  b->magic = 0;
+  delete b;
+  return LBF_OK;
+}
+
+lbf_status lbf_batch_run(lbf_batch_t b, const void *const *d_in, void *const *d_out, void *stream) {
+  if (!b || b->magic != kBatchMagic) return LBF_ESTATE;
+  lbf_status s = check_buffers(b, d_in, d_out);
+  if (s != LBF_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the pinned tables of parity 0 may still be read by an earlier copy on this stream
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return status_of(e);
+  fill_tables(b, 0, d_in, d_out);
+  e = enqueue(b, 0, st);
+  if (e != cudaSuccess) return status_of(e);
+  advance(b);
+  free_graphs(b);   // captured graphs described the previous state
+  return LBF_OK;
+}
+
+lbf_status lbf_batch_capture(lbf_batch_t b, const void *const *d_in, void *const *d_out, void *stream) {
+  if (!b || b->magic != kBatchMagic) return LBF_ESTATE;
+  lbf_status s = check_buffers(b, d_in, d_out);
+  if (s != LBF_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return status_of(e);
+  free_graphs(b);
+  for (int par = 0; par < 2 && e == cudaSuccess; ++par) {
+    fill_tables(b, par, d_in, d_out);
+    cudaStream_t cs;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) break;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const cudaError_t e1 = enqueue(b, par, cs);
+      e = cudaStreamEndCapture(cs, &graph);
+      if (e == cudaSuccess) e = e1;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph[par], graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+  }
+  if (e != cudaSuccess) {
+    free_graphs(b);
+    cudaGetLastError();
+    return status_of(e);
+  }
+  b->graph_parity = 0;
+  return LBF_OK;
+}
+
+lbf_status lbf_batch_launch(lbf_batch_t b, void *stream) {
+  if (!b || b->magic != kBatchMagic) return LBF_ESTATE;
+  if (!b->graph[0] || !b->graph[1]) return LBF_ESTATE;
+  cudaError_t e = cudaGraphLaunch(b->graph[b->graph_parity], (cudaStream_t)stream);
+  if (e != cudaSuccess) return status_of(e);
+  b->graph_parity ^= 1;
+  advance(b);
+  return LBF_OK;
+}
+
+lbf_status lbf_batch_tune(lbf_batch_t b, const void *const *d_in, void *const *d_out, void *stream, int32_t reps,
+                          lbf_batch_tuning *out) {
+  if (!b || b->magic != kBatchMagic) return LBF_ESTATE;
+  if (reps < 1 || reps > 1000) return LBF_EINVAL;
+  lbf_status s = check_buffers(b, d_in, d_out);
+  if (s != LBF_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = (int)b->plans.size();
+  const int spcs[3] = {64, 128, 256};
+  std::vector<int> base(n), alt(n);
+  bool has_mid = false;
+  for (int i = 0; i < n; ++i) {
+    lbf_plan_t p = b->plans[i];
+    base[i] = p->variant;
+    const bool mid = p->B > 8 && p->B <= 64 && p->S <= lbf::many_beam_max_stations();
+    alt[i] = mid ? (p->variant == 1 ? 2 : 1) : p->variant;
+    has_mid = has_mid || mid;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int best_spc = b->spc, best_v = 0;
+  lbf_batch_tuning t;
+  std::memset(&t, 0, sizeof(t));
+  cudaError_t e = cudaSuccess;
+  for (int v = 0; v < (has_mid ? 2 : 1) && e == cudaSuccess; ++v) {
+    b->variant = v ? alt : base;
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+      b->spc = spcs[k];
+      e = cudaStreamSynchronize(st);
+      fill_tables(b, 0, d_in, d_out);
+      if (e == cudaSuccess) e = enqueue(b, 0, st);   // warm-up
+      if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+      for (int r = 0; r < reps && e == cudaSuccess; ++r) e = enqueue(b, 0, st);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      ms /= reps;
+      const int idx = v * 3 + k;
+      t.ms[idx] = ms;
+      t.spc[idx] = spcs[k];
+      t.mid_variant[idx] = v ? 1 : 0;
+      if (e == cudaSuccess && ms < best) { best = ms; best_spc = spcs[k]; best_v = v; }
+    }
+  }
+  t.n_candidates = has_mid ? 6 : 3;
+  t.best_spc = best_spc;
+  t.best_mid_variant = best_v;
+  t.best_ms = best;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->spc = best_spc;
+  b->variant = best_v ? alt : base;
+  // the candidate runs advanced nothing (parity-0 tables, histories untouched by design of the
+  // tables: each run read hist[cur] and wrote hist[cur^1]); restart every stream cleanly
+  for (lbf_plan_t p : b->plans) {
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->hist[0], 0, p->hist_bytes ? p->hist_bytes : 16, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->hist[1], 0, p->hist_bytes ? p->hist_bytes : 16, st);
+    p->cur = 0;
+  }
+  free_graphs(b);
+  if (out) *out = t;
+  return status_of(e);
+}
+
+}  // extern "C"

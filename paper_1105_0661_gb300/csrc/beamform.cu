@@ -43,14 +43,33 @@ __device__ __forceinline__ float stokes_param(int st, float2 X, float2 Y) {
   }
 }
 
+// Incoherent beam (Section 3): the Stokes parameters of the unweighted station signals, summed
+// over stations as powers -- accumulated per spectrum as sum |X|^2, sum |Y|^2 and sum X conj Y.
+struct IncAcc {
+  float xx = 0.f, yy = 0.f, re = 0.f, im = 0.f;
+  __device__ __forceinline__ void add(float2 X, float2 Y) {
+    xx = fmaf(X.x, X.x, fmaf(X.y, X.y, xx));
+    yy = fmaf(Y.x, Y.x, fmaf(Y.y, Y.y, yy));
+    re = fmaf(X.x, Y.x, fmaf(X.y, Y.y, re));
+    im = fmaf(X.y, Y.x, fmaf(-X.x, Y.y, im));
+  }
+  __device__ __forceinline__ float param(int st) const {
+    switch (st) {
+      case 0: return xx + yy;
+      case 1: return xx - yy;
+      case 2: return 2.f * re;
+      default: return 2.f * im;
+    }
+  }
+};
+
 // ------------------------------------------------------------------------------- few beams
+// Work item: (subband, channel) fc, beams bgrp * 8 .. + 7.
 template <int OUT>
-__global__ void __launch_bounds__(kFewThreads)
-bf_few_kernel(Geometry g, const float2 *__restrict__ ct, void *__restrict__ out) {
-  extern __shared__ __align__(16) float2 wsm[];   // [S][kFewBeams]
-  const int fc = blockIdx.x;
+__device__ __forceinline__ void bf_few_item(const Geometry &g, const float2 *__restrict__ ct, void *__restrict__ out,
+                                            int fc, int bgrp, float2 *wsm /* [S][kFewBeams] */) {
   const int f = fc / kN, c = fc - f * kN;
-  const int b0 = blockIdx.y * kFewBeams;
+  const int b0 = bgrp * kFewBeams;
   const int tid = threadIdx.x;
   for (int i = tid; i < g.S * kFewBeams; i += kFewThreads) {
     const int s = i / kFewBeams, b = b0 + (i - s * kFewBeams);
@@ -66,10 +85,13 @@ bf_few_kernel(Geometry g, const float2 *__restrict__ ct, void *__restrict__ out)
     float2 acc[kFewBeams][kP];
 #pragma unroll
     for (int b = 0; b < kFewBeams; ++b) acc[b][0] = acc[b][1] = make_float2(0.f, 0.f);
+    const bool inc = OUT != OUT_VOLTAGES && g.inc && bgrp == 0;   // this item also forms beam B
+    IncAcc ia;
     if (active) {
       for (int s = 0; s < g.S; ++s) {
         const float2 yx = y[((long long)s * kP + 0) * g.M + m];
         const float2 yy = y[((long long)s * kP + 1) * g.M + m];
+        if (inc) ia.add(yx, yy);
         const float4 *w4 = reinterpret_cast<const float4 *>(wsm + s * kFewBeams);
 #pragma unroll
         for (int b2 = 0; b2 < kFewBeams / 2; ++b2) {
@@ -104,8 +126,25 @@ bf_few_kernel(Geometry g, const float2 *__restrict__ ct, void *__restrict__ out)
             o[((((long long)(b0 + b) * nS + st) * g.F + f) * kN + c) * Mq + m / g.Q] = v;
         }
       }
+      if (inc) {
+#pragma unroll
+        for (int st = 0; st < nS; ++st) {
+          float v = ia.param(st);
+          for (int o2 = 1; o2 < g.Q; o2 <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o2);
+          if (active && (m & (g.Q - 1)) == 0)
+            o[((((long long)g.B * nS + st) * g.F + f) * kN + c) * Mq + m / g.Q] = v;
+        }
+      }
     }
   }
+  __syncthreads();   // the weights in shared memory are rewritten by the next work item
+}
+
+template <int OUT>
+__global__ void __launch_bounds__(kFewThreads)
+bf_few_kernel(Geometry g, const float2 *__restrict__ ct, void *__restrict__ out) {
+  extern __shared__ __align__(16) float2 wsm[];
+  bf_few_item<OUT>(g, ct, out, blockIdx.x, blockIdx.y, wsm);
 }
 
 // ------------------------------------------------------------------------------- many beams
@@ -122,15 +161,13 @@ __device__ __forceinline__ void cp_async8(void *smem_dst, const void *gmem_src, 
 // 17 + 2 mg} of the 32-spectrum pass (so each 16-byte shared load of a warp covers 128 contiguous
 // bytes), both pols: 32 complex accumulators updated with packed FP32x2 FMAs,
 //   acc += (w.re, w.re) * (y.re, y.im) + (-w.im, w.im) * (y.im, y.re).
+// Work item: (subband, channel) fc, beams bt * 128 .. + 127.
 template <int OUT>
-__global__ void __launch_bounds__(kManyThreads, 2)
-bf_many_kernel(Geometry g, const float2 *__restrict__ ct, void *__restrict__ out, int nbt) {
-  extern __shared__ __align__(16) float2 smem[];
+__device__ __forceinline__ void bf_many_item(const Geometry &g, const float2 *__restrict__ ct, void *__restrict__ out,
+                                             int fc, int bt, float2 *smem) {
   float2 *wsm = smem;                      // [S][kBT]
   float2 *ysm = smem + (size_t)g.S * kBT;  // [2 buffers][S][kP][kMC]
   const int tid = threadIdx.x;
-  const int fc = blockIdx.x / nbt;
-  const int bt = blockIdx.x - fc * nbt;
   const int f = fc / kN, c = fc - f * kN;
   const int bbase = bt * kBT;
   const float2 *y = ct + (long long)fc * g.S * kP * g.M;
@@ -176,6 +213,18 @@ bf_many_kernel(Geometry g, const float2 *__restrict__ ct, void *__restrict__ out
     asm volatile("cp.async.wait_group 1;" ::: "memory");
     __syncthreads();   // pass mc (and the weights) visible to every thread
     const float2 *yb = ysm + buf * ybuf;
+    if (OUT != OUT_VOLTAGES && g.inc && bt == 0 && tid < kMC) {   // warp 0: incoherent beam B
+      IncAcc ia;
+      for (int s = 0; s < g.S; ++s) ia.add(yb[(s * kP + 0) * kMC + tid], yb[(s * kP + 1) * kMC + tid]);
+      float *o = reinterpret_cast<float *>(out);
+      const int m = mc + tid;
+      for (int st = 0; st < nS; ++st) {
+        float v = ia.param(st);
+        for (int o2 = 1; o2 < g.Q; o2 <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o2);
+        if (m < g.M && (m & (g.Q - 1)) == 0)
+          o[((((long long)g.B * nS + st) * g.F + f) * kN + c) * Mq + m / g.Q] = v;
+      }
+    }
 
     float2 acc[4][kP][4];
 #pragma unroll
@@ -258,6 +307,44 @@ bf_many_kernel(Geometry g, const float2 *__restrict__ ct, void *__restrict__ out
   asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
+template <int OUT>
+__global__ void __launch_bounds__(kManyThreads, 2)
+bf_many_kernel(Geometry g, const float2 *__restrict__ ct, void *__restrict__ out, int nbt) {
+  extern __shared__ __align__(16) float2 smem[];
+  const int fc = blockIdx.x / nbt;
+  bf_many_item<OUT>(g, ct, out, fc, blockIdx.x - fc * nbt, smem);
+}
+
+// Persistent beam former over the blocks of several observations (a batch): CTAs take work items
+// (subband-channel, beam group) from a shared counter; each item runs the few- or many-beam body
+// its observation was tuned to, with that observation's output kind.
+__global__ void __launch_bounds__(kManyThreads, 2)
+bf_group_kernel(const BfGroup *__restrict__ grp, int ngrp, long long total, unsigned long long *counter) {
+  extern __shared__ __align__(16) float2 smem[];
+  __shared__ long long item_s;
+  for (;;) {
+    if (threadIdx.x == 0) item_s = (long long)atomicAdd(counter, 1ull);
+    __syncthreads();
+    const long long item = item_s;
+    __syncthreads();
+    if (item >= total) break;
+    int o = 0;
+    while (o + 1 < ngrp && grp[o + 1].first_item <= item) ++o;
+    const BfGroup &G = grp[o];
+    const long long local = item - G.first_item;
+    const int fc = (int)(local / G.per_fc), sub = (int)(local - (long long)fc * G.per_fc);
+    if (G.variant == 1) {
+      if (G.out_kind == OUT_STOKES_I) bf_few_item<OUT_STOKES_I>(G.g, G.ct, G.out, fc, sub, smem);
+      else if (G.out_kind == OUT_STOKES_IQUV) bf_few_item<OUT_STOKES_IQUV>(G.g, G.ct, G.out, fc, sub, smem);
+      else bf_few_item<OUT_VOLTAGES>(G.g, G.ct, G.out, fc, sub, smem);
+    } else {
+      if (G.out_kind == OUT_STOKES_I) bf_many_item<OUT_STOKES_I>(G.g, G.ct, G.out, fc, sub, smem);
+      else if (G.out_kind == OUT_STOKES_IQUV) bf_many_item<OUT_STOKES_IQUV>(G.g, G.ct, G.out, fc, sub, smem);
+      else bf_many_item<OUT_VOLTAGES>(G.g, G.ct, G.out, fc, sub, smem);
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_beamform(const Geometry &g, int variant, int out_kind, const float2 *ct, void *out,
@@ -308,6 +395,23 @@ cudaError_t launch_beamform(const Geometry &g, int variant, int out_kind, const 
       break;
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_bf_group(const BfGroup *d_groups, int ngrp, long long total, unsigned long long *counter,
+                            int ctas, size_t smem, cudaStream_t st) {
+  if (total == 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(bf_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  bf_group_kernel<<<ctas, kManyThreads, smem, st>>>(d_groups, ngrp, total, counter);
+  return cudaGetLastError();
+}
+
+int few_beams_per_item() { return kFewBeams; }
+int many_beams_per_item() { return kBT; }
+size_t bf_smem_bytes(int variant, int S) {
+  return variant == 1 ? (size_t)S * kFewBeams * sizeof(float2) : (size_t)S * (kBT + 2 * kP * kMC) * sizeof(float2);
 }
 
 // Largest station count the many-beam kernel accepts (its shared memory holds S x (128 + 64) cf32).

@@ -50,7 +50,7 @@ delay_ct_kernel(Geometry g, const float2 *__restrict__ chan, float2 *__restrict_
   }
 }
 
-// ct [F][N][S][P][M] cf32 -> FP16 planes [F*N][kpad][Mb][P][32] (rows k = 2s re, 2s+1 im): an
+// ct [F][N][S][P][M] cf32 -> FP16 planes [F*N][Mb][kpad][P][32] (rows k = 2s re, 2s+1 im): an
 // elementwise split, both sides spectrum-fastest, so reads and writes are coalesced as they are.
 __global__ void __launch_bounds__(256)
 ct_to_ct16_kernel(Geometry g, const float2 *__restrict__ ct, Ct16Out o, long long n) {
@@ -65,8 +65,8 @@ ct_to_ct16_kernel(Geometry g, const float2 *__restrict__ ct, Ct16Out o, long lon
     const long long fc = fcs / g.S;
     const int s = (int)(fcs - fc * g.S);
     const float2 v = ct[i];
-    const long long re = (((fc * o.kpad + 2 * s) * mb + (m >> 5)) * 64) + pol * 32 + (m & 31);
-    const long long im = re + (long long)mb * 64;
+    const long long re = (((fc * mb + (m >> 5)) * o.kpad + 2 * s) * 64) + pol * 32 + (m & 31);
+    const long long im = re + 64;
     const __half hr = __float2half_rn(v.x), hm = __float2half_rn(v.y);
     hi[re] = hr;
     hi[im] = hm;
@@ -77,7 +77,96 @@ ct_to_ct16_kernel(Geometry g, const float2 *__restrict__ ct, Ct16Out o, long lon
   }
 }
 
+// Incoherent beam of a tensor-core plan (Section 3) from its FP16 planes [F*N][Mb][kpad][P][32]:
+// thread per (subband-channel, spectrum), summing over stations the Stokes parameters of
+// Y = hi (+ lo); writes beam index B of the Stokes output.  Lane l of a warp holds spectrum
+// 32 w + l, so the integration over Q <= 32 spectra is a warp-shuffle reduction.
+template <int NS>
+__global__ void __launch_bounds__(256)
+incoherent_ct16_kernel(Geometry g, Ct16Out o, float *__restrict__ out) {
+  const __half *hi = reinterpret_cast<const __half *>(o.hi);
+  const __half *lo = reinterpret_cast<const __half *>(o.lo);
+  const int mb = (g.M + 31) >> 5;
+  const long long fc = blockIdx.x;
+  const int f = (int)(fc / kN), c = (int)(fc - (long long)f * kN);
+  const int Mq = g.M / g.Q;
+  for (int m0 = 0; m0 < mb * 32; m0 += blockDim.x) {
+    const int m = m0 + threadIdx.x;
+    const bool active = m < g.M;
+    float xx = 0.f, yy = 0.f, re = 0.f, im = 0.f;
+    if (active) {
+      const long long blk = (fc * mb + (m >> 5)) * o.kpad;
+      for (int s = 0; s < g.S; ++s) {
+        const long long r0 = (blk + 2 * s) * 64 + (m & 31);            // k = 2s (re)
+        const long long r1 = r0 + 64;                                   // k = 2s+1 (im)
+        float xr = __half2float(hi[r0]), xi = __half2float(hi[r1]);
+        float yr = __half2float(hi[r0 + 32]), yi = __half2float(hi[r1 + 32]);
+        if (lo) {
+          xr += __half2float(lo[r0]); xi += __half2float(lo[r1]);
+          yr += __half2float(lo[r0 + 32]); yi += __half2float(lo[r1 + 32]);
+        }
+        xx = fmaf(xr, xr, fmaf(xi, xi, xx));
+        yy = fmaf(yr, yr, fmaf(yi, yi, yy));
+        re = fmaf(xr, yr, fmaf(xi, yi, re));
+        im = fmaf(xi, yr, fmaf(-xr, yi, im));
+      }
+    }
+#pragma unroll
+    for (int st = 0; st < NS; ++st) {
+      float v = st == 0 ? xx + yy : st == 1 ? xx - yy : st == 2 ? 2.f * re : 2.f * im;
+      for (int o2 = 1; o2 < g.Q; o2 <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o2);
+      if (active && (m & (g.Q - 1)) == 0)
+        out[((((long long)g.B * NS + st) * g.F + f) * kN + c) * Mq + m / g.Q] = v;
+    }
+  }
+}
+
+// Superstation beam former (Section 4.2): ss[f][c][g][pol][m] = sum of ct[f][c][s][pol][m] over the
+// stations s of group g (unit weights: the stations are already delay-compensated to the phase
+// centre).  members[] lists the stations group by group, offs[g]..offs[g+1] those of group g; a
+// thread owns one spectrum of one (subband-channel, group, pol) row, so reads and writes are
+// coalesced along the spectra.
+__global__ void __launch_bounds__(256)
+superstation_kernel(Geometry g, const float2 *__restrict__ ct, float2 *__restrict__ ss, const int *__restrict__ members,
+                    const int *__restrict__ offs, int ngroups, long long rows) {
+  for (long long r = blockIdx.y; r < rows; r += gridDim.y) {          // r = (fc * G + grp) * P + pol
+    const int pol = (int)(r % kP);
+    const long long fg = r / kP;
+    const int grp = (int)(fg % ngroups);
+    const long long fc = fg / ngroups;
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < g.M; m += gridDim.x * blockDim.x) {
+      float2 acc = make_float2(0.f, 0.f);
+      for (int i = offs[grp]; i < offs[grp + 1]; ++i) {
+        const float2 v = ct[((fc * g.S + members[i]) * kP + pol) * g.M + m];
+        acc.x += v.x;
+        acc.y += v.y;
+      }
+      ss[r * g.M + m] = acc;
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_superstation(const Geometry &g, const float2 *ct, float2 *ss, const int *members, const int *offs,
+                                int ngroups, cudaStream_t st) {
+  const long long rows = (long long)g.F * kN * ngroups * kP;
+  if (rows == 0 || g.M == 0) return cudaSuccess;
+  const unsigned bx = (unsigned)((g.M + 255) / 256 < 4 ? (g.M + 255) / 256 : 4);
+  const unsigned by = (unsigned)(rows < 65535 ? rows : 65535);
+  superstation_kernel<<<dim3(bx, by), 256, 0, st>>>(g, ct, ss, members, offs, ngroups, rows);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_incoherent_ct16(const Geometry &g, int out_kind, const Ct16Out &o, float *out, cudaStream_t st) {
+  const long long fcs = (long long)g.F * kN;
+  if (fcs == 0 || g.M == 0) return cudaSuccess;
+  if (out_kind == OUT_STOKES_IQUV)
+    incoherent_ct16_kernel<4><<<(unsigned)fcs, 256, 0, st>>>(g, o, out);
+  else
+    incoherent_ct16_kernel<1><<<(unsigned)fcs, 256, 0, st>>>(g, o, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_ct_to_ct16(const Geometry &g, const float2 *ct, const Ct16Out &o, cudaStream_t st) {
   const long long n = (long long)g.F * kN * g.S * kP * g.M;

@@ -10,56 +10,14 @@
 
 #include "lbf.h"
 #include "lbf_internal.cuh"
+#include "plan.h"
 
 namespace {
 
-constexpr uint32_t kMagic = 0x4c424650u;   // "LBFP"
+constexpr uint32_t kMagic = lbf::kPlanMagic;
 constexpr double kC = 299792458.0;         // m/s
 
 }  // namespace
-
-struct lbf_plan_s {
-  uint32_t magic = kMagic;
-  int device = 0;
-  int S = 0, F = 0, N = 0, L = 0, B = 0, T = 0, M = 0, Q = 1, nS = 0, bits = 16;
-  int out_kind = 0, variant = 1, d_max = 0, H = 0;
-  double fs = 0.0;
-  std::vector<int32_t> n_shift, d_shift;
-  float *taps = nullptr;
-  float2 *twiddle = nullptr;
-  float *bandpass = nullptr;
-  int *dshift = nullptr;
-  double *tau = nullptr, *resid = nullptr, *f0 = nullptr, *dtau = nullptr;
-  float *phase0 = nullptr, *step = nullptr;
-  // tensor-core precision: FP16 corner-turned planes and their TMA descriptors
-  bool tc = false;
-  int kpad = 0, planes = 0;
-  void *ct16[2] = {nullptr, nullptr};
-  alignas(64) CUtensorMap tmap[2];
-  size_t ct16_bytes = 0;
-  bool external_ws = false;     // scratch passed per call (lbf_run_block_ws)
-  size_t ws_need = 0;           // scratch bytes one block needs
-  int *d_err = nullptr;   // device error word set by bounded waits that gave up
-  void *hist[2] = {nullptr, nullptr};
-  int cur = 0;
-  float2 *ws = nullptr;
-  size_t word = 8, hist_bytes = 0, ws_bytes = 0;
-
-  // kernel timing trace (lbf_trace_begin / lbf_trace_end)
-  struct TraceSlot { int kernel; cudaEvent_t a, b; };
-  std::vector<TraceSlot> trace;
-  size_t trace_used = 0;
-  int trace_dropped = 0;
-  bool tracing = false;
-
-  lbf::Geometry geometry() const {
-    lbf::Geometry g;
-    g.S = S; g.F = F; g.B = B; g.T = T; g.M = M; g.Q = Q; g.nS = nS; g.H = H; g.fs = fs;
-    g.taps = taps; g.twiddle = twiddle; g.bandpass = bandpass; g.dshift = dshift;
-    g.tau = tau; g.resid = resid; g.f0 = f0; g.dtau = dtau; g.phase0 = phase0; g.step = step;
-    return g;
-  }
-};
 
 namespace {
 
@@ -98,7 +56,7 @@ void release(lbf_plan_s *p) {
   cudaFree(p->tau); cudaFree(p->resid); cudaFree(p->f0); cudaFree(p->dtau);
   cudaFree(p->hist[0]); cudaFree(p->hist[1]); cudaFree(p->ws);
   cudaFree(p->phase0); cudaFree(p->step);
-  cudaFree(p->ct16[0]); cudaFree(p->d_err);
+  cudaFree(p->ct16[0]); cudaFree(p->d_err); cudaFree(p->ss_members); cudaFree(p->ss_offs);
 }
 
 lbf_status validate(const lbf_config *c) {
@@ -110,7 +68,8 @@ lbf_status validate(const lbf_config *c) {
   if (c->output != LBF_VOLTAGES && c->output != LBF_STOKES_I && c->output != LBF_STOKES_IQUV) return LBF_EINVAL;
   if (c->precision != LBF_FP32 && c->precision != LBF_FP16_TC) return LBF_EINVAL;
   if (c->bf_variant < LBF_BF_AUTO || c->bf_variant > LBF_BF_MANY) return LBF_EINVAL;
-  if ((c->flags & ~LBF_FLAG_EXTERNAL_WORKSPACE) != 0) return LBF_EINVAL;
+  if ((c->flags & ~(LBF_FLAG_EXTERNAL_WORKSPACE | LBF_FLAG_INCOHERENT_BEAM)) != 0) return LBF_EINVAL;
+  if ((c->flags & LBF_FLAG_INCOHERENT_BEAM) && c->output == LBF_VOLTAGES) return LBF_EINVAL;
   if (!is_pow2_upto32(c->int_factor)) return LBF_EINVAL;
   const int M = c->block_samples / c->n_channels;
   if (c->output != LBF_VOLTAGES && M % c->int_factor != 0) return LBF_EINVAL;
@@ -133,9 +92,9 @@ lbf_status validate(const lbf_config *c) {
 
 bool valid_plan(lbf_plan_t p) { return p && p->magic == kMagic; }
 
-// TMA descriptor of one FP16 plane [F*N][kpad][Mb][P][32] (Mb = ceil(M/32) blocks of 32 spectra,
-// the two pols of a block side by side): boxes of 64 halves (one 128-byte swizzle row: 2 pols x 32
-// spectra) x 64 K rows, 128-byte swizzle.
+// TMA descriptor of one FP16 plane [F*N][Mb][kpad][P][32] (Mb = ceil(M/32) blocks of 32 spectra;
+// a block's kpad K rows hold the two pols side by side, 128 bytes per row, so one beam-former tile
+// is one contiguous kpad x 128-byte region): boxes of 64 halves x kpad rows, 128-byte swizzle.
 cudaError_t encode_ct16_map(CUtensorMap *map, void *base, int kpad, int M, long long fc_rows) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
@@ -147,9 +106,9 @@ cudaError_t encode_ct16_map(CUtensorMap *map, void *base, int kpad, int M, long 
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
   const cuuint64_t mb = (cuuint64_t)(M + 31) / 32;
-  const cuuint64_t dims[4] = {64, mb, (cuuint64_t)kpad, (cuuint64_t)fc_rows};
-  const cuuint64_t strides[3] = {128, mb * 128, (cuuint64_t)kpad * mb * 128};
-  const cuuint32_t box[4] = {64, 1, 64, 1};
+  const cuuint64_t dims[4] = {64, (cuuint64_t)kpad, mb, (cuuint64_t)fc_rows};
+  const cuuint64_t strides[3] = {128, (cuuint64_t)kpad * 128, mb * kpad * 128};
+  const cuuint32_t box[4] = {64, (cuuint32_t)kpad, 1, 1};   // one tile: all K rows of one block
   const cuuint32_t elem[4] = {1, 1, 1, 1};
   CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, base, dims, strides, box, elem,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -191,10 +150,10 @@ lbf_status check_call(lbf_plan_t p) {
 }
 
 enum KernelId { K_PPF = 0, K_PPF_CT, K_HIST, K_DELAY, K_BF_FEW, K_BF_MANY, K_STOKES, K_PPF_CT16, K_BF_TC,
-                K_CT16, K_COUNT };
+                K_CT16, K_INC16, K_COUNT };
 static_assert(K_COUNT <= 16, "lbf_trace holds 16 kernels");
 const char *const kKernelNames[K_COUNT] = {"ppf", "ppf_ct", "hist_update", "delay_ct", "bf_few", "bf_many",
-                                           "stokes", "ppf_ct16", "bf_tc", "ct_to_ct16"};
+                                           "stokes", "ppf_ct16", "bf_tc", "ct_to_ct16", "incoherent_ct16"};
 
 // Launch through `fn`, bracketed by trace events when a trace is active.
 template <typename Fn>
@@ -239,6 +198,10 @@ cudaError_t run_block_device(lbf_plan_t p, const void *d_in, void *d_out, void *
     if (e == cudaSuccess) e = traced(p, K_HIST, st, [&] { return lbf::launch_hist_update(g, p->bits, d_in, h, nh, st); });
     if (e != cudaSuccess) return e;
     p->cur ^= 1;
+    if (p->inc) {
+      e = traced(p, K_INC16, st, [&] { return lbf::launch_incoherent_ct16(g, p->out_kind, o, (float *)d_out, st); });
+      if (e != cudaSuccess) return e;
+    }
     return traced(p, K_BF_TC, st, [&] {
       return lbf::launch_bf_tc(g, p->out_kind, &maps[0], p->planes > 1 ? &maps[1] : nullptr, p->planes,
                                (float *)d_out, p->d_err, st); });
@@ -346,13 +309,18 @@ lbf_status lbf_plan(const lbf_config *cfg, lbf_plan_t *out) {
   }
   p->tc = cfg->precision == LBF_FP16_TC;
   p->external_ws = (cfg->flags & LBF_FLAG_EXTERNAL_WORKSPACE) != 0;
+  p->inc = (cfg->flags & LBF_FLAG_INCOHERENT_BEAM) ? 1 : 0;
+  if (e == cudaSuccess) e = cudaMalloc((void **)&p->ss_members, sizeof(int) * p->S);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&p->ss_offs, sizeof(int) * (p->S + 1));
   if (e == cudaSuccess) e = cudaMalloc((void **)&p->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
   if (p->tc) {
-    // FP16 planes [F*N][kpad][Mb][P][32], hi then lo in one buffer; pad rows k >= 2S and pad
-    // spectra m >= M stay zero
+    // FP16 planes [F*N][Mb][kpad][P][32], hi then lo in one buffer; pad rows k >= 2S and pad
+    // spectra m >= M stay zero.  Both sample widths keep a lo plane: an 8-bit sample is exact in
+    // FP16, but its filtered, delay-corrected spectrum is not, and a beam summed with cancellation
+    // magnifies that rounding past 1e-3 on Stokes I.
     p->kpad = lbf::tc_kpad(p->S);
-    p->planes = p->bits == 16 ? 2 : 1;
+    p->planes = 2;
     p->ct16_bytes = (size_t)p->F * p->N * p->kpad * ((p->M + 31) / 32) * 64 * 2;
     p->ws_need = p->planes * p->ct16_bytes;
     if (!p->external_ws && e == cudaSuccess) {
@@ -400,7 +368,7 @@ lbf_status lbf_plan_dims(lbf_plan_t p, lbf_dims *d) {
   d->chan_bytes = cplx;
   d->ct_bytes = cplx;
   d->vol_bytes = (size_t)p->B * p->F * lbf::kP * p->T * sizeof(float2);
-  d->stokes_bytes = p->nS ? (size_t)p->B * p->nS * p->F * p->N * (p->M / p->Q) * sizeof(float) : 0;
+  d->stokes_bytes = p->nS ? (size_t)(p->B + p->inc) * p->nS * p->F * p->N * (p->M / p->Q) * sizeof(float) : 0;
   d->out_bytes = p->nS ? d->stokes_bytes : d->vol_bytes;
   d->workspace_bytes = p->ws_need;
   d->plan_bytes = 2 * p->hist_bytes + (p->external_ws ? 0 : p->ws_need) +
@@ -478,6 +446,8 @@ lbf_status lbf_beamform_stokes(lbf_plan_t p, const void *d_ct, float *d_out, voi
     if (p->external_ws) return LBF_EUNSUPPORTED;
     const lbf::Ct16Out o = ct16_out(p);
     cudaError_t e = traced(p, K_CT16, st, [&] { return lbf::launch_ct_to_ct16(g, (const float2 *)d_ct, o, st); });
+    if (e == cudaSuccess && p->inc)
+      e = traced(p, K_INC16, st, [&] { return lbf::launch_incoherent_ct16(g, p->out_kind, o, d_out, st); });
     if (e != cudaSuccess) return cuda_status(e);
     return cuda_status(traced(p, K_BF_TC, st, [&] {
       return lbf::launch_bf_tc(g, p->out_kind, &p->tmap[0], p->planes > 1 ? &p->tmap[1] : nullptr, p->planes, d_out,
@@ -518,11 +488,12 @@ lbf_status lbf_run_block_ws(lbf_plan_t p, const void *d_in, void *d_out, void *d
   CUtensorMap maps[2];
   if (p->tc) {
     cudaError_t e = encode_planes(p, d_ws, maps);
-    // pad rows k in [2S, kpad) of each (subband, channel) must read as zero
-    const size_t row = (size_t)((p->M + 31) / 32) * 128;   // bytes of one K row
+    // pad rows k in [2S, kpad) of each (subband, channel, spectrum block) must read as zero
+    const size_t row = 128;   // bytes of one K row
+    const size_t blocks = (size_t)p->F * p->N * ((p->M + 31) / 32);
     for (int i = 0; i < p->planes && e == cudaSuccess && p->kpad > 2 * p->S; ++i)
       e = cudaMemset2DAsync(static_cast<unsigned char *>(d_ws) + i * p->ct16_bytes + 2 * p->S * row,
-                            p->kpad * row, 0, (p->kpad - 2 * p->S) * row, (size_t)p->F * p->N, st);
+                            p->kpad * row, 0, (p->kpad - 2 * p->S) * row, blocks, st);
     if (e != cudaSuccess) return cuda_status(e);
   }
   return cuda_status(run_block_device(p, d_in, d_out, d_ws, maps, st));
@@ -557,6 +528,34 @@ lbf_status lbf_device_status(lbf_plan_t p, int32_t *code) {
     return LBF_ETIMEOUT;
   }
   return LBF_OK;
+}
+
+lbf_status lbf_superstation(lbf_plan_t p, const int32_t *group_of_station, int32_t n_groups, const void *d_ct,
+                            void *d_ss, void *stream) {
+  lbf_status s = check_call(p);
+  if (s != LBF_OK) return s;
+  if (!group_of_station || n_groups < 1 || n_groups > p->S) return LBF_EINVAL;
+  for (int i = 0; i < p->S; ++i)
+    if (group_of_station[i] < 0 || group_of_station[i] >= n_groups) return LBF_EINVAL;
+  if (p->M == 0) return LBF_OK;
+  if (!device_ptr(d_ct, 8) || !device_ptr(d_ss, 8)) return LBF_EINVAL;
+  // stations listed group by group, in station order within a group
+  std::vector<int> members, offs(n_groups + 1, 0);
+  for (int g = 0; g < n_groups; ++g) {
+    offs[g] = (int)members.size();
+    for (int i = 0; i < p->S; ++i)
+      if (group_of_station[i] == g) members.push_back(i);
+  }
+  offs[n_groups] = (int)members.size();
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(p->ss_members, members.data(), sizeof(int) * members.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p->ss_offs, offs.data(), sizeof(int) * offs.size(), cudaMemcpyHostToDevice, st);
+  // the host vectors must outlive the copies: pageable copies are staged before the call returns
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e);
+  const lbf::Geometry g = p->geometry();
+  return cuda_status(lbf::launch_superstation(g, (const float2 *)d_ct, (float2 *)d_ss, p->ss_members, p->ss_offs,
+                                              n_groups, st));
 }
 
 lbf_status lbf_trace_begin(lbf_plan_t p, int32_t max_launches) {

@@ -12,36 +12,77 @@ constexpr int kP = 2;     // polarisations X, Y
 
 // Device-side description of one observation; every pointer is device memory owned by the plan.
 struct Geometry {
-  int S, F, B, T, M, Q, nS;   // stations, subbands, beams, samples/block, spectra, int. factor, Stokes
-  int H;                      // history samples per (station, subband)
-  double fs;                  // subband sample rate
-  const float *taps;          // [L*N]
-  const float2 *twiddle;      // [N] exp(-2 pi i n / N)
-  const float *bandpass;      // [N]
-  const int *dshift;          // [S] integer shift d_s
-  const double *tau;          // [S] phase-centre delay tau_s
-  const double *resid;        // [S] tau_s - n_s Ts
-  const double *f0;           // [F] subband centre frequency
-  const double *dtau;         // [B][S] beam delay difference
-  const float *phase0;        // [F][B][S] f0_f dtau[b,s] reduced to [-1/2, 1/2] cycle (FP64 -> FP32)
-  const float *step;          // [B][S] fs/N * dtau[b,s], cycles per channel
+  int S = 0, F = 0, B = 0, T = 0, M = 0, Q = 1, nS = 0;   // stations, subbands, beams, samples/block,
+                                                        // spectra, integration factor, Stokes
+  int H = 0;                  // history samples per (station, subband)
+  int inc = 0;                // 1: the Stokes output also holds the incoherent beam at index B
+  double fs = 0.0;            // subband sample rate
+  const float *taps = nullptr;          // [L*N]
+  const float2 *twiddle = nullptr;      // [N] exp(-2 pi i n / N)
+  const float *bandpass = nullptr;      // [N]
+  const int *dshift = nullptr;          // [S] integer shift d_s
+  const double *tau = nullptr;          // [S] phase-centre delay tau_s
+  const double *resid = nullptr;        // [S] tau_s - n_s Ts
+  const double *f0 = nullptr;           // [F] subband centre frequency
+  const double *dtau = nullptr;         // [B][S] beam delay difference
+  const float *phase0 = nullptr;        // [F][B][S] f0_f dtau[b,s] reduced to [-1/2, 1/2] cycle (FP64 -> FP32)
+  const float *step = nullptr;          // [B][S] fs/N * dtau[b,s], cycles per channel
 };
 
 enum OutKind { OUT_VOLTAGES = 0, OUT_STOKES_I = 1, OUT_STOKES_IQUV = 4 };
 
-// FP16 corner-turned scratch of the tensor-core beam former: [F*N][kpad][ceil(M/32)][P][32]
+// FP16 corner-turned scratch of the tensor-core beam former: [F*N][ceil(M/32)][kpad][P][32]
 // halves per plane (k = 2 station + re|im; blocks of 32 spectra, the two pols side by side).
 struct Ct16Out {
   void *hi, *lo;   // lo may be null (single-product form)
   int kpad;        // 2 S rounded up to a multiple of 16
 };
 
+// One observation of a batch (grouped persistent launches, batch.cu): its geometry, this
+// block's buffers, and its range of work items in the grouped filter bank and beam former.
+struct PpfGroup {
+  Geometry g;
+  const void *in;
+  const void *hist;
+  void *new_hist;
+  float2 *ct;                 // corner-turned scratch of this observation
+  int bits;
+  int spc;                    // spectra per filter-bank work item (a multiple of 16)
+  int chunks;                 // ceil(M / spc)
+  long long first_item;       // first filter-bank work item of this group
+  long long first_hist;       // first history element of this group
+};
+struct BfGroup {
+  Geometry g;
+  const float2 *ct;
+  void *out;
+  int variant;                // 1 few-beam, 2 many-beam
+  int out_kind;
+  int per_fc;                 // work items per (subband, channel): beam groups or beam tiles
+  long long first_item;
+};
+
 // --- launchers (return cudaGetLastError() of the launch) ---
 // a1-a3 (+ a4 when ct or ct16 is given): filter bank; reads history `hist`, block `in`.
 cudaError_t launch_ppf(const Geometry &g, int bits, const void *in, const void *hist,
                        float2 *chan, float2 *ct, cudaStream_t st, const Ct16Out *ct16 = nullptr);
+// batch: persistent grouped filter bank (FP32 corner-turned output), history update, beam former
+cudaError_t launch_ppf_group(const PpfGroup *d_groups, int ngrp, long long total, unsigned long long *counter,
+                             int ctas, cudaStream_t st);
+cudaError_t launch_hist_group(const PpfGroup *d_groups, int ngrp, long long total, cudaStream_t st);
+cudaError_t launch_bf_group(const BfGroup *d_groups, int ngrp, long long total, unsigned long long *counter,
+                            int ctas, size_t smem, cudaStream_t st);
+int ppf_spectra_per_cta();
+int few_beams_per_item();
+int many_beams_per_item();
+size_t bf_smem_bytes(int variant, int S);
 // FP32 corner-turned [F][N][S][P][M] -> FP16 [F][N][P][M][kpad] hi/lo planes (split-call TC path)
 cudaError_t launch_ct_to_ct16(const Geometry &g, const float2 *ct, const Ct16Out &o, cudaStream_t st);
+// superstation beam former: sum of delay-compensated stations per group (delay.cu)
+cudaError_t launch_superstation(const Geometry &g, const float2 *ct, float2 *ss, const int *members, const int *offs,
+                                int ngroups, cudaStream_t st);
+// incoherent beam (index B of the Stokes output) from the FP16 planes of a tensor-core plan
+cudaError_t launch_incoherent_ct16(const Geometry &g, int out_kind, const Ct16Out &o, float *out, cudaStream_t st);
 // tcgen05 beam former with fused Stokes epilogue (bf_tc.cu); tm_hi/tm_lo are CUtensorMap*
 cudaError_t launch_bf_tc(const Geometry &g, int out_kind, const void *tm_hi, const void *tm_lo, int planes,
                          float *out, int *err, cudaStream_t st);

@@ -104,7 +104,7 @@ struct PpfSmem {
 };
 
 // Output modes: the channelised layout, the FP32 corner-turned layout, or the FP16 layout of the
-// tensor-core beam former ([F*N][Kpad][M/32][P][32] with station s in rows k = 2s (re), 2s+1 (im);
+// tensor-core beam former ([F*N][M/32][Kpad][P][32] with station s in rows k = 2s (re), 2s+1 (im);
 // a hi plane fp16(Y) and optionally a lo plane fp16(Y - hi)).
 enum PpfMode { MODE_CHAN = 0, MODE_CT32 = 1, MODE_CT16 = 2 };
 
@@ -125,32 +125,20 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// One work item: spectra [chunk * spc, (chunk + 1) * spc) of stream (s, f), spc a multiple of 16.
 template <int BITS, int MODE>
-__global__ void __launch_bounds__(kThreads, 1)
-ppf_kernel(Geometry g, const typename SampleIO<BITS>::word *__restrict__ in,
-           const typename SampleIO<BITS>::word *__restrict__ hist, PpfOut po, int chunks) {
+__device__ __forceinline__ void ppf_item(const Geometry &g, const typename SampleIO<BITS>::word *__restrict__ in,
+                                         const typename SampleIO<BITS>::word *__restrict__ hist, const PpfOut &po,
+                                         int s, int f, int chunk, int spc, unsigned char *smem_raw) {
   using word = typename SampleIO<BITS>::word;
   constexpr bool CT = MODE != MODE_CHAN;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   PpfSmem<BITS> &sm = *reinterpret_cast<PpfSmem<BITS> *>(smem_raw);
   float2 *__restrict__ out = po.f32;
 
   const int tid = threadIdx.x;
-  int s, f, chunk;
-  if (MODE == MODE_CT16) {   // stations fastest: neighbouring CTAs fill neighbouring K rows of
-    s = (int)(blockIdx.x % g.S);                 // the same (channel) planes
-    const long long rest = blockIdx.x / g.S;
-    chunk = (int)(rest % chunks);
-    f = (int)(rest / chunks);
-  } else {
-    const long long sf = blockIdx.x / chunks;    // stream index s * F + f
-    chunk = (int)(blockIdx.x - sf * chunks);
-    s = (int)(sf / g.F);
-    f = (int)(sf - (long long)s * g.F);
-  }
   const long long sf = (long long)s * g.F + f;
-  const int m0 = chunk * kSpectraPerCta;
-  const int m_end = min(g.M, m0 + kSpectraPerCta);
+  const int m0 = chunk * spc;
+  const int m_end = min(g.M, m0 + spc);
   const int ntiles = (m_end - m0 + kTile - 1) / kTile;
 
   if (tid < kN) sm.tw[tid] = g.twiddle[tid];
@@ -244,7 +232,7 @@ ppf_kernel(Geometry g, const typename SampleIO<BITS>::word *__restrict__ in,
         stage[c * kTile + (gq ^ (c & 15))] = cmul(a[k2], sm.gain[c]);
       }
       __syncthreads();
-      // [F*N][Kpad][Mb][P][32]: rows k = 2s (re) and 2s+1 (im), runs of 16 spectra (32 B)
+      // [F*N][Mb][Kpad][P][32]: rows k = 2s (re) and 2s+1 (im), runs of 16 spectra (32 B)
       const int q = tid & 15;
       const int mb = (g.M + 31) >> 5;
       const int m = mt + q;
@@ -254,8 +242,8 @@ ppf_kernel(Geometry g, const typename SampleIO<BITS>::word *__restrict__ in,
           const int row2 = pass * 32 + (tid >> 4);     // (pol, c)
           const int pl = row2 >> 8, c = row2 & (kN - 1);
           const float2 v = (&sm.v[pl][0][0])[c * kTile + (q ^ (c & 15))];
-          const long long re = ((((long long)f * kN + c) * po.kpad + 2 * s) * mb + (m >> 5)) * 64 + pl * 32 + (m & 31);
-          const long long im = re + (long long)mb * 64;
+          const long long re = ((((long long)f * kN + c) * mb + (m >> 5)) * po.kpad + 2 * s) * 64 + pl * 32 + (m & 31);
+          const long long im = re + 64;
           const __half hr = __float2half_rn(v.x), hi_ = __float2half_rn(v.y);
           po.hi[re] = hr;
           po.hi[im] = hi_;
@@ -295,6 +283,74 @@ ppf_kernel(Geometry g, const typename SampleIO<BITS>::word *__restrict__ in,
     __syncthreads();
   }
   cp_async_wait<0>();
+}
+
+template <int BITS, int MODE>
+__global__ void __launch_bounds__(kThreads, 1)
+ppf_kernel(Geometry g, const typename SampleIO<BITS>::word *__restrict__ in,
+           const typename SampleIO<BITS>::word *__restrict__ hist, PpfOut po, int chunks) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int s, f, chunk;
+  if (MODE == MODE_CT16) {   // stations fastest: neighbouring CTAs fill neighbouring K rows of
+    s = (int)(blockIdx.x % g.S);                 // the same (channel) planes
+    const long long rest = blockIdx.x / g.S;
+    chunk = (int)(rest % chunks);
+    f = (int)(rest / chunks);
+  } else {
+    const long long sf = blockIdx.x / chunks;    // stream index s * F + f
+    chunk = (int)(blockIdx.x - sf * chunks);
+    s = (int)(sf / g.F);
+    f = (int)(sf - (long long)s * g.F);
+  }
+  ppf_item<BITS, MODE>(g, in, hist, po, s, f, chunk, kSpectraPerCta, smem_raw);
+}
+
+// Persistent filter bank over the blocks of several observations (a batch): CTAs take work items
+// (stream, spectrum chunk) from a shared counter until all groups are done.
+__global__ void __launch_bounds__(kThreads, 1)
+ppf_group_kernel(const PpfGroup *__restrict__ grp, int ngrp, long long total, unsigned long long *counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ long long item_s;
+  for (;;) {
+    if (threadIdx.x == 0) item_s = (long long)atomicAdd(counter, 1ull);
+    __syncthreads();
+    const long long item = item_s;
+    __syncthreads();
+    if (item >= total) break;
+    int o = 0;
+    while (o + 1 < ngrp && grp[o + 1].first_item <= item) ++o;
+    const PpfGroup &G = grp[o];
+    const long long local = item - G.first_item;
+    const long long sf = local / G.chunks;
+    const int chunk = (int)(local - sf * G.chunks);
+    const int s = (int)(sf / G.g.F), f = (int)(sf - (long long)s * G.g.F);
+    PpfOut po{G.ct, nullptr, nullptr, 0};
+    if (G.bits == 16)
+      ppf_item<16, MODE_CT32>(G.g, (const uint2 *)G.in, (const uint2 *)G.hist, po, s, f, chunk, G.spc, smem_raw);
+    else
+      ppf_item<8, MODE_CT32>(G.g, (const uint32_t *)G.in, (const uint32_t *)G.hist, po, s, f, chunk, G.spc, smem_raw);
+  }
+}
+
+// History update of every observation of a batch: element i of the concatenated histories.
+__global__ void hist_group_kernel(const PpfGroup *__restrict__ grp, int ngrp, long long total) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    int o = 0;
+    while (o + 1 < ngrp && grp[o + 1].first_hist <= i) ++o;
+    const PpfGroup &G = grp[o];
+    const long long j = i - G.first_hist;
+    const long long sf = j / G.g.H;
+    const int e = (int)(j - sf * G.g.H);
+    const long long src = (long long)G.g.T + e;
+    if (G.bits == 16) {
+      const uint2 *in = (const uint2 *)G.in, *h = (const uint2 *)G.hist;
+      ((uint2 *)G.new_hist)[j] = (src < G.g.H) ? h[sf * G.g.H + src] : in[sf * G.g.T + (src - G.g.H)];
+    } else {
+      const uint32_t *in = (const uint32_t *)G.in, *h = (const uint32_t *)G.hist;
+      ((uint32_t *)G.new_hist)[j] = (src < G.g.H) ? h[sf * G.g.H + src] : in[sf * G.g.T + (src - G.g.H)];
+    }
+  }
 }
 
 template <int BITS>
@@ -351,6 +407,27 @@ cudaError_t launch_ppf(const Geometry &g, int bits, const void *in, const void *
   return bits == 16 ? launch_ppf_bits<16>(g, in, hist, chan, ct, ct16, st)
                     : launch_ppf_bits<8>(g, in, hist, chan, ct, ct16, st);
 }
+
+cudaError_t launch_ppf_group(const PpfGroup *d_groups, int ngrp, long long total, unsigned long long *counter,
+                             int ctas, cudaStream_t st) {
+  if (total == 0) return cudaSuccess;
+  const size_t smem = sizeof(PpfSmem<16>);
+  cudaError_t e = cudaFuncSetAttribute(ppf_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  ppf_group_kernel<<<ctas, kThreads, smem, st>>>(d_groups, ngrp, total, counter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hist_group(const PpfGroup *d_groups, int ngrp, long long total, cudaStream_t st) {
+  if (total == 0) return cudaSuccess;
+  const long long want = (total + 255) / 256;
+  hist_group_kernel<<<(unsigned)(want < 152LL * 16 ? want : 152LL * 16), 256, 0, st>>>(d_groups, ngrp, total);
+  return cudaGetLastError();
+}
+
+int ppf_spectra_per_cta() { return kSpectraPerCta; }
 
 cudaError_t launch_hist_update(const Geometry &g, int bits, const void *in, const void *hist,
                                void *new_hist, cudaStream_t st) {

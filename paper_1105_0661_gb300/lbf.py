@@ -25,7 +25,9 @@ BF_VARIANTS = {"auto": 0, "few": 1, "many": 2}
 EXPORTED = ("lbf_plan", "lbf_plan_destroy", "lbf_plan_dims", "lbf_plan_shifts", "lbf_reset_state",
             "lbf_ppf", "lbf_delay_correct", "lbf_beamform", "lbf_beamform_stokes", "lbf_stokes",
             "lbf_run_block", "lbf_run_block_ws", "lbf_run_block_host", "lbf_trace_begin", "lbf_trace_end",
-            "lbf_device_status", "lbf_run_block_static", "lbf_status_string", "lbf_version")
+            "lbf_device_status", "lbf_run_block_static", "lbf_superstation", "lbf_batch_create", "lbf_batch_destroy",
+            "lbf_batch_run", "lbf_batch_capture", "lbf_batch_launch", "lbf_batch_tune",
+            "lbf_status_string", "lbf_version")
 
 
 class LbfError(RuntimeError):
@@ -54,6 +56,12 @@ class _Trace(ctypes.Structure):
     _fields_ = [("n_kernels", ctypes.c_int32), ("launches", ctypes.c_int32 * 16),
                 ("total_ms", ctypes.c_double * 16), ("names", (ctypes.c_char * 32) * 16),
                 ("dropped", ctypes.c_int32)]
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [("n_candidates", ctypes.c_int32), ("spc", ctypes.c_int32 * 6), ("mid_variant", ctypes.c_int32 * 6),
+                ("ms", ctypes.c_double * 6), ("best_spc", ctypes.c_int32), ("best_mid_variant", ctypes.c_int32),
+                ("best_ms", ctypes.c_double)]
 
 
 class _Dims(ctypes.Structure):
@@ -93,7 +101,15 @@ def load_library() -> ctypes.CDLL:
             "lbf_trace_begin": ([vp, ctypes.c_int32], ctypes.c_int),
             "lbf_trace_end": ([vp, ctypes.POINTER(_Trace)], ctypes.c_int),
             "lbf_device_status": ([vp, i32p], ctypes.c_int),
+            "lbf_superstation": ([vp, i32p, ctypes.c_int32, vp, vp, vp], ctypes.c_int),
             "lbf_run_block_static": ([ctypes.POINTER(_Config), vp, vp, vp], ctypes.c_int),
+            "lbf_batch_create": ([ctypes.POINTER(vp), ctypes.c_int32, ctypes.POINTER(vp)], ctypes.c_int),
+            "lbf_batch_destroy": ([vp], ctypes.c_int),
+            "lbf_batch_run": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp], ctypes.c_int),
+            "lbf_batch_capture": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp], ctypes.c_int),
+            "lbf_batch_launch": ([vp, vp], ctypes.c_int),
+            "lbf_batch_tune": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, ctypes.c_int32,
+                                ctypes.POINTER(_Tuning)], ctypes.c_int),
             "lbf_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "lbf_version": ([], ctypes.c_char_p),
         }
@@ -162,7 +178,8 @@ class Plan:
 
     def __init__(self, station_xyz, subband_hz, beam_dlm, phase_centre, taps, block_samples,
                  int_factor=1, output="I", sample_bits=16, bandpass=None, n_channels=256, n_taps=16,
-                 sample_rate_hz=195312.5, precision="fp32", bf_variant="auto", external_workspace=False):
+                 sample_rate_hz=195312.5, precision="fp32", bf_variant="auto", external_workspace=False,
+                 incoherent_beam=False):
         lib = load_library()
         self._keep = [np.ascontiguousarray(station_xyz, dtype=np.float64).reshape(-1, 3),
                       np.ascontiguousarray(subband_hz, dtype=np.float64).reshape(-1),
@@ -177,7 +194,8 @@ class Plan:
         cfg.output = OUTPUTS[output]
         cfg.precision = PRECISIONS[precision]
         cfg.bf_variant = BF_VARIANTS[bf_variant]
-        cfg.flags = 1 if external_workspace else 0
+        cfg.flags = (1 if external_workspace else 0) | (2 if incoherent_beam else 0)
+        self.incoherent_beam = bool(incoherent_beam)
         cfg.sample_rate_hz = sample_rate_hz
         cfg.phase_centre_l, cfg.phase_centre_m = float(phase_centre[0]), float(phase_centre[1])
         dp = ctypes.POINTER(ctypes.c_double)
@@ -213,7 +231,8 @@ class Plan:
         S, F, T, N, M, B = d.n_stations, d.n_subbands, d.block_samples, d.n_channels, d.n_spectra, d.n_beams
         return {"in": (S, F, T, 2, 2), "chan": (F, S, 2, M, N), "ct": (F, N, S, 2, M),
                 "vol": (B, F, N, 2, M),
-                "stokes": (B, d.n_stokes, F, N, M // d.int_factor if d.n_stokes else 0)}[which]
+                "stokes": (B + (1 if self.incoherent_beam and d.n_stokes else 0), d.n_stokes, F, N,
+                           M // d.int_factor if d.n_stokes else 0)}[which]
 
     def shifts(self):
         S = self.dims.n_stations
@@ -275,6 +294,17 @@ class Plan:
                                             _ptr(d_in, d.in_bytes), _ptr(d_out, d.out_bytes),
                                             _stream(stream)), "lbf_run_block_host")
 
+    def superstation(self, group_of_station, d_ct, d_ss, stream=None):
+        """Sum the delay-compensated stations of each group (Section 4.2); d_ss is
+        [F][N][G][P][M] cf32 with G = max(group) + 1."""
+        grp = np.ascontiguousarray(group_of_station, dtype=np.int32).reshape(-1)
+        G = int(grp.max()) + 1
+        d = self.dims
+        need = d.ct_bytes // d.n_stations * G
+        _check(self._lib.lbf_superstation(self._h, grp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), G,
+                                          _ptr(d_ct, d.ct_bytes), _ptr(d_ss, need), _stream(stream)),
+               "lbf_superstation")
+
     def device_status(self) -> int:
         """Synchronise and return the role code of a device-side wait that gave up (0 = none);
         raises LbfError(LBF_ETIMEOUT) when one did."""
@@ -299,6 +329,55 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.lbf_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several plans run together: one persistent grouped launch per stage for a block of every
+    plan (lbf_batch_*), optionally replayed as a CUDA graph and autotuned."""
+
+    def __init__(self, plans):
+        lib = load_library()
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
+        h = ctypes.c_void_p()
+        _check(lib.lbf_batch_create(arr, len(self.plans), ctypes.byref(h)), "lbf_batch_create")
+        self._h, self._lib = h, lib
+
+    def _bufs(self, d_ins, d_outs):
+        ins = (ctypes.c_void_p * len(self.plans))(*[_ptr(x, p.dims.in_bytes) for x, p in zip(d_ins, self.plans)])
+        outs = (ctypes.c_void_p * len(self.plans))(*[_ptr(x, p.dims.out_bytes) for x, p in zip(d_outs, self.plans)])
+        return ins, outs
+
+    def run(self, d_ins, d_outs, stream=None):
+        ins, outs = self._bufs(d_ins, d_outs)
+        _check(self._lib.lbf_batch_run(self._h, ins, outs, _stream(stream)), "lbf_batch_run")
+
+    def capture(self, d_ins, d_outs, stream=None):
+        ins, outs = self._bufs(d_ins, d_outs)
+        _check(self._lib.lbf_batch_capture(self._h, ins, outs, _stream(stream)), "lbf_batch_capture")
+
+    def launch(self, stream=None):
+        _check(self._lib.lbf_batch_launch(self._h, _stream(stream)), "lbf_batch_launch")
+
+    def tune(self, d_ins, d_outs, reps=3, stream=None) -> dict:
+        ins, outs = self._bufs(d_ins, d_outs)
+        t = _Tuning()
+        _check(self._lib.lbf_batch_tune(self._h, ins, outs, _stream(stream), int(reps), ctypes.byref(t)),
+               "lbf_batch_tune")
+        n = t.n_candidates
+        return {"candidates": [{"spc": t.spc[i], "mid_variant": t.mid_variant[i], "ms": t.ms[i]} for i in range(n)],
+                "best_spc": t.best_spc, "best_mid_variant": t.best_mid_variant, "best_ms": t.best_ms}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbf_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

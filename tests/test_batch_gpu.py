@@ -1,0 +1,78 @@
+"""Batches: one persistent grouped launch per stage for a block of every plan gives exactly the
+beams each plan gives alone (same item bodies), over consecutive blocks; the same holds when the
+batch block is replayed as a CUDA graph and after autotuning."""
+
+import numpy as np
+import pytest
+
+from synth import generate as G
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+N = 256
+
+
+def _specs():
+    rng = np.random.default_rng(31)
+    out = []
+    for i, (S, F, B, outk, bits, T) in enumerate([(12, 3, 1, "I", 16, 40 * N), (20, 2, 17, "IQUV", 8, 64 * N),
+                                                  (33, 1, 130, "I", 16, 48 * N), (8, 4, 6, "V", 16, 32 * N),
+                                                  (64, 1, 40, "IQUV", 8, 64 * N)]):
+        xyz = G.lofar_positions(rng, S // 2, S - S // 2)
+        wl = G.Workload(f"b{i}", xyz, G.subband_centres(F, 130e6 + 5e6 * i), G.hex_beam_grid(B, 0.05), (0.3, 0.4),
+                        T, 4 if outk != "V" else 1, outk, sample_bits=bits, sigma=32.0 if bits == 16 else 8.0,
+                        source="tone")
+        out.append(wl)
+    return out
+
+
+def _out(plan, dev):
+    return torch.empty(plan.dims.out_bytes // 4, dtype=torch.float32, device=dev)
+
+
+def test_batch_equals_separate_runs():
+    from paper_1105_0661_gb300 import Batch, Plan, build_lib
+    build_lib.build()
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    wls = _specs()
+    solo = [Plan.from_workload(wl) for wl in wls]
+    grouped = [Plan.from_workload(wl) for wl in wls]
+    batch = Batch(grouped)
+    nblk = 6
+    blocks = [[torch.from_numpy(G.make_block(wl, seed=i, block_index=k)).to(dev) for k in range(nblk)]
+              for i, wl in enumerate(wls)]
+    so = [_out(p, dev) for p in solo]
+    bo = [_out(p, dev) for p in grouped]
+    d_in = [torch.empty_like(blocks[i][0]) for i in range(len(wls))]
+    for k in range(nblk):
+        for i, p in enumerate(solo):
+            p.run_block(blocks[i][k], so[i])
+        for i in range(len(wls)):
+            d_in[i].copy_(blocks[i][k])
+        if k < 2:
+            batch.run(d_in, bo)                   # grouped launches
+        else:
+            if k == 2:
+                batch.capture(d_in, bo)           # then graph replays with fixed buffers
+            batch.launch()
+        torch.cuda.synchronize()
+        for i in range(len(wls)):
+            assert torch.equal(so[i], bo[i]), (k, i)
+    # autotune restarts every stream: compare with fresh plans from the first block on
+    info = batch.tune(d_in, bo, reps=2)
+    assert info["best_spc"] in (64, 128, 256) and len(info["candidates"]) in (3, 6)
+    fresh = [Plan.from_workload(wl) for wl in wls]
+    fo = [_out(p, dev) for p in fresh]
+    for k in range(2):
+        for i in range(len(wls)):
+            fresh[i].run_block(blocks[i][k], fo[i])
+            d_in[i].copy_(blocks[i][k])
+        batch.run(d_in, bo)
+        torch.cuda.synchronize()
+        for i in range(len(wls)):
+            r, g = fo[i].double().cpu().numpy(), bo[i].double().cpu().numpy()
+            scale = np.abs(r).max()
+            assert np.max(np.abs(g - r)) <= 1e-5 * scale, (k, i)
+    batch.close()

@@ -409,3 +409,69 @@ def test_pins_catch_wrong_fft_sign(monkeypatch):
         check_dft_is_numpy_fft(O)
     with pytest.raises(AssertionError):
         check_tone_lands_in_its_channel()
+
+
+# ----------------------------------------------------------------------------- incoherent beam (Section 3)
+def test_incoherent_single_station_equals_coherent_centre_beam():
+    """S = 1 at the origin, beam at the phase centre: the incoherent beam (Stokes of the unweighted
+    station signal) equals the coherent beam."""
+    wl = G.Workload("t", np.zeros((1, 3)), np.array([150e6]), np.zeros((1, 2)), (0.3, 0.4), 16 * N, 4, "IQUV")
+    ob = O.observation_from_workload(wl, incoherent_beam=True)
+    out = ob.run_block(G.make_block(wl, seed=3))
+    assert out.shape[0] == 2
+    assert np.allclose(out[1], out[0], rtol=1e-12, atol=0)
+
+
+def test_incoherent_beam_ignores_delay_phases():
+    """The delay phase has unit modulus and is common to both pols of a station, so the incoherent
+    Stokes parameters equal those of the bandpass-corrected channels without any phase."""
+    rng = np.random.default_rng(13)
+    xyz = G.lofar_positions(rng, 4, 4)
+    bp = G.bandpass_ripple(N)
+    ob = _obs(xyz=xyz, pc=(0.3, 0.4), bp=bp, output="IQUV", Q=4)
+    blk = rng.integers(-300, 300, (8, 1, 16 * N, 2, 2)).astype(np.int16)
+    chan = ob.ppf(blk, advance=False)                                   # [F, S, P, M, N]
+    inc = ob.incoherent(ob.delay_correct(chan))
+    y = chan * bp.astype(np.float64)                                    # no phase
+    p = O.stokes_from_voltages(y[:, :, 0], y[:, :, 1], "IQUV")          # [4, F, S, M, N]
+    ref = O.integrate(np.moveaxis(p.sum(axis=2), -1, 2), 4)             # [4, F, N, M/Q]
+    assert np.allclose(inc, ref, rtol=1e-10, atol=1e-6)
+
+
+def test_incoherent_beam_keeps_an_off_axis_source():
+    """Wide field of view (Section 3): a noise-free tone far outside the coherent beam still gives
+    the incoherent beam S |a|^2 per pol and spectrum in its channel, while the coherent beam at the
+    phase centre gets far less than the S^2 |a|^2 it would get on source."""
+    rng = np.random.default_rng(14)
+    xyz = G.lofar_positions(rng, 6, 10)
+    S = xyz.shape[0]
+    wl = G.Workload("t", xyz, np.array([150e6]), np.zeros((1, 2)), (0.3, 0.4), 16 * N, 4, "I")
+    ob = O.observation_from_workload(wl, incoherent_beam=True)
+    amp, k0 = 20.0, 32
+    hsum = float(np.sum(TAPS.astype(np.float64)))
+    far = (0.3 + np.radians(2.0), 0.4 - np.radians(1.5))
+    for bi in range(2):
+        x = G.tone_signal(wl, amp, k0, far, bi)[..., None] * np.ones(2)
+        out = ob.run_block(x)
+    c = N // 2 + k0
+    inc = out[1, 0, 0, c]                                  # [M/Q]
+    assert np.allclose(inc, S * 2 * 4 * (amp * hsum) ** 2, rtol=1e-9)
+    assert np.max(out[0, 0, 0, c]) < 0.25 * S * np.min(inc)
+
+
+# ----------------------------------------------------------------------------- superstation (Section 4.2)
+def test_superstation_of_all_stations_is_the_phase_centre_beam():
+    """One group holding every station equals the tied-array beam pointed at the phase centre
+    (unit weights); singleton groups reproduce the stations."""
+    rng = np.random.default_rng(15)
+    xyz = G.lofar_positions(rng, 5, 5)
+    ob = _obs(xyz=xyz, pc=(0.3, 0.4), beams=((0.0, 0.0),), bp=G.bandpass_ripple(N))
+    blk = rng.integers(-200, 200, (10, 1, 8 * N, 2, 2)).astype(np.int16)
+    ct = ob.delay_correct(ob.ppf(blk, advance=False))
+    one = ob.superstation(ct, np.zeros(10, dtype=int))             # [F, N, 1, P, M]
+    beam = ob.beamform(ct)                                          # [1, F, N, P, M]
+    assert np.max(np.abs(one[:, :, 0] - beam[0])) <= 1e-10 * np.max(np.abs(beam))
+    ident = ob.superstation(ct, np.arange(10))
+    assert np.array_equal(ident, ct)
+    two = ob.superstation(ct, np.array([0, 1] * 5))
+    assert np.allclose(two[:, :, 0], ct[:, :, 0::2].sum(axis=2)) and np.allclose(two[:, :, 1], ct[:, :, 1::2].sum(axis=2))

@@ -305,3 +305,43 @@ def test_maximum_paper_geometry(dev):
     p.run_block(_to_dev(blk, dev), o)
     _check_stokes(o.cpu().numpy().astype(np.float64), ob.run_block(blk))
     p.close()
+
+
+# ----------------------------------------------------------------------------- incoherent beam
+@pytest.mark.parametrize("variant,prec,bits,out,tol", [("few", "fp32", 16, "IQUV", TOL), ("many", "fp32", 8, "I", TOL),
+                                                       ("auto", "fp16tc", 16, "IQUV", 1e-3), ("auto", "fp16tc", 8, "I", 1e-3)])
+def test_incoherent_beam_matches_oracle(dev, variant, prec, bits, out, tol):
+    """LBF_FLAG_INCOHERENT_BEAM: beam index B of the Stokes output is the incoherent beam
+    (Section 3); the coherent beams are unchanged."""
+    wl = _wl(S=16, B=6 if variant == "few" else 70, out=out, bits=bits, Q=4, T=64 * N)
+    p = _plan(wl, bf_variant=variant, precision=prec, incoherent_beam=True)
+    ob = O.observation_from_workload(wl, incoherent_beam=True)
+    o = torch.empty(p.shape("stokes"), dtype=torch.float32, device=dev)
+    assert o.shape[0] == wl.n_beams + 1
+    for bi in range(2):
+        blk = G.make_block(wl, seed=20, block_index=bi)
+        p.run_block(_to_dev(blk, dev), o)
+        _check_stokes(o.cpu().numpy().astype(np.float64), ob.run_block(blk), tol)
+    p.close()
+
+
+# ----------------------------------------------------------------------------- superstation beam former
+def test_superstation_matches_oracle(dev):
+    wl = _wl(S=12, F=2, T=40 * N)
+    p = _plan(wl)
+    ob = O.observation_from_workload(wl)
+    rng = np.random.default_rng(40)
+    shp = p.shape("ct")
+    ct = (rng.standard_normal(shp) + 1j * rng.standard_normal(shp)).astype(np.complex64)
+    d_ct = _to_dev(ct, dev)
+    for groups in (np.array([0, 0, 1, 1, 1, 2, 0, 2, 1, 0, 2, 2]), np.zeros(12, dtype=int), np.arange(12)):
+        G_ = int(groups.max()) + 1
+        ss = torch.empty((wl.n_subbands, N, G_, 2, 40), dtype=torch.complex64, device=dev)
+        p.superstation(groups, d_ct, ss)
+        ref = ob.superstation(ct.astype(np.complex128), groups)
+        got = ss.cpu().numpy().astype(np.complex128)
+        if G_ == 12:
+            assert np.array_equal(got, ct.astype(np.complex128))
+        else:
+            assert np.max(np.abs(got - ref)) <= 1e-6 * np.max(np.abs(ref))
+    p.close()

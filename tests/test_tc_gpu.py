@@ -1,7 +1,7 @@
 """Tensor-core (tcgen05, FP16 operands, FP32 accumulation) beam former against the FP64 oracle.
 
 Bar (precision form): Stokes I within 1e-3 relative per element; Q, U, V within 1e-3 of I.
-16-bit samples use two FP16 planes (hi + lo), 8-bit samples one plane.  The maximum errors seen are
+Both sample widths use two FP16 planes of the filtered spectrum (hi + lo).  The maximum errors seen are
 printed so that the error of each output is reported.
 """
 
