@@ -4,25 +4,34 @@
 //
 // Per (subband f, channel c) the complex product V = W Y is run as a real GEMM
 //     D[r][n] = sum_k A[r][k] B[k][n],   r = (beam, re|im),  k = (station, re|im),  n = (pol, m)
-// with A rows (Re w, -Im w) / (Im w, Re w): D[2b] = Re V_b, D[2b+1] = Im V_b.  A is K-major and
-// generated by the CTA itself from the FP64-reduced phase tables and an FP32 sincos; B is the
-// filter bank's FP16 scratch [F*N][M/32][Kpad][P][32] (k = 2 station + re|im; a 128-byte row
-// holds the 2 pols x 32 spectra of one k; a tile is one contiguous Kpad x 128-byte region),
-// loaded by TMA as MN-major tiles; both with the 128-byte swizzle.  Both operands are split into FP16 hi and
-// lo = fp16(x - hi) parts; the products Whi Yhi + Whi Ylo + Wlo Yhi accumulate in FP32 into the
-// same TMEM tile, which keeps the error at the level of the FP32 path rather than of FP16
-// rounding.  (With `planes` = 1 the kernel runs Whi Y + Wlo Y; plans always pass 2, because even
-// for 8-bit samples the filtered spectrum Y is not exact in FP16.)
+// with A rows (Re w, -Im w) / (Im w, Re w): D[2b] = Re V_b, D[2b+1] = Im V_b.  Both operands are
+// split into FP16 hi and lo = fp16(x - hi) parts; the products Whi Yhi + Wlo Yhi + Whi Ylo
+// accumulate in FP32 into the same TMEM tile, which keeps the error at the level of the FP32 path
+// rather than of FP16 rounding (the filtered spectrum Y is not exact in FP16 for either sample
+// width, and beams summed with cancellation magnify its rounding).
 //
-// One CTA = one (f, c, block of 128 beams) work item = 2 UMMA M-tiles of 128 rows.  Warp roles:
-// warp 0 issues TMA loads of the B tiles (2 pols x 32 spectra = N 64, one box of Kpad K rows per
-// plane; as many stages as shared memory leaves after the weights, at most 8), warp 1
-// issues the MMAs (M 128 x N 64 x K 16) into a double-buffered TMEM accumulator (2 x 128 cols),
-// warps 2-9 (two per TMEM lane quadrant, one per M tile) drain TMEM with tcgen05.ld, integrate
-// each polarisation component over the window in registers and combine the (Re, Im) row pair
-// with one shuffle per window (plus one per spectrum for Stokes V).  Every mbarrier wait is
-// bounded: on expiry the kernel records an error code, stops issuing work, waits (bounded) for its
-// own copies and MMAs in flight, frees TMEM and returns.
+// Operands.  A (the weights) lives in tensor memory: the epilogue warps compute it from the
+// FP64-reduced phase tables with an FP32 sincos and write it with tcgen05.st, one TMEM lane per
+// row, two FP16 K elements per 32-bit column.  B is the filter bank's FP16 scratch
+// [F*N][Mt][Kpad][P][32] (Mt = ceil(M/64)*2 tiles of 32 spectra; k = 2 station + re|im; a 128-byte
+// row holds the 2 pols x 32 spectra of one k), brought into shared memory by TMA two tiles at a
+// time (one box of 2 x Kpad rows per plane, 128-byte swizzle) and read by the MMA as an MN-major
+// operand of N = 128 columns: two 64-column swizzle atoms, Kpad x 128 bytes apart.
+//
+// Work.  A persistent CTA per SM walks the work items (f, c, block of 128 beams) with a stride of
+// the grid, so the CTAs that run together share the (f, c) B tiles in L2.  An item is two UMMA M
+// tiles of 128 rows (64 beams each) by ceil(M/64) N tiles.  Warp roles: warp 0 issues the TMA
+// loads into a ring of stages, warp 1 issues the MMAs (M 128 x N 128 x K 16), warps 2-9 are the
+// epilogue: warp w serves M tile (w-2)/4 and the TMEM lane quadrant w%4.  Each M tile has one
+// accumulator of 128 columns; the two tiles ping-pong, so that the epilogue drains one while the
+// MMAs fill the other.  At an item boundary the epilogue warps of an M tile write that tile's new
+// weights as soon as its last accumulator has been committed (the MMAs that read the old weights
+// are then complete), while the other tile's MMAs still run.
+//
+// The epilogue integrates each polarisation component over the window in registers (one shuffle
+// per spectrum for Stokes V) and combines the (Re, Im) row pair with two shuffles per window.
+// Every mbarrier wait is bounded: on expiry the kernel records an error code, stops issuing work,
+// waits (bounded) for its own copies and MMAs in flight, frees TMEM and returns.
 #include <cuda.h>
 #include <cuda_fp16.h>
 
@@ -35,25 +44,26 @@ constexpr int kThreads = 320;               // 10 warps: TMA, MMA, 8 epilogue
 constexpr int kRows = 128;                  // UMMA M
 constexpr int kMTiles = 2;                  // 128 beams per work item
 constexpr int kBeamsPerItem = kMTiles * kRows / 2;
-constexpr int kSpec = 32;                   // spectra per N tile
-constexpr int kCols = 2 * kSpec;            // UMMA N (pol X then pol Y)
-constexpr int kKBox = 64;                   // fp16 per 128-byte swizzle row
-constexpr int kMaxKBoxes = 2;               // Kpad <= 128 (S <= 64)
-constexpr int kMaxStages = 8;               // B ring depth bound (the ring fills what A leaves)
-constexpr int kBox = kRows * 128;           // one A box: 128 rows x 128 bytes = 16 KB
-constexpr int kAPlane = kMTiles * kMaxKBoxes * kBox;             // one weight plane, 64 KB
-constexpr int kABytes = 2 * kAPlane;                             // Whi + Wlo, 128 KB
-constexpr int kBarBytes = 1024;                                  // barriers, TMEM slot, flags
+constexpr int kSpec = 32;                   // spectra per scratch tile (one 64-column atom)
+constexpr int kCols = 4 * kSpec;            // UMMA N: two tiles x (pol X, pol Y) x 32 spectra
+constexpr int kMaxKpad = 128;               // S <= 64
+constexpr int kMaxStages = 8;
+constexpr int kBarBytes = 1024;             // barriers, TMEM slot, flags
 constexpr int kSmemLimit = 227 * 1024;
-constexpr int kRingBytes = kSmemLimit - 1024 /* alignment slack */ - kBarBytes - kABytes;
-constexpr uint32_t kTmemCols = 256;
+constexpr int kRingBytes = kSmemLimit - 1024 /* alignment slack */ - kBarBytes;
+constexpr int kMinSmem = 120 * 1024;
+constexpr uint32_t kTmemCols = 512;         // 2 accumulators of 128 + 2 x 2 weight planes of <= 64
+constexpr uint32_t kAccCols = kCols;
+constexpr uint32_t kACol0 = kMTiles * kAccCols;   // weights: tile mt plane pl at kACol0 + (2 mt + pl) 64
 constexpr uint32_t kWaitIters = 1u << 20;
 
 enum ErrCode { ERR_NONE = 0, ERR_PRODUCER = 1, ERR_MMA = 2, ERR_EPILOGUE = 3 };
 
 struct TcParams {
-  int S, F, B, M, Q, nS, Kpad, kboxes, planes, ntiles, items_per_fc;
-  int nstages, stage_bytes;   // B ring: stages of `planes` tiles of Kpad K rows x 128 bytes
+  int S, F, B, M, Kpad, ntiles, items_per_fc;
+  long long items;
+  int nstages, stage_bytes;   // B ring: stages of 2 planes x 2 tiles x Kpad K rows x 128 bytes
+  int vec;                    // output rows 16-byte aligned (M/Q % 4 == 0, aligned base)
   const float *phase0, *step;
   float *out;
   int *err;
@@ -88,7 +98,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
         : "memory");
     if (done) return true;
     if (*abort_flag) return false;
-    if (i > 32) __nanosleep(256);
+    if (i > 64) __nanosleep(64);
   }
   return false;
 }
@@ -106,28 +116,29 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map
       : "memory");
 }
 
-// UMMA shared-memory descriptor, 128-byte swizzle, 8-row (1024 B) atoms.  K-major (the weights):
-// rows along M, atoms 1024 B apart.  MN-major (the samples, N = 64 = one atom wide): 8 K rows of
-// 128 B per atom, atoms along K 1024 B apart; both offset fields carry 1024 B.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+// UMMA shared-memory descriptor of the MN-major B operand with the 128-byte swizzle: atoms of 8 K
+// rows x 128 bytes; the next 8 K rows are 1024 bytes on (stride offset), the next 64 columns
+// `lbo` bytes on (leading offset).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo) {
   uint64_t d = 0;
   d |= (uint64_t)((addr >> 4) & 0x3FFFu);
-  d |= (uint64_t)(1024 >> 4) << 16;             // leading byte offset (unused for one-atom extents)
-  d |= (uint64_t)(1024 >> 4) << 32;             // stride byte offset: next 8-row group
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
   d |= (uint64_t)1 << 46;                       // descriptor version
   d |= (uint64_t)2 << 61;                       // SWIZZLE_128B
   return d;
 }
 
-// Instruction descriptor: kind::f16, D = F32, A = B = F16, A K-major, B MN-major, M = 128, N = 64.
+// Instruction descriptor: kind::f16, D = F32, A = B = F16, A K-major, B MN-major, M = 128, N = 128.
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 16) | ((uint32_t)(kCols >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
 
-__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+// D[tmem] (+)= A[tmem] B[smem]
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-      ::"r"(d_tmem), "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}"
+      ::"r"(d_tmem), "r"(a_tmem), "l"(b), "r"(kIdesc), "r"(accumulate)
       : "memory");
 }
 
@@ -147,51 +158,195 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+               ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+               : "memory");
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Byte offset of element (row, k) inside an M tile of A (or a B stage plane): K-major, 128-byte
-// swizzle (16-byte chunk index XOR row % 8), K boxes of 64 elements 16 KB apart.
-__device__ __forceinline__ uint32_t swz_offset(int row, int k) {
-  const int kb = k >> 6, kk = k & 63;
-  return (uint32_t)(kb * kBox + (row >> 3) * 1024 + (row & 7) * 128 + (((kk >> 3) ^ (row & 7)) << 4) + ((kk & 7) << 1));
+__device__ __forceinline__ uint32_t pack_half2(float lo_k, float hi_k) {
+  const __half2 h = __floats2half2_rn(lo_k, hi_k);   // .x (low 16 bits) is the lower K index
+  return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-template <int NS>
+// Weights of this thread's A row for work item (f, c) into its TMEM lane: column s of plane hi/lo
+// holds (Re w, -Im w) for a Re row and (Im w, Re w) for an Im row.  The two lanes of a beam each
+// evaluate every other station and swap the results; the two warps of a lane quadrant take
+// alternate groups of 8 columns (`half`).
+__device__ __forceinline__ void write_weights(const TcParams &p, uint32_t ta_hi, uint32_t ta_lo, int f, int c, int b,
+                                              int ro, int half) {
+  const bool beam_ok = b < p.B;
+  const float dc = (float)(c - kN / 2);
+  for (int g8 = half; g8 < p.Kpad / 16; g8 += 2) {   // 8 stations per store
+    uint32_t vh[8], vl[8];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int s = g8 * 8 + 2 * j + ro;
+      float2 w = make_float2(0.f, 0.f);
+      if (beam_ok && s < p.S) {
+        const long long bs = (long long)b * p.S + s;
+        const float phi = fmaf(dc, p.step[bs], p.phase0[(long long)f * p.B * p.S + bs]);
+        sincospif(2.0f * phi, &w.y, &w.x);
+      }
+      float2 o;
+      o.x = __shfl_xor_sync(0xffffffffu, w.x, 1);
+      o.y = __shfl_xor_sync(0xffffffffu, w.y, 1);
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {      // station 2j + e of the group
+        const float2 ws = (e == ro) ? w : o;
+        const __half2 hh = __floats2half2_rn(ws.x, ws.y);
+        const float2 hf = __half22float2(hh);
+        const float lx = ws.x - hf.x, ly = ws.y - hf.y;
+        vh[2 * j + e] = ro ? pack_half2(hf.y, hf.x) : pack_half2(hf.x, -hf.y);
+        vl[2 * j + e] = ro ? pack_half2(ly, lx) : pack_half2(lx, -ly);
+      }
+    }
+    tmem_st8(ta_hi + (uint32_t)(g8 * 8), vh);
+    tmem_st8(ta_lo + (uint32_t)(g8 * 8), vl);
+  }
+  tmem_wait_st();
+}
+
+// Output staging.  For Q >= 8 the epilogue collects 8 consecutive windows of every (beam, Stokes
+// parameter) row of its lane quadrant in shared memory and then writes each row segment as two
+// 16-byte stores (a whole 32-byte sector), instead of scattering 4-byte stores over rows that lie
+// megabytes apart.  A quadrant's buffer: 32 beams (16 per M tile) x NS parameters x 8 windows,
+// the 16-byte chunks of a beam XOR-swizzled by the beam index; two buffers alternate.
+template <int NS, int Q>
+struct Stage {
+  static constexpr bool kOn = Q >= 8;
+  static constexpr int kPeriod = Q >= 8 ? Q / 8 : 1;          // tile pairs per flush
+  static constexpr int kRow = NS * 8;                          // floats per beam
+  static constexpr int kBuf = 32 * kRow;                       // floats per quadrant buffer
+  static constexpr int kBytes = kOn ? 4 * 2 * kBuf * 4 : 0;    // 4 quadrants x 2 buffers
+  __device__ static int index(int jq, int param, int wl) {     // float index within a beam's row
+    const int chunk = (param * 2 + (wl >> 2)) ^ (jq & (2 * NS - 1));
+    return chunk * 4 + (wl & 3);
+  }
+};
+
+// One 32-spectrum tile of an accumulator (pol X at `taddr`, pol Y 32 columns on; spectra m0 ..
+// m0 + 31): integrate over windows of Q spectra and store the Stokes parameters, to the staging
+// row `srow` (window wl = w - wbase) or, when staging is off, to the output rows at `orow`.
+template <int NS, int Q>
+__device__ __forceinline__ void drain_tile(uint32_t taddr, int m0, int ro, int jq, int M, bool beam_ok, float *orow,
+                                           long long pstride, float *srow, int wbase) {
+  float x[2][16], y[2][16];
+#pragma unroll
+  for (int ch = 0; ch < 2; ++ch) {
+    tmem_ld16(taddr + (uint32_t)(ch * 16), x[ch]);
+    tmem_ld16(taddr + (uint32_t)(kSpec + ch * 16), y[ch]);
+  }
+  tmem_wait_ld();
+  float sxx = 0.f, syy = 0.f, sxy = 0.f, sv = 0.f;
+#pragma unroll
+  for (int ml = 0; ml < kSpec; ++ml) {
+    const float xv = x[ml >> 4][ml & 15], yv = y[ml >> 4][ml & 15];
+    sxx = fmaf(xv, xv, sxx);
+    syy = fmaf(yv, yv, syy);
+    if (NS == 4) {
+      sxy = fmaf(xv, yv, sxy);
+      sv = fmaf(xv, __shfl_xor_sync(0xffffffffu, yv, 1), sv);   // Im X Re Y (ro 1) or Re X Im Y (ro 0)
+    }
+    if ((ml + 1) % Q == 0) {             // a window ends here (compile-time)
+      const int m = m0 + ml;
+      const bool ok = beam_ok && m < M;
+      const int w = m / Q;
+      if (NS == 1) {
+        const float i_own = sxx + syy;
+        const float I = i_own + __shfl_xor_sync(0xffffffffu, i_own, 1);
+        if (ok && ro == 0) {
+          if (Stage<NS, Q>::kOn) srow[Stage<NS, Q>::index(jq, 0, w - wbase)] = I;
+          else orow[w] = I;
+        }
+      } else {
+        // lane ro 0 ends with (I, Q), lane ro 1 with (U, V): each sends what its partner keeps
+        const float i_own = sxx + syy, q_own = sxx - syy, u_own = sxy, v_own = ro ? sv : -sv;
+        float k0 = ro ? u_own : i_own, k1 = ro ? v_own : q_own;
+        const float s0 = ro ? i_own : u_own, s1 = ro ? q_own : v_own;
+        k0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+        k1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+        if (ro) { k0 *= 2.f; k1 *= 2.f; }
+        if (ok) {
+          const int p0 = ro ? 2 : 0;
+          if (Stage<NS, Q>::kOn) {
+            srow[Stage<NS, Q>::index(jq, p0, w - wbase)] = k0;
+            srow[Stage<NS, Q>::index(jq, p0 + 1, w - wbase)] = k1;
+          } else {
+            orow[p0 * pstride + w] = k0;
+            orow[(p0 + 1) * pstride + w] = k1;
+          }
+        }
+      }
+      sxx = syy = sxy = sv = 0.f;
+    }
+  }
+}
+
+// Write a quadrant's staged windows wbase .. wbase + 7 to the output (64 threads: the quadrant's
+// two epilogue warps; `t64` is the thread's index among them).
+template <int NS, int Q>
+__device__ __forceinline__ void flush_stage(const TcParams &p, const float *buf, int t64, int quad, int bb, int f,
+                                            int c, int wbase) {
+  const int Mq = p.M / Q;
+  for (int i = t64; i < 32 * NS * 2; i += 64) {
+    const int part = i & 1, param = (i >> 1) % NS, bq = (i >> 1) / NS;
+    const int jq = bq & 15, mt = bq >> 4;
+    const int b = bb * kBeamsPerItem + mt * (kRows / 2) + quad * 16 + jq;
+    const int w0 = wbase + part * 4;
+    if (b >= p.B || w0 >= Mq) continue;
+    const float4 v = *reinterpret_cast<const float4 *>(buf + bq * Stage<NS, Q>::kRow +
+                                                       ((param * 2 + part) ^ (jq & (2 * NS - 1))) * 4);
+    float *dst = p.out + ((((long long)b * NS + param) * p.F + f) * kN + c) * Mq + w0;
+    if (p.vec && w0 + 3 < Mq) {
+      *reinterpret_cast<float4 *>(dst) = v;
+    } else {
+      const float e[4] = {v.x, v.y, v.z, v.w};
+      for (int k = 0; k < 4 && w0 + k < Mq; ++k) dst[k] = e[k];
+    }
+  }
+}
+
+template <int NS, int Q>
 __global__ void __launch_bounds__(kThreads, 1)
 bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo, TcParams p) {
+  using St = Stage<NS, Q>;
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   unsigned char *sbase = smem_raw + (base - raw);
   const uint32_t bar0 = base;
-  const uint32_t sA = base + kBarBytes;
-  const uint32_t sB = sA + kABytes;
+  const uint32_t sB = base + kBarBytes;
   auto full_bar = [&](int s) { return bar0 + 8u * s; };                  // kMaxStages
   auto empty_bar = [&](int s) { return bar0 + 64u + 8u * s; };           // kMaxStages
-  auto accf_bar = [&](int s) { return bar0 + 128u + 8u * s; };           // 2
-  auto acce_bar = [&](int s) { return bar0 + 144u + 8u * s; };           // 2
-  const uint32_t drain_bar = bar0 + 160u;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sbase + 168);
-  volatile int *abort_flag = reinterpret_cast<volatile int *>(sbase + 172);
-  unsigned char *sAptr = sbase + kBarBytes;
+  auto accf_bar = [&](int mt) { return bar0 + 128u + 8u * mt; };         // accumulator mt committed
+  auto acce_bar = [&](int mt) { return bar0 + 144u + 8u * mt; };         // accumulator mt drained
+  auto afull_bar = [&](int mt) { return bar0 + 160u + 8u * mt; };        // weights of tile mt written
+  auto pair_bar = [&](int q) { return bar0 + 176u + 8u * q; };           // a quadrant's staging filled
+  const uint32_t drain_bar = bar0 + 208u;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sbase + 224);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(sbase + 228);
   const int nst = p.nstages;
+  float *const stage_out = reinterpret_cast<float *>(sbase + kBarBytes + (size_t)nst * p.stage_bytes);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int fc = blockIdx.x / p.items_per_fc;
-  const int bb = blockIdx.x - fc * p.items_per_fc;
-  const int f = fc / kN, c = fc - f * kN;
 
   if (tid == 0) {
     for (int s = 0; s < nst; ++s) {
       mbar_init(full_bar(s), 1);
       mbar_init(empty_bar(s), 1);
     }
-    for (int s = 0; s < 2; ++s) {
-      mbar_init(accf_bar(s), 1);
-      mbar_init(acce_bar(s), 256);
+    for (int mt = 0; mt < kMTiles; ++mt) {
+      mbar_init(accf_bar(mt), 1);
+      mbar_init(acce_bar(mt), 8);     // one arrival per epilogue warp
+      mbar_init(afull_bar(mt), 8);
     }
+    for (int q = 0; q < 4; ++q) mbar_init(pair_bar(q), 2);
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -202,54 +357,35 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-
-  // ---- weights -> A (rows 2b: (Re w, -Im w), rows 2b+1: (Im w, Re w)) as hi and lo = w - hi
-  //      FP16 planes; pad stations/beams are 0
-  const int half_k = p.Kpad >> 1;
-  for (int i = tid; i < kBeamsPerItem * half_k; i += kThreads) {
-    const int bl = i / half_k, s = i - bl * half_k;
-    const int b = bb * kBeamsPerItem + bl;
-    float2 w = make_float2(0.f, 0.f);
-    if (b < p.B && s < p.S) {
-      const long long bs = (long long)b * p.S + s;
-      const float phi = fmaf((float)(c - kN / 2), p.step[bs], p.phase0[(long long)f * p.B * p.S + bs]);
-      sincospif(2.0f * phi, &w.y, &w.x);
-    }
-    const int mt = bl >> 6, r0 = (2 * bl) & (kRows - 1);
-    unsigned char *At = sAptr + mt * kMaxKBoxes * kBox;
-    const __half2 hi = __floats2half2_rn(w.x, w.y);
-    const float2 hf = __half22float2(hi);
-    const __half2 lo = __floats2half2_rn(w.x - hf.x, w.y - hf.y);
-    *reinterpret_cast<__half2 *>(At + swz_offset(r0, 2 * s)) = __halves2half2(__low2half(hi), __hneg(__high2half(hi)));
-    *reinterpret_cast<__half2 *>(At + swz_offset(r0 + 1, 2 * s)) = __halves2half2(__high2half(hi), __low2half(hi));
-    *reinterpret_cast<__half2 *>(At + kAPlane + swz_offset(r0, 2 * s)) = __halves2half2(__low2half(lo), __hneg(__high2half(lo)));
-    *reinterpret_cast<__half2 *>(At + kAPlane + swz_offset(r0 + 1, 2 * s)) = __halves2half2(__high2half(lo), __low2half(lo));
-  }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  const uint32_t plane_bytes = (uint32_t)(2 * p.Kpad * 128);   // two tiles of one plane
 
   if (warp == 0) {
     // ---------------------------------------------------------------- TMA producer
     if (lane == 0) {
       const uint32_t bytes = (uint32_t)p.stage_bytes;
-      const uint32_t plane_bytes = (uint32_t)(p.Kpad * 128);
-      int last_issued = -1;
-      for (int t = 0; t < p.ntiles; ++t) {
-        const int s = t % nst;
-        const uint32_t ph = (uint32_t)(t / nst) & 1u;
-        if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag)) { fail(abort_flag, p.err, ERR_PRODUCER); break; }
-        mbar_expect_tx(full_bar(s), bytes);
-        for (int pl = 0; pl < p.planes; ++pl)   // one box per plane: Kpad K rows x (2 pols x 32 spectra)
-          tma_load_4d(sB + (uint32_t)s * bytes + pl * plane_bytes, pl ? &tm_lo : &tm_hi, 0, 0, t, fc, full_bar(s));
-        last_issued = t;
+      long long g = 0, last_issued = -1;
+      bool ok = true;
+      for (long long item = blockIdx.x; item < p.items && ok; item += gridDim.x) {
+        const int fc = (int)(item / p.items_per_fc);
+        for (int t = 0; t < p.ntiles; ++t, ++g) {
+          const int s = (int)(g % nst);
+          const uint32_t ph = (uint32_t)(g / nst) & 1u;
+          if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag)) { fail(abort_flag, p.err, ERR_PRODUCER); ok = false; break; }
+          mbar_expect_tx(full_bar(s), bytes);
+          const uint32_t dst = sB + (uint32_t)s * bytes;
+          tma_load_4d(dst, &tm_hi, 0, 0, 2 * t, fc, full_bar(s));
+          tma_load_4d(dst + plane_bytes, &tm_lo, 0, 0, 2 * t, fc, full_bar(s));
+          last_issued = g;
+        }
       }
       if (*abort_flag) {   // let our own copies land before the CTA's shared memory goes away
-        for (int t = (last_issued - nst + 1 > 0 ? last_issued - nst + 1 : 0); t <= last_issued; ++t) {
+        for (long long q = (last_issued - nst + 1 > 0 ? last_issued - nst + 1 : 0); q <= last_issued; ++q) {
           volatile int never = 0;
-          mbar_wait(full_bar(t % nst), (uint32_t)(t / nst) & 1u, &never);
+          mbar_wait(full_bar((int)(q % nst)), (uint32_t)(q / nst) & 1u, &never);
         }
       }
     }
@@ -257,30 +393,40 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
       const int ksteps = p.Kpad >> 4;
-      bool issued = false;
-      for (int t = 0; t < p.ntiles; ++t) {
-        const int s = t % nst, ab = t & 1;
-        const uint32_t ph = (uint32_t)(t / nst) & 1u, aph = (uint32_t)(t >> 1) & 1u;
-        if (!mbar_wait(acce_bar(ab), aph ^ 1u, abort_flag)) { fail(abort_flag, p.err, ERR_MMA); break; }
-        if (!mbar_wait(full_bar(s), ph, abort_flag)) { fail(abort_flag, p.err, ERR_MMA); break; }
-        tc_fence_after();
-        for (int mt = 0; mt < kMTiles; ++mt) {
-          const uint32_t d = tmem + (uint32_t)(ab * 2 * kCols + mt * kCols);
-          for (int ks = 0; ks < ksteps; ++ks) {
-            const int kb = ks >> 2, kin = ks & 3;
-            const uint32_t aoff = (uint32_t)(mt * kMaxKBoxes * kBox + kb * kBox + kin * 32);
-            const uint64_t a_hi = smem_desc(sA + aoff), a_lo = smem_desc(sA + kAPlane + aoff);
-            const uint32_t boff = (uint32_t)(s * p.stage_bytes + ks * 16 * 128);   // 16 K rows per step
-            const uint64_t b_hi = smem_desc(sB + boff);
-            umma(d, a_hi, b_hi, ks != 0);                  // Whi Yhi
-            umma(d, a_lo, b_hi, 1);                        // Wlo Yhi
-            if (p.planes > 1)                              // Whi Ylo
-              umma(d, a_hi, smem_desc(sB + boff + (uint32_t)(p.Kpad * 128)), 1);
+      const uint32_t tile_bytes = (uint32_t)(p.Kpad * 128);
+      bool issued = false, ok = true;
+      long long g = 0;
+      int it = 0;
+      for (long long item = blockIdx.x; item < p.items && ok; item += gridDim.x, ++it) {
+        for (int t = 0; t < p.ntiles && ok; ++t, ++g) {
+          const int s = (int)(g % nst);
+          const uint32_t ph = (uint32_t)(g / nst) & 1u;
+          if (!mbar_wait(full_bar(s), ph, abort_flag)) { fail(abort_flag, p.err, ERR_MMA); ok = false; break; }
+          for (int mt = 0; mt < kMTiles; ++mt) {
+            if (t == 0 && !mbar_wait(afull_bar(mt), (uint32_t)it & 1u, abort_flag)) {
+              fail(abort_flag, p.err, ERR_MMA); ok = false; break;
+            }
+            if (!mbar_wait(acce_bar(mt), ((uint32_t)g & 1u) ^ 1u, abort_flag)) {
+              fail(abort_flag, p.err, ERR_MMA); ok = false; break;
+            }
+            tc_fence_after();
+            const uint32_t d = tmem + (uint32_t)(mt * kAccCols);
+            const uint32_t a_hi = tmem + kACol0 + (uint32_t)(2 * mt * 64), a_lo = a_hi + 64u;
+            const uint32_t b0 = sB + (uint32_t)s * (uint32_t)p.stage_bytes;
+            for (int ks = 0; ks < ksteps; ++ks) {
+              const uint32_t boff = (uint32_t)(ks * 16 * 128);            // 16 K rows per step
+              const uint64_t b_hi = smem_desc(b0 + boff, tile_bytes);
+              const uint64_t b_lo = smem_desc(b0 + plane_bytes + boff, tile_bytes);
+              const uint32_t ac = (uint32_t)(ks * 8);                     // 16 K elements = 8 columns
+              umma(d, a_hi + ac, b_hi, ks != 0);   // Whi Yhi
+              umma(d, a_lo + ac, b_hi, 1);         // Wlo Yhi
+              umma(d, a_hi + ac, b_lo, 1);         // Whi Ylo
+            }
+            umma_commit(accf_bar(mt));
+            issued = true;
           }
+          if (ok) umma_commit(empty_bar(s));
         }
-        umma_commit(empty_bar(s));
-        umma_commit(accf_bar(ab));
-        issued = true;
       }
       if (issued) {   // every MMA (and its barrier arrivals) retired before TMEM is released
         umma_commit(drain_bar);
@@ -289,68 +435,68 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
       }
     }
   } else {
-    // ---------------------------------------------------------------- epilogue: TMEM -> Stokes
-    const int quad = warp & 3;            // TMEM lanes 32*quad .. +31 are this warp's
-    const int mt = (warp - 2) >> 2;       // and this M tile
-    const int row = quad * 32 + lane;     // row within the M tile
-    const int ro = row & 1;               // 0: Re V, 1: Im V
-    const int b = bb * kBeamsPerItem + mt * (kRows / 2) + (row >> 1);
-    const int Mq = p.M / p.Q;
-    for (int t = 0; t < p.ntiles; ++t) {
-      const int ab = t & 1;
-      const uint32_t aph = (uint32_t)(t >> 1) & 1u;
-      if (!mbar_wait(accf_bar(ab), aph, abort_flag)) { fail(abort_flag, p.err, ERR_EPILOGUE); break; }
-      tc_fence_after();
-      const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(ab * 2 * kCols + mt * kCols);
-      // this thread's component x of pol X and y of pol Y, integrated over the window:
-      // sxx = sum x^2, syy = sum y^2, sxy = sum x y, sv = sum of its half of (Im X Re Y - Re X Im Y)
-      float sxx = 0.f, syy = 0.f, sxy = 0.f, sv = 0.f;
-#pragma unroll
-      for (int ch = 0; ch < kSpec / 16; ++ch) {
-        float x[16], y[16];
-        tmem_ld16(taddr + (uint32_t)(ch * 16), x);
-        tmem_ld16(taddr + (uint32_t)(kSpec + ch * 16), y);
-        tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          sxx = fmaf(x[j], x[j], sxx);
-          syy = fmaf(y[j], y[j], syy);
-          if (NS == 4) {
-            sxy = fmaf(x[j], y[j], sxy);
-            const float yo = __shfl_xor_sync(0xffffffffu, y[j], 1);   // partner's component of Y
-            sv = fmaf(ro ? x[j] : -x[j], yo, sv);                      // ro 1: Im X Re Y, ro 0: -Re X Im Y
-          }
-          const int ml = ch * 16 + j;
-          if (((ml + 1) & (p.Q - 1)) == 0) {   // window complete (uniform across the warp)
-            const int m = t * kSpec + ml;
-            const float i_own = sxx + syy;
-            const float I = i_own + __shfl_xor_sync(0xffffffffu, i_own, 1);
-            float* const orow0 = p.out + ((((long long)b * NS) * p.F + f) * kN + c) * Mq;
-            const bool ok = b < p.B && m < p.M;
-            if (NS == 1) {
-              if (ok && ro == 0) orow0[m / p.Q] = I;
-            } else {
-              const float q_own = sxx - syy;
-              const float Qs = q_own + __shfl_xor_sync(0xffffffffu, q_own, 1);
-              const float U = 2.f * (sxy + __shfl_xor_sync(0xffffffffu, sxy, 1));
-              const float V = 2.f * (sv + __shfl_xor_sync(0xffffffffu, sv, 1));
-              const long long pstride = (long long)p.F * kN * Mq;      // between Stokes parameters
-              if (ok) {
-                if (ro == 0) {
-                  orow0[m / p.Q] = I;
-                  orow0[pstride + m / p.Q] = Qs;
-                } else {
-                  orow0[2 * pstride + m / p.Q] = U;
-                  orow0[3 * pstride + m / p.Q] = V;
-                }
-              }
-            }
-            sxx = syy = sxy = sv = 0.f;
-          }
+    // ---------------------------------------------------------------- epilogue: weights, TMEM -> Stokes
+    // warp (quad, half): TMEM lanes 32 quad .. +31 of both M tiles; weight columns of groups
+    // g8 = half (mod 2); accumulator tile 2t + half of every tile pair t
+    const int quad = warp & 3, half = (warp - 2) >> 2;
+    const int ro = lane & 1;              // 0: Re V rows, 1: Im V rows
+    const int jq = lane >> 1;             // beam within the quadrant (16 per M tile)
+    const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
+    const int Mq = p.M / Q;
+    const long long pstride = (long long)p.F * kN * Mq;      // between Stokes parameters
+    float *const qbuf = stage_out + quad * 2 * St::kBuf;
+    long long g = 0;
+    int fl = 0;
+    bool ok = true;
+    for (long long item = blockIdx.x; item < p.items && ok; item += gridDim.x) {
+      const int fc = (int)(item / p.items_per_fc);
+      const int bb = (int)(item - (long long)fc * p.items_per_fc);
+      const int f = fc / kN, c = fc - f * kN;
+      if (item == blockIdx.x) {           // weights of the first item; later ones follow each last tile
+        for (int mt = 0; mt < kMTiles; ++mt) {
+          const uint32_t ta_hi = tmem + lane_off + kACol0 + (uint32_t)(2 * mt * 64);
+          write_weights(p, ta_hi, ta_hi + 64u, f, c, bb * kBeamsPerItem + mt * (kRows / 2) + quad * 16 + jq, ro, half);
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(afull_bar(mt));
         }
       }
-      tc_fence_before();
-      mbar_arrive(acce_bar(ab));
+      const long long nitem = item + gridDim.x;
+      const int nfc = (int)(nitem / p.items_per_fc);
+      const int nbb = (int)(nitem - (long long)nfc * p.items_per_fc);
+      for (int t = 0; t < p.ntiles && ok; ++t, ++g) {
+        const int wbase = (t / St::kPeriod) * 8;
+        float *const buf = qbuf + (fl & 1) * St::kBuf;
+        for (int mt = 0; mt < kMTiles; ++mt) {
+          if (!mbar_wait(accf_bar(mt), (uint32_t)g & 1u, abort_flag)) { fail(abort_flag, p.err, ERR_EPILOGUE); ok = false; break; }
+          tc_fence_after();
+          const int b = bb * kBeamsPerItem + mt * (kRows / 2) + quad * 16 + jq;
+          float *const orow = p.out + (((long long)b * NS * p.F + f) * kN + c) * Mq;
+          drain_tile<NS, Q>(tmem + lane_off + (uint32_t)(mt * kAccCols + half * 2 * kSpec), t * 4 * kSpec / 2 + half * kSpec,
+                            ro, jq, p.M, b < p.B, orow, pstride, buf + (mt * 16 + jq) * St::kRow, wbase);
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(acce_bar(mt));
+          if (t == p.ntiles - 1 && nitem < p.items) {
+            // the MMAs that read this tile's weights are complete (its last accumulator was
+            // committed): write the next item's
+            const uint32_t ta_hi = tmem + lane_off + kACol0 + (uint32_t)(2 * mt * 64);
+            write_weights(p, ta_hi, ta_hi + 64u, nfc / kN, nfc % kN,
+                          nbb * kBeamsPerItem + mt * (kRows / 2) + quad * 16 + jq, ro, half);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(afull_bar(mt));
+          }
+        }
+        if (St::kOn && ok && ((t + 1) % St::kPeriod == 0 || t == p.ntiles - 1)) {
+          // both warps of the quadrant have staged their windows: write the rows out
+          __syncwarp();
+          if (lane == 0) mbar_arrive(pair_bar(quad));
+          if (!mbar_wait(pair_bar(quad), (uint32_t)fl & 1u, abort_flag)) { fail(abort_flag, p.err, ERR_EPILOGUE); ok = false; break; }
+          flush_stage<NS, Q>(p, buf, half * 32 + lane, quad, bb, f, c, wbase);
+          ++fl;
+        }
+      }
     }
   }
 
@@ -362,42 +508,72 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
   }
 }
 
+template <int NS, int Q>
+cudaError_t launch_q(const CUtensorMap *hi, const CUtensorMap *lo, TcParams p, int grid, cudaStream_t st) {
+  // B ring: as many stages as shared memory leaves after the barriers and the output staging
+  p.nstages = (kRingBytes - Stage<NS, Q>::kBytes) / p.stage_bytes;
+  if (p.nstages > kMaxStages) p.nstages = kMaxStages;
+  if (p.nstages < 2) return cudaErrorInvalidValue;
+  int smem = 1024 + kBarBytes + p.nstages * p.stage_bytes + Stage<NS, Q>::kBytes;
+  // at least half of an SM's shared memory, so that no two CTAs share an SM (each holds all of
+  // its TMEM columns)
+  if (smem < kMinSmem) smem = kMinSmem;
+  cudaError_t e = cudaFuncSetAttribute(bf_tc_kernel<NS, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  bf_tc_kernel<NS, Q><<<grid, kThreads, smem, st>>>(*hi, *lo, p);
+  return cudaGetLastError();
+}
+
+template <int NS>
+cudaError_t launch_ns(int Q, const CUtensorMap *hi, const CUtensorMap *lo, const TcParams &p, int grid,
+                      cudaStream_t st) {
+  switch (Q) {
+    case 1: return launch_q<NS, 1>(hi, lo, p, grid, st);
+    case 2: return launch_q<NS, 2>(hi, lo, p, grid, st);
+    case 4: return launch_q<NS, 4>(hi, lo, p, grid, st);
+    case 8: return launch_q<NS, 8>(hi, lo, p, grid, st);
+    case 16: return launch_q<NS, 16>(hi, lo, p, grid, st);
+    case 32: return launch_q<NS, 32>(hi, lo, p, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int sm_count() {
+  static int n[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  if (!n[dev] && cudaDeviceGetAttribute(&n[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n[dev] = 0;
+  return n[dev];
+}
+
 }  // namespace
 
-int tc_max_stations() { return kMaxKBoxes * kKBox / 2; }
+int tc_max_stations() { return kMaxKpad / 2; }
 int tc_spectra_per_tile() { return kSpec; }
 int tc_kpad(int S) { return ((2 * S + 15) / 16) * 16; }
 
-cudaError_t launch_bf_tc(const Geometry &g, int out_kind, const void *tm_hi, const void *tm_lo, int planes,
-                         float *out, int *err, cudaStream_t st) {
+cudaError_t launch_bf_tc(const Geometry &g, int out_kind, const void *tm_hi, const void *tm_lo, float *out, int *err,
+                         cudaStream_t st) {
   if (g.M == 0 || g.B == 0) return cudaSuccess;
+  if (!tm_hi || !tm_lo || g.S > tc_max_stations()) return cudaErrorInvalidValue;
   TcParams p;
-  p.S = g.S; p.F = g.F; p.B = g.B; p.M = g.M; p.Q = g.Q;
-  p.nS = out_kind == OUT_STOKES_IQUV ? 4 : 1;
+  p.S = g.S; p.F = g.F; p.B = g.B; p.M = g.M;
   p.Kpad = tc_kpad(g.S);
-  p.kboxes = (p.Kpad + kKBox - 1) / kKBox;
-  p.stage_bytes = planes * p.Kpad * 128;
-  p.nstages = kRingBytes / p.stage_bytes;
-  if (p.nstages > kMaxStages) p.nstages = kMaxStages;
-  const int smem_bytes = 1024 + kBarBytes + kABytes + p.nstages * p.stage_bytes;
-  p.planes = planes;
-  p.ntiles = (g.M + kSpec - 1) / kSpec;
+  p.stage_bytes = 4 * p.Kpad * 128;
+  p.nstages = 0;
+  p.ntiles = tc_tiles(g.M) / 2;
   p.items_per_fc = (g.B + kBeamsPerItem - 1) / kBeamsPerItem;
-  p.phase0 = g.phase0; p.step = g.step; p.out = reinterpret_cast<float *>(out); p.err = err;
-  const long long ctas = (long long)g.F * kN * p.items_per_fc;
+  p.items = (long long)g.F * kN * p.items_per_fc;
+  p.phase0 = g.phase0; p.step = g.step; p.out = out; p.err = err;
+  p.vec = (g.M / g.Q) % 4 == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+  const int sms = sm_count();
+  if (sms <= 0) return cudaErrorInvalidDevice;
+  const int grid = (int)(p.items < sms ? p.items : sms);
   const CUtensorMap *hi = reinterpret_cast<const CUtensorMap *>(tm_hi);
-  const CUtensorMap *lo = reinterpret_cast<const CUtensorMap *>(tm_lo ? tm_lo : tm_hi);
-  cudaError_t e;
-  if (p.nS == 4) {
-    e = cudaFuncSetAttribute(bf_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-    if (e != cudaSuccess) return e;
-    bf_tc_kernel<4><<<(unsigned)ctas, kThreads, smem_bytes, st>>>(*hi, *lo, p);
-  } else {
-    e = cudaFuncSetAttribute(bf_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-    if (e != cudaSuccess) return e;
-    bf_tc_kernel<1><<<(unsigned)ctas, kThreads, smem_bytes, st>>>(*hi, *lo, p);
-  }
-  return cudaGetLastError();
+  const CUtensorMap *lo = reinterpret_cast<const CUtensorMap *>(tm_lo);
+  if (out_kind == OUT_STOKES_IQUV) return launch_ns<4>(g.Q, hi, lo, p, grid, st);
+  if (out_kind == OUT_STOKES_I) return launch_ns<1>(g.Q, hi, lo, p, grid, st);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace lbf

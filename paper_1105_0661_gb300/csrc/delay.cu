@@ -50,13 +50,13 @@ delay_ct_kernel(Geometry g, const float2 *__restrict__ chan, float2 *__restrict_
   }
 }
 
-// ct [F][N][S][P][M] cf32 -> FP16 planes [F*N][Mb][kpad][P][32] (rows k = 2s re, 2s+1 im): an
+// ct [F][N][S][P][M] cf32 -> FP16 planes [F*N][Mt][kpad][P][32] (rows k = 2s re, 2s+1 im): an
 // elementwise split, both sides spectrum-fastest, so reads and writes are coalesced as they are.
 __global__ void __launch_bounds__(256)
 ct_to_ct16_kernel(Geometry g, const float2 *__restrict__ ct, Ct16Out o, long long n) {
   __half *hi = reinterpret_cast<__half *>(o.hi);
   __half *lo = reinterpret_cast<__half *>(o.lo);
-  const int mb = (g.M + 31) >> 5;
+  const int mb = tc_tiles(g.M);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const int m = (int)(i % g.M);
     const long long r = i / g.M;                             // (fc * S + s) * P + pol
@@ -77,7 +77,7 @@ ct_to_ct16_kernel(Geometry g, const float2 *__restrict__ ct, Ct16Out o, long lon
   }
 }
 
-// Incoherent beam of a tensor-core plan (Section 3) from its FP16 planes [F*N][Mb][kpad][P][32]:
+// Incoherent beam of a tensor-core plan (Section 3) from its FP16 planes [F*N][Mt][kpad][P][32]:
 // thread per (subband-channel, spectrum), summing over stations the Stokes parameters of
 // Y = hi (+ lo); writes beam index B of the Stokes output.  Lane l of a warp holds spectrum
 // 32 w + l, so the integration over Q <= 32 spectra is a warp-shuffle reduction.
@@ -86,11 +86,12 @@ __global__ void __launch_bounds__(256)
 incoherent_ct16_kernel(Geometry g, Ct16Out o, float *__restrict__ out) {
   const __half *hi = reinterpret_cast<const __half *>(o.hi);
   const __half *lo = reinterpret_cast<const __half *>(o.lo);
-  const int mb = (g.M + 31) >> 5;
+  const int mb = tc_tiles(g.M);
+  const int mspan = (g.M + 31) & ~31;
   const long long fc = blockIdx.x;
   const int f = (int)(fc / kN), c = (int)(fc - (long long)f * kN);
   const int Mq = g.M / g.Q;
-  for (int m0 = 0; m0 < mb * 32; m0 += blockDim.x) {
+  for (int m0 = 0; m0 < mspan; m0 += blockDim.x) {
     const int m = m0 + threadIdx.x;
     const bool active = m < g.M;
     float xx = 0.f, yy = 0.f, re = 0.f, im = 0.f;

@@ -92,9 +92,9 @@ lbf_status validate(const lbf_config *c) {
 
 bool valid_plan(lbf_plan_t p) { return p && p->magic == kMagic; }
 
-// TMA descriptor of one FP16 plane [F*N][Mb][kpad][P][32] (Mb = ceil(M/32) blocks of 32 spectra;
-// a block's kpad K rows hold the two pols side by side, 128 bytes per row, so one beam-former tile
-// is one contiguous kpad x 128-byte region): boxes of 64 halves x kpad rows, 128-byte swizzle.
+// TMA descriptor of one FP16 plane [F*N][Mt][kpad][P][32] (Mt = tc_tiles(M), an even number of
+// tiles of 32 spectra; a tile's kpad K rows hold the two pols side by side, 128 bytes per row, so
+// a tile is one contiguous kpad x 128-byte region): boxes of two tiles, 128-byte swizzle.
 cudaError_t encode_ct16_map(CUtensorMap *map, void *base, int kpad, int M, long long fc_rows) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
@@ -105,10 +105,10 @@ cudaError_t encode_ct16_map(CUtensorMap *map, void *base, int kpad, int M, long 
       return cudaErrorNotSupported;
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
-  const cuuint64_t mb = (cuuint64_t)(M + 31) / 32;
+  const cuuint64_t mb = (cuuint64_t)lbf::tc_tiles(M);
   const cuuint64_t dims[4] = {64, (cuuint64_t)kpad, mb, (cuuint64_t)fc_rows};
   const cuuint64_t strides[3] = {128, (cuuint64_t)kpad * 128, mb * kpad * 128};
-  const cuuint32_t box[4] = {64, (cuuint32_t)kpad, 1, 1};   // one tile: all K rows of one block
+  const cuuint32_t box[4] = {64, (cuuint32_t)kpad, 2, 1};   // two tiles: all K rows of 64 spectra
   const cuuint32_t elem[4] = {1, 1, 1, 1};
   CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, base, dims, strides, box, elem,
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -203,8 +203,7 @@ cudaError_t run_block_device(lbf_plan_t p, const void *d_in, void *d_out, void *
       if (e != cudaSuccess) return e;
     }
     return traced(p, K_BF_TC, st, [&] {
-      return lbf::launch_bf_tc(g, p->out_kind, &maps[0], p->planes > 1 ? &maps[1] : nullptr, p->planes,
-                               (float *)d_out, p->d_err, st); });
+      return lbf::launch_bf_tc(g, p->out_kind, &maps[0], &maps[1], (float *)d_out, p->d_err, st); });
   }
   float2 *ct = static_cast<float2 *>(ws);
   cudaError_t e = traced(p, K_PPF_CT, st, [&] { return lbf::launch_ppf(g, p->bits, d_in, h, nullptr, ct, st); });
@@ -321,7 +320,7 @@ lbf_status lbf_plan(const lbf_config *cfg, lbf_plan_t *out) {
     // magnifies that rounding past 1e-3 on Stokes I.
     p->kpad = lbf::tc_kpad(p->S);
     p->planes = 2;
-    p->ct16_bytes = (size_t)p->F * p->N * p->kpad * ((p->M + 31) / 32) * 64 * 2;
+    p->ct16_bytes = (size_t)p->F * p->N * p->kpad * lbf::tc_tiles(p->M) * 64 * 2;
     p->ws_need = p->planes * p->ct16_bytes;
     if (!p->external_ws && e == cudaSuccess) {
       e = cudaMalloc(&p->ct16[0], p->ws_need ? p->ws_need : 16);
@@ -450,8 +449,7 @@ lbf_status lbf_beamform_stokes(lbf_plan_t p, const void *d_ct, float *d_out, voi
       e = traced(p, K_INC16, st, [&] { return lbf::launch_incoherent_ct16(g, p->out_kind, o, d_out, st); });
     if (e != cudaSuccess) return cuda_status(e);
     return cuda_status(traced(p, K_BF_TC, st, [&] {
-      return lbf::launch_bf_tc(g, p->out_kind, &p->tmap[0], p->planes > 1 ? &p->tmap[1] : nullptr, p->planes, d_out,
-                               p->d_err, st); }));
+      return lbf::launch_bf_tc(g, p->out_kind, &p->tmap[0], &p->tmap[1], d_out, p->d_err, st); }));
   }
   return cuda_status(traced(p, bf_kernel_id(p), st, [&] {
     return lbf::launch_beamform(g, p->variant, p->out_kind, (const float2 *)d_ct, d_out, st); }));
@@ -490,7 +488,7 @@ lbf_status lbf_run_block_ws(lbf_plan_t p, const void *d_in, void *d_out, void *d
     cudaError_t e = encode_planes(p, d_ws, maps);
     // pad rows k in [2S, kpad) of each (subband, channel, spectrum block) must read as zero
     const size_t row = 128;   // bytes of one K row
-    const size_t blocks = (size_t)p->F * p->N * ((p->M + 31) / 32);
+    const size_t blocks = (size_t)p->F * p->N * lbf::tc_tiles(p->M);
     for (int i = 0; i < p->planes && e == cudaSuccess && p->kpad > 2 * p->S; ++i)
       e = cudaMemset2DAsync(static_cast<unsigned char *>(d_ws) + i * p->ct16_bytes + 2 * p->S * row,
                             p->kpad * row, 0, (p->kpad - 2 * p->S) * row, blocks, st);

@@ -31,12 +31,14 @@ struct Geometry {
 
 enum OutKind { OUT_VOLTAGES = 0, OUT_STOKES_I = 1, OUT_STOKES_IQUV = 4 };
 
-// FP16 corner-turned scratch of the tensor-core beam former: [F*N][ceil(M/32)][kpad][P][32]
-// halves per plane (k = 2 station + re|im; blocks of 32 spectra, the two pols side by side).
+// FP16 corner-turned scratch of the tensor-core beam former: [F*N][Mt][kpad][P][32] halves per
+// plane (k = 2 station + re|im; tiles of 32 spectra, the two pols side by side), Mt = tc_tiles(M)
+// an even count so that the beam former reads tiles in pairs.
 struct Ct16Out {
   void *hi, *lo;   // lo may be null (single-product form)
   int kpad;        // 2 S rounded up to a multiple of 16
 };
+__host__ __device__ inline int tc_tiles(int M) { return ((M + 63) / 64) * 2; }
 
 // One observation of a batch (grouped persistent launches, batch.cu): its geometry, this
 // block's buffers, and its range of work items in the grouped filter bank and beam former.
@@ -84,8 +86,8 @@ cudaError_t launch_superstation(const Geometry &g, const float2 *ct, float2 *ss,
 // incoherent beam (index B of the Stokes output) from the FP16 planes of a tensor-core plan
 cudaError_t launch_incoherent_ct16(const Geometry &g, int out_kind, const Ct16Out &o, float *out, cudaStream_t st);
 // tcgen05 beam former with fused Stokes epilogue (bf_tc.cu); tm_hi/tm_lo are CUtensorMap*
-cudaError_t launch_bf_tc(const Geometry &g, int out_kind, const void *tm_hi, const void *tm_lo, int planes,
-                         float *out, int *err, cudaStream_t st);
+cudaError_t launch_bf_tc(const Geometry &g, int out_kind, const void *tm_hi, const void *tm_lo, float *out, int *err,
+                         cudaStream_t st);
 int tc_max_stations();
 int tc_spectra_per_tile();   // TMA box height of the FP16 scratch (spectra per N tile)
 int tc_kpad(int S);

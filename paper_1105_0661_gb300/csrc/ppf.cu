@@ -234,7 +234,7 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
       __syncthreads();
       // [F*N][Mb][Kpad][P][32]: rows k = 2s (re) and 2s+1 (im), runs of 16 spectra (32 B)
       const int q = tid & 15;
-      const int mb = (g.M + 31) >> 5;
+      const int mb = tc_tiles(g.M);
       const int m = mt + q;
       if (m < m_end) {
 #pragma unroll 4

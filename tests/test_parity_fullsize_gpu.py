@@ -80,3 +80,33 @@ def test_lofar_full_size_sampled(dev):
         got = out[:, :, f][:, :, chans].double().cpu().numpy()
         _check_I(got, ref)
     plan.close()
+
+
+@pytest.mark.parametrize("bits", [8, 16])
+def test_lofar1024_tensor_core_full_size_sampled(dev, bits):
+    """The precision form at full size (48 stations x 244 subbands x 196608 samples, 1024 beams,
+    Stokes IQUV over 16, FP16 tensor cores): sampled (subband, channel) outputs against the oracle,
+    Stokes I within 1e-3 relative and Q, U, V within 1e-3 of I."""
+    from paper_1105_0661_gb300 import Plan
+    from synth.device import make_block_device
+    wl = G.workload_lofar_tc(bits, 0)
+    plan = Plan.from_workload(wl, precision="fp16tc")
+    assert plan.dims.bf_kernel == 3
+    d_in = make_block_device(wl, seed=0, device=dev)
+    out = torch.empty(plan.shape("stokes"), dtype=torch.float32, device=dev)
+    plan.run_block(d_in, out)
+    torch.cuda.synchronize()
+    assert plan.device_status() == 0
+    ob = O.observation_from_workload(wl)
+    chans = [0, 127, 128, 255]
+    for f in (0, 243):
+        ref = ob.run_block_sampled(d_in[:, f].cpu().numpy(), f, chans)        # [B, 4, nc, M/Q]
+        got = out[:, :, f][:, :, chans].double().cpu().numpy()
+        I = ref[:, 0]
+        assert np.all(I > 0)
+        eI = (np.abs(got[:, 0] - I) / I).max()
+        eq = (np.abs(got[:, 1:] - ref[:, 1:]) / I[:, None]).max()
+        print(f"bits={bits} f={f}: Stokes I max rel err {eI:.2e}, QUV/I {eq:.2e}")
+        assert eI <= 1e-3 and eq <= 1e-3
+    del out
+    plan.close()

@@ -97,3 +97,24 @@ def test_tc_equals_fp32_path_within_precision_bar(dev):
         p.close()
     eI, eq = _errors(outs[1], outs[0])
     assert eI <= TOL and eq <= TOL
+
+
+@pytest.mark.parametrize("Q,out", [(1, "IQUV"), (2, "I"), (4, "IQUV"), (8, "I"), (32, "IQUV"), (32, "I")])
+def test_tc_every_integration_length(dev, Q, out):
+    """Each integration length Q in {1, 2, 4, 8, 16, 32} has its own epilogue; M = 96 spectra leave
+    the last 64-spectrum tile half empty, and 200 beams leave the second beam block partial."""
+    from paper_1105_0661_gb300 import Plan
+    wl = _wl(S=24, B=200, out=out, bits=16, T=96 * N, Q=Q)
+    p = Plan.from_workload(wl, precision="fp16tc")
+    ob = O.observation_from_workload(wl)
+    rng = np.random.default_rng(Q)
+    shp = p.shape("ct")
+    ct = (rng.standard_normal(shp) + 1j * rng.standard_normal(shp)).astype(np.complex64)
+    o = torch.empty(p.shape("stokes"), dtype=torch.float32, device=dev)
+    p.beamform_stokes(torch.from_numpy(ct).to(dev), o)
+    assert p.device_status() == 0
+    ref = ob.stokes(ob.beamform(ct.astype(np.complex128)))
+    eI, eq = _errors(o.cpu().numpy().astype(np.float64), ref)
+    print(f"TC Q={Q} {out}: Stokes I max rel err {eI:.2e}, QUV/I {eq:.2e}")
+    assert eI <= TOL and eq <= TOL
+    p.close()
