@@ -146,19 +146,21 @@ def algorithmic_work(wl, dims):
     }
 
 
-def traffic_from_profiles(kernel: str):
-    """DRAM bytes per launch recorded from an ncu capture, if the kernel source is unchanged."""
+def traffic_from_profiles(kernel: str, workload_name: str):
+    """DRAM bytes per launch recorded from an ncu capture of this workload, if the kernel source
+    is unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic.md")
     if not os.path.exists(path):
         return None
     src = {"bf_many": "beamform.cu", "bf_few": "beamform.cu", "ppf_ct": "ppf.cu", "ppf": "ppf.cu",
-           "hist_update": "ppf.cu", "delay_ct": "delay.cu", "stokes": "stokes.cu"}.get(kernel)
+           "ppf_ct16": "ppf.cu", "bf_tc": "bf_tc.cu", "hist_update": "ppf.cu", "delay_ct": "delay.cu",
+           "stokes": "stokes.cu"}.get(kernel)
     if src is None:
         return None
     h = hashlib.sha256(open(os.path.join(ROOT, "paper_1105_0661_gb300", "csrc", src), "rb").read()).hexdigest()[:16]
     for line in open(path):
         cells = [c.strip() for c in line.strip().strip("|").split("|")]
-        if len(cells) >= 4 and cells[0] == kernel and cells[2] == h:
+        if len(cells) >= 5 and cells[0] == kernel and cells[2] == h and workload_name.startswith(cells[3]):
             try:
                 return float(cells[1])
             except ValueError:
@@ -381,7 +383,7 @@ def run_ours(args):
         peak_tf = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
         achieved = amount / avg_s / 1e12
         roof = {"bound": "tensor", "kernel": dom, "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
-                "frac": achieved / peak_tf, "traffic": traffic_from_profiles(dom),
+                "frac": achieved / peak_tf, "traffic": traffic_from_profiles(dom, wl.name),
                 "executed_tflops": achieved * 3,
                 "peak_source": f"{pk_kind} bf16_tflops_sustained (fp16 dense nominal ratio 1.0); achieved counts "
                                f"one complex product, the hi+lo form executes three (Whi.Yhi + Whi.Ylo + Wlo.Yhi)"}
@@ -389,18 +391,46 @@ def run_ours(args):
         peak_tf = N_SM * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         achieved = amount / avg_s / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
-                "frac": achieved / peak_tf, "traffic": traffic_from_profiles(dom),
+                "frac": achieved / peak_tf, "traffic": traffic_from_profiles(dom, wl.name),
                 "peak_source": f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 flop x "
                                f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind} max SM clock)"}
     else:
         peak = pk["hbm_gbs"]
         achieved = amount / avg_s / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic_from_profiles(dom),
+                "frac": achieved / peak, "traffic": traffic_from_profiles(dom, wl.name),
                 "peak_source": f"{pk_kind} hbm_gbs"}
 
     launches = sum(v[0] for k, v in trace.items() if not k.startswith("_")) + trace.get("_dropped", 0)
     bf_flop = 8.0 * wl.n_beams * ss_step * 2
+
+    # the same block through the other precision form (the metric compares FP16-TC with FP32)
+    compare = None
+    if not args.no_compare and dims.n_stokes and wl.n_stations <= 64:
+        other = "fp16tc" if args.precision == "fp32" else "fp32"
+        plan.close()
+        plan = Plan.from_workload(wl, precision=other)
+        for _ in range(args.warmup):
+            plan.run_block(d_in, d_out, stream)
+        stream.synchronize()
+        dist.barrier(dev)
+        plan.trace_begin(3 * args.steps + 8)
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(args.steps):
+            plan.run_block(d_in, d_out, stream)
+        c1.record(stream)
+        stream.synchronize()
+        ctrace = plan.trace_end()
+        cms = dist.reduce_scalar(c0.elapsed_time(c1), "max", dev)
+        bf_ms = sum(v[1] for k, v in ctrace.items() if k.startswith("bf_"))
+        compare = {"precision": other, "value": world * ss_step * args.steps / (cms / 1e3),
+                   "ms_per_step": cms / args.steps,
+                   "kernels_ms": {k: v[1] / v[0] for k, v in ctrace.items() if not k.startswith("_") and v[0]},
+                   "beamform_tflops": bf_flop * args.steps / (bf_ms / 1e3) / 1e12,
+                   "speedup_of_fp16tc": (ms / cms) if other == "fp16tc" else (cms / ms)}
+        launches_other = sum(v[0] for k, v in ctrace.items() if not k.startswith("_"))
+        compare["gpu_launches"] = launches_other
     line = {
         "metric": "station-samples/s", "value": value, "unit": "station-samples/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -410,7 +440,7 @@ def run_ours(args):
         "cpu_baseline": cpu, "clocks": clocks, "kernels": kernels,
         "beamform_tflops": bf_flop * args.steps / (sum(v[1] for k, v in trace.items() if k.startswith("bf_")) / 1e3) / 1e12,
         "dtype_detail": "fp16 tensor-core operands, fp32 accumulation" if args.precision == "fp16tc" else "fp32",
-        "parity": parity,
+        "parity": parity, "precision_compare": compare,
         "paper_context": "Blue Gene/P rack: up to 198 Gb/s = 3.1e9 station-samples/s (64 stations x 248 subbands)",
     }
     if rank == 0:
@@ -593,6 +623,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the other precision form on the same block")
     ap.add_argument("--serve", action="store_true", help="streaming serving run (p50/p99 block latency)")
     ap.add_argument("--batch", action="store_true", help="16 uneven sub-observations, grouped graph vs separate")
     ap.add_argument("--serve-obs", type=int, default=8)
