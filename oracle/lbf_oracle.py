@@ -23,7 +23,9 @@ Readings where the paper is silent (each also listed in the design notes):
     channels run in ascending frequency with baseband offset df_c = (c - N/2) fs/N;
   * delay compensation: Y = X * bp[c] * exp(+2 pi i [f0 tau_s + df_c (tau_s - n_s Ts)]);
   * weights: w[b, s] = exp(+2 pi i f_c (tau_s(beam b) - tau_s(phase centre))), f_c = f0 + df_c;
-  * Stokes: as printed in Section 4.5 (V = 2 Im(X conj(Y))); integration sums Q spectra.
+  * Stokes: as printed in Section 4.5 (V = 2 Im(X conj(Y))); integration sums Q spectra;
+  * channel-level dedispersion (Section 4.4): k-point FFT per run of k spectra of a channel, the
+    textbook coherent-dedispersion chirp, inverse FFT (no overlap between runs).
 
 Parity pins: every function here is pinned by tests marked not-gpu against closed forms, library
 special cases, invariants and the paper's printed rates; none is "parity unpinned".
@@ -97,6 +99,42 @@ def integrate(p: np.ndarray, q: int) -> np.ndarray:
     m = p.shape[-1]
     assert m % q == 0
     return p.reshape(p.shape[:-1] + (m // q, q)).sum(axis=-1)
+
+
+# ----------------------------------------------------------------------------- dedispersion (Section 4.4)
+# Dispersion constant of the cold-plasma delay law t(f) = K_DM * DM / f^2 (DM in pc cm^-3, f in Hz,
+# t in s): 4.148808e3 s MHz^2 = 4.148808e15 s Hz^2 (Lorimer & Kramer, Handbook of Pulsar Astronomy,
+# 2005, eq. 4.7).  The paper names the chirp but prints no formula; this constant and the transfer
+# function below are the textbook coherent-dedispersion filter of Hankins & Rickett (1975).
+K_DM = 4.148808e15
+
+
+def dedispersion_phase(f_centre: float, nu: np.ndarray, dm: float) -> np.ndarray:
+    """Phase in cycles of the interstellar medium's transfer function at sky frequency
+    f_centre + nu: phi(nu) = K_DM DM nu^2 / (f_centre^2 (f_centre + nu)).  Its derivative is
+    K_DM DM (1/f_centre^2 - 1/(f_centre + nu)^2), the extra dispersion delay of frequency
+    f_centre + nu relative to f_centre (with a sign, since a delay tau multiplies a spectrum by
+    exp(-2 pi i nu tau))."""
+    nu = np.asarray(nu, dtype=np.float64)
+    return K_DM * dm * nu * nu / (f_centre * f_centre * (f_centre + nu))
+
+
+def dedisperse_series(x: np.ndarray, f_centre: float, channel_rate_hz: float, dm: float, k: int) -> np.ndarray:
+    """Channel-level dedispersion (Section 4.4) of complex series x[..., M] sampled at
+    channel_rate_hz (one spectrum per sample) around sky frequency f_centre: every run of k
+    consecutive samples is transformed by a k-point FFT into sub-channels of width
+    channel_rate_hz / k, multiplied by the chirp exp(-2 pi i phi(nu_j)) that undoes the dispersion
+    (nu_j = j channel_rate/k for j < k/2, (j - k) channel_rate/k otherwise), and transformed back
+    (inverse FFT, scaled by 1/k).  M must be a multiple of k.  Library FFTs serve as the steps."""
+    x = np.asarray(x, dtype=np.complex128)
+    M = x.shape[-1]
+    assert M % k == 0
+    j = np.arange(k)
+    nu = np.where(j < k // 2, j, j - k) * (channel_rate_hz / k)
+    chirp = np.exp(-2j * np.pi * dedispersion_phase(f_centre, nu, dm))
+    runs = x.reshape(x.shape[:-1] + (M // k, k))
+    y = np.fft.ifft(np.fft.fft(runs, axis=-1) * chirp, axis=-1)
+    return y.reshape(x.shape)
 
 
 # ----------------------------------------------------------------------------- one observation
@@ -221,6 +259,16 @@ class Observation:
         out = np.zeros(ct.shape[:2] + (G,) + ct.shape[3:], dtype=np.complex128)
         for s in range(ct.shape[2]):
             out[:, :, grp[s]] += ct[:, :, s]
+        return out
+
+    # -- channel-level dedispersion of beam voltages (Section 4.4)
+    def dedisperse(self, vol: np.ndarray, dm: float, k: int) -> np.ndarray:
+        """vol [B][F][N][P][M] -> the same layout, each (beam, subband, channel, pol) series
+        dedispersed around its channel's sky frequency f0_f + df_c at the channel rate fs/N."""
+        out = np.empty(vol.shape, dtype=np.complex128)
+        for f in range(vol.shape[1]):
+            for c in range(vol.shape[2]):
+                out[:, f, c] = dedisperse_series(vol[:, f, c], self.f0[f] + self.df[c], self.fs / self.N, dm, k)
         return out
 
     # -- a7: Stokes + integration (Sections 4.5, 5.1)

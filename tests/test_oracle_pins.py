@@ -475,3 +475,45 @@ def test_superstation_of_all_stations_is_the_phase_centre_beam():
     assert np.array_equal(ident, ct)
     two = ob.superstation(ct, np.array([0, 1] * 5))
     assert np.allclose(two[:, :, 0], ct[:, :, 0::2].sum(axis=2)) and np.allclose(two[:, :, 1], ct[:, :, 1::2].sum(axis=2))
+
+
+# ----------------------------------------------------------------------------- dedispersion (Section 4.4)
+def test_dedispersion_zero_dm_is_identity_and_runs_keep_their_norm():
+    rng = np.random.default_rng(40)
+    x = rng.standard_normal((3, 256)) + 1j * rng.standard_normal((3, 256))
+    assert np.allclose(O.dedisperse_series(x, 120e6, 762.939453125, 0.0, 64), x, atol=1e-12)
+    y = O.dedisperse_series(x, 30e6, 762.939453125, 5e3, 64)
+    # unimodular chirp: Parseval per run of k samples
+    assert np.allclose(np.linalg.norm(y.reshape(3, 4, 64), axis=-1), np.linalg.norm(x.reshape(3, 4, 64), axis=-1))
+    # phi is linear in DM, so -DM applies the conjugate chirp and undoes +DM
+    assert np.allclose(O.dedisperse_series(y, 30e6, 762.939453125, -5e3, 64), x, atol=1e-10)
+
+
+def test_dedispersion_aligns_wave_packets_dispersed_by_the_cold_plasma_delay_law():
+    """Independent of the chirp formula: two narrow-band wave packets at sub-channel frequencies
+    nu1, nu2 arrive at T0 + K_DM DM (1/(f+nu)^2 - 1/f^2) (the textbook delay law t = K_DM DM / f^2).
+    After dedispersion both envelopes peak at T0; with the chirp's sign flipped they move apart."""
+    rate, k, f_c, dm = 762.939453125, 1024, 10e6, 40.0
+    m = np.arange(k)
+    t0 = 512.0
+    peaks, flipped = [], []
+    for jbin in (-268, 268):                      # nu = +-199.7 Hz, exactly on FFT bins
+        nu = jbin * rate / k
+        delay = O.K_DM * dm * (1.0 / (f_c + nu) ** 2 - 1.0 / f_c ** 2) * rate   # in samples
+        assert abs(delay) > 40
+        env = np.exp(-0.5 * ((m - t0 - delay) / 16.0) ** 2)
+        x = env * np.exp(2j * np.pi * jbin * m / k)
+        peaks.append(np.argmax(np.abs(O.dedisperse_series(x, f_c, rate, dm, k))))
+        flipped.append(np.argmax(np.abs(O.dedisperse_series(x, f_c, rate, -dm, k))))
+    assert all(abs(p - t0) <= 1 for p in peaks), peaks
+    assert abs(flipped[0] - flipped[1]) > 150, flipped
+
+
+def test_dedispersion_phase_derivative_is_the_relative_delay():
+    """d phi / d nu = K_DM DM (1/f^2 - 1/(f + nu)^2), checked by central differences."""
+    f_c, dm = 50e6, 123.0
+    nu = np.linspace(-300.0, 300.0, 7)
+    h = 1e-3
+    num = (O.dedispersion_phase(f_c, nu + h, dm) - O.dedispersion_phase(f_c, nu - h, dm)) / (2 * h)
+    ref = O.K_DM * dm * (1.0 / f_c ** 2 - 1.0 / (f_c + nu) ** 2)
+    assert np.allclose(num, ref, rtol=1e-6, atol=1e-18)
