@@ -197,11 +197,30 @@ lbf_status lbf_run_block(lbf_plan_t plan, const void *d_in, void *d_out, void *s
 lbf_status lbf_superstation(lbf_plan_t plan, const int32_t *group_of_station, int32_t n_groups, const void *d_ct,
                             void *d_ss, void *stream);
 
-/* lbf_run_block with HOST buffers: enqueues on `stream` the copy h_in -> d_in (in_bytes), the
- * fused path d_in -> d_out, and the copy d_out -> h_out (out_bytes), one cudaMemcpyAsync each.
- * h_in/h_out should be page-locked (cudaHostAlloc / pinned) for the copies to be asynchronous;
- * d_in/d_out are caller-owned device staging buffers of the documented sizes.  Returns once the
- * work is enqueued; synchronise the stream before reading h_out. */
+/* Channel-level dedispersion (Section 4.4) of beam voltages.  Every run of fft_len consecutive
+ * spectra of each (beam, subband, channel, pol) series is transformed by an fft_len-point FFT into
+ * sub-channels nu_j = j (fs/N)/fft_len (j - fft_len for j >= fft_len/2), multiplied by the
+ * coherent-dedispersion chirp exp(-2 pi i K_DM DM nu^2 / (f_c^2 (f_c + nu))) with f_c the channel's
+ * sky frequency f0_f + (c - N/2) fs/N and K_DM = 4.148808e15 s Hz^2 (cold-plasma delay
+ * t = K_DM DM / f^2), and transformed back (inverse FFT scaled by 1/fft_len).  Runs do not overlap
+ * (each is circular).  Apply it to the output of lbf_beamform, before lbf_stokes.
+ * d_vol_in, d_vol_out: device [B][F][N][P][M] cf32, 16-byte aligned; they may be the same buffer.
+ * dm: dispersion measure in pc cm^-3 (finite; 0 leaves the data unchanged up to rounding).
+ * fft_len: a power of two in [2, 4096] that divides M.
+ * Errors: LBF_EINVAL (fft_len, dm or pointers), LBF_ESTATE, LBF_ECUDA.  Stateless; enqueued on
+ * `stream`. */
+lbf_status lbf_dedisperse(lbf_plan_t plan, double dm, int32_t fft_len, const void *d_vol_in, void *d_vol_out,
+                          void *stream);
+
+/* lbf_run_block with HOST buffers: the copy h_in -> d_in (in_bytes), the fused path d_in -> d_out
+ * on `stream`, and the copy d_out -> h_out (out_bytes), one cudaMemcpyAsync each.  The copies run
+ * on two streams of the plan, ordered by events: a block's upload starts as soon as the previous
+ * block's kernels have read d_in, so it overlaps that block's beam former; `stream` waits for the
+ * download before anything enqueued on it later.  h_in/h_out should be page-locked (cudaHostAlloc
+ * / pinned) for the copies to be asynchronous; d_in/d_out are caller-owned device staging buffers
+ * of the documented sizes, reused across calls.  Returns once the work is enqueued; h_in must stay
+ * unchanged and h_out unread until `stream` has passed this call (e.g. cudaStreamSynchronize).
+ * Not available for plans with LBF_FLAG_EXTERNAL_WORKSPACE (LBF_EINVAL). */
 lbf_status lbf_run_block_host(lbf_plan_t plan, const void *h_in, void *h_out, void *d_in, void *d_out,
                               void *stream);
 
@@ -214,7 +233,8 @@ typedef struct lbf_trace {
   int32_t launches[16];        /* launches per kernel */
   double total_ms[16];         /* summed event time per kernel */
   char names[16][32];          /* kernel names: ppf, ppf_ct, hist_update, delay_ct, bf_few, bf_many,
-                                  stokes, ppf_ct16, bf_tc, ct_to_ct16 */
+                                  stokes, ppf_ct16, bf_tc, ct_to_ct16, incoherent_ct16,
+                                  dedisperse */
   int32_t dropped;             /* launches not recorded because max_launches was reached */
 } lbf_trace;
 lbf_status lbf_trace_begin(lbf_plan_t plan, int32_t max_launches);

@@ -11,8 +11,9 @@
 // width, and beams summed with cancellation magnify its rounding).
 //
 // Operands.  A (the weights) lives in tensor memory: the epilogue warps compute it from the
-// FP64-reduced phase tables with an FP32 sincos and write it with tcgen05.st, one TMEM lane per
-// row, two FP16 K elements per 32-bit column.  B is the filter bank's FP16 scratch
+// FP64-reduced phase tables with the hardware sincos of the reduced phase and write it with
+// tcgen05.st, one TMEM lane per row, two FP16 K elements per 32-bit column.  B is the filter
+// bank's FP16 scratch
 // [F*N][Mt][Kpad][P][32] (Mt = ceil(M/64)*2 tiles of 32 spectra; k = 2 station + re|im; a 128-byte
 // row holds the 2 pols x 32 spectra of one k), brought into shared memory by TMA two tiles at a
 // time (one box of 2 x Kpad rows per plane, 128-byte swizzle) and read by the MMA as an MN-major
@@ -177,21 +178,48 @@ __device__ __forceinline__ uint32_t pack_half2(float lo_k, float hi_k) {
 // Weights of this thread's A row for work item (f, c) into its TMEM lane: column s of plane hi/lo
 // holds (Re w, -Im w) for a Re row and (Im w, Re w) for an Im row.  The two lanes of a beam each
 // evaluate every other station and swap the results; the two warps of a lane quadrant take
-// alternate groups of 8 columns (`half`).
-__device__ __forceinline__ void write_weights(const TcParams &p, uint32_t ta_hi, uint32_t ta_lo, int f, int c, int b,
-                                              int ro, int half) {
-  const bool beam_ok = b < p.B;
+// alternate groups of 8 columns (`half`).  The phase-table values are loaded first
+// (load_weight_tables), so that their latency hides behind an accumulator wait.
+constexpr int kWStations = kMaxKpad / 32 * 4;   // stations one thread evaluates per M tile (16)
+
+struct WeightTables {
+  float ph[kWStations], st[kWStations];   // FP64-reduced phase of the subband, phase step per channel
+  uint32_t ok;                            // bit i: station i of this thread exists (else weight 0)
+};
+
+__device__ __forceinline__ void load_weight_tables(const TcParams &p, int f, int b, int ro, int half,
+                                                   WeightTables &w) {
+  w.ok = 0;
+#pragma unroll
+  for (int i = 0; i < kWStations; ++i) {
+    const int s = (half + 2 * (i >> 2)) * 8 + 2 * (i & 3) + ro;
+    const bool ok = b < p.B && s < p.S;
+    const long long bs = (long long)b * p.S + s;
+    w.ph[i] = ok ? __ldg(&p.phase0[(long long)f * p.B * p.S + bs]) : 0.f;
+    w.st[i] = ok ? __ldg(&p.step[bs]) : 0.f;
+    w.ok |= (ok ? 1u : 0u) << i;
+  }
+}
+
+__device__ __forceinline__ void write_weights(const TcParams &p, uint32_t ta_hi, uint32_t ta_lo, int c, int ro,
+                                              int half, const WeightTables &tab) {
   const float dc = (float)(c - kN / 2);
-  for (int g8 = half; g8 < p.Kpad / 16; g8 += 2) {   // 8 stations per store
+#pragma unroll
+  for (int gi = 0; gi < kWStations / 4; ++gi) {
+    const int g8 = half + 2 * gi;                    // 8 stations per store
+    if (g8 >= p.Kpad / 16) break;
     uint32_t vh[8], vl[8];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int s = g8 * 8 + 2 * j + ro;
+      const int i = gi * 4 + j;
       float2 w = make_float2(0.f, 0.f);
-      if (beam_ok && s < p.S) {
-        const long long bs = (long long)b * p.S + s;
-        const float phi = fmaf(dc, p.step[bs], p.phase0[(long long)f * p.B * p.S + bs]);
-        sincospif(2.0f * phi, &w.y, &w.x);
+      if ((tab.ok >> i) & 1u) {
+        // phase in cycles, reduced to [-1/2, 1/2] (exact in FP32), then the hardware sine and
+        // cosine of |x| <= pi: absolute error ~4e-7, twice the resolution of the hi+lo weight
+        // and far below the 1e-3 bar of this path
+        float phi = fmaf(dc, tab.st[i], tab.ph[i]);
+        phi -= rintf(phi);
+        __sincosf(6.283185307179586f * phi, &w.y, &w.x);
       }
       float2 o;
       o.x = __shfl_xor_sync(0xffffffffu, w.x, 1);
@@ -455,7 +483,9 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
       if (item == blockIdx.x) {           // weights of the first item; later ones follow each last tile
         for (int mt = 0; mt < kMTiles; ++mt) {
           const uint32_t ta_hi = tmem + lane_off + kACol0 + (uint32_t)(2 * mt * 64);
-          write_weights(p, ta_hi, ta_hi + 64u, f, c, bb * kBeamsPerItem + mt * (kRows / 2) + quad * 16 + jq, ro, half);
+          WeightTables tab;
+          load_weight_tables(p, f, bb * kBeamsPerItem + mt * (kRows / 2) + quad * 16 + jq, ro, half, tab);
+          write_weights(p, ta_hi, ta_hi + 64u, c, ro, half, tab);
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(afull_bar(mt));
@@ -468,6 +498,10 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
         const int wbase = (t / St::kPeriod) * 8;
         float *const buf = qbuf + (fl & 1) * St::kBuf;
         for (int mt = 0; mt < kMTiles; ++mt) {
+          const bool boundary = t == p.ntiles - 1 && nitem < p.items;
+          WeightTables tab;
+          if (boundary)   // the next item's table values, in flight while the last accumulator fills
+            load_weight_tables(p, nfc / kN, nbb * kBeamsPerItem + mt * (kRows / 2) + quad * 16 + jq, ro, half, tab);
           if (!mbar_wait(accf_bar(mt), (uint32_t)g & 1u, abort_flag)) { fail(abort_flag, p.err, ERR_EPILOGUE); ok = false; break; }
           tc_fence_after();
           const int b = bb * kBeamsPerItem + mt * (kRows / 2) + quad * 16 + jq;
@@ -477,12 +511,11 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(acce_bar(mt));
-          if (t == p.ntiles - 1 && nitem < p.items) {
+          if (boundary) {
             // the MMAs that read this tile's weights are complete (its last accumulator was
             // committed): write the next item's
             const uint32_t ta_hi = tmem + lane_off + kACol0 + (uint32_t)(2 * mt * 64);
-            write_weights(p, ta_hi, ta_hi + 64u, nfc / kN, nfc % kN,
-                          nbb * kBeamsPerItem + mt * (kRows / 2) + quad * 16 + jq, ro, half);
+            write_weights(p, ta_hi, ta_hi + 64u, nfc % kN, ro, half, tab);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(afull_bar(mt));

@@ -1,0 +1,150 @@
+// Channel-level dedispersion (Section 4.4) of tied-array beam voltages.
+//
+// Dispersion in the interstellar medium delays lower frequencies; inside one channel the delay
+// varies with the offset nu from the channel's sky frequency f_c.  Every run of K consecutive
+// spectra of a (beam, subband, channel, pol) series is transformed by a K-point FFT into
+// sub-channels of width (fs/N)/K, multiplied by the coherent-dedispersion chirp
+//     H(nu) = exp(-2 pi i K_DM DM nu^2 / (f_c^2 (f_c + nu)))
+// (the conjugate of the medium's transfer function, Hankins & Rickett 1975; K_DM is the constant of
+// the cold-plasma delay law t = K_DM DM / f^2) and transformed back.  Runs do not overlap.
+//
+// One CTA serves one (subband, channel) and a group of 8 beams, which share the chirp: it builds
+// the twiddle table exp(-2 pi i n / K) and the chirp (at bit-reversed positions, scaled by 1/K) in
+// shared memory once, then for each beam loads the 2 pols x M/K runs (contiguous in the voltage
+// layout) in passes, runs an in-place radix-2 decimation-in-frequency FFT (natural order in,
+// bit-reversed out), multiplies by the chirp, and runs the inverse as decimation in time
+// (bit-reversed in, natural out), so no reordering pass is needed.  FP32 throughout except the
+// chirp phase, whose large term is reduced exactly in 64-bit fixed point (see below).
+#include "lbf_internal.cuh"
+
+namespace lbf {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kBeamsPerCta = 8;
+constexpr double kKdm = 4.148808e15;     // s Hz^2 per (pc cm^-3): cold-plasma delay t = kKdm DM / f^2
+constexpr int kDataFloat2 = 8192;        // shared data per pass: 64 KB of complex samples
+
+struct DdParams {
+  int K, logK, runs, runs_per_pass;      // runs = 2 M / K per (beam, subband, channel)
+  double dm;
+};
+
+__global__ void __launch_bounds__(kThreads)
+dedisperse_kernel(Geometry g, DdParams d, const float2 *in, float2 *out) {   // in may equal out
+  extern __shared__ __align__(16) float2 sm[];
+  const int K = d.K, half = K >> 1;
+  float2 *x = sm;                              // [runs_per_pass][K] (16-byte aligned: float4 copies)
+  float2 *tw = x + d.runs_per_pass * K;        // [K/2]  exp(-2 pi i n / K)
+  float2 *chirp = tw + half;                   // [K]    H(nu_j) / K at position bitrev(j)
+  __shared__ unsigned long long frac_s;   // frac(C) in 64-bit fixed point (units of 2^-64 cycle)
+  __shared__ float c_s, eps_s;
+
+  const int bgroups = (g.B + kBeamsPerCta - 1) / kBeamsPerCta;
+  const long long fc = blockIdx.x / bgroups;
+  const int bg = (int)(blockIdx.x - fc * bgroups);
+  const int f = (int)(fc / kN), c = (int)(fc - (long long)f * kN);
+  const int tid = threadIdx.x;
+
+  // With nu = j' r (r = (fs/N)/K the sub-channel width, j' the signed bin) the chirp phase is
+  //     phi(j') = C j'^2 / (1 + eps j'),  C = K_DM DM r^2 / f_c^3,  eps = r / f_c,
+  // which can reach thousands of cycles, so it is split exactly: phi = C j'^2 - C eps j'^3/(1 + eps j').
+  // The first term is reduced modulo one in 64-bit fixed point (frac(C) j'^2 mod 2^64, exact); the
+  // second, at most phi eps |j'| (eps |j'| <= (fs/N/2)/f_c), is small enough for FP32.
+  if (tid == 0) {
+    const double f_c = g.f0[f] + (double)(c - kN / 2) * (g.fs / kN);
+    const double r = g.fs / kN / (double)K;
+    const double C = kKdm * d.dm * r * r / (f_c * f_c * f_c);
+    frac_s = (unsigned long long)ldexp(C - floor(C), 64);
+    c_s = (float)C;
+    eps_s = (float)(r / f_c);
+  }
+  for (int n = tid; n < half; n += kThreads) {
+    float s, co;
+    sincospif(2.0f * (float)n / (float)K, &s, &co);
+    tw[n] = make_float2(co, -s);
+  }
+  __syncthreads();
+  const float scale = 1.0f / (float)K;
+  for (int i = tid; i < K; i += kThreads) {
+    const int j = (int)(__brev((unsigned)i) >> (32 - d.logK));   // FFT bin held at position i
+    const int jj = j < half ? j : j - K;                           // signed bin j'
+    const unsigned long long sq = (unsigned long long)((long long)jj * jj);
+    const float main = (float)(long long)(frac_s * sq) * 5.421010862427522e-20f;   // x 2^-64: [-1/2, 1/2)
+    const float fj = (float)jj, a = eps_s * fj;
+    float ph = main - c_s * fj * fj * a / (1.0f + a);   // cycles
+    ph -= rintf(ph);
+    float s, co;
+    sincospif(2.0f * ph, &s, &co);
+    chirp[i] = make_float2(co * scale, -s * scale);   // exp(-2 pi i ph) / K
+  }
+  __syncthreads();
+
+  const int b_end = min(g.B, (bg + 1) * kBeamsPerCta);
+  for (int b = bg * kBeamsPerCta; b < b_end; ++b) {
+    const long long base = (((long long)b * g.F + f) * kN + c) * (long long)kP * g.M;   // [P][M] of (b, f, c)
+    for (int r0 = 0; r0 < d.runs; r0 += d.runs_per_pass) {
+      const int nr = min(d.runs_per_pass, d.runs - r0);
+      const int n = nr * K;
+      const float4 *src = reinterpret_cast<const float4 *>(in + base + (long long)r0 * K);
+      for (int i = tid; i < n / 2; i += kThreads) reinterpret_cast<float4 *>(x)[i] = src[i];
+      __syncthreads();
+      // forward FFT, decimation in frequency: stage size L = K .. 2
+      for (int hl = half; hl >= 1; hl >>= 1) {
+        const int lhl = __ffs(hl) - 1;
+        const int stride = half >> lhl;            // twiddle index step K / L
+        for (int u = tid; u < nr * half; u += kThreads) {
+          const int run = u >> (d.logK - 1), t_all = u & (half - 1);
+          const int grp = t_all >> lhl, t = t_all & (hl - 1);
+          float2 *p0 = x + run * K + grp * 2 * hl + t;
+          const float2 a = p0[0], bb = p0[hl];
+          p0[0] = make_float2(a.x + bb.x, a.y + bb.y);
+          p0[hl] = cmul(make_float2(a.x - bb.x, a.y - bb.y), tw[t * stride]);
+        }
+        __syncthreads();
+      }
+      for (int i = tid; i < n; i += kThreads) x[i] = cmul(x[i], chirp[i & (K - 1)]);
+      __syncthreads();
+      // inverse FFT, decimation in time: stage size L = 2 .. K, conjugate twiddles
+      for (int hl = 1; hl <= half; hl <<= 1) {
+        const int lhl = __ffs(hl) - 1;
+        const int stride = half >> lhl;
+        for (int u = tid; u < nr * half; u += kThreads) {
+          const int run = u >> (d.logK - 1), t_all = u & (half - 1);
+          const int grp = t_all >> lhl, t = t_all & (hl - 1);
+          float2 *p0 = x + run * K + grp * 2 * hl + t;
+          const float2 w = tw[t * stride];
+          const float2 a = p0[0], bw = cmul(p0[hl], make_float2(w.x, -w.y));
+          p0[0] = make_float2(a.x + bw.x, a.y + bw.y);
+          p0[hl] = make_float2(a.x - bw.x, a.y - bw.y);
+        }
+        __syncthreads();
+      }
+      float4 *dst = reinterpret_cast<float4 *>(out + base + (long long)r0 * K);
+      for (int i = tid; i < n / 2; i += kThreads) dst[i] = reinterpret_cast<const float4 *>(x)[i];
+      __syncthreads();
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_dedisperse(const Geometry &g, double dm, int K, const float2 *in, float2 *out, cudaStream_t st) {
+  if (g.M == 0 || g.B == 0) return cudaSuccess;
+  DdParams d;
+  d.K = K;
+  d.logK = 0;
+  while ((1 << d.logK) < K) ++d.logK;
+  d.runs = kP * g.M / K;
+  d.runs_per_pass = kDataFloat2 / K < d.runs ? kDataFloat2 / K : d.runs;
+  if (d.runs_per_pass < 1) d.runs_per_pass = 1;
+  d.dm = dm;
+  const size_t smem = sizeof(float2) * ((size_t)K / 2 + K + (size_t)d.runs_per_pass * K);
+  cudaError_t e = cudaFuncSetAttribute(dedisperse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long ctas = (long long)g.F * kN * ((g.B + kBeamsPerCta - 1) / kBeamsPerCta);
+  dedisperse_kernel<<<(unsigned)ctas, kThreads, smem, st>>>(g, d, in, out);
+  return cudaGetLastError();
+}
+
+}  // namespace lbf

@@ -57,6 +57,10 @@ void release(lbf_plan_s *p) {
   cudaFree(p->hist[0]); cudaFree(p->hist[1]); cudaFree(p->ws);
   cudaFree(p->phase0); cudaFree(p->step);
   cudaFree(p->ct16[0]); cudaFree(p->d_err); cudaFree(p->ss_members); cudaFree(p->ss_offs);
+  if (p->h2d) cudaStreamDestroy(p->h2d);
+  if (p->d2h) cudaStreamDestroy(p->d2h);
+  for (cudaEvent_t ev : {p->ev_in_free, p->ev_in_ready, p->ev_out_ready, p->ev_out_done})
+    if (ev) cudaEventDestroy(ev);
 }
 
 lbf_status validate(const lbf_config *c) {
@@ -150,10 +154,11 @@ lbf_status check_call(lbf_plan_t p) {
 }
 
 enum KernelId { K_PPF = 0, K_PPF_CT, K_HIST, K_DELAY, K_BF_FEW, K_BF_MANY, K_STOKES, K_PPF_CT16, K_BF_TC,
-                K_CT16, K_INC16, K_COUNT };
+                K_CT16, K_INC16, K_DEDISP, K_COUNT };
 static_assert(K_COUNT <= 16, "lbf_trace holds 16 kernels");
 const char *const kKernelNames[K_COUNT] = {"ppf", "ppf_ct", "hist_update", "delay_ct", "bf_few", "bf_many",
-                                           "stokes", "ppf_ct16", "bf_tc", "ct_to_ct16", "incoherent_ct16"};
+                                           "stokes", "ppf_ct16", "bf_tc", "ct_to_ct16", "incoherent_ct16",
+                                           "dedisperse"};
 
 // Launch through `fn`, bracketed by trace events when a trace is active.
 template <typename Fn>
@@ -185,7 +190,7 @@ int bf_kernel_id(lbf_plan_t p) { return p->variant == 1 ? K_BF_FEW : K_BF_MANY; 
 // The fused path on device buffers (a1-a7).  `ws` is the scratch of this call: the FP32
 // corner-turned block, or the FP16 planes of a tensor-core plan (with `maps` their descriptors).
 cudaError_t run_block_device(lbf_plan_t p, const void *d_in, void *d_out, void *ws, const CUtensorMap *maps,
-                             cudaStream_t st) {
+                             cudaStream_t st, cudaEvent_t input_read = nullptr) {
   const lbf::Geometry g = p->geometry();
   const void *h = p->hist[p->cur];
   void *nh = p->hist[p->cur ^ 1];
@@ -196,6 +201,7 @@ cudaError_t run_block_device(lbf_plan_t p, const void *d_in, void *d_out, void *
     o.kpad = p->kpad;
     cudaError_t e = traced(p, K_PPF_CT16, st, [&] { return lbf::launch_ppf(g, p->bits, d_in, h, nullptr, nullptr, st, &o); });
     if (e == cudaSuccess) e = traced(p, K_HIST, st, [&] { return lbf::launch_hist_update(g, p->bits, d_in, h, nh, st); });
+    if (e == cudaSuccess && input_read) e = cudaEventRecord(input_read, st);
     if (e != cudaSuccess) return e;
     p->cur ^= 1;
     if (p->inc) {
@@ -208,6 +214,7 @@ cudaError_t run_block_device(lbf_plan_t p, const void *d_in, void *d_out, void *
   float2 *ct = static_cast<float2 *>(ws);
   cudaError_t e = traced(p, K_PPF_CT, st, [&] { return lbf::launch_ppf(g, p->bits, d_in, h, nullptr, ct, st); });
   if (e == cudaSuccess) e = traced(p, K_HIST, st, [&] { return lbf::launch_hist_update(g, p->bits, d_in, h, nh, st); });
+  if (e == cudaSuccess && input_read) e = cudaEventRecord(input_read, st);
   if (e != cudaSuccess) return e;
   p->cur ^= 1;
   return traced(p, bf_kernel_id(p), st,
@@ -507,10 +514,43 @@ lbf_status lbf_run_block_host(lbf_plan_t p, const void *h_in, void *h_out, void 
   lbf_dims d;
   lbf_plan_dims(p, &d);
   cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = cudaMemcpyAsync(d_in, h_in, d.in_bytes, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = run_block_device(p, d_in, d_out, own_ws(p), p->tmap, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h_out, d_out, d.out_bytes, cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaSuccess;
+  if (!p->h2d) {   // first call: the plan's copy streams and events
+    e = cudaStreamCreateWithFlags(&p->h2d, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->d2h, cudaStreamNonBlocking);
+    for (cudaEvent_t *ev : {&p->ev_in_free, &p->ev_in_ready, &p->ev_out_ready, &p->ev_out_done})
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  // upload once the previous block's kernels have read d_in (its history update), so that the
+  // upload overlaps that block's beam former
+  e = cudaStreamWaitEvent(p->h2d, p->ev_in_free, 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_in, h_in, d.in_bytes, cudaMemcpyHostToDevice, p->h2d);
+  if (e == cudaSuccess) e = cudaEventRecord(p->ev_in_ready, p->h2d);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, p->ev_in_ready, 0);
+  if (e == cudaSuccess) e = run_block_device(p, d_in, d_out, own_ws(p), p->tmap, st, p->ev_in_free);
+  // download on its own stream; `stream` then waits for it, so later work on `stream` (and the
+  // next block's kernels, which rewrite d_out) follow the copy
+  if (e == cudaSuccess) e = cudaEventRecord(p->ev_out_ready, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(p->d2h, p->ev_out_ready, 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_out, d_out, d.out_bytes, cudaMemcpyDeviceToHost, p->d2h);
+  if (e == cudaSuccess) e = cudaEventRecord(p->ev_out_done, p->d2h);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, p->ev_out_done, 0);
   return cuda_status(e);
+}
+
+lbf_status lbf_dedisperse(lbf_plan_t p, double dm, int32_t fft_len, const void *d_vol_in, void *d_vol_out,
+                          void *stream) {
+  lbf_status s = check_call(p);
+  if (s != LBF_OK) return s;
+  if (fft_len < 2 || fft_len > 4096 || (fft_len & (fft_len - 1)) != 0 || !std::isfinite(dm)) return LBF_EINVAL;
+  if (p->M % fft_len != 0) return LBF_EINVAL;
+  if (p->M == 0) return LBF_OK;
+  if (!device_ptr(d_vol_in, 16) || !device_ptr(d_vol_out, 16)) return LBF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const lbf::Geometry g = p->geometry();
+  return cuda_status(traced(p, K_DEDISP, st, [&] {
+    return lbf::launch_dedisperse(g, dm, fft_len, static_cast<const float2 *>(d_vol_in), static_cast<float2 *>(d_vol_out), st); }));
 }
 
 lbf_status lbf_device_status(lbf_plan_t p, int32_t *code) {

@@ -88,6 +88,8 @@ cudaError_t launch_incoherent_ct16(const Geometry &g, int out_kind, const Ct16Ou
 // tcgen05 beam former with fused Stokes epilogue (bf_tc.cu); tm_hi/tm_lo are CUtensorMap*
 cudaError_t launch_bf_tc(const Geometry &g, int out_kind, const void *tm_hi, const void *tm_lo, float *out, int *err,
                          cudaStream_t st);
+// channel-level dedispersion of vol [B][F][N][P][M] (in may equal out); K a power of two dividing M
+cudaError_t launch_dedisperse(const Geometry &g, double dm, int K, const float2 *in, float2 *out, cudaStream_t st);
 int tc_max_stations();
 int tc_spectra_per_tile();   // TMA box height of the FP16 scratch (spectra per N tile)
 int tc_kpad(int S);

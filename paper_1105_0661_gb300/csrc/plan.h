@@ -42,6 +42,10 @@ struct lbf_plan_s {
   float2 *ws = nullptr;
   size_t word = 8, hist_bytes = 0, ws_bytes = 0;
 
+  // lbf_run_block_host: copy streams and the events that order them against the kernels
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  cudaEvent_t ev_in_free = nullptr, ev_in_ready = nullptr, ev_out_ready = nullptr, ev_out_done = nullptr;
+
   // kernel timing trace (lbf_trace_begin / lbf_trace_end)
   struct TraceSlot { int kernel; cudaEvent_t a, b; };
   std::vector<TraceSlot> trace;

@@ -25,7 +25,8 @@ BF_VARIANTS = {"auto": 0, "few": 1, "many": 2}
 EXPORTED = ("lbf_plan", "lbf_plan_destroy", "lbf_plan_dims", "lbf_plan_shifts", "lbf_reset_state",
             "lbf_ppf", "lbf_delay_correct", "lbf_beamform", "lbf_beamform_stokes", "lbf_stokes",
             "lbf_run_block", "lbf_run_block_ws", "lbf_run_block_host", "lbf_trace_begin", "lbf_trace_end",
-            "lbf_device_status", "lbf_run_block_static", "lbf_superstation", "lbf_batch_create", "lbf_batch_destroy",
+            "lbf_device_status", "lbf_run_block_static", "lbf_superstation", "lbf_dedisperse",
+            "lbf_batch_create", "lbf_batch_destroy",
             "lbf_batch_run", "lbf_batch_capture", "lbf_batch_launch", "lbf_batch_tune",
             "lbf_status_string", "lbf_version")
 
@@ -102,6 +103,7 @@ def load_library() -> ctypes.CDLL:
             "lbf_trace_end": ([vp, ctypes.POINTER(_Trace)], ctypes.c_int),
             "lbf_device_status": ([vp, i32p], ctypes.c_int),
             "lbf_superstation": ([vp, i32p, ctypes.c_int32, vp, vp, vp], ctypes.c_int),
+            "lbf_dedisperse": ([vp, ctypes.c_double, ctypes.c_int32, vp, vp, vp], ctypes.c_int),
             "lbf_run_block_static": ([ctypes.POINTER(_Config), vp, vp, vp], ctypes.c_int),
             "lbf_batch_create": ([ctypes.POINTER(vp), ctypes.c_int32, ctypes.POINTER(vp)], ctypes.c_int),
             "lbf_batch_destroy": ([vp], ctypes.c_int),
@@ -288,11 +290,19 @@ class Plan:
         return self.dims.plan_bytes
 
     def run_block_host(self, h_in, h_out, d_in, d_out, stream=None):
-        """H2D copy of h_in, the fused path, D2H copy into h_out, all enqueued on `stream`."""
+        """H2D copy of h_in, the fused path on `stream`, D2H copy into h_out; the copies run on the
+        plan's copy streams (the next block's upload overlaps this block's kernels) and `stream`
+        waits for the download.  Synchronise `stream` before reading h_out or reusing h_in."""
         d = self.dims
         _check(self._lib.lbf_run_block_host(self._h, _ptr(h_in, d.in_bytes), _ptr(h_out, d.out_bytes),
                                             _ptr(d_in, d.in_bytes), _ptr(d_out, d.out_bytes),
                                             _stream(stream)), "lbf_run_block_host")
+
+    def dedisperse(self, dm, fft_len, d_vol_in, d_vol_out, stream=None):
+        """Channel-level dedispersion (Section 4.4) of voltages [B][F][N][P][M] (may be in place)."""
+        d = self.dims
+        _check(self._lib.lbf_dedisperse(self._h, float(dm), int(fft_len), _ptr(d_vol_in, d.vol_bytes),
+                                        _ptr(d_vol_out, d.vol_bytes), _stream(stream)), "lbf_dedisperse")
 
     def superstation(self, group_of_station, d_ct, d_ss, stream=None):
         """Sum the delay-compensated stations of each group (Section 4.2); d_ss is

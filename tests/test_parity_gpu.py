@@ -345,3 +345,32 @@ def test_superstation_matches_oracle(dev):
         else:
             assert np.max(np.abs(got - ref)) <= 1e-6 * np.max(np.abs(ref))
     p.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16tc"])
+def test_host_buffer_calls_pipeline_in_order(dev, prec):
+    """lbf_run_block_host on a stream of blocks enqueued back to back (no synchronisation between
+    calls, shared device staging buffers): the upload of block k+1 overlaps block k's kernels, and
+    every block still gives exactly the outputs of the device-buffer path, and the oracle's."""
+    wl = _wl(S=16, B=70, out="IQUV", Q=4, T=64 * N)
+    p_host = _plan(wl, precision=prec)
+    p_dev = _plan(wl, precision=prec)
+    ob = O.observation_from_workload(wl)
+    nblk = 3
+    blocks = [G.make_block(wl, seed=30, block_index=k) for k in range(nblk)]
+    h_in = [torch.from_numpy(b).pin_memory() for b in blocks]
+    h_out = [torch.empty(p_host.shape("stokes"), dtype=torch.float32).pin_memory() for _ in range(nblk)]
+    d_in = torch.empty(blocks[0].shape, dtype=torch.int16, device=dev)
+    d_out = torch.empty(p_host.shape("stokes"), dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    for k in range(nblk):
+        p_host.run_block_host(h_in[k], h_out[k], d_in, d_out, stream)
+    stream.synchronize()
+    o = torch.empty(p_dev.shape("stokes"), dtype=torch.float32, device=dev)
+    tol = TOL if prec == "fp32" else 1e-3
+    for k in range(nblk):
+        p_dev.run_block(_to_dev(blocks[k], dev), o)
+        assert torch.equal(o.cpu(), h_out[k]), k
+        _check_stokes(h_out[k].numpy().astype(np.float64), ob.run_block(blocks[k]), tol)
+    p_host.close()
+    p_dev.close()
