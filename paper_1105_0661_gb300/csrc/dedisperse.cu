@@ -8,13 +8,15 @@
 // (the conjugate of the medium's transfer function, Hankins & Rickett 1975; K_DM is the constant of
 // the cold-plasma delay law t = K_DM DM / f^2) and transformed back.  Runs do not overlap.
 //
-// One CTA serves one (subband, channel) and a group of 8 beams, which share the chirp: it builds
-// the twiddle table exp(-2 pi i n / K) and the chirp (at bit-reversed positions, scaled by 1/K) in
-// shared memory once, then for each beam loads the 2 pols x M/K runs (contiguous in the voltage
-// layout) in passes, runs an in-place radix-2 decimation-in-frequency FFT (natural order in,
-// bit-reversed out), multiplies by the chirp, and runs the inverse as decimation in time
-// (bit-reversed in, natural out), so no reordering pass is needed.  FP32 throughout except the
-// chirp phase, whose large term is reduced exactly in 64-bit fixed point (see below).
+// One CTA serves one (subband, channel) and a group of 8 beams, which share the chirp.  Run length
+// 256 (the default: 3 Hz sub-channels) uses the filter bank's 16 x 16 register FFT; any other
+// power of two builds the twiddle table exp(-2 pi i n / K) and the chirp (at bit-reversed
+// positions, scaled by 1/K) in shared memory once, then for each beam loads the 2 pols x M/K runs
+// (contiguous in the voltage layout) in passes, runs an in-place radix-2 decimation-in-frequency
+// FFT (natural order in, bit-reversed out), multiplies by the chirp, and runs the inverse as
+// decimation in time (bit-reversed in, natural out), so no reordering pass is needed.  FP32
+// throughout except the chirp phase, whose large term is reduced exactly in 64-bit fixed point.
+#include "fft16.cuh"
 #include "lbf_internal.cuh"
 
 namespace lbf {
@@ -30,6 +32,40 @@ struct DdParams {
   double dm;
 };
 
+// Per-channel chirp coefficients.  With nu = j' r (r = (fs/N)/K the sub-channel width, j' the
+// signed bin) the chirp phase is
+//     phi(j') = C j'^2 / (1 + eps j'),  C = K_DM DM r^2 / f_c^3,  eps = r / f_c,
+// which can reach thousands of cycles, so it is split exactly: phi = C j'^2 - C eps j'^3/(1 + eps j').
+// The first term is reduced modulo one in 64-bit fixed point (frac(C) j'^2 mod 2^64, exact); the
+// second, at most phi eps |j'| (eps |j'| <= (fs/N/2)/f_c), is small enough for FP32.
+struct ChirpCoef {
+  unsigned long long frac;   // frac(C) in units of 2^-64 cycle
+  float c, eps;
+};
+
+__device__ __forceinline__ ChirpCoef chirp_coef(const Geometry &g, int f, int c, int K, double dm) {
+  const double f_c = g.f0[f] + (double)(c - kN / 2) * (g.fs / kN);
+  const double r = g.fs / kN / (double)K;
+  const double C = kKdm * dm * r * r / (f_c * f_c * f_c);
+  ChirpCoef k;
+  k.frac = (unsigned long long)ldexp(C - floor(C), 64);
+  k.c = (float)C;
+  k.eps = (float)(r / f_c);
+  return k;
+}
+
+// exp(-2 pi i phi(j')) / K for the signed bin j'
+__device__ __forceinline__ float2 chirp_value(const ChirpCoef &k, int jj, float scale) {
+  const unsigned long long sq = (unsigned long long)((long long)jj * jj);
+  const float main = (float)(long long)(k.frac * sq) * 5.421010862427522e-20f;   // x 2^-64: [-1/2, 1/2)
+  const float fj = (float)jj, a = k.eps * fj;
+  float ph = main - k.c * fj * fj * a / (1.0f + a);   // cycles
+  ph -= rintf(ph);
+  float s, co;
+  sincospif(2.0f * ph, &s, &co);
+  return make_float2(co * scale, -s * scale);
+}
+
 __global__ void __launch_bounds__(kThreads)
 dedisperse_kernel(Geometry g, DdParams d, const float2 *in, float2 *out) {   // in may equal out
   extern __shared__ __align__(16) float2 sm[];
@@ -37,8 +73,7 @@ dedisperse_kernel(Geometry g, DdParams d, const float2 *in, float2 *out) {   // 
   float2 *x = sm;                              // [runs_per_pass][K] (16-byte aligned: float4 copies)
   float2 *tw = x + d.runs_per_pass * K;        // [K/2]  exp(-2 pi i n / K)
   float2 *chirp = tw + half;                   // [K]    H(nu_j) / K at position bitrev(j)
-  __shared__ unsigned long long frac_s;   // frac(C) in 64-bit fixed point (units of 2^-64 cycle)
-  __shared__ float c_s, eps_s;
+  __shared__ ChirpCoef coef_s;
 
   const int bgroups = (g.B + kBeamsPerCta - 1) / kBeamsPerCta;
   const long long fc = blockIdx.x / bgroups;
@@ -46,19 +81,7 @@ dedisperse_kernel(Geometry g, DdParams d, const float2 *in, float2 *out) {   // 
   const int f = (int)(fc / kN), c = (int)(fc - (long long)f * kN);
   const int tid = threadIdx.x;
 
-  // With nu = j' r (r = (fs/N)/K the sub-channel width, j' the signed bin) the chirp phase is
-  //     phi(j') = C j'^2 / (1 + eps j'),  C = K_DM DM r^2 / f_c^3,  eps = r / f_c,
-  // which can reach thousands of cycles, so it is split exactly: phi = C j'^2 - C eps j'^3/(1 + eps j').
-  // The first term is reduced modulo one in 64-bit fixed point (frac(C) j'^2 mod 2^64, exact); the
-  // second, at most phi eps |j'| (eps |j'| <= (fs/N/2)/f_c), is small enough for FP32.
-  if (tid == 0) {
-    const double f_c = g.f0[f] + (double)(c - kN / 2) * (g.fs / kN);
-    const double r = g.fs / kN / (double)K;
-    const double C = kKdm * d.dm * r * r / (f_c * f_c * f_c);
-    frac_s = (unsigned long long)ldexp(C - floor(C), 64);
-    c_s = (float)C;
-    eps_s = (float)(r / f_c);
-  }
+  if (tid == 0) coef_s = chirp_coef(g, f, c, K, d.dm);
   for (int n = tid; n < half; n += kThreads) {
     float s, co;
     sincospif(2.0f * (float)n / (float)K, &s, &co);
@@ -68,15 +91,7 @@ dedisperse_kernel(Geometry g, DdParams d, const float2 *in, float2 *out) {   // 
   const float scale = 1.0f / (float)K;
   for (int i = tid; i < K; i += kThreads) {
     const int j = (int)(__brev((unsigned)i) >> (32 - d.logK));   // FFT bin held at position i
-    const int jj = j < half ? j : j - K;                           // signed bin j'
-    const unsigned long long sq = (unsigned long long)((long long)jj * jj);
-    const float main = (float)(long long)(frac_s * sq) * 5.421010862427522e-20f;   // x 2^-64: [-1/2, 1/2)
-    const float fj = (float)jj, a = eps_s * fj;
-    float ph = main - c_s * fj * fj * a / (1.0f + a);   // cycles
-    ph -= rintf(ph);
-    float s, co;
-    sincospif(2.0f * ph, &s, &co);
-    chirp[i] = make_float2(co * scale, -s * scale);   // exp(-2 pi i ph) / K
+    chirp[i] = chirp_value(coef_s, j < half ? j : j - K, scale);
   }
   __syncthreads();
 
@@ -127,6 +142,86 @@ dedisperse_kernel(Geometry g, DdParams d, const float2 *in, float2 *out) {   // 
   }
 }
 
+// K = 256 (sub-channels of (fs/N)/256 = 3 Hz): 16 transforms at a time, 16 threads each, as the
+// filter bank's 16 x 16 decomposition in registers.  Thread j of a group ends the forward
+// transform holding bins j + 16 k2; it multiplies them by the chirp, conjugates, and runs the same
+// forward transform again: the inverse is conj(FFT(conj(.))).
+__global__ void __launch_bounds__(kThreads)
+dedisperse256_kernel(Geometry g, DdParams d, const float2 *in, float2 *out) {   // in may equal out
+  constexpr int K = 256;
+  __shared__ __align__(16) float2 x[16][K];    // one transform per 16-thread group
+  __shared__ float2 tw[K];                     // exp(-2 pi i n / 256)
+  __shared__ float2 chirp[K];                  // natural bin order, scaled by 1/256
+  __shared__ ChirpCoef coef_s;
+  const int bgroups = (g.B + kBeamsPerCta - 1) / kBeamsPerCta;
+  const long long fc = blockIdx.x / bgroups;
+  const int bg = (int)(blockIdx.x - fc * bgroups);
+  const int f = (int)(fc / kN), c = (int)(fc - (long long)f * kN);
+  const int tid = threadIdx.x, j = tid & 15, grp = tid >> 4;
+  if (tid == 0) coef_s = chirp_coef(g, f, c, K, d.dm);
+  {
+    float s, co;
+    sincospif(2.0f * (float)tid / (float)K, &s, &co);
+    tw[tid] = make_float2(co, -s);
+  }
+  __syncthreads();
+  chirp[tid] = chirp_value(coef_s, tid < K / 2 ? tid : tid - K, 1.0f / (float)K);
+  __syncthreads();
+
+  const int b0 = bg * kBeamsPerCta;
+  const int ntr = (min(g.B, b0 + kBeamsPerCta) - b0) * d.runs;   // transforms of this CTA
+  // forward 256-point FFT of row `r` (natural order in smem), result: thread j holds X[j + 16 k2]
+  auto fft = [&](float2 *r, float2 (&a)[16]) {
+#pragma unroll
+    for (int p1 = 0; p1 < 16; ++p1) a[p1] = r[16 * p1 + j];
+    __syncwarp();
+    dft16(a);
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) r[k1 * 16 + (j ^ k1)] = cmul(a[k1], tw[j * k1]);
+    __syncwarp();
+#pragma unroll
+    for (int p2 = 0; p2 < 16; ++p2) a[p2] = r[j * 16 + (p2 ^ j)];
+    __syncwarp();
+    dft16(a);
+  };
+  for (int t0 = 0; t0 < ntr; t0 += 16) {
+    const int nt = min(16, ntr - t0);
+    // load nt transforms (each 2 KB contiguous) with 16-byte copies
+    for (int i = tid; i < nt * (K / 2); i += kThreads) {
+      const int tr = t0 + i / (K / 2), q = i % (K / 2);
+      const int b = b0 + tr / d.runs, run = tr % d.runs;
+      const float4 *src = reinterpret_cast<const float4 *>(
+          in + ((((long long)b * g.F + f) * kN + c) * (long long)kP * g.M + (long long)run * K));
+      reinterpret_cast<float4 *>(x[i / (K / 2)])[q] = src[q];
+    }
+    __syncthreads();
+    {   // every group transforms its row (rows past nt hold stale data and are not stored), so
+        // the warp-wide __syncwarp calls see all 32 lanes
+      float2 a[16];
+      float2 *r = x[grp];
+      fft(r, a);
+#pragma unroll
+      for (int k2 = 0; k2 < 16; ++k2) {     // chirp (with 1/256), then conjugate for the inverse
+        const float2 v = cmul(a[k2], chirp[j + 16 * k2]);
+        r[j + 16 * k2] = make_float2(v.x, -v.y);
+      }
+      __syncwarp();
+      fft(r, a);
+#pragma unroll
+      for (int k2 = 0; k2 < 16; ++k2) r[j + 16 * k2] = make_float2(a[k2].x, -a[k2].y);
+    }
+    __syncthreads();
+    for (int i = tid; i < nt * (K / 2); i += kThreads) {
+      const int tr = t0 + i / (K / 2), q = i % (K / 2);
+      const int b = b0 + tr / d.runs, run = tr % d.runs;
+      float4 *dst = reinterpret_cast<float4 *>(
+          out + ((((long long)b * g.F + f) * kN + c) * (long long)kP * g.M + (long long)run * K));
+      dst[q] = reinterpret_cast<const float4 *>(x[i / (K / 2)])[q];
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_dedisperse(const Geometry &g, double dm, int K, const float2 *in, float2 *out, cudaStream_t st) {
@@ -139,10 +234,14 @@ cudaError_t launch_dedisperse(const Geometry &g, double dm, int K, const float2 
   d.runs_per_pass = kDataFloat2 / K < d.runs ? kDataFloat2 / K : d.runs;
   if (d.runs_per_pass < 1) d.runs_per_pass = 1;
   d.dm = dm;
+  const long long ctas = (long long)g.F * kN * ((g.B + kBeamsPerCta - 1) / kBeamsPerCta);
+  if (K == 256) {
+    dedisperse256_kernel<<<(unsigned)ctas, kThreads, 0, st>>>(g, d, in, out);
+    return cudaGetLastError();
+  }
   const size_t smem = sizeof(float2) * ((size_t)K / 2 + K + (size_t)d.runs_per_pass * K);
   cudaError_t e = cudaFuncSetAttribute(dedisperse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const long long ctas = (long long)g.F * kN * ((g.B + kBeamsPerCta - 1) / kBeamsPerCta);
   dedisperse_kernel<<<(unsigned)ctas, kThreads, smem, st>>>(g, d, in, out);
   return cudaGetLastError();
 }

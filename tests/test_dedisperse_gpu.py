@@ -38,7 +38,8 @@ def _rel_rms(got, ref, axes):
 
 
 @pytest.mark.parametrize("K,M,dm,inplace", [(2, 64, 3e3, False), (16, 64, 3e3, True), (64, 64, 8e3, False),
-                                            (4096, 4096, 2e3, True), (256, 768, 0.0, False)])
+                                            (4096, 4096, 2e3, True), (256, 768, 0.0, False),
+                                            (256, 768, 4e3, True), (256, 256, 9e3, False)])
 def test_dedisperse_matches_oracle(dev, K, M, dm, inplace):
     from paper_1105_0661_gb300 import Plan
     wl = _wl(M, B=2 if M > 1000 else 5, F=1 if M > 1000 else 2)
