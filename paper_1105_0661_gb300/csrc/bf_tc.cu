@@ -421,7 +421,7 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
       const int ksteps = p.Kpad >> 4;
-      const uint32_t tile_bytes = (uint32_t)(p.Kpad * 128);
+      const uint64_t desc_b0 = smem_desc(sB, (uint32_t)(p.Kpad * 128));   // stage 0, hi plane, k step 0
       bool issued = false, ok = true;
       long long g = 0;
       int it = 0;
@@ -439,16 +439,17 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
             }
             tc_fence_after();
             const uint32_t d = tmem + (uint32_t)(mt * kAccCols);
-            const uint32_t a_hi = tmem + kACol0 + (uint32_t)(2 * mt * 64), a_lo = a_hi + 64u;
-            const uint32_t b0 = sB + (uint32_t)s * (uint32_t)p.stage_bytes;
+            uint32_t a_hi = tmem + kACol0 + (uint32_t)(2 * mt * 64);
+            // descriptors advance by adding the byte offset / 16 to the start-address field (all
+            // shared addresses are below 256 KB, so the 14-bit field never carries)
+            uint64_t b_hi = desc_b0 + (uint64_t)((s * p.stage_bytes) >> 4);
             for (int ks = 0; ks < ksteps; ++ks) {
-              const uint32_t boff = (uint32_t)(ks * 16 * 128);            // 16 K rows per step
-              const uint64_t b_hi = smem_desc(b0 + boff, tile_bytes);
-              const uint64_t b_lo = smem_desc(b0 + plane_bytes + boff, tile_bytes);
-              const uint32_t ac = (uint32_t)(ks * 8);                     // 16 K elements = 8 columns
-              umma(d, a_hi + ac, b_hi, ks != 0);   // Whi Yhi
-              umma(d, a_lo + ac, b_hi, 1);         // Wlo Yhi
-              umma(d, a_hi + ac, b_lo, 1);         // Whi Ylo
+              const uint64_t b_lo = b_hi + (uint64_t)(plane_bytes >> 4);
+              umma(d, a_hi, b_hi, ks != 0);           // Whi Yhi
+              umma(d, a_hi + 64u, b_hi, 1);           // Wlo Yhi
+              umma(d, a_hi, b_lo, 1);                 // Whi Ylo
+              a_hi += 8u;                             // 16 K elements = 8 TMEM columns
+              b_hi += (uint64_t)((16 * 128) >> 4);    // 16 K rows of 128 bytes
             }
             umma_commit(accf_bar(mt));
             issued = true;

@@ -189,25 +189,38 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
         stage[c * kTile + (gq ^ (c & 15))] = cmul(a[k2], sm.gain[c]);
       }
       __syncthreads();
-      // [F*N][Mb][Kpad][P][32]: rows k = 2s (re) and 2s+1 (im), runs of 16 spectra (32 B)
-      const int q = tid & 15;
+      // [F*N][Mt][Kpad][P][32]: rows k = 2s (re) and 2s+1 (im).  Thread (row (pol, c), h8) packs
+      // 8 consecutive spectra into one 16-byte store per plane and component; spectra at or past
+      // the block's end go out as zeros (the pad columns of the last tile).
       const int mb = tc_tiles(g.M);
-      const int m = mt + q;
-      if (m < m_end) {
-#pragma unroll 4
-        for (int pass = 0; pass < kP * kN / 32; ++pass) {
-          const int row2 = pass * 32 + (tid >> 4);     // (pol, c)
-          const int pl = row2 >> 8, c = row2 & (kN - 1);
-          const float2 v = (&sm.v[pl][0][0])[c * kTile + (q ^ (c & 15))];
-          const long long re = ((((long long)f * kN + c) * mb + (m >> 5)) * po.kpad + 2 * s) * 64 + pl * 32 + (m & 31);
-          const long long im = re + 64;
-          const __half hr = __float2half_rn(v.x), hi_ = __float2half_rn(v.y);
-          po.hi[re] = hr;
-          po.hi[im] = hi_;
-          if (po.lo) {
-            po.lo[re] = __float2half_rn(v.x - __half2float(hr));
-            po.lo[im] = __float2half_rn(v.y - __half2float(hi_));
-          }
+      const int h8 = tid & 1;
+      const int m0 = mt + 8 * h8;
+#pragma unroll
+      for (int pass = 0; pass < kP * kN / (kThreads / 2); ++pass) {
+        const int row2 = pass * (kThreads / 2) + (tid >> 1);   // (pol, c)
+        const int pl = row2 >> 8, c = row2 & (kN - 1);
+        const float2 *srow = &sm.v[pl][0][0] + c * kTile;
+        uint32_t hr[4], hm[4], lr[4], lm[4];
+#pragma unroll
+        for (int k = 0; k < 8; k += 2) {
+          float2 v0 = srow[(8 * h8 + k) ^ (c & 15)], v1 = srow[(8 * h8 + k + 1) ^ (c & 15)];
+          if (m0 + k >= m_end) v0 = make_float2(0.f, 0.f);
+          if (m0 + k + 1 >= m_end) v1 = make_float2(0.f, 0.f);
+          const __half2 h_re = __floats2half2_rn(v0.x, v1.x), h_im = __floats2half2_rn(v0.y, v1.y);
+          const float2 f_re = __half22float2(h_re), f_im = __half22float2(h_im);
+          const __half2 l_re = __floats2half2_rn(v0.x - f_re.x, v1.x - f_re.y);
+          const __half2 l_im = __floats2half2_rn(v0.y - f_im.x, v1.y - f_im.y);
+          hr[k / 2] = *reinterpret_cast<const uint32_t *>(&h_re);
+          hm[k / 2] = *reinterpret_cast<const uint32_t *>(&h_im);
+          lr[k / 2] = *reinterpret_cast<const uint32_t *>(&l_re);
+          lm[k / 2] = *reinterpret_cast<const uint32_t *>(&l_im);
+        }
+        const long long re = ((((long long)f * kN + c) * mb + (m0 >> 5)) * po.kpad + 2 * s) * 64 + pl * 32 + (m0 & 31);
+        *reinterpret_cast<uint4 *>(po.hi + re) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
+        *reinterpret_cast<uint4 *>(po.hi + re + 64) = make_uint4(hm[0], hm[1], hm[2], hm[3]);
+        if (po.lo) {
+          *reinterpret_cast<uint4 *>(po.lo + re) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
+          *reinterpret_cast<uint4 *>(po.lo + re + 64) = make_uint4(lm[0], lm[1], lm[2], lm[3]);
         }
       }
     } else if (!CT) {
@@ -225,15 +238,24 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
         stage[c * kTile + (gq ^ (c & 15))] = cmul(a[k2], sm.gain[c]);
       }
       __syncthreads();
-      // ct[f][c][s][pol][m]: runs of 16 consecutive spectra (128 B) per (c, pol)
-      const int q = tid & 15;
-      if (mt + q < m_end) {
+      // ct[f][c][s][pol][m]: runs of 16 consecutive spectra (128 B) per (c, pol).  Eight threads
+      // write a run, two spectra each as one 16-byte store (rows 16-byte aligned when M is even),
+      // so a warp's store covers four whole 128-byte runs.
+      const int pr = tid & 7;
+      const int m0 = mt + 2 * pr;
+      const bool vec = (g.M & 1) == 0 && m0 + 1 < m_end;
 #pragma unroll 4
-        for (int pass = 0; pass < kP * kN / 32; ++pass) {
-          const int row2 = pass * 32 + (tid >> 4);     // (pol, c)
-          const int pl = row2 >> 8, c = row2 & (kN - 1);
-          out[((((long long)f * kN + c) * g.S + s) * kP + pl) * g.M + mt + q] =
-              (&sm.v[pl][0][0])[c * kTile + (q ^ (c & 15))];
+      for (int pass = 0; pass < kP * kN / (kThreads / 8); ++pass) {
+        const int row2 = pass * (kThreads / 8) + (tid >> 3);   // (pol, c)
+        const int pl = row2 >> 8, c = row2 & (kN - 1);
+        const float2 *srow = &sm.v[pl][0][0] + c * kTile;
+        const float2 v0 = srow[(2 * pr) ^ (c & 15)], v1 = srow[(2 * pr + 1) ^ (c & 15)];
+        float2 *dst = out + ((((long long)f * kN + c) * g.S + s) * kP + pl) * g.M + m0;
+        if (vec) {
+          *reinterpret_cast<float4 *>(dst) = make_float4(v0.x, v0.y, v1.x, v1.y);
+        } else {
+          if (m0 < m_end) dst[0] = v0;
+          if (m0 + 1 < m_end) dst[1] = v1;
         }
       }
     }
