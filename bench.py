@@ -348,7 +348,7 @@ def run_ours(args):
         stream.synchronize()
         dist.barrier(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        k2 = max(1, min(args.steps, args.e2e_steps))
+        k2 = args.steps if args.e2e_steps <= 0 else max(1, args.e2e_steps)
         e0.record(stream)
         for _ in range(k2):
             plan.run_block_host(h_in, h_out, d_stage, d_out, stream)
@@ -700,7 +700,7 @@ def main():
                     help="use only the first N subbands (small profiling cases; 0 = all)")
     ap.add_argument("--cpu-subbands", type=int, default=0,
                     help="subbands in the oracle sample (default 4; 1 for the 1024-beam workload)")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=0, help="end-to-end steps (0: the same K as the timed steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the other precision form on the same block")

@@ -142,14 +142,17 @@ dedisperse_kernel(Geometry g, DdParams d, const float2 *in, float2 *out) {   // 
   }
 }
 
-// K = 256 (sub-channels of (fs/N)/256 = 3 Hz): 16 transforms at a time, 16 threads each, as the
-// filter bank's 16 x 16 decomposition in registers.  Thread j of a group ends the forward
-// transform holding bins j + 16 k2; it multiplies them by the chirp, conjugates, and runs the same
-// forward transform again: the inverse is conj(FFT(conj(.))).
+// K = 256 (sub-channels of (fs/N)/256 = 3 Hz): the filter bank's 16 x 16 decomposition in
+// registers, one transform per 16-thread group at a time.  Each group streams its own transforms:
+// thread j loads x[16 p1 + j] straight from global memory (a half-warp reads 128 contiguous bytes
+// per load), transposes once through its 2 KB shared row, and ends holding bins j + 16 k2; it
+// multiplies them by the chirp, conjugates, and runs the same forward transform again (the
+// inverse is conj(FFT(conj(.)))), then stores y[j + 16 k2] straight to global memory.  Groups
+// synchronise only among their own 16 lanes.
 __global__ void __launch_bounds__(kThreads)
 dedisperse256_kernel(Geometry g, DdParams d, const float2 *in, float2 *out) {   // in may equal out
   constexpr int K = 256;
-  __shared__ __align__(16) float2 x[16][K];    // one transform per 16-thread group
+  __shared__ float2 x[16][K];                  // one row per 16-thread group
   __shared__ float2 tw[K];                     // exp(-2 pi i n / 256)
   __shared__ float2 chirp[K];                  // natural bin order, scaled by 1/256
   __shared__ ChirpCoef coef_s;
@@ -158,6 +161,7 @@ dedisperse256_kernel(Geometry g, DdParams d, const float2 *in, float2 *out) {   
   const int bg = (int)(blockIdx.x - fc * bgroups);
   const int f = (int)(fc / kN), c = (int)(fc - (long long)f * kN);
   const int tid = threadIdx.x, j = tid & 15, grp = tid >> 4;
+  const unsigned mask = 0xFFFFu << (16 * (grp & 1));   // this group's lanes of the warp
   if (tid == 0) coef_s = chirp_coef(g, f, c, K, d.dm);
   {
     float s, co;
@@ -168,57 +172,39 @@ dedisperse256_kernel(Geometry g, DdParams d, const float2 *in, float2 *out) {   
   chirp[tid] = chirp_value(coef_s, tid < K / 2 ? tid : tid - K, 1.0f / (float)K);
   __syncthreads();
 
-  const int b0 = bg * kBeamsPerCta;
-  const int ntr = (min(g.B, b0 + kBeamsPerCta) - b0) * d.runs;   // transforms of this CTA
-  // forward 256-point FFT of row `r` (natural order in smem), result: thread j holds X[j + 16 k2]
-  auto fft = [&](float2 *r, float2 (&a)[16]) {
-#pragma unroll
-    for (int p1 = 0; p1 < 16; ++p1) a[p1] = r[16 * p1 + j];
-    __syncwarp();
+  float2 *r = x[grp];
+  // rest of the forward transform from a[p1] = x[16 p1 + j]: thread j ends with X[j + 16 k2]
+  auto fft_tail = [&](float2 (&a)[16]) {
     dft16(a);
 #pragma unroll
     for (int k1 = 0; k1 < 16; ++k1) r[k1 * 16 + (j ^ k1)] = cmul(a[k1], tw[j * k1]);
-    __syncwarp();
+    __syncwarp(mask);
 #pragma unroll
     for (int p2 = 0; p2 < 16; ++p2) a[p2] = r[j * 16 + (p2 ^ j)];
-    __syncwarp();
+    __syncwarp(mask);
     dft16(a);
   };
-  for (int t0 = 0; t0 < ntr; t0 += 16) {
-    const int nt = min(16, ntr - t0);
-    // load nt transforms (each 2 KB contiguous) with 16-byte copies
-    for (int i = tid; i < nt * (K / 2); i += kThreads) {
-      const int tr = t0 + i / (K / 2), q = i % (K / 2);
-      const int b = b0 + tr / d.runs, run = tr % d.runs;
-      const float4 *src = reinterpret_cast<const float4 *>(
-          in + ((((long long)b * g.F + f) * kN + c) * (long long)kP * g.M + (long long)run * K));
-      reinterpret_cast<float4 *>(x[i / (K / 2)])[q] = src[q];
-    }
-    __syncthreads();
-    {   // every group transforms its row (rows past nt hold stale data and are not stored), so
-        // the warp-wide __syncwarp calls see all 32 lanes
-      float2 a[16];
-      float2 *r = x[grp];
-      fft(r, a);
+  const int b0 = bg * kBeamsPerCta;
+  const int ntr = (min(g.B, b0 + kBeamsPerCta) - b0) * d.runs;   // transforms of this CTA
+  for (int tr = grp; tr < ntr; tr += 16) {
+    const int b = b0 + tr / d.runs, run = tr % d.runs;
+    const long long off = (((long long)b * g.F + f) * kN + c) * (long long)kP * g.M + (long long)run * K;
+    float2 a[16];
 #pragma unroll
-      for (int k2 = 0; k2 < 16; ++k2) {     // chirp (with 1/256), then conjugate for the inverse
-        const float2 v = cmul(a[k2], chirp[j + 16 * k2]);
-        r[j + 16 * k2] = make_float2(v.x, -v.y);
-      }
-      __syncwarp();
-      fft(r, a);
+    for (int p1 = 0; p1 < 16; ++p1) a[p1] = in[off + 16 * p1 + j];
+    fft_tail(a);
 #pragma unroll
-      for (int k2 = 0; k2 < 16; ++k2) r[j + 16 * k2] = make_float2(a[k2].x, -a[k2].y);
+    for (int k2 = 0; k2 < 16; ++k2) {     // chirp (with 1/256), then conjugate for the inverse
+      const float2 v = cmul(a[k2], chirp[j + 16 * k2]);
+      r[j + 16 * k2] = make_float2(v.x, -v.y);
     }
-    __syncthreads();
-    for (int i = tid; i < nt * (K / 2); i += kThreads) {
-      const int tr = t0 + i / (K / 2), q = i % (K / 2);
-      const int b = b0 + tr / d.runs, run = tr % d.runs;
-      float4 *dst = reinterpret_cast<float4 *>(
-          out + ((((long long)b * g.F + f) * kN + c) * (long long)kP * g.M + (long long)run * K));
-      dst[q] = reinterpret_cast<const float4 *>(x[i / (K / 2)])[q];
-    }
-    __syncthreads();
+    __syncwarp(mask);
+#pragma unroll
+    for (int p1 = 0; p1 < 16; ++p1) a[p1] = r[16 * p1 + j];
+    __syncwarp(mask);
+    fft_tail(a);
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) out[off + j + 16 * k2] = make_float2(a[k2].x, -a[k2].y);
   }
 }
 
