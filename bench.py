@@ -155,6 +155,7 @@ def traffic_from_profiles(kernel: str, workload_name: str):
         return None
     src = {"bf_many": "beamform.cu", "bf_few": "beamform.cu", "ppf_ct": "ppf.cu", "ppf": "ppf.cu",
            "ppf_ct16": "ppf.cu", "bf_tc": "bf_tc.cu", "hist_update": "ppf.cu", "delay_ct": "delay.cu",
+           "dedisperse": "dedisperse.cu",
            "stokes": "stokes.cu"}.get(kernel)
     if src is None:
         return None
@@ -621,7 +622,8 @@ def run_dedisperse(args):
                    "voltage_bytes": dims.vol_bytes, "l2": "inputs larger than L2"},
         "gpu_launches": sum(v["launches"] for v in kernels.values()),
         "roofline": {"bound": "hbm", "kernel": "dedisperse", "achieved": dd["achieved_gbs"], "peak": pk["hbm_gbs"],
-                     "unit": "GB/s", "frac": dd["achieved_gbs"] / pk["hbm_gbs"], "traffic": None,
+                     "unit": "GB/s", "frac": dd["achieved_gbs"] / pk["hbm_gbs"],
+                     "traffic": traffic_from_profiles("dedisperse", wl.name),
                      "peak_source": f"{pk_kind} hbm_gbs"},
         "kernels": kernels, "clocks": clk.summary(),
     }
