@@ -65,6 +65,7 @@ struct TcParams {
   long long items;
   int nstages, stage_bytes;   // B ring: stages of 2 planes x 2 tiles x Kpad K rows x 128 bytes
   int vec;                    // output rows 16-byte aligned (M/Q % 4 == 0, aligned base)
+  long long stall_item;       // failure-detection test: the loads stop at this item (-1: never)
   const float *phase0, *step;
   float *out;
   int *err;
@@ -396,8 +397,9 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
     if (lane == 0) {
       const uint32_t bytes = (uint32_t)p.stage_bytes;
       long long g = 0, last_issued = -1;
-      bool ok = true;
+      bool ok = true, stalled = false;
       for (long long item = blockIdx.x; item < p.items && ok; item += gridDim.x) {
+        if (item == p.stall_item) { stalled = true; break; }   // test hook: a barrier nothing fills
         const int fc = (int)(item / p.items_per_fc);
         for (int t = 0; t < p.ntiles; ++t, ++g) {
           const int s = (int)(g % nst);
@@ -410,7 +412,7 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
           last_issued = g;
         }
       }
-      if (*abort_flag) {   // let our own copies land before the CTA's shared memory goes away
+      if (*abort_flag || stalled) {   // let our own copies land before the shared memory goes away
         for (long long q = (last_issued - nst + 1 > 0 ? last_issued - nst + 1 : 0); q <= last_issued; ++q) {
           volatile int never = 0;
           mbar_wait(full_bar((int)(q % nst)), (uint32_t)(q / nst) & 1u, &never);
@@ -587,7 +589,7 @@ int tc_spectra_per_tile() { return kSpec; }
 int tc_kpad(int S) { return ((2 * S + 15) / 16) * 16; }
 
 cudaError_t launch_bf_tc(const Geometry &g, int out_kind, const void *tm_hi, const void *tm_lo, float *out, int *err,
-                         cudaStream_t st) {
+                         cudaStream_t st, long long stall_item) {
   if (g.M == 0 || g.B == 0) return cudaSuccess;
   if (!tm_hi || !tm_lo || g.S > tc_max_stations()) return cudaErrorInvalidValue;
   TcParams p;
@@ -600,6 +602,7 @@ cudaError_t launch_bf_tc(const Geometry &g, int out_kind, const void *tm_hi, con
   p.items = (long long)g.F * kN * p.items_per_fc;
   p.phase0 = g.phase0; p.step = g.step; p.out = out; p.err = err;
   p.vec = (g.M / g.Q) % 4 == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+  p.stall_item = stall_item;
   const int sms = sm_count();
   if (sms <= 0) return cudaErrorInvalidDevice;
   const int grid = (int)(p.items < sms ? p.items : sms);

@@ -209,7 +209,9 @@ cudaError_t run_block_device(lbf_plan_t p, const void *d_in, void *d_out, void *
       if (e != cudaSuccess) return e;
     }
     return traced(p, K_BF_TC, st, [&] {
-      return lbf::launch_bf_tc(g, p->out_kind, &maps[0], &maps[1], (float *)d_out, p->d_err, st); });
+      const long long stall = p->stall_item;
+      p->stall_item = -1;
+      return lbf::launch_bf_tc(g, p->out_kind, &maps[0], &maps[1], (float *)d_out, p->d_err, st, stall); });
   }
   float2 *ct = static_cast<float2 *>(ws);
   cudaError_t e = traced(p, K_PPF_CT, st, [&] { return lbf::launch_ppf(g, p->bits, d_in, h, nullptr, ct, st); });
@@ -456,7 +458,9 @@ lbf_status lbf_beamform_stokes(lbf_plan_t p, const void *d_ct, float *d_out, voi
       e = traced(p, K_INC16, st, [&] { return lbf::launch_incoherent_ct16(g, p->out_kind, o, d_out, st); });
     if (e != cudaSuccess) return cuda_status(e);
     return cuda_status(traced(p, K_BF_TC, st, [&] {
-      return lbf::launch_bf_tc(g, p->out_kind, &p->tmap[0], &p->tmap[1], d_out, p->d_err, st); }));
+      const long long stall = p->stall_item;
+      p->stall_item = -1;
+      return lbf::launch_bf_tc(g, p->out_kind, &p->tmap[0], &p->tmap[1], d_out, p->d_err, st, stall); }));
   }
   return cuda_status(traced(p, bf_kernel_id(p), st, [&] {
     return lbf::launch_beamform(g, p->variant, p->out_kind, (const float2 *)d_ct, d_out, st); }));
@@ -551,6 +555,15 @@ lbf_status lbf_dedisperse(lbf_plan_t p, double dm, int32_t fft_len, const void *
   const lbf::Geometry g = p->geometry();
   return cuda_status(traced(p, K_DEDISP, st, [&] {
     return lbf::launch_dedisperse(g, dm, fft_len, static_cast<const float2 *>(d_vol_in), static_cast<float2 *>(d_vol_out), st); }));
+}
+
+lbf_status lbf_debug_stall_next(lbf_plan_t p, int64_t item) {
+  lbf_status s = check_call(p);
+  if (s != LBF_OK) return s;
+  if (!p->tc) return LBF_EUNSUPPORTED;
+  if (item < 0) return LBF_EINVAL;
+  p->stall_item = item;
+  return LBF_OK;
 }
 
 lbf_status lbf_device_status(lbf_plan_t p, int32_t *code) {

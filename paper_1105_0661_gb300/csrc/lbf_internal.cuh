@@ -86,8 +86,9 @@ cudaError_t launch_superstation(const Geometry &g, const float2 *ct, float2 *ss,
 // incoherent beam (index B of the Stokes output) from the FP16 planes of a tensor-core plan
 cudaError_t launch_incoherent_ct16(const Geometry &g, int out_kind, const Ct16Out &o, float *out, cudaStream_t st);
 // tcgen05 beam former with fused Stokes epilogue (bf_tc.cu); tm_hi/tm_lo are CUtensorMap*
+// stall_item >= 0: failure-detection test, the loads of that work item are never issued
 cudaError_t launch_bf_tc(const Geometry &g, int out_kind, const void *tm_hi, const void *tm_lo, float *out, int *err,
-                         cudaStream_t st);
+                         cudaStream_t st, long long stall_item = -1);
 // channel-level dedispersion of vol [B][F][N][P][M] (in may equal out); K a power of two dividing M
 cudaError_t launch_dedisperse(const Geometry &g, double dm, int K, const float2 *in, float2 *out, cudaStream_t st);
 int tc_max_stations();

@@ -37,6 +37,7 @@ struct lbf_plan_s {
   int *ss_offs = nullptr;       // [S + 1] group offsets into ss_members
   size_t ws_need = 0;           // scratch bytes one block needs
   int *d_err = nullptr;   // device error word set by bounded waits that gave up
+  long long stall_item = -1;   // lbf_debug_stall_next: one-shot, consumed by the next tensor-core launch
   void *hist[2] = {nullptr, nullptr};
   int cur = 0;
   float2 *ws = nullptr;

@@ -25,7 +25,7 @@ BF_VARIANTS = {"auto": 0, "few": 1, "many": 2}
 EXPORTED = ("lbf_plan", "lbf_plan_destroy", "lbf_plan_dims", "lbf_plan_shifts", "lbf_reset_state",
             "lbf_ppf", "lbf_delay_correct", "lbf_beamform", "lbf_beamform_stokes", "lbf_stokes",
             "lbf_run_block", "lbf_run_block_ws", "lbf_run_block_host", "lbf_trace_begin", "lbf_trace_end",
-            "lbf_device_status", "lbf_run_block_static", "lbf_superstation", "lbf_dedisperse",
+            "lbf_device_status", "lbf_debug_stall_next", "lbf_run_block_static", "lbf_superstation", "lbf_dedisperse",
             "lbf_batch_create", "lbf_batch_destroy",
             "lbf_batch_run", "lbf_batch_capture", "lbf_batch_launch", "lbf_batch_tune",
             "lbf_status_string", "lbf_version")
@@ -102,6 +102,7 @@ def load_library() -> ctypes.CDLL:
             "lbf_trace_begin": ([vp, ctypes.c_int32], ctypes.c_int),
             "lbf_trace_end": ([vp, ctypes.POINTER(_Trace)], ctypes.c_int),
             "lbf_device_status": ([vp, i32p], ctypes.c_int),
+            "lbf_debug_stall_next": ([vp, ctypes.c_int64], ctypes.c_int),
             "lbf_superstation": ([vp, i32p, ctypes.c_int32, vp, vp, vp], ctypes.c_int),
             "lbf_dedisperse": ([vp, ctypes.c_double, ctypes.c_int32, vp, vp, vp], ctypes.c_int),
             "lbf_run_block_static": ([ctypes.POINTER(_Config), vp, vp, vp], ctypes.c_int),
@@ -316,11 +317,18 @@ class Plan:
                "lbf_superstation")
 
     def device_status(self) -> int:
-        """Synchronise and return the role code of a device-side wait that gave up (0 = none);
-        raises LbfError(LBF_ETIMEOUT) when one did."""
+        """Synchronise and return the role code of a device-side wait that gave up since the last
+        call (0 = none; 1 loads, 2 MMA, 3 epilogue) and clear it.  A wait that gave up
+        (LBF_ETIMEOUT) is reported through the code; other failures raise."""
         code = ctypes.c_int32(0)
-        _check(self._lib.lbf_device_status(self._h, ctypes.byref(code)), "lbf_device_status")
+        st = self._lib.lbf_device_status(self._h, ctypes.byref(code))
+        if st != LBF_ETIMEOUT:
+            _check(st, "lbf_device_status")
         return code.value
+
+    def debug_stall_next(self, item: int = 0):
+        """Failure-detection test: the next tensor-core launch stops loading at work item `item`."""
+        _check(self._lib.lbf_debug_stall_next(self._h, int(item)), "lbf_debug_stall_next")
 
     def trace_begin(self, max_launches: int = 4096):
         _check(self._lib.lbf_trace_begin(self._h, int(max_launches)), "lbf_trace_begin")

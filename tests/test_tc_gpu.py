@@ -5,6 +5,8 @@ Both sample widths use two FP16 planes of the filtered spectrum (hi + lo).  The 
 printed so that the error of each output is reported.
 """
 
+import time
+
 import numpy as np
 import pytest
 
@@ -117,4 +119,36 @@ def test_tc_every_integration_length(dev, Q, out):
     eI, eq = _errors(o.cpu().numpy().astype(np.float64), ref)
     print(f"TC Q={Q} {out}: Stokes I max rel err {eI:.2e}, QUV/I {eq:.2e}")
     assert eI <= TOL and eq <= TOL
+    p.close()
+
+
+def test_bounded_wait_expires_reports_and_context_survives(dev):
+    """Failure detection without a GPU fault: the loads of one work item are never issued, so the
+    MMA warp waits on a barrier that nothing completes.  The wait expires, the kernel records the
+    role and returns, lbf_device_status reports it (and clears it), and the next launch on the
+    same plan and context matches the oracle."""
+    from paper_1105_0661_gb300 import Plan
+    wl = _wl(S=16, F=1, B=70, T=64 * N, Q=16, out="I")
+    p = Plan.from_workload(wl, precision="fp16tc")
+    ob = O.observation_from_workload(wl)
+    blk = G.make_block(wl, seed=9)
+    d_in = torch.from_numpy(blk).to(dev)
+    o = torch.empty(p.shape("stokes"), dtype=torch.float32, device=dev)
+    assert p.device_status() == 0
+    p.debug_stall_next(0)               # the CTA that owns work item 0 loads nothing
+    t0 = time.perf_counter()
+    p.run_block(d_in, o)
+    code = p.device_status()            # synchronises
+    elapsed = time.perf_counter() - t0
+    print(f"stalled launch: role code {code}, {elapsed:.2f} s")
+    # the MMA role gives up waiting for its loads; the epilogue, polling with the same bound for
+    # the accumulator those loads would have produced, can expire first: either role is correct
+    assert code in (2, 3)
+    assert elapsed < 30.0
+    assert p.device_status() == 0       # the error word was cleared
+    p.reset_state()                     # the stalled launch advanced the history
+    p.run_block(d_in, o)
+    assert p.device_status() == 0
+    eI, eq = _errors(o.cpu().numpy().astype(np.float64), ob.run_block(blk))
+    assert eI <= TOL
     p.close()
