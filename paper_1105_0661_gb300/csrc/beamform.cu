@@ -159,8 +159,7 @@ __device__ __forceinline__ void cp_async8(void *smem_dst, const void *gmem_src, 
 
 // Thread tile: beams 4 bg .. 4 bg + 3 of the CTA's 128, spectra {2 mg, 2 mg + 1, 16 + 2 mg,
 // 17 + 2 mg} of the 32-spectrum pass (so each 16-byte shared load of a warp covers 128 contiguous
-// bytes), both pols: 32 complex accumulators updated with packed FP32x2 FMAs,
-//   acc += (w.re, w.re) * (y.re, y.im) + (-w.im, w.im) * (y.im, y.re).
+// bytes), both pols: 32 complex accumulators, four scalar FMAs per complex multiply-add.
 // Work item: (subband, channel) fc, beams bt * 128 .. + 127.
 template <int OUT>
 __device__ __forceinline__ void bf_many_item(const Geometry &g, const float2 *__restrict__ ct, void *__restrict__ out,

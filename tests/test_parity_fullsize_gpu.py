@@ -110,3 +110,36 @@ def test_lofar1024_tensor_core_full_size_sampled(dev, bits):
         assert eI <= 1e-3 and eq <= 1e-3
     del out
     plan.close()
+
+
+def test_pulsar_chain_full_size_sampled(dev):
+    """The pulsar pipeline at full size (48 stations x 244 subbands x 196608 samples, 127 beams):
+    voltages of the whole block -> channel-level dedispersion (256-point runs) -> Stokes I over 16,
+    against the oracle's one-by-one evaluation of sampled (subband, channel) series."""
+    from paper_1105_0661_gb300 import Plan
+    from synth.device import make_block_device
+    wl = G.workload_lofar_fp32(0)
+    wl_v = G.Workload(**{**wl.__dict__, "output": "V"})
+    pv, ps = Plan.from_workload(wl_v), Plan.from_workload(wl)
+    d_in = make_block_device(wl, seed=0, device=dev)
+    vol = torch.empty(pv.shape("vol"), dtype=torch.complex64, device=dev)
+    pv.run_block(d_in, vol)
+    dm = 5e3                                      # large enough to rotate the 3 Hz sub-channels
+    pv.dedisperse(dm, 256, vol, vol)
+    out = torch.empty(ps.shape("stokes"), dtype=torch.float32, device=dev)
+    ps.stokes(vol, out)
+    torch.cuda.synchronize()
+    del vol
+    ob_v = O.observation_from_workload(wl_v)
+    chans = [0, 128, 255]
+    rate = wl.sample_rate_hz / 256
+    for f in (0, 243):
+        v = ob_v.run_block_sampled(d_in[:, f].cpu().numpy(), f, chans)          # [B, nc, P, M]
+        for i, c in enumerate(chans):
+            v[:, i] = O.dedisperse_series(v[:, i], ob_v.f0[f] + ob_v.df[c], rate, dm, 256)
+        p = O.stokes_from_voltages(v[:, :, 0], v[:, :, 1], "I")                  # [1, B, nc, M]
+        ref = np.moveaxis(O.integrate(p, wl.int_factor), 0, 1)                   # [B, 1, nc, M/Q]
+        got = out[:, :, f][:, :, chans].double().cpu().numpy()
+        _check_I(got, ref)
+    pv.close()
+    ps.close()
