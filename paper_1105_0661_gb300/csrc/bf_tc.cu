@@ -62,7 +62,7 @@ enum ErrCode { ERR_NONE = 0, ERR_PRODUCER = 1, ERR_MMA = 2, ERR_EPILOGUE = 3 };
 
 struct TcParams {
   int S, F, B, M, Kpad, ntiles, items_per_fc;
-  long long items;
+  int items;                  // F * 256 * items_per_fc (< 2^31 for any plan that fits in memory)
   int nstages, stage_bytes;   // B ring: stages of 2 planes x 2 tiles x Kpad K rows x 128 bytes
   int vec;                    // output rows 16-byte aligned (M/Q % 4 == 0, aligned base)
   long long stall_item;       // failure-detection test: the loads stop at this item (-1: never)
@@ -396,26 +396,31 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
     // ---------------------------------------------------------------- TMA producer
     if (lane == 0) {
       const uint32_t bytes = (uint32_t)p.stage_bytes;
-      long long g = 0, last_issued = -1;
+      int s = 0, issued_n = 0;           // ring stage and the number of stages filled so far
+      uint32_t ph = 0;                   // phase parity of stage s
       bool ok = true, stalled = false;
-      for (long long item = blockIdx.x; item < p.items && ok; item += gridDim.x) {
-        if (item == p.stall_item) { stalled = true; break; }   // test hook: a barrier nothing fills
-        const int fc = (int)(item / p.items_per_fc);
-        for (int t = 0; t < p.ntiles; ++t, ++g) {
-          const int s = (int)(g % nst);
-          const uint32_t ph = (uint32_t)(g / nst) & 1u;
+      for (int item = blockIdx.x; item < p.items && ok; item += gridDim.x) {
+        if ((long long)item == p.stall_item) { stalled = true; break; }   // test hook: a barrier nothing fills
+        const int fc = item / p.items_per_fc;
+        for (int t = 0; t < p.ntiles; ++t) {
           if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag)) { fail(abort_flag, p.err, ERR_PRODUCER); ok = false; break; }
           mbar_expect_tx(full_bar(s), bytes);
           const uint32_t dst = sB + (uint32_t)s * bytes;
           tma_load_4d(dst, &tm_hi, 0, 0, 2 * t, fc, full_bar(s));
           tma_load_4d(dst + plane_bytes, &tm_lo, 0, 0, 2 * t, fc, full_bar(s));
-          last_issued = g;
+          ++issued_n;
+          if (++s == nst) { s = 0; ph ^= 1u; }
         }
       }
       if (*abort_flag || stalled) {   // let our own copies land before the shared memory goes away
-        for (long long q = (last_issued - nst + 1 > 0 ? last_issued - nst + 1 : 0); q <= last_issued; ++q) {
+        // the last min(issued, nst) fills, newest first: stage s - 1, s - 2, ... (wrapping)
+        int q = s;
+        uint32_t qph = ph;
+        for (int k = 0; k < nst && k < issued_n; ++k) {
+          if (q == 0) { q = nst; qph ^= 1u; }
+          --q;
           volatile int never = 0;
-          mbar_wait(full_bar((int)(q % nst)), (uint32_t)(q / nst) & 1u, &never);
+          mbar_wait(full_bar(q), qph, &never);
         }
       }
     }
@@ -425,18 +430,16 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
       const int ksteps = p.Kpad >> 4;
       const uint64_t desc_b0 = smem_desc(sB, (uint32_t)(p.Kpad * 128));   // stage 0, hi plane, k step 0
       bool issued = false, ok = true;
-      long long g = 0;
-      int it = 0;
-      for (long long item = blockIdx.x; item < p.items && ok; item += gridDim.x, ++it) {
-        for (int t = 0; t < p.ntiles && ok; ++t, ++g) {
-          const int s = (int)(g % nst);
-          const uint32_t ph = (uint32_t)(g / nst) & 1u;
+      int s = 0, it = 0;
+      uint32_t ph = 0, gpar = 0;         // ring stage and its phase parity; tile-pair parity
+      for (int item = blockIdx.x; item < p.items && ok; item += gridDim.x, ++it) {
+        for (int t = 0; t < p.ntiles && ok; ++t, gpar ^= 1u) {
           if (!mbar_wait(full_bar(s), ph, abort_flag)) { fail(abort_flag, p.err, ERR_MMA); ok = false; break; }
           for (int mt = 0; mt < kMTiles; ++mt) {
             if (t == 0 && !mbar_wait(afull_bar(mt), (uint32_t)it & 1u, abort_flag)) {
               fail(abort_flag, p.err, ERR_MMA); ok = false; break;
             }
-            if (!mbar_wait(acce_bar(mt), ((uint32_t)g & 1u) ^ 1u, abort_flag)) {
+            if (!mbar_wait(acce_bar(mt), gpar ^ 1u, abort_flag)) {
               fail(abort_flag, p.err, ERR_MMA); ok = false; break;
             }
             tc_fence_after();
@@ -457,6 +460,7 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
             issued = true;
           }
           if (ok) umma_commit(empty_bar(s));
+          if (++s == nst) { s = 0; ph ^= 1u; }
         }
       }
       if (issued) {   // every MMA (and its barrier arrivals) retired before TMEM is released
@@ -476,14 +480,14 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
     const int Mq = p.M / Q;
     const long long pstride = (long long)p.F * kN * Mq;      // between Stokes parameters
     float *const qbuf = stage_out + quad * 2 * St::kBuf;
-    long long g = 0;
+    uint32_t gpar = 0;                   // tile-pair parity
     int fl = 0;
     bool ok = true;
-    for (long long item = blockIdx.x; item < p.items && ok; item += gridDim.x) {
-      const int fc = (int)(item / p.items_per_fc);
-      const int bb = (int)(item - (long long)fc * p.items_per_fc);
+    for (int item = blockIdx.x; item < p.items && ok; item += gridDim.x) {
+      const int fc = item / p.items_per_fc;
+      const int bb = item - fc * p.items_per_fc;
       const int f = fc / kN, c = fc - f * kN;
-      if (item == blockIdx.x) {           // weights of the first item; later ones follow each last tile
+      if (item == (int)blockIdx.x) {      // weights of the first item; later ones follow each last tile
         for (int mt = 0; mt < kMTiles; ++mt) {
           const uint32_t ta_hi = tmem + lane_off + kACol0 + (uint32_t)(2 * mt * 64);
           WeightTables tab;
@@ -494,10 +498,10 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
           if (lane == 0) mbar_arrive(afull_bar(mt));
         }
       }
-      const long long nitem = item + gridDim.x;
-      const int nfc = (int)(nitem / p.items_per_fc);
-      const int nbb = (int)(nitem - (long long)nfc * p.items_per_fc);
-      for (int t = 0; t < p.ntiles && ok; ++t, ++g) {
+      const int nitem = item + gridDim.x;
+      const int nfc = nitem / p.items_per_fc;
+      const int nbb = nitem - nfc * p.items_per_fc;
+      for (int t = 0; t < p.ntiles && ok; ++t, gpar ^= 1u) {
         const int wbase = (t / St::kPeriod) * 8;
         float *const buf = qbuf + (fl & 1) * St::kBuf;
         for (int mt = 0; mt < kMTiles; ++mt) {
@@ -505,7 +509,7 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
           WeightTables tab;
           if (boundary)   // the next item's table values, in flight while the last accumulator fills
             load_weight_tables(p, nfc / kN, nbb * kBeamsPerItem + mt * (kRows / 2) + quad * 16 + jq, ro, half, tab);
-          if (!mbar_wait(accf_bar(mt), (uint32_t)g & 1u, abort_flag)) { fail(abort_flag, p.err, ERR_EPILOGUE); ok = false; break; }
+          if (!mbar_wait(accf_bar(mt), gpar, abort_flag)) { fail(abort_flag, p.err, ERR_EPILOGUE); ok = false; break; }
           tc_fence_after();
           const int b = bb * kBeamsPerItem + mt * (kRows / 2) + quad * 16 + jq;
           float *const orow = p.out + (((long long)b * NS * p.F + f) * kN + c) * Mq;
@@ -599,13 +603,15 @@ cudaError_t launch_bf_tc(const Geometry &g, int out_kind, const void *tm_hi, con
   p.nstages = 0;
   p.ntiles = tc_tiles(g.M) / 2;
   p.items_per_fc = (g.B + kBeamsPerItem - 1) / kBeamsPerItem;
-  p.items = (long long)g.F * kN * p.items_per_fc;
+  const long long items = (long long)g.F * kN * p.items_per_fc;
+  if (items >= (1ll << 31)) return cudaErrorInvalidValue;
+  p.items = (int)items;
   p.phase0 = g.phase0; p.step = g.step; p.out = out; p.err = err;
   p.vec = (g.M / g.Q) % 4 == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0;
   p.stall_item = stall_item;
   const int sms = sm_count();
   if (sms <= 0) return cudaErrorInvalidDevice;
-  const int grid = (int)(p.items < sms ? p.items : sms);
+  const int grid = p.items < sms ? p.items : sms;
   const CUtensorMap *hi = reinterpret_cast<const CUtensorMap *>(tm_hi);
   const CUtensorMap *lo = reinterpret_cast<const CUtensorMap *>(tm_lo);
   if (out_kind == OUT_STOKES_IQUV) return launch_ns<4>(g.Q, hi, lo, p, grid, st);
