@@ -569,7 +569,7 @@ def run_dedisperse(args):
     pk, pk_kind = peaks()
     wl = workload(args.workload, args.subbands, args.bits)
     wl_v = G.Workload(**{**wl.__dict__, "output": "V", "name": wl.name + "-voltages"})
-    pv = Plan.from_workload(wl_v)
+    pv = Plan.from_workload(wl_v, precision=args.precision)
     ps = Plan.from_workload(wl)
     d_in = make_block_device(wl, seed=0, device=dev)
     vol = torch.empty(pv.shape("vol"), dtype=torch.complex64, device=dev)
@@ -616,8 +616,9 @@ def run_dedisperse(args):
     line = {
         "metric": "station-samples/s", "value": ss / (ms / 1e3), "unit": "station-samples/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"pulsar pipeline: {wl.name}, voltages -> channel-level dedispersion "
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f16+f32",
+        "data": "synthetic",
+        "config": {"workload": f"pulsar pipeline: {wl.name}, voltages ({args.precision}) -> channel-level dedispersion "
                                f"({K}-point FFT, DM {dm}) -> Stokes {wl.output} over {wl.int_factor}",
                    "voltage_bytes": dims.vol_bytes, "l2": "inputs larger than L2"},
         "gpu_launches": sum(v["launches"] for v in kernels.values()),

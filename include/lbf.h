@@ -136,9 +136,9 @@ typedef struct lbf_plan_s *lbf_plan_t;
  * With precision LBF_FP16_TC the many-beam beam former runs on the tensor cores (tcgen05, FP16
  * operands, FP32 accumulation): the filtered spectrum Y of either sample width feeds it as two
  * FP16 planes (hi = fp16(Y), lo = fp16(Y - hi)) and the weights are split the same way, three
- * products per tile; it needs S <= 64 and a Stokes output.
+ * products per tile, writing Stokes or beam voltages; it needs S <= 64.
  * Errors: LBF_EINVAL (bad config), LBF_EUNSUPPORTED (N != 256, L != 16, or an FP16_TC plan with
- * S > 64 or voltage output), LBF_ENOMEM, LBF_ECUDA. */
+ * S > 64), LBF_ENOMEM, LBF_ECUDA. */
 lbf_status lbf_plan(const lbf_config *cfg, lbf_plan_t *out);
 
 /* Release every device buffer of the plan (synchronises the device first). NULL is a no-op. */
@@ -165,7 +165,8 @@ lbf_status lbf_delay_correct(lbf_plan_t plan, const void *d_chan, void *d_ct, vo
 
 /* Steps a5-a6: weights generated on the device (FP64 phase, reduced to one cycle, FP32 sincos)
  * and the tied-array beam sum (Section 4.3).  d_ct: device `ct` (read); d_vol: device `vol`
- * layout (written).  Stateless. */
+ * layout (written).  Stateless.  A tensor-core plan converts `ct` into its FP16 scratch first
+ * (not available with LBF_FLAG_EXTERNAL_WORKSPACE: LBF_EUNSUPPORTED). */
 lbf_status lbf_beamform(lbf_plan_t plan, const void *d_ct, void *d_vol, void *stream);
 
 /* Steps a5-a7 fused: beam former with the Stokes/integration epilogue (Sections 4.3, 4.5, 5.1).

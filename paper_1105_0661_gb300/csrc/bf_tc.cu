@@ -1,6 +1,6 @@
 // Tensor-core tied-array beam former (Section 4.3) for many beams: tcgen05 UMMA with FP16 operands
 // and FP32 accumulation in TMEM, fused with the Stokes I / IQUV integration epilogue (Sections 4.5,
-// 5.1).
+// 5.1) or writing the beam voltages (complex-voltage output, Section 3).
 //
 // Per (subband f, channel c) the complex product V = W Y is run as a real GEMM
 //     D[r][n] = sum_k A[r][k] B[k][n],   r = (beam, re|im),  k = (station, re|im),  n = (pol, m)
@@ -241,6 +241,8 @@ __device__ __forceinline__ void write_weights(const TcParams &p, uint32_t ta_hi,
   tmem_wait_st();
 }
 
+constexpr int kVStageBytes = 8 * 2 * kSpec * 8;   // voltages: 8 beams x 2 pols x 32 spectra, cf32
+
 // Output staging.  For Q >= 8 the epilogue collects 8 consecutive windows of every (beam, Stokes
 // parameter) row of its lane quadrant in shared memory and then writes each row segment as two
 // 16-byte stores (a whole 32-byte sector), instead of scattering 4-byte stores over rows that lie
@@ -250,9 +252,10 @@ template <int NS, int Q>
 struct Stage {
   static constexpr bool kOn = Q >= 8;
   static constexpr int kPeriod = Q >= 8 ? Q / 8 : 1;          // tile pairs per flush
-  static constexpr int kRow = NS * 8;                          // floats per beam
+  static constexpr int kRow = NS * 8;                          // floats per beam (0: voltages)
   static constexpr int kBuf = 32 * kRow;                       // floats per quadrant buffer
-  static constexpr int kBytes = kOn ? 4 * 2 * kBuf * 4 : 0;    // 4 quadrants x 2 buffers
+  static constexpr int kBytes = NS == 0 ? 8 * kVStageBytes       // voltages: 4 KB per epilogue warp
+                                        : kOn ? 4 * 2 * kBuf * 4 : 0;   // 4 quadrants x 2 buffers
   __device__ static int index(int jq, int param, int wl) {     // float index within a beam's row
     const int chunk = (param * 2 + (wl >> 2)) ^ (jq & (2 * NS - 1));
     return chunk * 4 + (wl & 3);
@@ -314,6 +317,65 @@ __device__ __forceinline__ void drain_tile(uint32_t taddr, int m0, int ro, int j
       }
       sxx = syy = sxy = sv = 0.f;
     }
+  }
+}
+
+// One 32-spectrum tile of an accumulator as beam voltages (pol X at `taddr`, pol Y 32 columns on;
+// spectra m0 .. m0 + 31) for the 16 beams of this warp's lanes (beam b0 + jq), into vol
+// [B][F][N][P][M] cf32 (`vrow0` is the pol-X row of beam b0; rows of one beam are M apart, beams
+// `bstride` apart).  The Re lane of a beam keeps the real parts of spectra 0..15 and receives their
+// imaginary parts from the Im lane, which keeps the imaginary parts of 16..31 and receives their
+// real parts (one shuffle per value).  The complex values then go through the warp's 4 KB of
+// shared memory, 8 beams at a time (spectrum index XOR 2 x beam, so the writes hit distinct
+// banks), and out as whole 256-byte rows: 16 lanes per (beam, pol) row, two rows per store.
+__device__ __forceinline__ void drain_tile_v(uint32_t taddr, int m0, int ro, int jq, int lane, int M, int B, int b0,
+                                             float2 *vrow0, long long bstride, bool vec, float2 *stage) {
+  float v[2][2][16];   // [pol][spectrum half][16]
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    tmem_ld16(taddr + (uint32_t)(h * 16), v[0][h]);
+    tmem_ld16(taddr + (uint32_t)(kSpec + h * 16), v[1][h]);
+  }
+  tmem_wait_ld();
+  float2 o[2][16];     // this lane's complex values: spectra 16 ro + j, both pols
+#pragma unroll
+  for (int pol = 0; pol < 2; ++pol)
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const float recv = __shfl_xor_sync(0xffffffffu, ro ? v[pol][0][j] : v[pol][1][j], 1);
+      o[pol][j] = ro ? make_float2(recv, v[pol][1][j]) : make_float2(v[pol][0][j], recv);
+    }
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {          // beams 8 r .. 8 r + 7 of the warp's 16
+    if ((jq >> 3) == r) {
+      const int bl = jq & 7;
+#pragma unroll
+      for (int pol = 0; pol < 2; ++pol)
+#pragma unroll
+        for (int j = 0; j < 16; ++j) stage[(bl * 2 + pol) * kSpec + 16 * ro + (j ^ (2 * bl))] = o[pol][j];
+    }
+    __syncwarp();
+    const int j2 = lane & 15;            // spectra 2 j2, 2 j2 + 1 of the row
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int row = 2 * k + (lane >> 4);   // (beam, pol) of the 8 staged beams
+      const int bl = row >> 1, pol = row & 1;
+      const int b = b0 + 8 * r + bl;
+      const int s0 = 2 * j2;                 // spectrum within the tile (even)
+      const float4 val = *reinterpret_cast<const float4 *>(
+          stage + row * kSpec + (s0 & 16) + ((s0 & 15) ^ (2 * bl)));
+      const int m = m0 + s0;
+      if (b < B) {
+        float2 *dst = vrow0 + (long long)(8 * r + bl) * bstride + (long long)pol * M + m;
+        if (vec && m + 1 < M) {
+          *reinterpret_cast<float4 *>(dst) = val;
+        } else {
+          if (m < M) dst[0] = make_float2(val.x, val.y);
+          if (m + 1 < M) dst[1] = make_float2(val.z, val.w);
+        }
+      }
+    }
+    __syncwarp();
   }
 }
 
@@ -512,9 +574,18 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
           if (!mbar_wait(accf_bar(mt), gpar, abort_flag)) { fail(abort_flag, p.err, ERR_EPILOGUE); ok = false; break; }
           tc_fence_after();
           const int b = bb * kBeamsPerItem + mt * (kRows / 2) + quad * 16 + jq;
-          float *const orow = p.out + (((long long)b * NS * p.F + f) * kN + c) * Mq;
-          drain_tile<NS, Q>(tmem + lane_off + (uint32_t)(mt * kAccCols + half * 2 * kSpec), t * 4 * kSpec / 2 + half * kSpec,
-                            ro, jq, p.M, b < p.B, orow, pstride, buf + (mt * 16 + jq) * St::kRow, wbase);
+          const uint32_t taddr = tmem + lane_off + (uint32_t)(mt * kAccCols + half * 2 * kSpec);
+          const int m0 = t * 2 * kSpec + half * kSpec;
+          if constexpr (NS == 0) {
+            const int b0 = bb * kBeamsPerItem + mt * (kRows / 2) + quad * 16;   // beam of lanes 0, 1
+            const long long bstride = (long long)p.F * kN * kP * p.M;             // between beams
+            float2 *const v0 = reinterpret_cast<float2 *>(p.out) + (((long long)b0 * p.F + f) * kN + c) * kP * p.M;
+            drain_tile_v(taddr, m0, ro, jq, lane, p.M, p.B, b0, v0, bstride, p.vec != 0,
+                         reinterpret_cast<float2 *>(stage_out) + (warp - 2) * (kVStageBytes / 8));
+          } else {
+            float *const orow = p.out + (((long long)b * NS * p.F + f) * kN + c) * Mq;
+            drain_tile<NS, Q>(taddr, m0, ro, jq, p.M, b < p.B, orow, pstride, buf + (mt * 16 + jq) * St::kRow, wbase);
+          }
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(acce_bar(mt));
@@ -528,13 +599,15 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
             if (lane == 0) mbar_arrive(afull_bar(mt));
           }
         }
-        if (St::kOn && ok && ((t + 1) % St::kPeriod == 0 || t == p.ntiles - 1)) {
+        if constexpr (St::kOn) {
+        if (ok && ((t + 1) % St::kPeriod == 0 || t == p.ntiles - 1)) {
           // both warps of the quadrant have staged their windows: write the rows out
           __syncwarp();
           if (lane == 0) mbar_arrive(pair_bar(quad));
           if (!mbar_wait(pair_bar(quad), (uint32_t)fl & 1u, abort_flag)) { fail(abort_flag, p.err, ERR_EPILOGUE); ok = false; break; }
           flush_stage<NS, Q>(p, buf, half * 32 + lane, quad, bb, f, c, wbase);
           ++fl;
+        }
         }
       }
     }
@@ -607,13 +680,15 @@ cudaError_t launch_bf_tc(const Geometry &g, int out_kind, const void *tm_hi, con
   if (items >= (1ll << 31)) return cudaErrorInvalidValue;
   p.items = (int)items;
   p.phase0 = g.phase0; p.step = g.step; p.out = out; p.err = err;
-  p.vec = (g.M / g.Q) % 4 == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+  const bool aligned = (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+  p.vec = out_kind == OUT_VOLTAGES ? (g.M % 2 == 0 && aligned) : ((g.M / g.Q) % 4 == 0 && aligned);
   p.stall_item = stall_item;
   const int sms = sm_count();
   if (sms <= 0) return cudaErrorInvalidDevice;
   const int grid = p.items < sms ? p.items : sms;
   const CUtensorMap *hi = reinterpret_cast<const CUtensorMap *>(tm_hi);
   const CUtensorMap *lo = reinterpret_cast<const CUtensorMap *>(tm_lo);
+  if (out_kind == OUT_VOLTAGES) return launch_q<0, 1>(hi, lo, p, grid, st);
   if (out_kind == OUT_STOKES_IQUV) return launch_ns<4>(g.Q, hi, lo, p, grid, st);
   if (out_kind == OUT_STOKES_I) return launch_ns<1>(g.Q, hi, lo, p, grid, st);
   return cudaErrorInvalidValue;

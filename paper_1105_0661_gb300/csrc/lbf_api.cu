@@ -84,9 +84,7 @@ lbf_status validate(const lbf_config *c) {
   for (int i = 0; i < c->n_subbands; ++i) if (!std::isfinite(c->subband_centre_hz[i])) return LBF_EINVAL;
   for (int i = 0; i < 2 * c->n_beams; ++i) if (!std::isfinite(c->beam_dlm[i])) return LBF_EINVAL;
   if (c->n_channels != lbf::kN || c->n_taps != lbf::kL) return LBF_EUNSUPPORTED;
-  if (c->precision == LBF_FP16_TC &&
-      (c->output == LBF_VOLTAGES || c->n_stations > lbf::tc_max_stations()))
-    return LBF_EUNSUPPORTED;
+  if (c->precision == LBF_FP16_TC && c->n_stations > lbf::tc_max_stations()) return LBF_EUNSUPPORTED;
   if (c->bf_variant == LBF_BF_MANY && c->n_stations > lbf::many_beam_max_stations()) return LBF_EUNSUPPORTED;
   // index arithmetic: per-plan sizes must keep grid dimensions in range
   const long long ctas = (long long)c->n_subbands * lbf::kN * ((c->n_beams + 7) / 8);
@@ -435,9 +433,19 @@ lbf_status lbf_beamform(lbf_plan_t p, const void *d_ct, void *d_vol, void *strea
   if (s != LBF_OK) return s;
   if (p->M == 0) return LBF_OK;
   if (!device_ptr(d_ct, 8) || !device_ptr(d_vol, 8)) return LBF_EINVAL;
-  if (p->tc) return LBF_EUNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   const lbf::Geometry g = p->geometry();
+  if (p->tc) {   // the tensor-core beam former writing voltages, from the plan's FP16 scratch
+    if (p->external_ws) return LBF_EUNSUPPORTED;
+    const lbf::Ct16Out o = ct16_out(p);
+    cudaError_t e = traced(p, K_CT16, st, [&] { return lbf::launch_ct_to_ct16(g, (const float2 *)d_ct, o, st); });
+    if (e != cudaSuccess) return cuda_status(e);
+    return cuda_status(traced(p, K_BF_TC, st, [&] {
+      const long long stall = p->stall_item;
+      p->stall_item = -1;
+      return lbf::launch_bf_tc(g, lbf::OUT_VOLTAGES, &p->tmap[0], &p->tmap[1], static_cast<float *>(d_vol), p->d_err,
+                               st, stall); }));
+  }
   return cuda_status(traced(p, bf_kernel_id(p), st, [&] {
     return lbf::launch_beamform(g, p->variant, lbf::OUT_VOLTAGES, (const float2 *)d_ct, d_vol, st); }));
 }

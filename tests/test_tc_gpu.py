@@ -152,3 +152,66 @@ def test_bounded_wait_expires_reports_and_context_survives(dev):
     eI, eq = _errors(o.cpu().numpy().astype(np.float64), ob.run_block(blk))
     assert eI <= TOL
     p.close()
+
+
+@pytest.mark.parametrize("S,B,M,Q,out", [(1, 1, 16, 16, "I"), (3, 3, 32, 1, "IQUV"), (64, 129, 16, 8, "IQUV")])
+def test_tc_degenerate_shapes(dev, S, B, M, Q, out):
+    """One station (Kpad 16, a single K step), a single beam, fewer spectra than one 32-spectrum
+    tile (the second tile of the pair is all padding), and the largest station count with one
+    beam past a 128-beam block."""
+    from paper_1105_0661_gb300 import Plan
+    wl = _wl(S=S, B=B, out=out, bits=16, T=M * N, Q=Q, F=1)
+    p = Plan.from_workload(wl, precision="fp16tc")
+    ob = O.observation_from_workload(wl)
+    blk = G.make_block(wl, seed=S + B)
+    o = torch.empty(p.shape("stokes"), dtype=torch.float32, device=dev)
+    p.run_block(torch.from_numpy(blk).to(dev), o)
+    assert p.device_status() == 0
+    eI, eq = _errors(o.cpu().numpy().astype(np.float64), ob.run_block(blk))
+    print(f"TC S={S} B={B} M={M} Q={Q} {out}: I {eI:.2e} QUV/I {eq:.2e}")
+    assert eI <= TOL and eq <= TOL
+    p.close()
+
+
+def _vol_rel_rms(got, ref):
+    """max over (beam, subband) of the relative RMS error of [B][F][N][P][M] voltages"""
+    num = np.sqrt(np.sum(np.abs(got - ref) ** 2, axis=(2, 3, 4)))
+    den = np.sqrt(np.sum(np.abs(ref) ** 2, axis=(2, 3, 4)))
+    return float((num / den).max())
+
+
+@pytest.mark.parametrize("S,B,M,bits", [(48, 130, 80, 16), (16, 70, 64, 8), (8, 5, 47, 16)])
+def test_tc_voltages_match_oracle(dev, S, B, M, bits):
+    """Complex-voltage output from the tensor cores (run_block, plan output V): beam voltages
+    [B][F][N][P][M] within 1e-4 relative RMS per (beam, subband); M = 47 takes the unaligned
+    store path and a ragged last tile."""
+    from paper_1105_0661_gb300 import Plan
+    wl = _wl(S=S, B=B, out="V", bits=bits, T=M * N, Q=1)
+    p = Plan.from_workload(wl, precision="fp16tc")
+    ob = O.observation_from_workload(wl)
+    blk = G.make_block(wl, seed=11)
+    vol = torch.empty(p.shape("vol"), dtype=torch.complex64, device=dev)
+    p.run_block(torch.from_numpy(blk).to(dev), vol)
+    assert p.device_status() == 0
+    err = _vol_rel_rms(vol.cpu().numpy().astype(np.complex128), ob.run_block(blk))
+    print(f"TC voltages S={S} B={B} M={M} bits={bits}: max rel RMS {err:.2e}")
+    assert err <= 1e-4
+    p.close()
+
+
+def test_tc_split_beamform_voltages(dev):
+    """lbf_beamform on a tensor-core plan (corner-turned input converted to the FP16 scratch)."""
+    from paper_1105_0661_gb300 import Plan
+    wl = _wl(S=48, B=130, out="I", T=64 * N, Q=16)
+    p = Plan.from_workload(wl, precision="fp16tc")
+    ob = O.observation_from_workload(wl)
+    rng = np.random.default_rng(5)
+    shp = p.shape("ct")
+    ct = (rng.standard_normal(shp) + 1j * rng.standard_normal(shp)).astype(np.complex64)
+    vol = torch.empty(p.shape("vol"), dtype=torch.complex64, device=dev)
+    p.beamform(torch.from_numpy(ct).to(dev), vol)
+    assert p.device_status() == 0
+    err = _vol_rel_rms(vol.cpu().numpy().astype(np.complex128), ob.beamform(ct.astype(np.complex128)))
+    print(f"TC split beamform: max rel RMS {err:.2e}")
+    assert err <= 1e-4
+    p.close()
