@@ -284,10 +284,12 @@ lbf_status lbf_run_block_static(const lbf_config *cfg, const void *d_in, void *d
  * a batch runs as ONE persistent grouped launch per stage -- filter bank (with the delay / bandpass
  * / corner-turn epilogue), history update, beam former with its Stokes epilogue -- instead of
  * three launches per plan; CTAs take work items from a shared counter, so uneven observations
- * load-balance.  Plans of a batch must be FP32 plans with their own scratch (no
- * LBF_FLAG_EXTERNAL_WORKSPACE), on the current device, each in at most one active batch; their
- * history advances exactly as with lbf_run_block.  d_in[i] / d_out[i] are plan i's device `in`
- * and `out` (or `vol`) buffers. */
+ * load-balance.  Tensor-core plans join the grouped filter bank and history update and then
+ * run their own persistent tensor-core beam former (one launch per such plan, after the grouped
+ * FP32 beam former).  Plans of a batch must use their own scratch (no
+ * LBF_FLAG_EXTERNAL_WORKSPACE), be on the current device and be in at most one active batch;
+ * their history advances exactly as with lbf_run_block.  d_in[i] / d_out[i] are plan i's device
+ * `in` and `out` (or `vol`) buffers. */
 typedef struct lbf_batch_s *lbf_batch_t;
 
 typedef struct lbf_batch_tuning {

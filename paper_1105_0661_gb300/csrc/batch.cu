@@ -5,6 +5,10 @@
 // (observation, subband-channel, beam group) items until all are done, so small observations do
 // not leave the GPU idle and large ones do not serialise the batch.
 //
+// Tensor-core plans join the grouped filter bank (writing their FP16 planes) and the grouped
+// history update; each then adds its own persistent tensor-core beam-former launch (one CTA per
+// SM already) after the grouped FP32 beam former.
+//
 // A batch can be captured as CUDA graphs (one per history parity: each block flips every plan's
 // history ping-pong) and replayed with a single graph launch per block, and its tile shapes --
 // spectra per filter-bank item and, for observations with 9..64 beams, the few- or many-beam
@@ -54,6 +58,7 @@ struct lbf_batch_s {
   long long bf_items[2] = {0, 0};
   size_t bf_smem[2] = {0, 0};
   int ppf_ctas = 0, sms = 0;
+  std::vector<void *> tc_out;          // output of each plan's block (used by tensor-core plans)
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int graph_parity = 0;                // which graph describes the current state
 };
@@ -81,6 +86,10 @@ void fill_tables(lbf_batch_t b, int par, const void *const *d_in, void *const *d
     G.hist = p->hist[cur];
     G.new_hist = p->hist[cur ^ 1];
     G.ct = p->ws;
+    G.tc = p->tc ? 1 : 0;
+    G.ct16.hi = p->ct16[0];
+    G.ct16.lo = p->tc ? static_cast<unsigned char *>(p->ct16[0]) + p->ct16_bytes : nullptr;
+    G.ct16.kpad = p->kpad;
     G.bits = p->bits;
     G.spc = b->spc;
     G.chunks = (p->M + b->spc - 1) / b->spc;
@@ -91,6 +100,7 @@ void fill_tables(lbf_batch_t b, int par, const void *const *d_in, void *const *d
   }
   b->ppf_items = pi;
   b->hist_items = hi;
+  b->tc_out.assign(d_out, d_out + n);
   // beam former: class 0 (two CTAs per SM fit) first, then class 1
   int slot = par * n;
   for (int cls = 0; cls < 2; ++cls) {
@@ -99,6 +109,7 @@ void fill_tables(lbf_batch_t b, int par, const void *const *d_in, void *const *d
     int cnt = 0;
     for (int i = 0; i < n; ++i) {
       lbf_plan_t p = b->plans[i];
+      if (p->tc) continue;                  // its own tensor-core launch
       const size_t sm = lbf::bf_smem_bytes(b->variant[i], p->S);
       if ((sm > kTwoPerSm) != (cls == 1)) continue;
       lbf::BfGroup &Bg = b->h_bf[slot++];
@@ -135,6 +146,20 @@ cudaError_t enqueue(lbf_batch_t b, int par, cudaStream_t st) {
   if (e == cudaSuccess && b->bf_n[1])
     e = lbf::launch_bf_group(b->d_bf + par * n + b->bf_n[0], b->bf_n[1], b->bf_items[1], b->d_counter + 2, b->sms,
                              b->bf_smem[1], st);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    lbf_plan_t p = b->plans[i];
+    if (!p->tc || p->M == 0) continue;
+    const lbf::Geometry g = p->geometry();
+    if (p->inc) {
+      lbf::Ct16Out o;
+      o.hi = p->ct16[0];
+      o.lo = static_cast<unsigned char *>(p->ct16[0]) + p->ct16_bytes;
+      o.kpad = p->kpad;
+      e = lbf::launch_incoherent_ct16(g, p->out_kind, o, static_cast<float *>(b->tc_out[i]), st);
+    }
+    if (e == cudaSuccess)
+      e = lbf::launch_bf_tc(g, p->out_kind, &p->tmap[0], &p->tmap[1], static_cast<float *>(b->tc_out[i]), p->d_err, st);
+  }
   return e;
 }
 
@@ -165,7 +190,7 @@ lbf_status lbf_batch_create(const lbf_plan_t *plans, int32_t n, lbf_batch_t *out
     lbf_plan_t p = plans[i];
     if (!plan_ok(p)) return LBF_ESTATE;
     if (p->device != dev) return LBF_ESTATE;
-    if (p->tc || p->external_ws) return LBF_EUNSUPPORTED;   // batches run the FP32 path on plan scratch
+    if (p->external_ws) return LBF_EUNSUPPORTED;   // batches use each plan's own scratch
     for (int j = 0; j < i; ++j)
       if (plans[j] == p) return LBF_EINVAL;
   }
@@ -278,7 +303,7 @@ lbf_status lbf_batch_tune(lbf_batch_t b, const void *const *d_in, void *const *d
   for (int i = 0; i < n; ++i) {
     lbf_plan_t p = b->plans[i];
     base[i] = p->variant;
-    const bool mid = p->B > 8 && p->B <= 64 && p->S <= lbf::many_beam_max_stations();
+    const bool mid = !p->tc && p->B > 8 && p->B <= 64 && p->S <= lbf::many_beam_max_stations();
     alt[i] = mid ? (p->variant == 1 ? 2 : 1) : p->variant;
     has_mid = has_mid || mid;
   }

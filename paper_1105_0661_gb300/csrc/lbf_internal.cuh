@@ -47,7 +47,9 @@ struct PpfGroup {
   const void *in;
   const void *hist;
   void *new_hist;
-  float2 *ct;                 // corner-turned scratch of this observation
+  float2 *ct;                 // corner-turned scratch of this observation (FP32 plans)
+  Ct16Out ct16;               // FP16 hi+lo planes (tensor-core plans)
+  int tc;                     // 1: write ct16 instead of ct
   int bits;
   int spc;                    // spectra per filter-bank work item (a multiple of 16)
   int chunks;                 // ceil(M / spc)

@@ -303,11 +303,19 @@ ppf_group_kernel(const PpfGroup *__restrict__ grp, int ngrp, long long total, un
     const long long sf = local / G.chunks;
     const int chunk = (int)(local - sf * G.chunks);
     const int s = (int)(sf / G.g.F), f = (int)(sf - (long long)s * G.g.F);
-    PpfOut po{G.ct, nullptr, nullptr, 0};
-    if (G.bits == 16)
-      ppf_item<16, MODE_CT32>(G.g, (const uint2 *)G.in, (const uint2 *)G.hist, po, s, f, chunk, G.spc, smem_raw);
-    else
-      ppf_item<8, MODE_CT32>(G.g, (const uint32_t *)G.in, (const uint32_t *)G.hist, po, s, f, chunk, G.spc, smem_raw);
+    if (G.tc) {   // tensor-core plan: FP16 hi+lo planes
+      PpfOut po{nullptr, reinterpret_cast<__half *>(G.ct16.hi), reinterpret_cast<__half *>(G.ct16.lo), G.ct16.kpad};
+      if (G.bits == 16)
+        ppf_item<16, MODE_CT16>(G.g, (const uint2 *)G.in, (const uint2 *)G.hist, po, s, f, chunk, G.spc, smem_raw);
+      else
+        ppf_item<8, MODE_CT16>(G.g, (const uint32_t *)G.in, (const uint32_t *)G.hist, po, s, f, chunk, G.spc, smem_raw);
+    } else {
+      PpfOut po{G.ct, nullptr, nullptr, 0};
+      if (G.bits == 16)
+        ppf_item<16, MODE_CT32>(G.g, (const uint2 *)G.in, (const uint2 *)G.hist, po, s, f, chunk, G.spc, smem_raw);
+      else
+        ppf_item<8, MODE_CT32>(G.g, (const uint32_t *)G.in, (const uint32_t *)G.hist, po, s, f, chunk, G.spc, smem_raw);
+    }
   }
 }
 

@@ -76,3 +76,42 @@ def test_batch_equals_separate_runs():
             scale = np.abs(r).max()
             assert np.max(np.abs(g - r)) <= 1e-5 * scale, (k, i)
     batch.close()
+
+
+def test_batch_with_tensor_core_plans_equals_separate_runs():
+    """Tensor-core plans (Stokes I, IQUV with the incoherent beam, voltages) and FP32 plans in one
+    batch: grouped filter bank writing the FP16 planes, then one tensor-core launch per plan;
+    every output equals the same plan run alone, block after block, also as graph replays."""
+    from paper_1105_0661_gb300 import Batch, Plan, build_lib
+    build_lib.build()
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    wls = _specs()
+    kinds = [dict(), dict(precision="fp16tc"), dict(precision="fp16tc", incoherent_beam=True),
+             dict(precision="fp16tc"), dict(precision="fp16tc")]
+    solo = [Plan.from_workload(wl, **kw) for wl, kw in zip(wls, kinds)]
+    grouped = [Plan.from_workload(wl, **kw) for wl, kw in zip(wls, kinds)]
+    batch = Batch(grouped)
+    nblk = 4
+    blocks = [[torch.from_numpy(G.make_block(wl, seed=40 + i, block_index=k)).to(dev) for k in range(nblk)]
+              for i, wl in enumerate(wls)]
+    so = [_out(p, dev) for p in solo]
+    bo = [_out(p, dev) for p in grouped]
+    d_in = [torch.empty_like(blocks[i][0]) for i in range(len(wls))]
+    for k in range(nblk):
+        for i, p in enumerate(solo):
+            p.run_block(blocks[i][k], so[i])
+        for i in range(len(wls)):
+            d_in[i].copy_(blocks[i][k])
+        if k < 2:
+            batch.run(d_in, bo)
+        else:
+            if k == 2:
+                batch.capture(d_in, bo)
+            batch.launch()
+        torch.cuda.synchronize()
+        for i in range(len(wls)):
+            assert torch.equal(so[i], bo[i]), (k, i)
+    for p in grouped:
+        assert p.device_status() == 0
+    batch.close()
