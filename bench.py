@@ -634,6 +634,109 @@ def run_dedisperse(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- Section 8(f) rows
+def run_superstation(args):
+    """Superstation beam former (Section 4.2) on the LOFAR observation's corner-turned block:
+    48 stations summed in 24 pairs; HBM-bound (read every station, write every group)."""
+    import numpy as np
+    import torch
+
+    from paper_1105_0661_gb300 import Plan
+    from paper_1105_0661_gb300.build_lib import build
+
+    build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    pk, pk_kind = peaks()
+    wl = workload(args.workload, args.subbands, args.bits)
+    plan = Plan.from_workload(wl)
+    S = wl.n_stations
+    groups = np.arange(S) // 2
+    G_n = int(groups.max()) + 1
+    gen = torch.Generator(device=dev).manual_seed(0)
+    ct = torch.randn(plan.shape("ct"), dtype=torch.complex64, device=dev, generator=gen)
+    F, N, _, P, M = plan.shape("ct")
+    ss = torch.empty((F, N, G_n, P, M), dtype=torch.complex64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    for _ in range(args.warmup):
+        plan.superstation(groups, ct, ss, stream)
+    stream.synchronize()
+    with ClockSampler("0") as clk:
+        plan.trace_begin(args.steps + 8)
+        for _ in range(args.steps):
+            plan.superstation(groups, ct, ss, stream)
+        stream.synchronize()
+        tr = plan.trace_end()
+    n, tms = tr["superstation"]
+    avg_s = tms / n / 1e3
+    nbytes = ct.numel() * 8 + ss.numel() * 8
+    gbs = nbytes / avg_s / 1e9
+    line = {
+        "metric": "station-samples/s", "value": wl.station_samples() / avg_s, "unit": "station-samples/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tms / n, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"superstations: {wl.name} corner-turned block, {S} stations in {G_n} groups of 2",
+                   "l2": "inputs larger than L2 (%.1f GB read per step)" % (ct.numel() * 8 / 1e9)},
+        "gpu_launches": n,
+        "roofline": {"bound": "hbm", "kernel": "superstation", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": gbs / pk["hbm_gbs"], "traffic": None, "peak_source": f"{pk_kind} hbm_gbs"},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    plan.close()
+    return 0
+
+
+def run_incoherent(args):
+    """Cost of the incoherent beam (Section 3) on the LOFAR block, fused into the FP32 many-beam
+    kernel and as a separate kernel on the tensor-core path: steps with and without it."""
+    import torch
+
+    from paper_1105_0661_gb300 import Plan
+    from paper_1105_0661_gb300.build_lib import build
+    from synth.device import make_block_device
+
+    build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    wl = workload(args.workload, args.subbands, args.bits)
+    d_in = make_block_device(wl, seed=0, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    res = {}
+    for prec in ("fp32", "fp16tc"):
+        for inc in (False, True):
+            plan = Plan.from_workload(wl, precision=prec, incoherent_beam=inc)
+            out = torch.empty(plan.shape("stokes"), dtype=torch.float32, device=dev)
+            for _ in range(args.warmup):
+                plan.run_block(d_in, out, stream)
+            stream.synchronize()
+            plan.trace_begin(4 * args.steps + 8)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                plan.run_block(d_in, out, stream)
+            e1.record(stream)
+            stream.synchronize()
+            tr = plan.trace_end()
+            res[f"{prec}{'_incoherent' if inc else ''}"] = {
+                "ms_per_step": e0.elapsed_time(e1) / args.steps,
+                "kernels_ms": {k: v[1] / v[0] for k, v in tr.items() if not k.startswith("_") and v[0]}}
+            plan.close()
+            del out
+    line = {
+        "metric": "station-samples/s", "value": wl.station_samples() / (res["fp32_incoherent"]["ms_per_step"] / 1e3),
+        "unit": "station-samples/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": res["fp32_incoherent"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{wl.name} with the incoherent beam appended (Stokes {wl.output})"},
+        "runs": res,
+        "overhead_fp32": res["fp32_incoherent"]["ms_per_step"] / res["fp32"]["ms_per_step"] - 1.0,
+        "overhead_fp16tc": res["fp16tc_incoherent"]["ms_per_step"] / res["fp16tc"]["ms_per_step"] - 1.0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def batch_launches(wls, prec, tuning):
     """Kernel launches in one batch graph: the grouped filter bank and history update, one grouped
     FP32 beam former per shared-memory class in use (many-beam CTAs with more than 56 stations
@@ -734,6 +837,8 @@ def main():
     ap.add_argument("--dedisperse", action="store_true",
                     help="voltages -> channel-level dedispersion -> Stokes (pulsar pipeline)")
     ap.add_argument("--dd-fft", type=int, default=256, help="dedispersion FFT length (spectra)")
+    ap.add_argument("--superstation", action="store_true", help="superstation beam former on the corner-turned block")
+    ap.add_argument("--incoherent", action="store_true", help="cost of the incoherent beam on both precision paths")
     ap.add_argument("--dm", type=float, default=13.8, help="dispersion measure, pc cm^-3")
     ap.add_argument("--serve-obs", type=int, default=8)
     ap.add_argument("--serve-blocks", type=int, default=8)
@@ -752,6 +857,10 @@ def main():
         return run_batch(args)
     if args.dedisperse:
         return run_dedisperse(args)
+    if args.superstation:
+        return run_superstation(args)
+    if args.incoherent:
+        return run_incoherent(args)
     return run_ours(args)
 
 

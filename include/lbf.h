@@ -235,7 +235,7 @@ typedef struct lbf_trace {
   double total_ms[16];         /* summed event time per kernel */
   char names[16][32];          /* kernel names: ppf, ppf_ct, hist_update, delay_ct, bf_few, bf_many,
                                   stokes, ppf_ct16, bf_tc, ct_to_ct16, incoherent_ct16,
-                                  dedisperse */
+                                  dedisperse, superstation */
   int32_t dropped;             /* launches not recorded because max_launches was reached */
 } lbf_trace;
 lbf_status lbf_trace_begin(lbf_plan_t plan, int32_t max_launches);

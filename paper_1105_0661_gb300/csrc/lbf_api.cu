@@ -152,11 +152,11 @@ lbf_status check_call(lbf_plan_t p) {
 }
 
 enum KernelId { K_PPF = 0, K_PPF_CT, K_HIST, K_DELAY, K_BF_FEW, K_BF_MANY, K_STOKES, K_PPF_CT16, K_BF_TC,
-                K_CT16, K_INC16, K_DEDISP, K_COUNT };
+                K_CT16, K_INC16, K_DEDISP, K_SS, K_COUNT };
 static_assert(K_COUNT <= 16, "lbf_trace holds 16 kernels");
 const char *const kKernelNames[K_COUNT] = {"ppf", "ppf_ct", "hist_update", "delay_ct", "bf_few", "bf_many",
                                            "stokes", "ppf_ct16", "bf_tc", "ct_to_ct16", "incoherent_ct16",
-                                           "dedisperse"};
+                                           "dedisperse", "superstation"};
 
 // Launch through `fn`, bracketed by trace events when a trace is active.
 template <typename Fn>
@@ -613,8 +613,8 @@ lbf_status lbf_superstation(lbf_plan_t p, const int32_t *group_of_station, int32
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_status(e);
   const lbf::Geometry g = p->geometry();
-  return cuda_status(lbf::launch_superstation(g, (const float2 *)d_ct, (float2 *)d_ss, p->ss_members, p->ss_offs,
-                                              n_groups, st));
+  return cuda_status(traced(p, K_SS, st, [&] {
+    return lbf::launch_superstation(g, (const float2 *)d_ct, (float2 *)d_ss, p->ss_members, p->ss_offs, n_groups, st); }));
 }
 
 lbf_status lbf_trace_begin(lbf_plan_t p, int32_t max_launches) {
