@@ -42,6 +42,11 @@ def workload(name: str, subbands: int = 0, bits: int = 0):
         wl = G.workload_lofar_fp32(0)
     elif name == "lofar1024":
         wl = G.workload_lofar_tc(bits or 8, 0)
+    elif name == "lofar8":
+        # the same observation with 8 tied-array beams (the few-beam, bandwidth-bound beam former)
+        wl = G.workload_lofar_fp32(0)
+        wl.beam_dlm = G.hex_beam_grid(8, 0.05)
+        wl.name = "lofar-48st-244sb-8beam-I16"
     elif name == "tiny":
         wl = G.workload_tiny(0)
     else:
@@ -821,7 +826,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="lofar", choices=["lofar", "lofar1024", "tiny"])
+    ap.add_argument("--workload", default="lofar", choices=["lofar", "lofar1024", "lofar8", "tiny"])
     ap.add_argument("--bits", type=int, default=0, choices=[0, 8, 16], help="sample width override")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16tc"])
     ap.add_argument("--subbands", type=int, default=0,

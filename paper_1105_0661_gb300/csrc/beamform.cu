@@ -88,6 +88,9 @@ __device__ __forceinline__ void bf_few_item(const Geometry &g, const float2 *__r
     const bool inc = OUT != OUT_VOLTAGES && g.inc && bgrp == 0;   // this item also forms beam B
     IncAcc ia;
     if (active) {
+      // unrolled so that the loads of several stations are in flight together (the kernel is
+      // bound by HBM latency x loads in flight, not by its arithmetic)
+#pragma unroll 4
       for (int s = 0; s < g.S; ++s) {
         const float2 yx = y[((long long)s * kP + 0) * g.M + m];
         const float2 yy = y[((long long)s * kP + 1) * g.M + m];
