@@ -379,26 +379,52 @@ __device__ __forceinline__ void drain_tile_v(uint32_t taddr, int m0, int ro, int
   }
 }
 
-// Write a quadrant's staged windows wbase .. wbase + 7 to the output (64 threads: the quadrant's
-// two epilogue warps; `t64` is the thread's index among them).
+// The rows a thread writes in every flush of a work item (64 threads per quadrant: thread t64 of
+// the quadrant's two epilogue warps): rows (beam, Stokes parameter) i = t64 + 64 k, each written
+// as the 16-byte part `part` of a 32-byte segment.  Their addresses depend only on the item, so
+// they are formed once per item (null for beams past B).
 template <int NS, int Q>
-__device__ __forceinline__ void flush_stage(const TcParams &p, const float *buf, int t64, int quad, int bb, int f,
-                                            int c, int wbase) {
+struct FlushRows {
+  static constexpr int kRowsPer = NS * 2 * 32 / 64 > 0 ? NS * 2 * 32 / 64 : 1;   // rows per thread
+  float *row[kRowsPer];
+  int soff[kRowsPer];     // float offset of the row's part within the quadrant buffer
+  int part;
+};
+
+template <int NS, int Q>
+__device__ __forceinline__ void flush_rows(const TcParams &p, FlushRows<NS, Q> &fr, int t64, int quad, int bb, int f,
+                                           int c) {
   const int Mq = p.M / Q;
-  for (int i = t64; i < 32 * NS * 2; i += 64) {
-    const int part = i & 1, param = (i >> 1) % NS, bq = (i >> 1) / NS;
+  fr.part = t64 & 1;
+#pragma unroll
+  for (int k = 0; k < FlushRows<NS, Q>::kRowsPer; ++k) {
+    const int i = t64 + 64 * k;
+    const int param = (i >> 1) % NS, bq = (i >> 1) / NS;
     const int jq = bq & 15, mt = bq >> 4;
     const int b = bb * kBeamsPerItem + mt * (kRows / 2) + quad * 16 + jq;
-    const int w0 = wbase + part * 4;
-    if (b >= p.B || w0 >= Mq) continue;
-    const float4 v = *reinterpret_cast<const float4 *>(buf + bq * Stage<NS, Q>::kRow +
-                                                       ((param * 2 + part) ^ (jq & (2 * NS - 1))) * 4);
-    float *dst = p.out + ((((long long)b * NS + param) * p.F + f) * kN + c) * Mq + w0;
+    fr.row[k] = (i < 32 * NS * 2 && b < p.B) ? p.out + ((((long long)b * NS + param) * p.F + f) * kN + c) * Mq
+                                              : nullptr;
+    fr.soff[k] = bq * Stage<NS, Q>::kRow + ((param * 2 + fr.part) ^ (jq & (2 * NS - 1))) * 4;
+  }
+}
+
+// Write a quadrant's staged windows wbase .. wbase + 7 to the output rows.
+template <int NS, int Q>
+__device__ __forceinline__ void flush_stage(const TcParams &p, const float *buf, const FlushRows<NS, Q> &fr,
+                                            int wbase) {
+  const int Mq = p.M / Q;
+  const int w0 = wbase + fr.part * 4;
+  if (w0 >= Mq) return;
+#pragma unroll
+  for (int k = 0; k < FlushRows<NS, Q>::kRowsPer; ++k) {
+    if (!fr.row[k]) continue;
+    const float4 v = *reinterpret_cast<const float4 *>(buf + fr.soff[k]);
+    float *dst = fr.row[k] + w0;
     if (p.vec && w0 + 3 < Mq) {
       *reinterpret_cast<float4 *>(dst) = v;
     } else {
       const float e[4] = {v.x, v.y, v.z, v.w};
-      for (int k = 0; k < 4 && w0 + k < Mq; ++k) dst[k] = e[k];
+      for (int q = 0; q < 4 && w0 + q < Mq; ++q) dst[q] = e[q];
     }
   }
 }
@@ -563,6 +589,8 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
       const int nitem = item + gridDim.x;
       const int nfc = nitem / p.items_per_fc;
       const int nbb = nitem - nfc * p.items_per_fc;
+      FlushRows<NS, Q> frows;
+      if constexpr (St::kOn) flush_rows<NS, Q>(p, frows, half * 32 + lane, quad, bb, f, c);
       for (int t = 0; t < p.ntiles && ok; ++t, gpar ^= 1u) {
         const int wbase = (t / St::kPeriod) * 8;
         float *const buf = qbuf + (fl & 1) * St::kBuf;
@@ -605,7 +633,7 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
           __syncwarp();
           if (lane == 0) mbar_arrive(pair_bar(quad));
           if (!mbar_wait(pair_bar(quad), (uint32_t)fl & 1u, abort_flag)) { fail(abort_flag, p.err, ERR_EPILOGUE); ok = false; break; }
-          flush_stage<NS, Q>(p, buf, half * 32 + lane, quad, bb, f, c, wbase);
+          flush_stage<NS, Q>(p, buf, frows, wbase);
           ++fl;
         }
         }
