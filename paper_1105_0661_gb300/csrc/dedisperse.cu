@@ -149,7 +149,7 @@ dedisperse_kernel(Geometry g, DdParams d, const float2 *in, float2 *out) {   // 
 // multiplies them by the chirp, conjugates, and runs the same forward transform again (the
 // inverse is conj(FFT(conj(.)))), then stores y[j + 16 k2] straight to global memory.  Groups
 // synchronise only among their own 16 lanes.
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)   // 3 CTAs per SM: more transforms' loads in flight
 dedisperse256_kernel(Geometry g, DdParams d, const float2 *in, float2 *out) {   // in may equal out
   constexpr int K = 256;
   __shared__ float2 x[16][K];                  // one row per 16-thread group
