@@ -29,17 +29,29 @@ stokes_kernel(Geometry g, const float2 *__restrict__ vol, float *__restrict__ ou
   const float2 *vx = vol + (row * kP + 0) * g.M;
   const float2 *vy = vol + (row * kP + 1) * g.M;
   const int Mq = g.M / g.Q;
-  for (int mb = 0; mb < g.M; mb += blockDim.x) {
-    const int m = mb + threadIdx.x;
-    const bool active = m < g.M;
-    const float2 X = active ? vx[m] : make_float2(0.f, 0.f);
-    const float2 Y = active ? vy[m] : make_float2(0.f, 0.f);
+  // the loads of kPasses passes are issued before any of their arithmetic, so that each thread
+  // keeps several requests in flight (the kernel is bound by DRAM latency x requests in flight)
+  constexpr int kPasses = 4;
+  for (int mb = 0; mb < g.M; mb += kPasses * blockDim.x) {
+    float2 X[kPasses], Y[kPasses];
 #pragma unroll
-    for (int st = 0; st < NS; ++st) {
-      float v = stokes_value(st, X, Y);
-      for (int o = 1; o < g.Q; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (active && (m & (g.Q - 1)) == 0)
-        out[((((long long)b * NS + st) * g.F + f) * kN + c) * Mq + m / g.Q] = v;
+    for (int u = 0; u < kPasses; ++u) {
+      const int m = mb + u * blockDim.x + threadIdx.x;
+      X[u] = m < g.M ? vx[m] : make_float2(0.f, 0.f);
+      Y[u] = m < g.M ? vy[m] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < kPasses; ++u) {
+      const int m = mb + u * blockDim.x + threadIdx.x;
+      if (mb + u * blockDim.x >= g.M) break;   // uniform across the CTA
+      const bool active = m < g.M;
+#pragma unroll
+      for (int st = 0; st < NS; ++st) {
+        float v = stokes_value(st, X[u], Y[u]);
+        for (int o = 1; o < g.Q; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (active && (m & (g.Q - 1)) == 0)
+          out[((((long long)b * NS + st) * g.F + f) * kN + c) * Mq + m / g.Q] = v;
+      }
     }
   }
 }
