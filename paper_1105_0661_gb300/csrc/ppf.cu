@@ -15,6 +15,8 @@
 // table, a swizzled in-place shared-memory transpose, and a second 16-point DFT.
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "fft16.cuh"
 #include "lbf_internal.cuh"
 
@@ -52,11 +54,18 @@ template <> struct SampleIO<8> {    // X.re, X.im, Y.re, Y.im as four int8
   }
 };
 
+// A transform's 256 points are kept as 16 rows of 16 with one float2 of padding per row, so that
+// both the row and the column walks of the 16 x 16 decomposition are conflict-free with fixed
+// per-thread offsets (no index arithmetic in the FFT).
+constexpr int kRow = 16 * 17;
 template <int BITS>
 struct PpfSmem {
-  float2 v[kP][kTile][kN];                                  // 64 KB: FIR out -> FFT -> staging
-  typename SampleIO<BITS>::word in[kStages][kTile][kN];     // input ring (64 KB int16, 32 KB int8)
-  float2 tw[kN];                                            // exp(-2 pi i n / 256)
+  using word = typename SampleIO<BITS>::word;
+  static constexpr int kAlign = 16 / (int)sizeof(word);     // samples per 16 bytes
+  static constexpr int kSlot = kTile * kN + kAlign;         // one tile of frames + alignment slack
+  float2 v[kP][kTile][kRow];                                // 68 KB: FIR out -> FFT -> staging
+  word in[kStages][kSlot];                                  // input ring (64 KB int16, 32 KB int8)
+  float2 tw[kN];                                            // [k1][j] = exp(-2 pi i j k1 / 256)
   float2 gain[kN];                                          // bandpass * delay phasor per channel
 };
 
@@ -78,6 +87,10 @@ __device__ __forceinline__ void cp_async(void *smem_dst, const void *gmem_src, i
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gmem_src) : "memory");
 }
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
@@ -97,8 +110,9 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
   const int m0 = chunk * spc;
   const int m_end = min(g.M, m0 + spc);
   const int ntiles = (m_end - m0 + kTile - 1) / kTile;
+  constexpr int kAlign = PpfSmem<BITS>::kAlign;
 
-  if (tid < kN) sm.tw[tid] = g.twiddle[tid];
+  if (tid < kN) sm.tw[tid] = g.twiddle[(tid & 15) * (tid >> 4)];
   if (CT && tid < kN) {
     // Y = X * bp[c] * exp(+2 pi i (f0 tau_s + df_c (tau_s - n_s Ts))), phase in FP64 cycles
     const int c = tid;
@@ -113,20 +127,41 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
   // [history (H samples) | block (T samples)].  Frames r >= -15, r < M.
   const int pol = tid >> 8;        // this thread's polarisation
   const int p = tid & (kN - 1);    // and FIR point
-  const long long base = (long long)g.H - g.dshift[s] + p;
+  const int dsh = g.dshift[s];
+  const long long base = (long long)g.H - dsh + p;
   const word *hs = hist + sf * g.H;
   const word *bs = in + sf * g.T;
   auto src_of = [&](int r) -> const word * {
     const long long e = base + (long long)r * kN;
     return (e < g.H) ? hs + e : bs + (e - g.H);
   };
-  // async copies of tile t's frames: sample p of frame q is copied by the thread of pol q & 1
+  // Tile t's frames start at block sample e0 = mt N - d_s.  A tile wholly inside the block (e0 >= 0)
+  // is one contiguous run of samples: it is copied as 16-byte pieces of the aligned run that covers
+  // it (never past the stream's end, T being a multiple of N), and its frames start at slot offset
+  // e0 mod kAlign.  A tile that reaches into the history takes one copy per sample.
+  const bool in16 = ((reinterpret_cast<uintptr_t>(in) & 15) == 0);
+  auto slot_off = [&](int mt) -> int {
+    const long long e0 = (long long)mt * kN - dsh;
+    return (in16 && e0 >= 0) ? (int)(e0 & (kAlign - 1)) : 0;
+  };
   auto issue_tile = [&](int t) {
     if (t < ntiles) {
       const int mt = m0 + t * kTile;
+      const int nfr = min(kTile, m_end - mt);
+      word *slot = sm.in[t % kStages];
+      const long long e0 = (long long)mt * kN - dsh;
+      if (in16 && e0 >= 0) {
+        const long long a = e0 & ~(long long)(kAlign - 1);
+        const int nchunks = (int)((e0 - a + (long long)nfr * kN + kAlign - 1) / kAlign);
+        const char *src = reinterpret_cast<const char *>(bs + a);
+        char *dst = reinterpret_cast<char *>(slot);
+        for (int i = tid; i < nchunks; i += kThreads) cp_async16(dst + 16 * i, src + 16 * i);
+      } else {
+        // sample p of frame q is copied by the thread of pol q & 1
 #pragma unroll
-      for (int q = pol; q < kTile; q += 2)
-        if (mt + q < m_end) cp_async(&sm.in[t % kStages][q][p], src_of(mt + q), (int)sizeof(word));
+        for (int q = pol; q < kTile; q += 2)
+          if (q < nfr) cp_async(slot + q * kN + p, src_of(mt + q), (int)sizeof(word));
+      }
     }
     cp_async_commit();
   };
@@ -144,6 +179,7 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
   const int grp = tid >> 4;        // transform group 0..31
   const int gpol = grp >> 4;       // its polarisation
   const int gq = grp & 15;         // its spectrum within the tile
+  const int pv = 17 * (p >> 4) + (p & 15);   // point p in a padded row
 
   for (int t = 0; t < ntiles; ++t) {
     const int mt = m0 + t * kTile;
@@ -151,33 +187,39 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
     cp_async_wait<1>();            // this thread's copies of tile t have landed
     __syncthreads();               // ... and everyone's
     // ---- FIR: v_m[p] = sum_t h[tN + p] x'[(m - 15 + t) N + p], 16 spectra, this pol
+    const word *fr = sm.in[t % kStages] + slot_off(mt) + p;
+    float2 *vout = &sm.v[pol][0][pv];
+    auto fir = [&](auto full) {
 #pragma unroll
-    for (int q = 0; q < kTile; ++q) {
-      const int m = mt + q;
-      win[q] = (m < m_end) ? SampleIO<BITS>::cvt_pol(sm.in[t % kStages][q][p], pol) : make_float2(0.f, 0.f);
-      float2 acc = make_float2(0.f, 0.f);
+      for (int q = 0; q < kTile; ++q) {
+        if (decltype(full)::value || mt + q < m_end) win[q] = SampleIO<BITS>::cvt_pol(fr[q * kN], pol);
+        else win[q] = make_float2(0.f, 0.f);
+        float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int tap = 0; tap < kL; ++tap) {
-        const float2 x = win[(q + 1 + tap) & 15];
-        acc.x = fmaf(h[tap], x.x, acc.x);
-        acc.y = fmaf(h[tap], x.y, acc.y);
+        for (int tap = 0; tap < kL; ++tap) {
+          const float2 x = win[(q + 1 + tap) & 15];
+          acc.x = fmaf(h[tap], x.x, acc.x);
+          acc.y = fmaf(h[tap], x.y, acc.y);
+        }
+        vout[q * kRow] = acc;
       }
-      sm.v[pol][q][p] = acc;
-    }
+    };
+    if (mt + kTile <= m_end) fir(std::true_type());
+    else fir(std::false_type());
     __syncthreads();
 
-    // ---- FFT-256 of the 32 transforms (pol, spectrum) of the tile, 16 threads each
+    // ---- FFT-256 of the 32 transforms (pol, spectrum) of the tile, 16 threads each:
+    // n = 16 p1 + p2, k = k1 + 16 k2; thread j first owns column p2 = j, then row k1 = j
     float2 *row = sm.v[gpol][gq];
     float2 a[16];
 #pragma unroll
-    for (int p1 = 0; p1 < 16; ++p1) a[p1] = row[16 * p1 + j];   // thread j = p2
-    __syncwarp();
+    for (int p1 = 0; p1 < 16; ++p1) a[p1] = row[17 * p1 + j];
     dft16(a);
 #pragma unroll
-    for (int k1 = 0; k1 < 16; ++k1) row[k1 * 16 + (j ^ k1)] = cmul(a[k1], sm.tw[j * k1]);
+    for (int k1 = 0; k1 < 16; ++k1) row[17 * k1 + j] = cmul(a[k1], sm.tw[16 * k1 + j]);
     __syncwarp();
 #pragma unroll
-    for (int p2 = 0; p2 < 16; ++p2) a[p2] = row[j * 16 + (p2 ^ j)];   // thread j = k1
+    for (int p2 = 0; p2 < 16; ++p2) a[p2] = row[17 * j + p2];
     dft16(a);   // a[k2] = X[j + 16 k2]
     const int m = mt + gq;
     if (MODE == MODE_CT16) {
