@@ -2,17 +2,20 @@
 // 16-tap FIR and 256-point FFT into channels, with an optional fused epilogue that applies the
 // sub-sample delay phase and bandpass (Sections 3, 4.3) and writes a corner-turned layout.
 //
-// One CTA filters up to 128 consecutive spectra of one (station, subband) stream in tiles of 16
-// spectra, with 512 threads: thread (pol, p) owns polarisation pol of FIR point p.
+// One CTA filters one polarisation of up to 128 consecutive spectra of one (station, subband)
+// stream in tiles of 16 spectra, with 256 threads: thread p owns FIR point p.  Two CTAs fit on an
+// SM, so one CTA's FIR (FP32-pipe bound) overlaps the other's FFT (shared-memory latency bound);
+// the two polarisations of a stream chunk are neighbouring CTAs, and the second reads the dual-pol
+// input from L2.
 //  * The tile's input samples arrive through a two-stage cp.async ring in shared memory (whole
-//    dual-pol samples, one 8-byte copy each, issued one tile ahead), so global-load latency
-//    overlaps the filtering and the FFTs of the tile before.
+//    dual-pol samples, issued one tile ahead), so global-load latency overlaps the filtering and
+//    the FFTs of the tile before.
 //  * Each thread converts its polarisation exactly to float with the 2^23 magic-number method
 //    (integer ops + one packed add instead of the conversion pipe) and slides a 16-frame window
 //    of complex values through registers, producing v_m[p] for 16 spectra into shared memory.
-// The 32 FFTs of a tile (16 spectra x 2 pols) then run as 16x16 decompositions, 16 threads per
-// transform: a 16-point DFT in registers (packed FP32x2 butterflies), a twiddle from a shared
-// table, a swizzled in-place shared-memory transpose, and a second 16-point DFT.
+// The 16 FFTs of a tile then run as 16x16 decompositions, 16 threads per transform: a 16-point DFT
+// in registers (packed FP32x2 butterflies), a twiddle from a shared table, an in-place transpose
+// through padded shared-memory rows, and a second 16-point DFT.
 #include <cuda_fp16.h>
 
 #include <type_traits>
@@ -23,8 +26,8 @@
 namespace lbf {
 namespace {
 
-constexpr int kThreads = 512;
-constexpr int kTile = 16;                  // spectra per tile: 32 transforms = one FFT round
+constexpr int kThreads = 256;
+constexpr int kTile = 16;                  // spectra per tile: 16 transforms = one FFT round
 constexpr int kTilesPerCta = 8;
 constexpr int kSpectraPerCta = kTile * kTilesPerCta;   // 128
 constexpr int kStages = 2;                 // input ring depth (tiles)
@@ -63,7 +66,7 @@ struct PpfSmem {
   using word = typename SampleIO<BITS>::word;
   static constexpr int kAlign = 16 / (int)sizeof(word);     // samples per 16 bytes
   static constexpr int kSlot = kTile * kN + kAlign;         // one tile of frames + alignment slack
-  float2 v[kP][kTile][kRow];                                // 68 KB: FIR out -> FFT -> staging
+  float2 v[kTile][kRow];                                    // 34 KB: FIR out -> FFT -> staging
   word in[kStages][kSlot];                                  // input ring (64 KB int16, 32 KB int8)
   float2 tw[kN];                                            // [k1][j] = exp(-2 pi i j k1 / 256)
   float2 gain[kN];                                          // bandpass * delay phasor per channel
@@ -95,11 +98,12 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// One work item: spectra [chunk * spc, (chunk + 1) * spc) of stream (s, f), spc a multiple of 16.
+// One work item: polarisation pol of spectra [chunk * spc, (chunk + 1) * spc) of stream (s, f),
+// spc a multiple of 16.
 template <int BITS, int MODE>
 __device__ __forceinline__ void ppf_item(const Geometry &g, const typename SampleIO<BITS>::word *__restrict__ in,
                                          const typename SampleIO<BITS>::word *__restrict__ hist, const PpfOut &po,
-                                         int s, int f, int chunk, int spc, unsigned char *smem_raw) {
+                                         int s, int f, int pol, int chunk, int spc, unsigned char *smem_raw) {
   using word = typename SampleIO<BITS>::word;
   constexpr bool CT = MODE != MODE_CHAN;
   PpfSmem<BITS> &sm = *reinterpret_cast<PpfSmem<BITS> *>(smem_raw);
@@ -112,8 +116,8 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
   const int ntiles = (m_end - m0 + kTile - 1) / kTile;
   constexpr int kAlign = PpfSmem<BITS>::kAlign;
 
-  if (tid < kN) sm.tw[tid] = g.twiddle[(tid & 15) * (tid >> 4)];
-  if (CT && tid < kN) {
+  sm.tw[tid] = g.twiddle[(tid & 15) * (tid >> 4)];
+  if (CT) {
     // Y = X * bp[c] * exp(+2 pi i (f0 tau_s + df_c (tau_s - n_s Ts))), phase in FP64 cycles
     const int c = tid;
     const double df = (double)(c - kN / 2) * (g.fs / kN);
@@ -125,8 +129,7 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
 
   // x'[j] = x[j - d_s]; block-relative x' index j lives at extended index H - d_s + j of
   // [history (H samples) | block (T samples)].  Frames r >= -15, r < M.
-  const int pol = tid >> 8;        // this thread's polarisation
-  const int p = tid & (kN - 1);    // and FIR point
+  const int p = tid;               // this thread's FIR point
   const int dsh = g.dshift[s];
   const long long base = (long long)g.H - dsh + p;
   const word *hs = hist + sf * g.H;
@@ -157,9 +160,8 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
         char *dst = reinterpret_cast<char *>(slot);
         for (int i = tid; i < nchunks; i += kThreads) cp_async16(dst + 16 * i, src + 16 * i);
       } else {
-        // sample p of frame q is copied by the thread of pol q & 1
 #pragma unroll
-        for (int q = pol; q < kTile; q += 2)
+        for (int q = 0; q < kTile; ++q)
           if (q < nfr) cp_async(slot + q * kN + p, src_of(mt + q), (int)sizeof(word));
       }
     }
@@ -176,9 +178,7 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
   for (int i = 0; i < kL - 1; ++i) win[i + 1] = SampleIO<BITS>::cvt_pol(*src_of(m0 - (kL - 1) + i), pol);
 
   const int j = tid & 15;          // lane within a 16-thread transform group
-  const int grp = tid >> 4;        // transform group 0..31
-  const int gpol = grp >> 4;       // its polarisation
-  const int gq = grp & 15;         // its spectrum within the tile
+  const int gq = tid >> 4;         // the group's spectrum within the tile
   const int pv = 17 * (p >> 4) + (p & 15);   // point p in a padded row
 
   for (int t = 0; t < ntiles; ++t) {
@@ -188,7 +188,7 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
     __syncthreads();               // ... and everyone's
     // ---- FIR: v_m[p] = sum_t h[tN + p] x'[(m - 15 + t) N + p], 16 spectra, this pol
     const word *fr = sm.in[t % kStages] + slot_off(mt) + p;
-    float2 *vout = &sm.v[pol][0][pv];
+    float2 *vout = &sm.v[0][pv];
     auto fir = [&](auto full) {
 #pragma unroll
       for (int q = 0; q < kTile; ++q) {
@@ -208,9 +208,9 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
     else fir(std::false_type());
     __syncthreads();
 
-    // ---- FFT-256 of the 32 transforms (pol, spectrum) of the tile, 16 threads each:
+    // ---- FFT-256 of the 16 transforms (spectra) of the tile, 16 threads each:
     // n = 16 p1 + p2, k = k1 + 16 k2; thread j first owns column p2 = j, then row k1 = j
-    float2 *row = sm.v[gpol][gq];
+    float2 *row = sm.v[gq];
     float2 a[16];
 #pragma unroll
     for (int p1 = 0; p1 < 16; ++p1) a[p1] = row[17 * p1 + j];
@@ -223,25 +223,24 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
     dft16(a);   // a[k2] = X[j + 16 k2]
     const int m = mt + gq;
     if (MODE == MODE_CT16) {
-      __syncthreads();   // every group has read its row: each pol plane becomes staging [c][q]
-      float2 *stage = &sm.v[gpol][0][0];
+      __syncthreads();   // every group has read its row: the buffer becomes staging [c][q]
+      float2 *stage = &sm.v[0][0];
 #pragma unroll
       for (int k2 = 0; k2 < 16; ++k2) {
         const int c = j + 16 * ((k2 + 8) & 15);
         stage[c * kTile + (gq ^ (c & 15))] = cmul(a[k2], sm.gain[c]);
       }
       __syncthreads();
-      // [F*N][Mt][Kpad][P][32]: rows k = 2s (re) and 2s+1 (im).  Thread (row (pol, c), h8) packs
+      // [F*N][Mt][Kpad][P][32]: rows k = 2s (re) and 2s+1 (im).  Thread (channel c, h8) packs
       // 8 consecutive spectra into one 16-byte store per plane and component; spectra at or past
       // the block's end go out as zeros (the pad columns of the last tile).
       const int mb = tc_tiles(g.M);
       const int h8 = tid & 1;
       const int m0 = mt + 8 * h8;
 #pragma unroll
-      for (int pass = 0; pass < kP * kN / (kThreads / 2); ++pass) {
-        const int row2 = pass * (kThreads / 2) + (tid >> 1);   // (pol, c)
-        const int pl = row2 >> 8, c = row2 & (kN - 1);
-        const float2 *srow = &sm.v[pl][0][0] + c * kTile;
+      for (int pass = 0; pass < kN / (kThreads / 2); ++pass) {
+        const int c = pass * (kThreads / 2) + (tid >> 1);
+        const float2 *srow = stage + c * kTile;
         uint32_t hr[4], hm[4], lr[4], lm[4];
 #pragma unroll
         for (int k = 0; k < 8; k += 2) {
@@ -257,7 +256,7 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
           lr[k / 2] = *reinterpret_cast<const uint32_t *>(&l_re);
           lm[k / 2] = *reinterpret_cast<const uint32_t *>(&l_im);
         }
-        const long long re = ((((long long)f * kN + c) * mb + (m0 >> 5)) * po.kpad + 2 * s) * 64 + pl * 32 + (m0 & 31);
+        const long long re = ((((long long)f * kN + c) * mb + (m0 >> 5)) * po.kpad + 2 * s) * 64 + pol * 32 + (m0 & 31);
         *reinterpret_cast<uint4 *>(po.hi + re) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
         *reinterpret_cast<uint4 *>(po.hi + re + 64) = make_uint4(hm[0], hm[1], hm[2], hm[3]);
         if (po.lo) {
@@ -267,32 +266,34 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
       }
     } else if (!CT) {
       if (m < m_end) {
-        float2 *dst = out + ((((long long)f * g.S + s) * kP + gpol) * g.M + m) * kN;
+        float2 *dst = out + ((((long long)f * g.S + s) * kP + pol) * g.M + m) * kN;
 #pragma unroll
         for (int k2 = 0; k2 < 16; ++k2) dst[j + 16 * ((k2 + 8) & 15)] = a[k2];   // c = (k + N/2) mod N
       }
     } else {
-      __syncthreads();   // every group has read its row: each pol plane becomes staging [c][q]
-      float2 *stage = &sm.v[gpol][0][0];
+      __syncthreads();   // every group has read its row: the buffer becomes staging [c][q]
+      float2 *stage = &sm.v[0][0];
 #pragma unroll
       for (int k2 = 0; k2 < 16; ++k2) {
         const int c = j + 16 * ((k2 + 8) & 15);
         stage[c * kTile + (gq ^ (c & 15))] = cmul(a[k2], sm.gain[c]);
       }
       __syncthreads();
-      // ct[f][c][s][pol][m]: runs of 16 consecutive spectra (128 B) per (c, pol).  Eight threads
+      // ct[f][c][s][pol][m]: runs of 16 consecutive spectra (128 B) per channel.  Eight threads
       // write a run, two spectra each as one 16-byte store (rows 16-byte aligned when M is even),
-      // so a warp's store covers four whole 128-byte runs.
+      // so a warp's store covers four whole 128-byte runs.  Pass k writes channels 32 k + tid / 8.
       const int pr = tid & 7;
       const int m0 = mt + 2 * pr;
       const bool vec = (g.M & 1) == 0 && m0 + 1 < m_end;
-#pragma unroll 4
-      for (int pass = 0; pass < kP * kN / (kThreads / 8); ++pass) {
-        const int row2 = pass * (kThreads / 8) + (tid >> 3);   // (pol, c)
-        const int pl = row2 >> 8, c = row2 & (kN - 1);
-        const float2 *srow = &sm.v[pl][0][0] + c * kTile;
-        const float2 v0 = srow[(2 * pr) ^ (c & 15)], v1 = srow[(2 * pr + 1) ^ (c & 15)];
-        float2 *dst = out + ((((long long)f * kN + c) * g.S + s) * kP + pl) * g.M + m0;
+      const int c0 = tid >> 3;
+      const float2 *srow = stage + c0 * kTile;
+      const int sw = c0 & 15;   // the swizzle of every channel this thread writes
+      float2 *dst = out + ((((long long)f * kN + c0) * g.S + s) * kP + pol) * g.M + m0;
+      const long long cstep = (long long)(kThreads / 8) * g.S * kP * g.M;
+#pragma unroll
+      for (int pass = 0; pass < kN / (kThreads / 8); ++pass, dst += cstep) {
+        const float2 v0 = srow[pass * (kThreads / 8) * kTile + ((2 * pr) ^ sw)];
+        const float2 v1 = srow[pass * (kThreads / 8) * kTile + ((2 * pr + 1) ^ sw)];
         if (vec) {
           *reinterpret_cast<float4 *>(dst) = make_float4(v0.x, v0.y, v1.x, v1.y);
         } else {
@@ -306,29 +307,32 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
   cp_async_wait<0>();
 }
 
+// Polarisation fastest in the CTA index: the two CTAs of a stream chunk read the same input run.
 template <int BITS, int MODE>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
 ppf_kernel(Geometry g, const typename SampleIO<BITS>::word *__restrict__ in,
            const typename SampleIO<BITS>::word *__restrict__ hist, PpfOut po, int chunks) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int s, f, chunk;
-  if (MODE == MODE_CT16) {   // stations fastest: neighbouring CTAs fill neighbouring K rows of
-    s = (int)(blockIdx.x % g.S);                 // the same (channel) planes
-    const long long rest = blockIdx.x / g.S;
+  const int pol = (int)(blockIdx.x & 1);
+  const long long item = blockIdx.x >> 1;
+  if (MODE == MODE_CT16) {   // then stations: neighbouring CTAs fill neighbouring K rows of
+    s = (int)(item % g.S);                       // the same (channel) planes
+    const long long rest = item / g.S;
     chunk = (int)(rest % chunks);
     f = (int)(rest / chunks);
   } else {
-    const long long sf = blockIdx.x / chunks;    // stream index s * F + f
-    chunk = (int)(blockIdx.x - sf * chunks);
+    const long long sf = item / chunks;          // stream index s * F + f
+    chunk = (int)(item - sf * chunks);
     s = (int)(sf / g.F);
     f = (int)(sf - (long long)s * g.F);
   }
-  ppf_item<BITS, MODE>(g, in, hist, po, s, f, chunk, kSpectraPerCta, smem_raw);
+  ppf_item<BITS, MODE>(g, in, hist, po, s, f, pol, chunk, kSpectraPerCta, smem_raw);
 }
 
 // Persistent filter bank over the blocks of several observations (a batch): CTAs take work items
-// (stream, spectrum chunk) from a shared counter until all groups are done.
-__global__ void __launch_bounds__(kThreads, 1)
+// (stream, spectrum chunk, polarisation) from a shared counter until all groups are done.
+__global__ void __launch_bounds__(kThreads, 2)
 ppf_group_kernel(const PpfGroup *__restrict__ grp, int ngrp, long long total, unsigned long long *counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ long long item_s;
@@ -341,22 +345,23 @@ ppf_group_kernel(const PpfGroup *__restrict__ grp, int ngrp, long long total, un
     int o = 0;
     while (o + 1 < ngrp && grp[o + 1].first_item <= item) ++o;
     const PpfGroup &G = grp[o];
-    const long long local = item - G.first_item;
+    const long long local = (item - G.first_item) >> 1;
+    const int pol = (int)((item - G.first_item) & 1);
     const long long sf = local / G.chunks;
     const int chunk = (int)(local - sf * G.chunks);
     const int s = (int)(sf / G.g.F), f = (int)(sf - (long long)s * G.g.F);
     if (G.tc) {   // tensor-core plan: FP16 hi+lo planes
       PpfOut po{nullptr, reinterpret_cast<__half *>(G.ct16.hi), reinterpret_cast<__half *>(G.ct16.lo), G.ct16.kpad};
       if (G.bits == 16)
-        ppf_item<16, MODE_CT16>(G.g, (const uint2 *)G.in, (const uint2 *)G.hist, po, s, f, chunk, G.spc, smem_raw);
+        ppf_item<16, MODE_CT16>(G.g, (const uint2 *)G.in, (const uint2 *)G.hist, po, s, f, pol, chunk, G.spc, smem_raw);
       else
-        ppf_item<8, MODE_CT16>(G.g, (const uint32_t *)G.in, (const uint32_t *)G.hist, po, s, f, chunk, G.spc, smem_raw);
+        ppf_item<8, MODE_CT16>(G.g, (const uint32_t *)G.in, (const uint32_t *)G.hist, po, s, f, pol, chunk, G.spc, smem_raw);
     } else {
       PpfOut po{G.ct, nullptr, nullptr, 0};
       if (G.bits == 16)
-        ppf_item<16, MODE_CT32>(G.g, (const uint2 *)G.in, (const uint2 *)G.hist, po, s, f, chunk, G.spc, smem_raw);
+        ppf_item<16, MODE_CT32>(G.g, (const uint2 *)G.in, (const uint2 *)G.hist, po, s, f, pol, chunk, G.spc, smem_raw);
       else
-        ppf_item<8, MODE_CT32>(G.g, (const uint32_t *)G.in, (const uint32_t *)G.hist, po, s, f, chunk, G.spc, smem_raw);
+        ppf_item<8, MODE_CT32>(G.g, (const uint32_t *)G.in, (const uint32_t *)G.hist, po, s, f, pol, chunk, G.spc, smem_raw);
     }
   }
 }
@@ -401,7 +406,7 @@ template <int BITS, int MODE>
 cudaError_t launch_ppf_t(const Geometry &g, const void *in, const void *hist, PpfOut po, cudaStream_t st) {
   using word = typename SampleIO<BITS>::word;
   const int chunks = (g.M + kSpectraPerCta - 1) / kSpectraPerCta;
-  const long long ctas = (long long)g.S * g.F * chunks;
+  const long long ctas = (long long)g.S * g.F * chunks * kP;
   if (ctas == 0) return cudaSuccess;
   const size_t smem = sizeof(PpfSmem<BITS>);
   auto kern = ppf_kernel<BITS, MODE>;
