@@ -194,14 +194,17 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
       for (int q = 0; q < kTile; ++q) {
         if (decltype(full)::value || mt + q < m_end) win[q] = SampleIO<BITS>::cvt_pol(fr[q * kN], pol);
         else win[q] = make_float2(0.f, 0.f);
-        float2 acc = make_float2(0.f, 0.f);
+        // two partial sums per component halve the FMA dependency chain
+        float2 acc = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int tap = 0; tap < kL; ++tap) {
-          const float2 x = win[(q + 1 + tap) & 15];
+        for (int tap = 0; tap < kL; tap += 2) {
+          const float2 x = win[(q + 1 + tap) & 15], x1 = win[(q + 2 + tap) & 15];
           acc.x = fmaf(h[tap], x.x, acc.x);
           acc.y = fmaf(h[tap], x.y, acc.y);
+          acc1.x = fmaf(h[tap + 1], x1.x, acc1.x);
+          acc1.y = fmaf(h[tap + 1], x1.y, acc1.y);
         }
-        vout[q * kRow] = acc;
+        vout[q * kRow] = __fadd2_rn(acc, acc1);
       }
     };
     if (mt + kTile <= m_end) fir(std::true_type());
