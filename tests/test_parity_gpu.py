@@ -179,9 +179,13 @@ def test_beamform_voltages_match_oracle(dev, variant, B):
 
 
 # ----------------------------------------------------------------------------- a7 Stokes
-@pytest.mark.parametrize("out,Q", [("I", 1), ("I", 8), ("IQUV", 4), ("IQUV", 32), ("I", 2)])
-def test_stokes_matches_oracle(dev, out, Q):
-    wl = _wl(T=64 * N, out=out, Q=Q, B=3)
+# M a multiple of 4 takes the four-spectra-per-lane kernel (ragged last unit group at M = 100,
+# several lane passes at M = 160); M = 66 and 70 take the one-spectrum-per-lane kernel.
+@pytest.mark.parametrize("out,Q,M", [("I", 1, 64), ("I", 8, 64), ("IQUV", 4, 64), ("IQUV", 32, 64), ("I", 2, 64),
+                                     ("I", 4, 100), ("IQUV", 16, 160), ("I", 32, 160),
+                                     ("I", 2, 66), ("IQUV", 1, 70)])
+def test_stokes_matches_oracle(dev, out, Q, M):
+    wl = _wl(T=M * N, out=out, Q=Q, B=3)
     p = _plan(wl)
     ob = O.observation_from_workload(wl)
     rng = np.random.default_rng(8)
