@@ -145,15 +145,17 @@ dedisperse_kernel(Geometry g, DdParams d, const float2 *in, float2 *out) {   // 
 // K = 256 (sub-channels of (fs/N)/256 = 3 Hz): the filter bank's 16 x 16 decomposition in
 // registers, one transform per 16-thread group at a time.  Each group streams its own transforms:
 // thread j loads x[16 p1 + j] straight from global memory (a half-warp reads 128 contiguous bytes
-// per load), transposes once through its 2 KB shared row, and ends holding bins j + 16 k2; it
-// multiplies them by the chirp, conjugates, and runs the same forward transform again (the
-// inverse is conj(FFT(conj(.)))), then stores y[j + 16 k2] straight to global memory.  Groups
-// synchronise only among their own 16 lanes.
+// per load), transposes once through its shared row (rows of 16 padded to 17, so both walks are
+// conflict-free with fixed offsets), and ends holding bins j + 16 k2.  Those are exactly the
+// inputs x[16 p1 + j], p1 = k2, of its next transform, so it multiplies them by the chirp,
+// conjugates, and runs the same forward transform again in registers (the inverse is
+// conj(FFT(conj(.)))), then stores y[j + 16 k2] straight to global memory.  Groups synchronise
+// only among their own 16 lanes.
 __global__ void __launch_bounds__(kThreads, 3)   // 3 CTAs per SM: more transforms' loads in flight
 dedisperse256_kernel(Geometry g, DdParams d, const float2 *in, float2 *out) {   // in may equal out
   constexpr int K = 256;
-  __shared__ float2 x[16][K];                  // one row per 16-thread group
-  __shared__ float2 tw[K];                     // exp(-2 pi i n / 256)
+  __shared__ float2 x[16][16 * 17];            // one padded row per 16-thread group
+  __shared__ float2 tw[K];                     // [k1][j] = exp(-2 pi i j k1 / 256)
   __shared__ float2 chirp[K];                  // natural bin order, scaled by 1/256
   __shared__ ChirpCoef coef_s;
   const int bgroups = (g.B + kBeamsPerCta - 1) / kBeamsPerCta;
@@ -165,7 +167,7 @@ dedisperse256_kernel(Geometry g, DdParams d, const float2 *in, float2 *out) {   
   if (tid == 0) coef_s = chirp_coef(g, f, c, K, d.dm);
   {
     float s, co;
-    sincospif(2.0f * (float)tid / (float)K, &s, &co);
+    sincospif(2.0f * (float)((tid & 15) * (tid >> 4)) / (float)K, &s, &co);
     tw[tid] = make_float2(co, -s);
   }
   __syncthreads();
@@ -177,11 +179,11 @@ dedisperse256_kernel(Geometry g, DdParams d, const float2 *in, float2 *out) {   
   auto fft_tail = [&](float2 (&a)[16]) {
     dft16(a);
 #pragma unroll
-    for (int k1 = 0; k1 < 16; ++k1) r[k1 * 16 + (j ^ k1)] = cmul(a[k1], tw[j * k1]);
+    for (int k1 = 0; k1 < 16; ++k1) r[17 * k1 + j] = cmul(a[k1], tw[16 * k1 + j]);
     __syncwarp(mask);
 #pragma unroll
-    for (int p2 = 0; p2 < 16; ++p2) a[p2] = r[j * 16 + (p2 ^ j)];
-    __syncwarp(mask);
+    for (int p2 = 0; p2 < 16; ++p2) a[p2] = r[17 * j + p2];
+    __syncwarp(mask);   // the row is rewritten by the next transform
     dft16(a);
   };
   const int b0 = bg * kBeamsPerCta;
@@ -196,12 +198,8 @@ dedisperse256_kernel(Geometry g, DdParams d, const float2 *in, float2 *out) {   
 #pragma unroll
     for (int k2 = 0; k2 < 16; ++k2) {     // chirp (with 1/256), then conjugate for the inverse
       const float2 v = cmul(a[k2], chirp[j + 16 * k2]);
-      r[j + 16 * k2] = make_float2(v.x, -v.y);
+      a[k2] = make_float2(v.x, -v.y);
     }
-    __syncwarp(mask);
-#pragma unroll
-    for (int p1 = 0; p1 < 16; ++p1) a[p1] = r[16 * p1 + j];
-    __syncwarp(mask);
     fft_tail(a);
 #pragma unroll
     for (int k2 = 0; k2 < 16; ++k2) out[off + j + 16 * k2] = make_float2(a[k2].x, -a[k2].y);
