@@ -158,7 +158,18 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
         const int nchunks = (int)((e0 - a + (long long)nfr * kN + kAlign - 1) / kAlign);
         const char *src = reinterpret_cast<const char *>(bs + a);
         char *dst = reinterpret_cast<char *>(slot);
-        for (int i = tid; i < nchunks; i += kThreads) cp_async16(dst + 16 * i, src + 16 * i);
+        // nchunks is kTile N / kAlign + (0 or 1) for full tiles: whole rounds at fixed offsets
+        const char *s0 = src + 16 * tid;
+        char *d0 = dst + 16 * tid;
+        const int rounds = nchunks / kThreads;
+        if (rounds == kTile * kN / kAlign / kThreads) {
+#pragma unroll
+          for (int r = 0; r < kTile * kN / kAlign / kThreads; ++r) cp_async16(d0 + 16 * kThreads * r, s0 + 16 * kThreads * r);
+        } else {
+          for (int r = 0; r < rounds; ++r) cp_async16(d0 + 16 * kThreads * r, s0 + 16 * kThreads * r);
+        }
+        const int i = rounds * kThreads + tid;
+        if (i < nchunks) cp_async16(dst + 16 * i, src + 16 * i);
       } else {
 #pragma unroll
         for (int q = 0; q < kTile; ++q)
@@ -169,9 +180,9 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
   };
   issue_tile(0);
 
-  float h[kL];
+  float2 h2[kL];   // (h, h): one packed FMA updates both components
 #pragma unroll
-  for (int t = 0; t < kL; ++t) h[t] = g.taps[t * kN + p];
+  for (int t = 0; t < kL; ++t) { const float hv = g.taps[t * kN + p]; h2[t] = make_float2(hv, hv); }
 
   float2 win[kL];   // frame r of this pol is kept in slot r & 15 (m0 is a multiple of 16)
 #pragma unroll
@@ -198,11 +209,8 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
         float2 acc = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
 #pragma unroll
         for (int tap = 0; tap < kL; tap += 2) {
-          const float2 x = win[(q + 1 + tap) & 15], x1 = win[(q + 2 + tap) & 15];
-          acc.x = fmaf(h[tap], x.x, acc.x);
-          acc.y = fmaf(h[tap], x.y, acc.y);
-          acc1.x = fmaf(h[tap + 1], x1.x, acc1.x);
-          acc1.y = fmaf(h[tap + 1], x1.y, acc1.y);
+          acc = __ffma2_rn(h2[tap], win[(q + 1 + tap) & 15], acc);
+          acc1 = __ffma2_rn(h2[tap + 1], win[(q + 2 + tap) & 15], acc1);
         }
         vout[q * kRow] = __fadd2_rn(acc, acc1);
       }
@@ -238,6 +246,7 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
       // 8 consecutive spectra into one 16-byte store per plane and component; spectra at or past
       // the block's end go out as zeros (the pad columns of the last tile).
       const int mb = tc_tiles(g.M);
+      const bool full = mt + kTile <= m_end;
       const int h8 = tid & 1;
       const int m0 = mt + 8 * h8;
 #pragma unroll
@@ -248,8 +257,10 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
 #pragma unroll
         for (int k = 0; k < 8; k += 2) {
           float2 v0 = srow[(8 * h8 + k) ^ (c & 15)], v1 = srow[(8 * h8 + k + 1) ^ (c & 15)];
-          if (m0 + k >= m_end) v0 = make_float2(0.f, 0.f);
-          if (m0 + k + 1 >= m_end) v1 = make_float2(0.f, 0.f);
+          if (!full) {
+            if (m0 + k >= m_end) v0 = make_float2(0.f, 0.f);
+            if (m0 + k + 1 >= m_end) v1 = make_float2(0.f, 0.f);
+          }
           const __half2 h_re = __floats2half2_rn(v0.x, v1.x), h_im = __floats2half2_rn(v0.y, v1.y);
           const float2 f_re = __half22float2(h_re), f_im = __half22float2(h_im);
           const __half2 l_re = __floats2half2_rn(v0.x - f_re.x, v1.x - f_re.y);
