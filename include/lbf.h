@@ -225,6 +225,22 @@ lbf_status lbf_dedisperse(lbf_plan_t plan, double dm, int32_t fft_len, const voi
 lbf_status lbf_run_block_host(lbf_plan_t plan, const void *h_in, void *h_out, void *d_in, void *d_out,
                               void *stream);
 
+/* n consecutive blocks of the stream from HOST buffers, pipelined: the result equals n calls of
+ * lbf_run_block_host (block k from h_in[k] into h_out[k], the history advancing n times).
+ * Block k is uploaded into d_in0 (k even) or d_in1 (k odd), so its upload overlaps the kernels of
+ * block k - 1 and waits only for block k - 2 to have read that buffer; the kernels run on a
+ * stream of the plan; block k's download overlaps block k + 1's filter bank, and block k + 1's
+ * first write of d_out waits for it.  Everything is ordered after the work already on `stream`,
+ * and `stream` waits for the last download: once `stream` has passed the call, every h_out[k] is
+ * complete and every h_in[k] may be reused.  Returns once the work is enqueued.
+ * h_in, h_out: HOST arrays of n pointers (in_bytes / out_bytes each; page-locked for asynchronous
+ * copies; entries may repeat).  d_in0, d_in1: distinct device buffers of in_bytes (d_in1 unused
+ * and may be NULL when n == 1); d_out: device buffer of out_bytes.  All caller-owned.
+ * Errors: LBF_EINVAL (n < 0, NULL arrays or entries, bad or equal device buffers, or a plan with
+ * LBF_FLAG_EXTERNAL_WORKSPACE), LBF_ESTATE, LBF_ECUDA.  n == 0 does nothing. */
+lbf_status lbf_run_blocks_host(lbf_plan_t plan, int32_t n, const void *const *h_in, void *const *h_out,
+                               void *d_in0, void *d_in1, void *d_out, void *stream);
+
 /* Kernel timing trace (CUDA events around every kernel the plan launches).
  * lbf_trace_begin allocates event pairs for up to `max_launches` launches and starts recording;
  * lbf_trace_end synchronises on the recorded events, writes per-kernel totals to `out` and frees

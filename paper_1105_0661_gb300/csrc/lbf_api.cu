@@ -59,7 +59,9 @@ void release(lbf_plan_s *p) {
   cudaFree(p->ct16[0]); cudaFree(p->d_err); cudaFree(p->ss_members); cudaFree(p->ss_offs);
   if (p->h2d) cudaStreamDestroy(p->h2d);
   if (p->d2h) cudaStreamDestroy(p->d2h);
-  for (cudaEvent_t ev : {p->ev_in_free, p->ev_in_ready, p->ev_out_ready, p->ev_out_done})
+  if (p->cs) cudaStreamDestroy(p->cs);
+  for (cudaEvent_t ev : {p->ev_in_free, p->ev_in_ready, p->ev_out_ready, p->ev_out_done, p->ev_start,
+                         p->ev_in_free2[0], p->ev_in_free2[1]})
     if (ev) cudaEventDestroy(ev);
 }
 
@@ -187,8 +189,10 @@ int bf_kernel_id(lbf_plan_t p) { return p->variant == 1 ? K_BF_FEW : K_BF_MANY; 
 
 // The fused path on device buffers (a1-a7).  `ws` is the scratch of this call: the FP32
 // corner-turned block, or the FP16 planes of a tensor-core plan (with `maps` their descriptors).
+// input_read (optional) is recorded once d_in has been read; the first kernel that writes d_out
+// waits for out_free (optional).
 cudaError_t run_block_device(lbf_plan_t p, const void *d_in, void *d_out, void *ws, const CUtensorMap *maps,
-                             cudaStream_t st, cudaEvent_t input_read = nullptr) {
+                             cudaStream_t st, cudaEvent_t input_read = nullptr, cudaEvent_t out_free = nullptr) {
   const lbf::Geometry g = p->geometry();
   const void *h = p->hist[p->cur];
   void *nh = p->hist[p->cur ^ 1];
@@ -200,6 +204,7 @@ cudaError_t run_block_device(lbf_plan_t p, const void *d_in, void *d_out, void *
     cudaError_t e = traced(p, K_PPF_CT16, st, [&] { return lbf::launch_ppf(g, p->bits, d_in, h, nullptr, nullptr, st, &o); });
     if (e == cudaSuccess) e = traced(p, K_HIST, st, [&] { return lbf::launch_hist_update(g, p->bits, d_in, h, nh, st); });
     if (e == cudaSuccess && input_read) e = cudaEventRecord(input_read, st);
+    if (e == cudaSuccess && out_free) e = cudaStreamWaitEvent(st, out_free, 0);
     if (e != cudaSuccess) return e;
     p->cur ^= 1;
     if (p->inc) {
@@ -215,6 +220,7 @@ cudaError_t run_block_device(lbf_plan_t p, const void *d_in, void *d_out, void *
   cudaError_t e = traced(p, K_PPF_CT, st, [&] { return lbf::launch_ppf(g, p->bits, d_in, h, nullptr, ct, st); });
   if (e == cudaSuccess) e = traced(p, K_HIST, st, [&] { return lbf::launch_hist_update(g, p->bits, d_in, h, nh, st); });
   if (e == cudaSuccess && input_read) e = cudaEventRecord(input_read, st);
+  if (e == cudaSuccess && out_free) e = cudaStreamWaitEvent(st, out_free, 0);
   if (e != cudaSuccess) return e;
   p->cur ^= 1;
   return traced(p, bf_kernel_id(p), st,
@@ -547,6 +553,64 @@ lbf_status lbf_run_block_host(lbf_plan_t p, const void *h_in, void *h_out, void 
   if (e == cudaSuccess) e = cudaStreamWaitEvent(p->d2h, p->ev_out_ready, 0);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h_out, d_out, d.out_bytes, cudaMemcpyDeviceToHost, p->d2h);
   if (e == cudaSuccess) e = cudaEventRecord(p->ev_out_done, p->d2h);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, p->ev_out_done, 0);
+  return cuda_status(e);
+}
+
+lbf_status lbf_run_blocks_host(lbf_plan_t p, int32_t n, const void *const *h_in, void *const *h_out, void *d_in0,
+                               void *d_in1, void *d_out, void *stream) {
+  lbf_status s = check_call(p);
+  if (s != LBF_OK) return s;
+  if (n < 0 || (n > 0 && (!h_in || !h_out)) || p->external_ws) return LBF_EINVAL;
+  if (n == 0 || p->M == 0) return LBF_OK;
+  for (int k = 0; k < n; ++k)
+    if (!h_in[k] || !h_out[k]) return LBF_EINVAL;
+  void *const din[2] = {d_in0, d_in1};
+  if (!device_ptr(d_in0, p->word) || !device_ptr(d_out, p->nS ? 4 : 8)) return LBF_EINVAL;
+  if (n > 1 && (!device_ptr(d_in1, p->word) || d_in1 == d_in0)) return LBF_EINVAL;
+  lbf_dims d;
+  lbf_plan_dims(p, &d);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (!p->h2d) {
+    e = cudaStreamCreateWithFlags(&p->h2d, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->d2h, cudaStreamNonBlocking);
+    for (cudaEvent_t *ev : {&p->ev_in_free, &p->ev_in_ready, &p->ev_out_ready, &p->ev_out_done})
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  if (!p->cs) {
+    e = cudaStreamCreateWithFlags(&p->cs, cudaStreamNonBlocking);
+    for (cudaEvent_t *ev : {&p->ev_start, &p->ev_in_free2[0], &p->ev_in_free2[1]})
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  // everything after the work already on `stream` (and after this plan's earlier host calls,
+  // which `stream` waits for)
+  e = cudaEventRecord(p->ev_start, st);
+  for (cudaStream_t q : {p->h2d, p->cs, p->d2h})
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(q, p->ev_start, 0);
+  // the input buffers have no pending reads from an earlier call (those finished before ev_start)
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventRecord(p->ev_in_free2[i], p->cs);
+  if (e == cudaSuccess) e = cudaEventRecord(p->ev_out_done, p->d2h);
+  for (int k = 0; k < n && e == cudaSuccess; ++k) {
+    void *di = din[k & 1];
+    // upload block k into its buffer once block k - 2 (the buffer's last reader) has read it
+    e = cudaStreamWaitEvent(p->h2d, p->ev_in_free2[k & 1], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(di, h_in[k], d.in_bytes, cudaMemcpyHostToDevice, p->h2d);
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev_in_ready, p->h2d);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->cs, p->ev_in_ready, 0);
+    // kernels of block k; its first write of d_out waits for block k - 1's download
+    if (e == cudaSuccess) e = run_block_device(p, di, d_out, own_ws(p), p->tmap, p->cs, p->ev_in_free2[k & 1],
+                                               p->ev_out_done);
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev_out_ready, p->cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->d2h, p->ev_out_ready, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_out[k], d_out, d.out_bytes, cudaMemcpyDeviceToHost, p->d2h);
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev_out_done, p->d2h);
+  }
+  // a later lbf_run_block_host upload waits for these kernels' reads; `stream` passes this call
+  // once the last download (and so every kernel and copy) is done
+  if (e == cudaSuccess) e = cudaEventRecord(p->ev_in_free, p->cs);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(st, p->ev_out_done, 0);
   return cuda_status(e);
 }

@@ -46,6 +46,10 @@ struct lbf_plan_s {
   // lbf_run_block_host: copy streams and the events that order them against the kernels
   cudaStream_t h2d = nullptr, d2h = nullptr;
   cudaEvent_t ev_in_free = nullptr, ev_in_ready = nullptr, ev_out_ready = nullptr, ev_out_done = nullptr;
+  // lbf_run_blocks_host: the plan's compute stream, its start event and one input-free event per
+  // device input buffer (the two alternate)
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_in_free2[2] = {nullptr, nullptr};
 
   // kernel timing trace (lbf_trace_begin / lbf_trace_end)
   struct TraceSlot { int kernel; cudaEvent_t a, b; };

@@ -24,7 +24,8 @@ BF_VARIANTS = {"auto": 0, "few": 1, "many": 2}
 # Every symbol include/lbf.h declares; the test suite checks the library exports all of them.
 EXPORTED = ("lbf_plan", "lbf_plan_destroy", "lbf_plan_dims", "lbf_plan_shifts", "lbf_reset_state",
             "lbf_ppf", "lbf_delay_correct", "lbf_beamform", "lbf_beamform_stokes", "lbf_stokes",
-            "lbf_run_block", "lbf_run_block_ws", "lbf_run_block_host", "lbf_trace_begin", "lbf_trace_end",
+            "lbf_run_block", "lbf_run_block_ws", "lbf_run_block_host", "lbf_run_blocks_host",
+            "lbf_trace_begin", "lbf_trace_end",
             "lbf_device_status", "lbf_debug_stall_next", "lbf_run_block_static", "lbf_superstation", "lbf_dedisperse",
             "lbf_batch_create", "lbf_batch_destroy",
             "lbf_batch_run", "lbf_batch_capture", "lbf_batch_launch", "lbf_batch_tune",
@@ -99,6 +100,8 @@ def load_library() -> ctypes.CDLL:
             "lbf_run_block": ([vp, vp, vp, vp], ctypes.c_int),
             "lbf_run_block_ws": ([vp, vp, vp, vp, ctypes.c_size_t, vp], ctypes.c_int),
             "lbf_run_block_host": ([vp, vp, vp, vp, vp, vp], ctypes.c_int),
+            "lbf_run_blocks_host": ([vp, ctypes.c_int32, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp, vp, vp],
+                                    ctypes.c_int),
             "lbf_trace_begin": ([vp, ctypes.c_int32], ctypes.c_int),
             "lbf_trace_end": ([vp, ctypes.POINTER(_Trace)], ctypes.c_int),
             "lbf_device_status": ([vp, i32p], ctypes.c_int),
@@ -298,6 +301,20 @@ class Plan:
         _check(self._lib.lbf_run_block_host(self._h, _ptr(h_in, d.in_bytes), _ptr(h_out, d.out_bytes),
                                             _ptr(d_in, d.in_bytes), _ptr(d_out, d.out_bytes),
                                             _stream(stream)), "lbf_run_block_host")
+
+    def run_blocks_host(self, h_ins, h_outs, d_in0, d_in1, d_out, stream=None):
+        """len(h_ins) consecutive blocks from host buffers, pipelined (uploads alternate between
+        d_in0 and d_in1 and overlap the previous block's kernels); `stream` waits for the last
+        download.  Synchronise `stream` before reading the h_outs or reusing the h_ins."""
+        d = self.dims
+        n = len(h_ins)
+        if len(h_outs) != n:
+            raise ValueError("h_ins and h_outs differ in length")
+        arr_in = (ctypes.c_void_p * max(n, 1))(*[_ptr(h, d.in_bytes) for h in h_ins])
+        arr_out = (ctypes.c_void_p * max(n, 1))(*[_ptr(h, d.out_bytes) for h in h_outs])
+        d1 = _ptr(d_in1, d.in_bytes) if d_in1 is not None else None
+        _check(self._lib.lbf_run_blocks_host(self._h, n, arr_in, arr_out, _ptr(d_in0, d.in_bytes), d1,
+                                             _ptr(d_out, d.out_bytes), _stream(stream)), "lbf_run_blocks_host")
 
     def dedisperse(self, dm, fft_len, d_vol_in, d_vol_out, stream=None):
         """Channel-level dedispersion (Section 4.4) of voltages [B][F][N][P][M] (may be in place)."""

@@ -1,6 +1,7 @@
 """The C-ABI library builds, loads and exports every entry point include/lbf.h declares; config
 validation happens on the host before any device work (runs without a GPU)."""
 
+import ctypes
 import os
 import re
 
@@ -77,3 +78,12 @@ def test_voltage_output_ignores_integration_divisibility(lbf):
     # plan then fails at the first device call (not at validation)
     st = lbf.plan_status(_cfg(block_samples=256 * 6, int_factor=4, output="V"))
     assert st != 1
+
+
+def test_null_plan_rejected_by_the_host_buffer_calls(lbf):
+    # no device work: a null plan fails the handle check (LBF_ESTATE) before any CUDA call
+    lib = lbf.load_library()
+    vp = ctypes.c_void_p
+    arr = (vp * 1)(None)
+    assert lib.lbf_run_blocks_host(None, 1, arr, arr, None, None, None, None) == 4
+    assert lib.lbf_run_block_host(None, None, None, None, None, None) == 4
