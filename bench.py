@@ -507,6 +507,20 @@ def run_serve(args):
     h_in[:blk.numel() * blk.element_size()].copy_(blk.view(torch.uint8).reshape(-1))
     del blk
     torch.cuda.empty_cache()
+    # the host-copy rates of this process's pinned buffers (the server's copies are most of its
+    # per-block time), reported beside the latencies
+    copy_gbs = {}
+    nb = min(max_in, 4 << 30)
+    d_probe = torch.empty(nb, dtype=torch.uint8, device=dev)
+    for name, (dst, src) in {"h2d": (d_probe, h_in[:nb]), "d2h": (h_in[:nb], d_probe)}.items():
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        copy_gbs[name] = nb / (time.perf_counter() - t0) / 1e9
+    del d_probe
+    torch.cuda.empty_cache()
     for oid, p in enumerate(plans):
         srv.add(oid, p, h_in, h_out)
     # warm-up: one block per observation, outside the measured schedule
@@ -527,7 +541,7 @@ def run_serve(args):
                                f"real-time period with late-arrival jitter (exponential, mean period/4)",
                    "observations": [wl.name + f" ({prec})" for wl, prec in specs],
                    "hbm_budget_gb": args.budget_gb, "period_s": period},
-        "latency": summ, "sustained_station_samples_per_s": ss / wall,
+        "latency": summ, "sustained_station_samples_per_s": ss / wall, "host_copy_gbs": copy_gbs,
         "realtime_station_samples_per_s": sum(wl.station_samples() for wl, _ in specs) / period,
         "e2e": {"value": summ["p99_s"], "unit": "s", "h2d_bytes_per_step": int(np.mean([p.dims.in_bytes for p in plans])),
                 "d2h_bytes_per_step": int(np.mean([p.dims.out_bytes for p in plans]))},
