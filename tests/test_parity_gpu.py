@@ -380,32 +380,39 @@ def test_host_buffer_calls_pipeline_in_order(dev, prec):
     p_dev.close()
 
 
-@pytest.mark.parametrize("prec,nblk", [("fp32", 3), ("fp16tc", 4), ("fp32", 1)])
-def test_multi_block_host_call_matches_per_block_path(dev, prec, nblk):
+@pytest.mark.parametrize("prec,nblk,out,bits", [("fp32", 3, "IQUV", 16), ("fp16tc", 4, "IQUV", 16),
+                                              ("fp32", 1, "IQUV", 16), ("fp32", 2, "V", 8), ("fp16tc", 3, "V", 16)])
+def test_multi_block_host_call_matches_per_block_path(dev, prec, nblk, out, bits):
     """lbf_run_blocks_host: n blocks from host buffers in one call, uploads alternating between two
     device buffers and overlapping the previous block's kernels, downloads overlapping the next
     block's filter bank.  Every block equals the device-buffer path bit for bit (the same kernels on
     the same inputs) and the oracle within tolerance; a second call continues the stream."""
-    wl = _wl(S=16, B=70, out="IQUV", Q=4, T=64 * N)
+    wl = _wl(S=16, B=70, out=out, Q=4, T=64 * N, bits=bits)
     p_host = _plan(wl, precision=prec)
     p_dev = _plan(wl, precision=prec)
     ob = O.observation_from_workload(wl)
     blocks = [G.make_block(wl, seed=31, block_index=k) for k in range(2 * nblk)]
+    kind, dt = ("vol", torch.complex64) if out == "V" else ("stokes", torch.float32)
     h_in = [torch.from_numpy(b).pin_memory() for b in blocks]
-    h_out = [torch.empty(p_host.shape("stokes"), dtype=torch.float32).pin_memory() for _ in blocks]
-    d_in0 = torch.empty(blocks[0].shape, dtype=torch.int16, device=dev)
+    h_out = [torch.empty(p_host.shape(kind), dtype=dt).pin_memory() for _ in blocks]
+    d_in0 = torch.empty(blocks[0].shape, dtype=torch.from_numpy(blocks[0]).dtype, device=dev)
     d_in1 = torch.empty_like(d_in0) if nblk > 1 else None
-    d_out = torch.empty(p_host.shape("stokes"), dtype=torch.float32, device=dev)
+    d_out = torch.empty(p_host.shape(kind), dtype=dt, device=dev)
     stream = torch.cuda.Stream(device=dev)
     p_host.run_blocks_host(h_in[:nblk], h_out[:nblk], d_in0, d_in1, d_out, stream)
     p_host.run_blocks_host(h_in[nblk:], h_out[nblk:], d_in0, d_in1, d_out, stream)
     stream.synchronize()
-    o = torch.empty(p_dev.shape("stokes"), dtype=torch.float32, device=dev)
+    o = torch.empty(p_dev.shape(kind), dtype=dt, device=dev)
     tol = TOL if prec == "fp32" else 1e-3
     for k in range(2 * nblk):
         p_dev.run_block(_to_dev(blocks[k], dev), o)
         assert torch.equal(o.cpu(), h_out[k]), k
-        _check_stokes(h_out[k].numpy().astype(np.float64), ob.run_block(blocks[k]), tol)
+        ref = ob.run_block(blocks[k])
+        if out == "V":
+            err = _rel_rms(h_out[k].numpy().astype(np.complex128), ref, (2, 3, 4))
+            assert err.max() <= (TOL if prec == "fp32" else 1e-4), (k, err.max())
+        else:
+            _check_stokes(h_out[k].numpy().astype(np.float64), ref, tol)
     from paper_1105_0661_gb300.lbf import LbfError
     with pytest.raises(LbfError):   # two blocks need two distinct input buffers
         p_host.run_blocks_host(h_in[:2], h_out[:2], d_in0, d_in0, d_out, stream)
