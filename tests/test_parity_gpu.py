@@ -418,3 +418,31 @@ def test_multi_block_host_call_matches_per_block_path(dev, prec, nblk, out, bits
         p_host.run_blocks_host(h_in[:2], h_out[:2], d_in0, d_in0, d_out, stream)
     p_host.close()
     p_dev.close()
+
+
+@pytest.mark.parametrize("bits,prec", [(16, "fp32"), (8, "fp32"), (16, "fp16tc")])
+def test_input_not_16_byte_aligned_gives_the_same_block(dev, bits, prec):
+    """The filter bank copies in-block tiles as 16-byte pieces when the input is 16-byte aligned and
+    one sample at a time otherwise: an input that starts one sample word past a 16-byte boundary
+    (still word-aligned, as the ABI requires) takes the second path and must give the same bits."""
+    wl = _wl(S=6, F=2, T=40 * N, B=5, Q=4, bits=bits)
+    p_a = _plan(wl, precision=prec)
+    p_b = _plan(wl, precision=prec)
+    blk = G.make_block(wl, seed=12, block_index=0)
+    word = 8 if bits == 16 else 4
+    flat = torch.from_numpy(np.ascontiguousarray(blk)).view(torch.uint8).reshape(-1)
+    raw = torch.zeros(flat.numel() + 16, dtype=torch.uint8, device=dev)
+    raw[word:word + flat.numel()].copy_(flat.to(dev))
+    d_mis = raw[word:word + flat.numel()].view(torch.from_numpy(blk).dtype).view(blk.shape)
+    assert d_mis.data_ptr() % 16 == word
+    o_a = torch.empty(p_a.shape("stokes"), dtype=torch.float32, device=dev)
+    o_b = torch.empty_like(o_a)
+    for bi in range(2):   # the second block also reads the history written from the first
+        if bi == 1:
+            blk = G.make_block(wl, seed=12, block_index=1)
+            raw[word:word + flat.numel()].copy_(torch.from_numpy(np.ascontiguousarray(blk)).view(torch.uint8).reshape(-1).to(dev))
+        p_a.run_block(_to_dev(blk, dev), o_a)
+        p_b.run_block(d_mis, o_b)
+        assert torch.equal(o_a, o_b), bi
+    p_a.close()
+    p_b.close()
