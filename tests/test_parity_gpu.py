@@ -330,8 +330,9 @@ def test_incoherent_beam_matches_oracle(dev, variant, prec, bits, out, tol):
 
 
 # ----------------------------------------------------------------------------- superstation beam former
-def test_superstation_matches_oracle(dev):
-    wl = _wl(S=12, F=2, T=40 * N)
+@pytest.mark.parametrize("M", [40, 41])   # even M: two spectra per thread; odd M: one
+def test_superstation_matches_oracle(dev, M):
+    wl = _wl(S=12, F=2, T=M * N) if M % 4 == 0 else _wl(S=12, F=2, T=M * N, out="V", Q=1)
     p = _plan(wl)
     ob = O.observation_from_workload(wl)
     rng = np.random.default_rng(40)
@@ -340,7 +341,7 @@ def test_superstation_matches_oracle(dev):
     d_ct = _to_dev(ct, dev)
     for groups in (np.array([0, 0, 1, 1, 1, 2, 0, 2, 1, 0, 2, 2]), np.zeros(12, dtype=int), np.arange(12)):
         G_ = int(groups.max()) + 1
-        ss = torch.empty((wl.n_subbands, N, G_, 2, 40), dtype=torch.complex64, device=dev)
+        ss = torch.empty((wl.n_subbands, N, G_, 2, M), dtype=torch.complex64, device=dev)
         p.superstation(groups, d_ct, ss)
         ref = ob.superstation(ct.astype(np.complex128), groups)
         got = ss.cpu().numpy().astype(np.complex128)
