@@ -312,12 +312,17 @@ def test_maximum_paper_geometry(dev):
 
 
 # ----------------------------------------------------------------------------- incoherent beam
-@pytest.mark.parametrize("variant,prec,bits,out,tol", [("few", "fp32", 16, "IQUV", TOL), ("many", "fp32", 8, "I", TOL),
-                                                       ("auto", "fp16tc", 16, "IQUV", 1e-3), ("auto", "fp16tc", 8, "I", 1e-3)])
-def test_incoherent_beam_matches_oracle(dev, variant, prec, bits, out, tol):
+# the tensor-core cases also cover windows longer than a thread's 8 spectra (Q = 16, 32) and a
+# last group of 8 spectra that runs past M (M = 36)
+@pytest.mark.parametrize("variant,prec,bits,out,tol,M,Q", [
+    ("few", "fp32", 16, "IQUV", TOL, 64, 4), ("many", "fp32", 8, "I", TOL, 64, 4),
+    ("auto", "fp16tc", 16, "IQUV", 1e-3, 64, 4), ("auto", "fp16tc", 8, "I", 1e-3, 64, 4),
+    ("auto", "fp16tc", 16, "I", 1e-3, 96, 32), ("auto", "fp16tc", 16, "IQUV", 1e-3, 36, 2),
+    ("auto", "fp16tc", 8, "I", 1e-3, 80, 16)])
+def test_incoherent_beam_matches_oracle(dev, variant, prec, bits, out, tol, M, Q):
     """LBF_FLAG_INCOHERENT_BEAM: beam index B of the Stokes output is the incoherent beam
     (Section 3); the coherent beams are unchanged."""
-    wl = _wl(S=16, B=6 if variant == "few" else 70, out=out, bits=bits, Q=4, T=64 * N)
+    wl = _wl(S=16, B=6 if variant == "few" else 70, out=out, bits=bits, Q=Q, T=M * N)
     p = _plan(wl, bf_variant=variant, precision=prec, incoherent_beam=True)
     ob = O.observation_from_workload(wl, incoherent_beam=True)
     o = torch.empty(p.shape("stokes"), dtype=torch.float32, device=dev)
