@@ -353,6 +353,15 @@ def run_ours(args):
         d_stage = [torch.empty_like(d_in), torch.empty_like(d_in)]
         plan.run_blocks_host([h_in] * 2, [h_out] * 2, d_stage[0], d_stage[1], d_out, stream)
         stream.synchronize()
+        # the pinned-copy rates of these buffers right now (the host link is shared with other
+        # jobs on the machine and varies between runs): the end-to-end figure is read against them
+        copy_gbs = {}
+        for name, (dst, src) in {"h2d": (d_stage[0], h_in), "d2h": (h_out, d_out)}.items():
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            copy_gbs[name] = src.numel() * src.element_size() / (time.perf_counter() - t0) / 1e9
         dist.barrier(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         # a stream of blocks: one upload fills the pipeline, so it is timed over at least 30 blocks
@@ -364,7 +373,7 @@ def run_ours(args):
         ems = dist.reduce_scalar(e0.elapsed_time(e1), "max", dev)
         e2e = {"value": world * ss_step * k2 / (ems / 1e3), "unit": "station-samples/s",
                "h2d_bytes_per_step": dims.in_bytes, "d2h_bytes_per_step": dims.out_bytes,
-               "steps": k2, "ms_per_step": ems / k2, "call": "lbf_run_blocks_host"}
+               "steps": k2, "ms_per_step": ems / k2, "call": "lbf_run_blocks_host", "host_copy_gbs": copy_gbs}
         del h_in, h_out, d_stage
 
     # roofline of the dominant kernel from the live trace

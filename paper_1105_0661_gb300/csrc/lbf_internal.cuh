@@ -76,7 +76,6 @@ cudaError_t launch_ppf_group(const PpfGroup *d_groups, int ngrp, long long total
 cudaError_t launch_hist_group(const PpfGroup *d_groups, int ngrp, long long total, cudaStream_t st);
 cudaError_t launch_bf_group(const BfGroup *d_groups, int ngrp, long long total, unsigned long long *counter,
                             int ctas, size_t smem, cudaStream_t st);
-int ppf_spectra_per_cta();
 int few_beams_per_item();
 int many_beams_per_item();
 size_t bf_smem_bytes(int variant, int S);
