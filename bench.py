@@ -538,7 +538,18 @@ def run_serve(args):
         o.results.clear()
     rng = np.random.default_rng(11)
     sched = poisson_schedule(len(plans), args.serve_blocks, period, rng)
-    res, wall = srv.run(sched)
+    # kernel times of every observation's blocks and the clocks while the schedule runs, so that
+    # a slow run can be told apart from a slow host link
+    for p in plans:
+        p.trace_begin(8 * args.serve_blocks + 8)
+    with ClockSampler("0") as clk:
+        res, wall = srv.run(sched)
+    kernel_ms = {}
+    for p in plans:
+        for k, v in p.trace_end().items():
+            if k.startswith("_") or not v[0]:
+                continue
+            kernel_ms[k] = kernel_ms.get(k, 0.0) + v[1]
     summ = latency_summary(res, period)
     ss = sum(specs[r.obs][0].station_samples() for r in res)
     line = {
@@ -551,6 +562,8 @@ def run_serve(args):
                    "observations": [wl.name + f" ({prec})" for wl, prec in specs],
                    "hbm_budget_gb": args.budget_gb, "period_s": period},
         "latency": summ, "sustained_station_samples_per_s": ss / wall, "host_copy_gbs": copy_gbs,
+        "kernel_s_per_period": sum(kernel_ms.values()) / 1e3 / (wall / period), "kernels_ms_total": kernel_ms,
+        "clocks": clk.summary(),
         "realtime_station_samples_per_s": sum(wl.station_samples() for wl, _ in specs) / period,
         "e2e": {"value": summ["p99_s"], "unit": "s", "h2d_bytes_per_step": int(np.mean([p.dims.in_bytes for p in plans])),
                 "d2h_bytes_per_step": int(np.mean([p.dims.out_bytes for p in plans]))},
