@@ -232,7 +232,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     wl = workload(args.workload, args.subbands, args.bits)
-    nsub = args.cpu_subbands
+    nsub = min(args.cpu_subbands, wl.n_subbands)
     subbands = list(range(nsub))
     blocks = host_block_slices(wl, 0, subbands)
     for _ in range(args.warmup):
@@ -284,6 +284,7 @@ def run_ours(args):
     dist.barrier(dev)
     wl = workload(args.workload, args.subbands, args.bits)
     pk, pk_kind = peaks()
+    args.cpu_subbands = min(args.cpu_subbands, wl.n_subbands)
 
     # cpu baseline first (spawned workers, before the large device allocations)
     cpu = None
@@ -869,7 +870,7 @@ def main():
     ap.add_argument("--subbands", type=int, default=0,
                     help="use only the first N subbands (small profiling cases; 0 = all)")
     ap.add_argument("--cpu-subbands", type=int, default=0,
-                    help="subbands in the oracle sample (default 4; 1 for the 1024-beam workload)")
+                    help="subbands in the oracle sample, one process each (default: one per host core, <= 16)")
     ap.add_argument("--e2e-steps", type=int, default=0,
                     help="end-to-end blocks in the streaming host call (0: max(K, 30))")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -887,8 +888,8 @@ def main():
     ap.add_argument("--serve-blocks", type=int, default=8)
     ap.add_argument("--budget-gb", type=float, default=120.0)
     args = ap.parse_args()
-    if args.cpu_subbands <= 0:
-        args.cpu_subbands = 1 if args.workload == "lofar1024" else 4
+    if args.cpu_subbands <= 0:   # one oracle process per subband, one per host core
+        args.cpu_subbands = min(16, os.cpu_count() or 4)
     if args.warmup < 3:
         print("bench: warm-up must be >= 3 steps", file=sys.stderr)
         return 2
