@@ -60,7 +60,7 @@ typedef enum {
   LBF_ESTATE = 4,      /* plan in an unusable state (e.g. destroyed, or device mismatch) */
   LBF_ETIMEOUT = 5,    /* a bounded device-side wait gave up */
   LBF_EBUSY = 6,       /* resource temporarily unavailable */
-  LBF_EUNSUPPORTED = 7, /* valid request this build does not implement */
+  LBF_EUNSUPPORTED = 7, /* valid request this library does not implement */
   LBF_ETOOBIG = 8       /* request exceeds the fixed scratch of lbf_run_block_static */
 } lbf_status;
 
@@ -87,8 +87,8 @@ typedef enum { LBF_BF_AUTO = 0, LBF_BF_FEW = 1, LBF_BF_MANY = 2 } lbf_bf_variant
 typedef struct lbf_config {
   int32_t n_stations;     /* S >= 1 */
   int32_t n_subbands;     /* F >= 1 */
-  int32_t n_channels;     /* N; this build supports 256 */
-  int32_t n_taps;         /* L; this build supports 16 */
+  int32_t n_channels;     /* N; the library supports 256 */
+  int32_t n_taps;         /* L; the library supports 16 */
   int32_t n_beams;        /* B >= 1 */
   int32_t block_samples;  /* T >= 0, a multiple of N (T = 0: every call is a no-op) */
   int32_t int_factor;     /* Q in {1,2,4,8,16,32}; for Stokes outputs M = T/N must be a multiple */

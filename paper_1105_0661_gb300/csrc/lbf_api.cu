@@ -243,7 +243,7 @@ const char *lbf_status_string(lbf_status s) {
     case LBF_ESTATE: return "LBF_ESTATE: plan in an unusable state";
     case LBF_ETIMEOUT: return "LBF_ETIMEOUT: device wait timed out";
     case LBF_EBUSY: return "LBF_EBUSY: resource busy";
-    case LBF_EUNSUPPORTED: return "LBF_EUNSUPPORTED: not supported by this build";
+    case LBF_EUNSUPPORTED: return "LBF_EUNSUPPORTED: not supported by this library";
     case LBF_ETOOBIG: return "LBF_ETOOBIG: exceeds the fixed scratch of the allocation-free entry point";
   }
   return "LBF_?: unknown status";

@@ -65,7 +65,7 @@ def _cfg(**over):
     (dict(station_xyz=np.zeros((0, 3))), 1),          # no stations
     (dict(beam_dlm=np.zeros((0, 2))), 1),             # no beams
     (dict(station_xyz=np.full((2, 3), np.nan)), 1),   # non-finite geometry
-    (dict(n_channels=128, taps=np.ones(128 * 16, np.float32)), 7),   # only N = 256 in this build
+    (dict(n_channels=128, taps=np.ones(128 * 16, np.float32)), 7),   # only N = 256 is supported
     (dict(precision="fp16tc", output="V", incoherent_beam=True), 1),   # no incoherent beam in voltages
     (dict(precision="fp16tc", station_xyz=np.zeros((65, 3))), 7),   # K = 2 S <= 128
 ])
