@@ -161,7 +161,7 @@ def traffic_from_profiles(kernel: str, workload_name: str):
     src = {"bf_many": "beamform.cu", "bf_few": "beamform.cu", "ppf_ct": "ppf.cu", "ppf": "ppf.cu",
            "ppf_ct16": "ppf.cu", "bf_tc": "bf_tc.cu", "hist_update": "ppf.cu", "delay_ct": "delay.cu",
            "dedisperse": "dedisperse.cu",
-           "stokes": "stokes.cu"}.get(kernel)
+           "stokes": "stokes.cu", "superstation": "delay.cu"}.get(kernel)
     if src is None:
         return None
     h = hashlib.sha256(open(os.path.join(ROOT, "paper_1105_0661_gb300", "csrc", src), "rb").read()).hexdigest()[:16]
@@ -722,7 +722,8 @@ def run_superstation(args):
                    "l2": "inputs larger than L2 (%.1f GB read per step)" % (ct.numel() * 8 / 1e9)},
         "gpu_launches": n,
         "roofline": {"bound": "hbm", "kernel": "superstation", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": gbs / pk["hbm_gbs"], "traffic": None, "peak_source": f"{pk_kind} hbm_gbs"},
+                     "frac": gbs / pk["hbm_gbs"], "traffic": traffic_from_profiles("superstation", wl.name),
+                     "peak_source": f"{pk_kind} hbm_gbs"},
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
