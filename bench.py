@@ -33,8 +33,6 @@ sys.path.insert(0, ROOT)
 from paper_1105_0661_gb300 import dist  # noqa: E402
 from synth import generate as G  # noqa: E402
 
-FP32_LANES_PER_SM = 128      # FFMA lanes per SM (4 sub-partitions x 32)
-N_SM = 152
 
 
 def workload(name: str, subbands: int = 0, bits: int = 0):
@@ -173,6 +171,18 @@ def traffic_from_profiles(kernel: str, workload_name: str):
             except ValueError:
                 return None
     return None
+
+
+def measure_alu_peak(stream, smi_index):
+    """FP32 SIMT throughput of this GPU now (lbf_measure_fp32_peak) with the SM clock seen."""
+    from paper_1105_0661_gb300 import lbf
+    with ClockSampler(smi_index) as clk:
+        r = lbf.measure_fp32_peak(5, stream)
+        time.sleep(0.25)
+    c = clk.summary()
+    r["tflops"] = max(r["ffma_tflops"], r["ffma2_tflops"])
+    r["clocks"] = f"{c['sm_mhz']:.0f} MHz median (max {c['sm_max_mhz']:.0f})" if c else "not sampled"
+    return r
 
 
 # ----------------------------------------------------------------------------- CPU oracle
@@ -318,14 +328,17 @@ def run_ours(args):
             errs.append(float((abs(got[:, 0] - I) / I).max()))
         parity = {"max_rel_err_stokes_I": max(errs), "subbands": args.cpu_subbands}
 
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
+    smi_index = vis[local].strip() if len(vis) > local and vis[local].strip() else str(local)
+    # the FP32 SIMT peak of this GPU, measured now (the denominator of the FP32 kernels' roofline)
+    alu_peak = measure_alu_peak(stream, smi_index)
+
     for _ in range(args.warmup):
         plan.run_block(d_in, d_out, stream)
     stream.synchronize()
     dist.barrier(dev)
 
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
-    smi_index = vis[local].strip() if len(vis) > local and vis[local].strip() else str(local)
     with ClockSampler(smi_index) as clk:
         plan.trace_begin(3 * args.steps + 8)
         torch.cuda.synchronize(dev)
@@ -354,15 +367,20 @@ def run_ours(args):
         d_stage = [torch.empty_like(d_in), torch.empty_like(d_in)]
         plan.run_blocks_host([h_in] * 2, [h_out] * 2, d_stage[0], d_stage[1], d_out, stream)
         stream.synchronize()
-        # the pinned-copy rates of these buffers right now (the host link is shared with other
-        # jobs on the machine and varies between runs): the end-to-end figure is read against them
-        copy_gbs = {}
-        for name, (dst, src) in {"h2d": (d_stage[0], h_in), "d2h": (h_out, d_out)}.items():
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            dst.copy_(src, non_blocking=True)
-            torch.cuda.synchronize()
-            copy_gbs[name] = src.numel() * src.element_size() / (time.perf_counter() - t0) / 1e9
+
+        # the pinned-copy rates of these buffers just before and just after the timed region (the
+        # host link is shared with other jobs on the machine and varies between and within runs):
+        # the end-to-end figure is read against them
+        def copy_rates():
+            r = {}
+            for name, (dst, src) in {"h2d": (d_stage[0], h_in), "d2h": (h_out, d_out)}.items():
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                dst.copy_(src, non_blocking=True)
+                torch.cuda.synchronize()
+                r[name] = src.numel() * src.element_size() / (time.perf_counter() - t0) / 1e9
+            return r
+        copy_before = copy_rates()
         dist.barrier(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         # a stream of blocks: one upload fills the pipeline, so it is timed over at least 30 blocks
@@ -372,9 +390,11 @@ def run_ours(args):
         e1.record(stream)
         stream.synchronize()
         ems = dist.reduce_scalar(e0.elapsed_time(e1), "max", dev)
+        copy_after = copy_rates()
         e2e = {"value": world * ss_step * k2 / (ems / 1e3), "unit": "station-samples/s",
                "h2d_bytes_per_step": dims.in_bytes, "d2h_bytes_per_step": dims.out_bytes,
-               "steps": k2, "ms_per_step": ems / k2, "call": "lbf_run_blocks_host", "host_copy_gbs": copy_gbs}
+               "steps": k2, "ms_per_step": ems / k2, "call": "lbf_run_blocks_host",
+               "host_copy_gbs": {"before": copy_before, "after": copy_after}}
         del h_in, h_out, d_stage
 
     # roofline of the dominant kernel from the live trace
@@ -406,12 +426,13 @@ def run_ours(args):
                 "peak_source": f"{pk_kind} bf16_tflops_sustained (fp16 dense nominal ratio 1.0); achieved counts "
                                f"one complex product, the hi+lo form executes three (Whi.Yhi + Whi.Ylo + Wlo.Yhi)"}
     elif bound == "alu":
-        peak_tf = N_SM * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        peak_tf = alu_peak["tflops"]
         achieved = amount / avg_s / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": achieved / peak_tf, "traffic": traffic_from_profiles(dom, wl.name),
-                "peak_source": f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x 2 flop x "
-                               f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({pk_kind} max SM clock)"}
+                "peak_source": "measured in this run: lbf_measure_fp32_peak, the faster of scalar FFMA "
+                               f"({alu_peak['ffma_tflops']:.1f}) and packed FP32x2 ({alu_peak['ffma2_tflops']:.1f}) "
+                               f"FMA chains on all {alu_peak['sms']} SMs, SM clock {alu_peak['clocks']}"}
     else:
         peak = pk["hbm_gbs"]
         achieved = amount / avg_s / 1e9
@@ -455,7 +476,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.precision == "fp32" else "f16", "data": "synthetic",
         "config": config_dict(wl, args), "e2e": e2e, "gpu_launches": launches, "roofline": roof,
-        "cpu_baseline": cpu, "clocks": clocks, "kernels": kernels,
+        "cpu_baseline": cpu, "clocks": clocks, "kernels": kernels, "fp32_peak": alu_peak,
         "beamform_tflops": bf_flop * args.steps / (sum(v[1] for k, v in trace.items() if k.startswith("bf_")) / 1e3) / 1e12,
         "dtype_detail": "fp16 tensor-core operands, fp32 accumulation" if args.precision == "fp16tc" else "fp32",
         "parity": parity, "precision_compare": compare,
@@ -472,8 +493,9 @@ def run_ours(args):
 # ----------------------------------------------------------------------------- serving
 def serving_observations(n: int, seed: int = 5):
     """The streaming workload: n observations with stations 24-64, subbands 61-244, beams 7-1024,
-    Stokes I or IQUV (integration 16), 196608-sample int16 blocks, drawn from a seeded rng.  Many
-    beams (>= 64) run on the tensor cores, few beams on the FP32 path."""
+    Stokes I or IQUV (integration 16), 196608-sample int16 blocks, drawn from a seeded rng.  Every
+    plan asks for the tensor-core precision; the library keeps the tensor cores for more than 8
+    beams and gives fewer beams the bandwidth-bound FP32 few-beam kernel."""
     import numpy as np
     rng = np.random.default_rng(seed)
     out = []
@@ -485,7 +507,7 @@ def serving_observations(n: int, seed: int = 5):
         xyz = G.lofar_positions(rng, S // 2, S - S // 2)
         wl = G.Workload(f"serve{i}-{S}st-{F}sb-{B}beam-{kind}16", xyz, G.subband_centres(F, 110e6),
                         G.hex_beam_grid(B, 0.05), (0.3, 0.4), 196608, 16, kind, source="noise")
-        out.append((wl, "fp16tc" if (B >= 64 and S <= 64) else "fp32"))
+        out.append((wl, "fp16tc" if S <= 64 else "fp32"))
     return out
 
 

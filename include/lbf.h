@@ -71,8 +71,8 @@ typedef enum { LBF_VOLTAGES = 0, LBF_STOKES_I = 1, LBF_STOKES_IQUV = 4 } lbf_out
 
 typedef enum { LBF_FP32 = 0, LBF_FP16_TC = 1 } lbf_precision;
 
-/* Beam-former kernel choice: AUTO picks the bandwidth-bound few-beam kernel for small B and the
- * register-tiled many-beam kernel otherwise. */
+/* Beam-former kernel choice: AUTO picks the bandwidth-bound few-beam kernel for B <= 8 and the
+ * register-tiled many-beam kernel (FP32) or the tensor-core kernel (LBF_FP16_TC) otherwise. */
 typedef enum { LBF_BF_AUTO = 0, LBF_BF_FEW = 1, LBF_BF_MANY = 2 } lbf_bf_variant;
 
 /* The plan does not allocate the run_block scratch; the caller passes one to lbf_run_block_ws
@@ -136,7 +136,11 @@ typedef struct lbf_plan_s *lbf_plan_t;
  * With precision LBF_FP16_TC the many-beam beam former runs on the tensor cores (tcgen05, FP16
  * operands, FP32 accumulation): the filtered spectrum Y of either sample width feeds it as two
  * FP16 planes (hi = fp16(Y), lo = fp16(Y - hi)) and the weights are split the same way, three
- * products per tile, writing Stokes or beam voltages; it needs S <= 64.
+ * products per tile, writing Stokes or beam voltages; it needs S <= 64.  The tensor cores are used
+ * only where the beam count makes the beam former a dense contraction: with bf_variant AUTO and
+ * B <= 8 beams, or bf_variant FEW, an LBF_FP16_TC plan runs the bandwidth-bound FP32 few-beam
+ * kernel on the FP32 corner-turned block instead (lbf_plan_dims reports bf_kernel 1); with MANY,
+ * or AUTO and B > 8, it runs the tensor-core kernel (bf_kernel 3).
  * Errors: LBF_EINVAL (bad config), LBF_EUNSUPPORTED (N != 256, L != 16, or an FP16_TC plan with
  * S > 64), LBF_ENOMEM, LBF_ECUDA. */
 lbf_status lbf_plan(const lbf_config *cfg, lbf_plan_t *out);
@@ -289,10 +293,16 @@ lbf_status lbf_debug_stall_next(lbf_plan_t plan, int64_t item);
  * station-samples), S*F*((L-1)N + d_max)*sample-bytes <= 4 MiB, and the weight tables
  * (about 4*F*B*S + 12*B*S bytes) <= 4 MiB; beyond them it returns LBF_ETOOBIG before touching the
  * device.  The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.  Every call shares
- * the array and overwrites the previous call's contents (the zero history is cleared on each
- * call); calls whose device work overlaps in time race on it.  Other errors as lbf_plan/
- * lbf_run_block: LBF_EINVAL, LBF_EUNSUPPORTED, LBF_ECUDA. */
+ * with that device current; make that first call before any stream capture.  The address is kept
+ * for the life of the process, so the entry point must not be called on a device after
+ * cudaDeviceReset of that device.  Every call shares the array and overwrites the previous call's
+ * contents (the zero history is cleared on each call); calls whose device work overlaps in time
+ * race on it.  The host-side staging of the tables is process-wide as well and is serialised by a
+ * lock, so concurrent calls from several host threads are safe on the host side (their device
+ * work still races unless it is ordered, e.g. on one stream).  The caller's buffers must hold
+ * S*F*T*sample-bytes (d_in) and the Stokes or voltage output size (d_out); the C entry point
+ * cannot check raw device pointers for length.  Other errors as lbf_plan/lbf_run_block:
+ * LBF_EINVAL, LBF_EUNSUPPORTED, LBF_ECUDA. */
 lbf_status lbf_run_block_static(const lbf_config *cfg, const void *d_in, void *d_out, void *stream);
 
 /* ---- Batches: several observations processed together (Section 7: independent observations can
@@ -336,6 +346,23 @@ lbf_status lbf_batch_launch(lbf_batch_t batch, void *stream);
  * histories, so every plan's stream is restarted (history zeroed) afterwards.  `out` may be NULL. */
 lbf_status lbf_batch_tune(lbf_batch_t batch, const void *const *d_in, void *const *d_out, void *stream,
                           int32_t reps, lbf_batch_tuning *out);
+
+/* ---- Measurement (roofline denominators, not a step of the paper's path).
+ * The FP32 SIMT throughput of the current device, measured: kernels of independent FMA chains on
+ * every SM (four 256-thread CTAs per SM, 16 chains per thread), each timed with CUDA events on
+ * `stream` over `reps` launches after one warm-up, in two forms -- scalar FFMA and packed FP32x2
+ * (fma.rn.f32x2) -- keeping the fastest launch of each.  The paper rates its beam-former kernel
+ * against the FPU's peak (Section 4.3); this gives the GPU's peak at the clocks it runs at now.
+ * Synchronous (waits for its own launches).  Errors: LBF_EINVAL (reps outside 1..100 or NULL
+ * out), LBF_ECUDA. */
+typedef struct lbf_alu_peak {
+  int32_t sms;              /* streaming multiprocessors of the device */
+  double ffma_ms;           /* fastest launch, scalar FFMA form */
+  double ffma2_ms;          /* fastest launch, packed FP32x2 form */
+  double ffma_tflops;       /* 2 flop per lane FMA over the fastest launch */
+  double ffma2_tflops;
+} lbf_alu_peak;
+lbf_status lbf_measure_fp32_peak(int32_t reps, void *stream, lbf_alu_peak *out);
 
 /* Human-readable name of a status code (static string). */
 const char *lbf_status_string(lbf_status s);

@@ -268,6 +268,13 @@ lbf_status lbf_plan(const lbf_config *cfg, lbf_plan_t *out) {
     p->variant = (p->B <= 8 || p->S > lbf::many_beam_max_stations()) ? 1 : 2;
   else
     p->variant = cfg->bf_variant;
+  // Tensor cores only where the beam count makes the beam former a dense contraction: a
+  // tensor-core plan with few beams (AUTO and B <= 8, or FEW asked for) runs the bandwidth-bound
+  // few-beam kernel on the FP32 corner-turned block instead (Section 4.3: few beams stream the
+  // stations once; many beams reuse each station sample across beams).
+  const bool tc_asked = cfg->precision == LBF_FP16_TC;
+  const bool tc_few = tc_asked && (cfg->bf_variant == LBF_BF_FEW || (cfg->bf_variant == LBF_BF_AUTO && p->B <= 8));
+  if (tc_few) p->variant = 1;
 
   // ---- FP64 geometry on the host (Section 3: delays, integer shifts, beam delay differences)
   const double ts = 1.0 / p->fs;
@@ -319,7 +326,7 @@ lbf_status lbf_plan(const lbf_config *cfg, lbf_plan_t *out) {
     e = cudaMalloc(&p->hist[i], p->hist_bytes ? p->hist_bytes : 16);
     if (e == cudaSuccess) e = cudaMemset(p->hist[i], 0, p->hist_bytes ? p->hist_bytes : 16);
   }
-  p->tc = cfg->precision == LBF_FP16_TC;
+  p->tc = tc_asked && !tc_few;
   p->external_ws = (cfg->flags & LBF_FLAG_EXTERNAL_WORKSPACE) != 0;
   p->inc = (cfg->flags & LBF_FLAG_INCOHERENT_BEAM) ? 1 : 0;
   if (e == cudaSuccess) e = cudaMalloc((void **)&p->ss_members, sizeof(int) * p->S);

@@ -8,9 +8,12 @@
 //
 // The array is shared by every call on a device and keeps the previous call's contents; the parts
 // that must start at zero are cleared on each call.  Calls whose device work overlaps (two streams,
-// two host threads) race on it.
+// two host threads) race on it.  The host side -- the per-device address cache and the host
+// staging area of the tables -- is process-wide too, so a lock serialises it: two host threads may
+// call at once (on the same or different devices) without corrupting each other's tables.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "lbf.h"
 #include "lbf_internal.cuh"
@@ -26,8 +29,11 @@ constexpr double kC = 299792458.0;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
 
-unsigned char *g_scratch_addr[kMaxDevices] = {nullptr};   // device address per device ordinal
-unsigned char g_host_tables[kTableBytes];                   // host staging of the tables
+// Host-side state, guarded by g_lock: the device address of the array per device ordinal (looked
+// up once per device and process), and the staging area the tables are built in before upload.
+std::mutex g_lock;
+unsigned char *g_scratch_addr[kMaxDevices] = {nullptr};
+unsigned char g_host_tables[kTableBytes];
 
 size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
 
@@ -112,6 +118,11 @@ extern "C" lbf_status lbf_run_block_static(const lbf_config *c, const void *d_in
   const int variant = c->bf_variant == LBF_BF_AUTO ? ((B <= 8 || S > lbf::many_beam_max_stations()) ? 1 : 2)
                                                    : c->bf_variant;
   if (!on_device(d_in, word) || !on_device(d_out, c->output == LBF_VOLTAGES ? 8 : 4)) return LBF_EINVAL;
+
+  // From here to the last enqueue the host-side state is in use: one caller at a time.  The lock
+  // is held until cudaMemcpyAsync has returned, by which time the pageable staging area has been
+  // copied out by the runtime and may be rebuilt by the next caller.
+  std::lock_guard<std::mutex> hold(g_lock);
 
   // ---- once per device: the device address of the static array (host code only sees a stand-in)
   int dev = -1;

@@ -29,7 +29,7 @@ EXPORTED = ("lbf_plan", "lbf_plan_destroy", "lbf_plan_dims", "lbf_plan_shifts", 
             "lbf_device_status", "lbf_debug_stall_next", "lbf_run_block_static", "lbf_superstation", "lbf_dedisperse",
             "lbf_batch_create", "lbf_batch_destroy",
             "lbf_batch_run", "lbf_batch_capture", "lbf_batch_launch", "lbf_batch_tune",
-            "lbf_status_string", "lbf_version")
+            "lbf_measure_fp32_peak", "lbf_status_string", "lbf_version")
 
 
 class LbfError(RuntimeError):
@@ -64,6 +64,11 @@ class _Tuning(ctypes.Structure):
     _fields_ = [("n_candidates", ctypes.c_int32), ("spc", ctypes.c_int32 * 6), ("mid_variant", ctypes.c_int32 * 6),
                 ("ms", ctypes.c_double * 6), ("best_spc", ctypes.c_int32), ("best_mid_variant", ctypes.c_int32),
                 ("best_ms", ctypes.c_double)]
+
+
+class _AluPeak(ctypes.Structure):
+    _fields_ = [("sms", ctypes.c_int32), ("ffma_ms", ctypes.c_double), ("ffma2_ms", ctypes.c_double),
+                ("ffma_tflops", ctypes.c_double), ("ffma2_tflops", ctypes.c_double)]
 
 
 class _Dims(ctypes.Structure):
@@ -116,6 +121,7 @@ def load_library() -> ctypes.CDLL:
             "lbf_batch_launch": ([vp, vp], ctypes.c_int),
             "lbf_batch_tune": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, ctypes.c_int32,
                                 ctypes.POINTER(_Tuning)], ctypes.c_int),
+            "lbf_measure_fp32_peak": ([ctypes.c_int32, vp, ctypes.POINTER(_AluPeak)], ctypes.c_int),
             "lbf_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "lbf_version": ([], ctypes.c_char_p),
         }
@@ -422,6 +428,16 @@ class Batch:
             pass
 
 
+def measure_fp32_peak(reps: int = 5, stream=None) -> dict:
+    """Measured FP32 SIMT throughput of the current device (lbf_measure_fp32_peak): scalar FFMA
+    and packed FP32x2 forms, TFLOP/s at 2 flop per lane FMA; synchronous."""
+    r = _AluPeak()
+    _check(load_library().lbf_measure_fp32_peak(int(reps), _stream(stream), ctypes.byref(r)),
+           "lbf_measure_fp32_peak")
+    return {"sms": r.sms, "ffma_tflops": r.ffma_tflops, "ffma2_tflops": r.ffma2_tflops,
+            "ffma_ms": r.ffma_ms, "ffma2_ms": r.ffma2_ms}
+
+
 def plan_status(cfg_kwargs) -> int:
     """Status lbf_plan returns for a configuration (validation only; LBF_OK needs a GPU)."""
     try:
@@ -460,5 +476,14 @@ def run_block_static(station_xyz, subband_hz, beam_dlm, phase_centre, taps, bloc
     cfg.beam_dlm = dlm.ctypes.data_as(dp)
     cfg.fir_taps = h.ctypes.data_as(fp)
     cfg.bandpass = bp.ctypes.data_as(fp) if bp is not None else ctypes.cast(None, fp)
-    _check(lib.lbf_run_block_static(ctypes.byref(cfg), _ptr(d_in), _ptr(d_out), _stream(stream)),
-           "lbf_run_block_static")
+    # the kernels read and write whole blocks: a short buffer must not reach them
+    S, F, B = cfg.n_stations, cfg.n_subbands, cfg.n_beams
+    T, M = int(block_samples), int(block_samples) // 256
+    in_bytes = S * F * T * (8 if sample_bits == 16 else 4)
+    if output == "V":
+        out_bytes = B * F * T * 2 * 8                               # [B][F][N][P][M] cf32
+    else:
+        n_stokes = 1 if output == "I" else 4
+        out_bytes = B * n_stokes * F * 256 * (M // int_factor) * 4  # [B][nS][F][N][M/Q] f32
+    _check(lib.lbf_run_block_static(ctypes.byref(cfg), _ptr(d_in, in_bytes), _ptr(d_out, out_bytes),
+                                    _stream(stream)), "lbf_run_block_static")

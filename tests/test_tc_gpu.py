@@ -46,15 +46,19 @@ def _errors(got, ref):
     return eI, eq
 
 
-@pytest.mark.parametrize("S,bits,out,B,M", [(48, 16, "I", 130, 64), (48, 8, "IQUV", 127, 80),
-                                            (16, 16, "IQUV", 64, 64), (64, 16, "I", 256, 48),
-                                            (8, 8, "I", 5, 64)])
-def test_tc_beamform_stokes_matches_oracle(dev, S, bits, out, B, M):
+@pytest.mark.parametrize("S,bits,out,B,M,variant", [(48, 16, "I", 130, 64, "auto"), (48, 8, "IQUV", 127, 80, "auto"),
+                                                    (16, 16, "IQUV", 64, 64, "auto"), (64, 16, "I", 256, 48, "auto"),
+                                                    (8, 8, "I", 5, 64, "many"), (8, 8, "I", 5, 64, "auto"),
+                                                    (24, 16, "IQUV", 8, 64, "auto"), (24, 16, "I", 9, 64, "auto")])
+def test_tc_beamform_stokes_matches_oracle(dev, S, bits, out, B, M, variant):
+    """A tensor-core plan uses the tensor cores only where the beam count makes the beam former a
+    dense contraction: up to 8 beams (AUTO) it runs the bandwidth-bound few-beam kernel (1); MANY
+    forces the tensor-core kernel (3) even for 5 beams, which leaves the beam block mostly empty."""
     from paper_1105_0661_gb300 import Plan
     Q = 16
     wl = _wl(S=S, B=B, out=out, bits=bits, T=M * N, Q=Q)
-    p = Plan.from_workload(wl, precision="fp16tc")
-    assert p.dims.bf_kernel == 3
+    p = Plan.from_workload(wl, precision="fp16tc", bf_variant=variant)
+    assert p.dims.bf_kernel == (1 if (variant == "auto" and B <= 8) else 3)
     ob = O.observation_from_workload(wl)
     rng = np.random.default_rng(1)
     shp = p.shape("ct")
