@@ -92,10 +92,10 @@ void fill_tables(lbf_batch_t b, int par, const void *const *d_in, void *const *d
     G.ct16.kpad = p->kpad;
     G.bits = p->bits;
     G.spc = b->spc;
-    G.chunks = (p->M + b->spc - 1) / b->spc;
+    G.chunks = lbf::ppf_items_per_stream(p->M, b->spc);
     G.first_item = pi;
     G.first_hist = hi;
-    pi += (long long)p->S * p->F * G.chunks * 2;   // one item per polarisation
+    pi += (long long)p->S * p->F * G.chunks;   // one item: both polarisations of a chunk
     hi += (long long)p->S * p->F * p->H;
   }
   b->ppf_items = pi;
@@ -203,7 +203,7 @@ lbf_status lbf_batch_create(const lbf_plan_t *plans, int32_t n, lbf_batch_t *out
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   b->sms = sms > 0 ? sms : 152;
-  b->ppf_ctas = 2 * b->sms;                   // two 256-thread filter-bank CTAs per SM
+  b->ppf_ctas = lbf::ppf_ctas_per_sm() * b->sms;   // persistent filter-bank CTAs
   cudaError_t e = cudaMallocHost((void **)&b->h_ppf, sizeof(lbf::PpfGroup) * 2 * n);
   if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_bf, sizeof(lbf::BfGroup) * 2 * n);
   if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_ppf, sizeof(lbf::PpfGroup) * 2 * n);

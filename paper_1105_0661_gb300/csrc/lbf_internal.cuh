@@ -27,7 +27,11 @@ struct Geometry {
   const double *dtau = nullptr;         // [B][S] beam delay difference
   const float *phase0 = nullptr;        // [F][B][S] f0_f dtau[b,s] reduced to [-1/2, 1/2] cycle (FP64 -> FP32)
   const float *step = nullptr;          // [B][S] fs/N * dtau[b,s], cycles per channel
+  int *err = nullptr;                   // device error word: a bounded wait that gave up records here
 };
+
+// Codes of the device error word (lbf_device_status): the role whose bounded wait expired.
+enum DeviceErr { DERR_NONE = 0, DERR_TC_LOADS = 1, DERR_TC_MMA = 2, DERR_TC_EPILOGUE = 3, DERR_PPF_INPUT = 4 };
 
 enum OutKind { OUT_VOLTAGES = 0, OUT_STOKES_I = 1, OUT_STOKES_IQUV = 4 };
 
@@ -51,7 +55,7 @@ struct PpfGroup {
   Ct16Out ct16;               // FP16 hi+lo planes (tensor-core plans)
   int tc;                     // 1: write ct16 instead of ct
   int bits;
-  int spc;                    // spectra per filter-bank work item (a multiple of 16)
+  int spc;                    // spectra per filter-bank work item (a multiple of 16; both pols)
   int chunks;                 // ceil(M / spc)
   long long first_item;       // first filter-bank work item of this group
   long long first_hist;       // first history element of this group
@@ -74,6 +78,9 @@ cudaError_t launch_ppf(const Geometry &g, int bits, const void *in, const void *
 cudaError_t launch_ppf_group(const PpfGroup *d_groups, int ngrp, long long total, unsigned long long *counter,
                              int ctas, cudaStream_t st);
 cudaError_t launch_hist_group(const PpfGroup *d_groups, int ngrp, long long total, cudaStream_t st);
+// filter-bank work items (both polarisations of one stream chunk) per (station, subband) stream
+int ppf_items_per_stream(int M, int spc);
+int ppf_ctas_per_sm();
 cudaError_t launch_bf_group(const BfGroup *d_groups, int ngrp, long long total, unsigned long long *counter,
                             int ctas, size_t smem, cudaStream_t st);
 int few_beams_per_item();

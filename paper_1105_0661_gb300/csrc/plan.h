@@ -64,6 +64,7 @@ struct lbf_plan_s {
     g.taps = taps; g.twiddle = twiddle; g.bandpass = bandpass; g.dshift = dshift;
     g.tau = tau; g.resid = resid; g.f0 = f0; g.dtau = dtau; g.phase0 = phase0; g.step = step;
     g.inc = inc;
+    g.err = d_err;
     return g;
   }
 };

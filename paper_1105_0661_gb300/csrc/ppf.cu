@@ -2,22 +2,34 @@
 // 16-tap FIR and 256-point FFT into channels, with an optional fused epilogue that applies the
 // sub-sample delay phase and bandpass (Sections 3, 4.3) and writes a corner-turned layout.
 //
-// One CTA filters one polarisation of up to 128 consecutive spectra of one (station, subband)
-// stream in tiles of 16 spectra, with 256 threads: thread p owns FIR point p.  Two CTAs fit on an
-// SM, so one CTA's FIR (FP32-pipe bound) overlaps the other's FFT (shared-memory latency bound);
-// the two polarisations of a stream chunk are neighbouring CTAs, and the second reads the dual-pol
-// input from L2.
-//  * The tile's input samples arrive through a two-stage cp.async ring in shared memory (whole
-//    dual-pol samples, issued one tile ahead), so global-load latency overlaps the filtering and
-//    the FFTs of the tile before.
-//  * Each thread converts its polarisation exactly to float with the 2^23 magic-number method
-//    (integer ops + one packed add instead of the conversion pipe) and slides a 16-frame window
-//    of complex values through registers, producing v_m[p] for 16 spectra into shared memory.
-// The 16 FFTs of a tile then run as 16x16 decompositions, 16 threads per transform: a 16-point DFT
-// in registers (packed FP32x2 butterflies), a twiddle from a shared table, an in-place transpose
-// through padded shared-memory rows, and a second 16-point DFT.
+// One 512-thread CTA filters both polarisations of up to `spc` consecutive spectra of one
+// (station, subband) stream, in tiles of 16 spectra.  Each half of the CTA (256 threads) owns one
+// polarisation; thread p of a half owns FIR point p.  The halves share the input staging and the
+// per-channel tables and otherwise run on their own named barriers, so one half's FIR (FP32 pipe)
+// overlaps the other half's FFT (shared memory).
+//  * Input: a two-slot ring in shared memory filled by bulk asynchronous copies (cp.async.bulk,
+//    completion counted on an mbarrier).  A tile inside the block is one contiguous run of
+//    dual-polarisation samples: one copy of the 16-byte-aligned run that covers it (the integer
+//    shift d_s only moves the start inside the slot).  The slot of tile t is refilled with tile
+//    t + 2 by whichever half finishes reading it second.  A tile that reaches into the history
+//    (the first one of a stream) is read from global memory directly.
+//  * FIR: each thread converts its polarisation's samples exactly to float (2^23 magic-number
+//    method: integer ops and one packed add), slides a 16-frame window through registers and
+//    sums 16 taps (each held as an (h, h) pair for packed FP32x2 FMAs), writing v_m[p] for the
+//    tile's 16 spectra into the half's FIR buffer.
+//  * FFT-256 as 16 x 16 (n = 16 p1 + p2, k = k1 + 16 k2).  Pass 1: thread (m, p2) takes column p2
+//    of spectrum m, a 16-point DFT over p1 in registers, the twiddle exp(-2 pi i p2 k1 / 256), and
+//    writes row segment k1 of the half's second buffer.  Pass 2: thread (m = p & 15, k1 = p >> 4)
+//    reads 16 contiguous values, a 16-point DFT over p2 gives X[k1 + 16 k2]; sixteen lanes then
+//    hold sixteen consecutive spectra of one channel, so the corner-turned output is written
+//    straight from registers as whole 128-byte runs, with the delay phasor and bandpass applied.
+//  * Two buffers per half (FIR output, pass-1 output) leave two named barriers per tile: FIR ->
+//    pass 1 and pass 1 -> pass 2.
+// Every wait on a copy is bounded: on expiry the CTA records DERR_PPF_INPUT in the device error
+// word, stops, waits (bounded) for its copies in flight and returns.
 #include <cuda_fp16.h>
 
+#include <cstddef>
 #include <type_traits>
 
 #include "fft16.cuh"
@@ -26,24 +38,31 @@
 namespace lbf {
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kTile = 16;                  // spectra per tile: 16 transforms = one FFT round
-// Spectra per CTA: as many as still give at least kMinCtas CTAs (16 waves of two CTAs per SM on
-// 152 SMs), since each CTA's setup (taps, FIR window, delay phasors) is then spread over more
-// tiles: the whole 768-spectrum block of a stream for the LOFAR observation (4.7 % faster than 128
-// spectra per CTA), 16 spectra for an observation of a few streams.
-constexpr long long kMinCtas = 152LL * 2 * 16;
+constexpr int kHalf = 256;                 // threads per polarisation: thread p owns FIR point p
+constexpr int kThreads = kP * kHalf;       // one CTA: both polarisations of a stream chunk
+constexpr int kTile = 16;                  // spectra per tile: 16 transforms
+// Spectra per CTA: as many as still give at least kMinCtas CTAs (16 waves of one CTA per SM on
+// 152 SMs): the whole 768-spectrum block of a stream for the LOFAR observation, 16 spectra for an
+// observation of a few streams.
+constexpr long long kMinCtas = 152LL * 16;
 constexpr int kStages = 2;                 // input ring depth (tiles)
+constexpr int kRowV = 258;                 // float2 per transform row: 256 points + 2 of padding
+constexpr uint32_t kWaitIters = 1u << 20;  // polls before a wait on a copy gives up
 constexpr float kMagic16 = 8421376.0f;     // 2^23 + 2^15
 constexpr float kMagic8 = 8388736.0f;      // 2^23 + 2^7
 
 template <int BITS> struct SampleIO;
 template <> struct SampleIO<16> {   // X.re, X.im, Y.re, Y.im as four little-endian int16
   using word = uint2;
-  // One polarisation (re, im as two int16 in a 32-bit word) to float: the bits
-  // 0x4B00 | (v + 2^15) are the float 2^23 + v + 2^15, so one packed subtract is exact.
-  __device__ static float2 cvt_pol(const word &w, int pol) {
-    const uint32_t a = (pol ? w.y : w.x) ^ 0x80008000u;
+  static constexpr int kAlign = 2;   // samples per 16 bytes
+  // polarisation pol's (re, im) of sample i as one 32-bit word
+  __device__ static uint32_t pair(const word *base, long long i, int pol) {
+    return reinterpret_cast<const uint32_t *>(base)[2 * i + pol];
+  }
+  // (re, im) int16 pair to float: the bits 0x4B00 | (v + 2^15) are the float 2^23 + v + 2^15, so
+  // one packed subtract is exact.
+  __device__ static float2 cvt(uint32_t a, int) {
+    a ^= 0x80008000u;
     return __fadd2_rn(make_float2(__uint_as_float(__byte_perm(a, 0x4B00u, 0x5410u)),
                                   __uint_as_float(__byte_perm(a, 0x4B00u, 0x5432u))),
                       make_float2(-kMagic16, -kMagic16));
@@ -51,8 +70,10 @@ template <> struct SampleIO<16> {   // X.re, X.im, Y.re, Y.im as four little-end
 };
 template <> struct SampleIO<8> {    // X.re, X.im, Y.re, Y.im as four int8
   using word = uint32_t;
-  // One polarisation (two int8) to float: 0x4B0000 | (v + 2^7) is the float 2^23 + v + 2^7.
-  __device__ static float2 cvt_pol(const word &w, int pol) {
+  static constexpr int kAlign = 4;
+  __device__ static uint32_t pair(const word *base, long long i, int) { return base[i]; }
+  // polarisation pol's two int8 to float: 0x4B0000 | (v + 2^7) is the float 2^23 + v + 2^7
+  __device__ static float2 cvt(uint32_t w, int pol) {
     const uint32_t a = (w ^ 0x80808080u) >> (16 * pol);
     return __fadd2_rn(make_float2(__uint_as_float(__byte_perm(a, 0x4B00u, 0x5440u)),
                                   __uint_as_float(__byte_perm(a, 0x4B00u, 0x5441u))),
@@ -60,20 +81,29 @@ template <> struct SampleIO<8> {    // X.re, X.im, Y.re, Y.im as four int8
   }
 };
 
-// A transform's 256 points are kept as 16 rows of 16 with one float2 of padding per row, so that
-// both the row and the column walks of the 16 x 16 decomposition are conflict-free with fixed
-// per-thread offsets (no index arithmetic in the FFT).
-constexpr int kRow = 16 * 17;
+// Ring control, first in the shared memory of either sample width: the persistent batch kernel
+// runs items of both widths through one ring, so the barriers must not move with the layout.
+struct PpfCtl {
+  uint64_t full[kStages];         // copy-complete barriers of the ring slots
+  int slot_done[kStages];         // halves done reading a slot's current tile
+  int issued[kStages];            // copies issued into each slot since the kernel began
+  int abort;                      // a wait gave up: every half stops at its next tile
+};
+
 template <int BITS>
 struct PpfSmem {
   using word = typename SampleIO<BITS>::word;
-  static constexpr int kAlign = 16 / (int)sizeof(word);     // samples per 16 bytes
-  static constexpr int kSlot = kTile * kN + kAlign;         // one tile of frames + alignment slack
-  float2 v[kTile][kRow];                                    // 34 KB: FIR out -> FFT -> staging
-  word in[kStages][kSlot];                                  // input ring (64 KB int16, 32 KB int8)
-  float2 tw[kN];                                            // [k1][j] = exp(-2 pi i j k1 / 256)
-  float2 gain[kN];                                          // bandpass * delay phasor per channel
+  static constexpr int kSlot = kTile * kN + SampleIO<BITS>::kAlign;   // a tile + alignment slack
+  PpfCtl ctl;
+  alignas(16) float4 gain[kN / 2];             // [k1][k2 / 2]: bandpass x delay phasor, pairs of k2
+  alignas(16) float2 tw[kN];                   // [k1][p2] = exp(-2 pi i k1 p2 / 256)
+  alignas(16) float2 w[kP][kTile][kRowV];      // FIR output v_m[p] per polarisation        (66 KB)
+  alignas(16) float2 z[kP][kTile][kRowV];      // pass-1 output: column DFTs x twiddles      (66 KB)
+  alignas(16) word in[kStages][kSlot];         // input ring of dual-pol samples (64 KB int16, 32 KB int8)
 };
+static_assert(offsetof(PpfSmem<16>, ctl) == 0 && offsetof(PpfSmem<8>, ctl) == 0, "ring control first");
+static_assert((PpfSmem<16>::kSlot * sizeof(uint2)) % 16 == 0 && (PpfSmem<8>::kSlot * sizeof(uint32_t)) % 16 == 0,
+              "ring slots 16-byte aligned");
 
 // Output modes: the channelised layout, the FP32 corner-turned layout, or the FP16 layout of the
 // tensor-core beam former ([F*N][M/32][Kpad][P][32] with station s in rows k = 2s (re), 2s+1 (im);
@@ -86,255 +116,317 @@ struct PpfOut {
   int kpad;
 };
 
-__device__ __forceinline__ void cp_async(void *smem_dst, const void *gmem_src, int bytes) {
-  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
-  if (bytes == 8)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gmem_src) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gmem_src) : "memory");
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
-  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// One work item: polarisation pol of spectra [chunk * spc, (chunk + 1) * spc) of stream (s, f),
-// spc a multiple of 16.
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Bounded wait for the phase of the given parity; false on expiry or once another thread aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+  for (uint32_t i = 0; i < kWaitIters; ++i) {
+    if (mbar_test(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (i > 32) __nanosleep(32);
+  }
+  return false;
+}
+
+// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned) from global memory into
+// this CTA's shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// Named barrier of one half (256 threads); returns whether any of them passed `pred`.
+__device__ __forceinline__ bool half_sync_any(uint32_t id, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "barrier.cta.red.or.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(id), "n"(kHalf)
+      : "memory");
+  return r != 0;
+}
+
+__device__ __forceinline__ void half_sync(uint32_t id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(kHalf) : "memory");
+}
+
+// Barriers and counters of the ring, once per kernel (thread 0; the caller synchronises).
+__device__ __forceinline__ void ppf_setup(PpfCtl &c) {
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(&c.full[i], 1);
+      c.slot_done[i] = 0;
+      c.issued[i] = 0;
+    }
+    c.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+}
+
+// After the last item, with every thread of the CTA past a barrier: a CTA that gave up waits
+// (bounded) for the copies it still has in flight before its shared memory is released.
+__device__ __forceinline__ void ppf_drain(PpfCtl &c) {
+  if (threadIdx.x == 0 && c.abort) {
+    for (int i = 0; i < kStages; ++i) {
+      if (c.issued[i] == 0) continue;
+      const uint32_t parity = (uint32_t)(c.issued[i] - 1) & 1u;   // the last copy into slot i
+      for (uint32_t k = 0; k < kWaitIters && !mbar_test(&c.full[i], parity); ++k) __nanosleep(64);
+    }
+  }
+}
+
+// One work item: both polarisations of spectra [chunk * spc, (chunk + 1) * spc) of stream (s, f),
+// spc a multiple of 16.  On entry every thread of the CTA is done with the previous item (if any);
+// `ph` holds this thread's parity bit per ring slot.
 template <int BITS, int MODE>
 __device__ __forceinline__ void ppf_item(const Geometry &g, const typename SampleIO<BITS>::word *__restrict__ in,
                                          const typename SampleIO<BITS>::word *__restrict__ hist, const PpfOut &po,
-                                         int s, int f, int pol, int chunk, int spc, unsigned char *smem_raw) {
+                                         int s, int f, int chunk, int spc, PpfSmem<BITS> &sm, uint32_t &ph) {
   using word = typename SampleIO<BITS>::word;
-  constexpr bool CT = MODE != MODE_CHAN;
-  PpfSmem<BITS> &sm = *reinterpret_cast<PpfSmem<BITS> *>(smem_raw);
-  float2 *__restrict__ out = po.f32;
-
+  using IO = SampleIO<BITS>;
+  constexpr int kAlign = IO::kAlign;
   const int tid = threadIdx.x;
+  const int pol = tid / kHalf;
+  const int p = tid % kHalf;
   const long long sf = (long long)s * g.F + f;
   const int m0 = chunk * spc;
   const int m_end = min(g.M, m0 + spc);
   const int ntiles = (m_end - m0 + kTile - 1) / kTile;
-  constexpr int kAlign = PpfSmem<BITS>::kAlign;
-
-  sm.tw[tid] = g.twiddle[(tid & 15) * (tid >> 4)];
-  if (CT) {
-    // Y = X * bp[c] * exp(+2 pi i (f0 tau_s + df_c (tau_s - n_s Ts))), phase in FP64 cycles
-    const int c = tid;
-    const double df = (double)(c - kN / 2) * (g.fs / kN);
-    const double phi = g.f0[f] * g.tau[s] + df * g.resid[s];
-    const float2 ph = unit_phasor_cycles(phi);
-    const float b = g.bandpass[c];
-    sm.gain[c] = make_float2(b * ph.x, b * ph.y);
-  }
 
   // x'[j] = x[j - d_s]; block-relative x' index j lives at extended index H - d_s + j of
   // [history (H samples) | block (T samples)].  Frames r >= -15, r < M.
-  const int p = tid;               // this thread's FIR point
   const int dsh = g.dshift[s];
-  const long long base = (long long)g.H - dsh + p;
   const word *hs = hist + sf * g.H;
   const word *bs = in + sf * g.T;
-  auto src_of = [&](int r) -> const word * {
-    const long long e = base + (long long)r * kN;
-    return (e < g.H) ? hs + e : bs + (e - g.H);
-  };
-  // Tile t's frames start at block sample e0 = mt N - d_s.  A tile wholly inside the block (e0 >= 0)
-  // is one contiguous run of samples: it is copied as 16-byte pieces of the aligned run that covers
-  // it (never past the stream's end, T being a multiple of N), and its frames start at slot offset
-  // e0 mod kAlign.  A tile that reaches into the history takes one copy per sample.
   const bool in16 = ((reinterpret_cast<uintptr_t>(in) & 15) == 0);
-  auto slot_off = [&](int mt) -> int {
+  auto gpair = [&](int r) -> uint32_t {   // this thread's sample of frame r, from global memory
+    const long long e = (long long)g.H - dsh + (long long)r * kN + p;
+    return (e < g.H) ? IO::pair(hs, e, pol) : IO::pair(bs, e - g.H, pol);
+  };
+  // A tile wholly inside the block (first sample e0 = mt N - d_s >= 0) arrives by bulk copy: the
+  // 16-byte-aligned run covering it, never past the stream's end (T is a multiple of N); its
+  // frames start at slot offset e0 mod kAlign.
+  auto is_bulk = [&](int mt) { return in16 && (long long)mt * kN - dsh >= 0; };
+  auto issue = [&](int t) {   // one thread
+    if (t >= ntiles) return;
+    const int mt = m0 + t * kTile;
+    if (!is_bulk(mt)) return;
+    const int nfr = min(kTile, m_end - mt);
     const long long e0 = (long long)mt * kN - dsh;
-    return (in16 && e0 >= 0) ? (int)(e0 & (kAlign - 1)) : 0;
+    const long long a = e0 & ~(long long)(kAlign - 1);
+    const uint32_t bytes = (uint32_t)((e0 - a + (long long)nfr * kN + kAlign - 1) / kAlign) * 16u;
+    const int st = t % kStages;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // earlier generic reads of the slot
+    mbar_expect_tx(&sm.ctl.full[st], bytes);
+    bulk_g2s(sm.in[st], bs + a, bytes, &sm.ctl.full[st]);
+    sm.ctl.issued[st] += 1;
   };
-  auto issue_tile = [&](int t) {
-    if (t < ntiles) {
-      const int mt = m0 + t * kTile;
-      const int nfr = min(kTile, m_end - mt);
-      word *slot = sm.in[t % kStages];
-      const long long e0 = (long long)mt * kN - dsh;
-      if (in16 && e0 >= 0) {
-        const long long a = e0 & ~(long long)(kAlign - 1);
-        const int nchunks = (int)((e0 - a + (long long)nfr * kN + kAlign - 1) / kAlign);
-        const char *src = reinterpret_cast<const char *>(bs + a);
-        char *dst = reinterpret_cast<char *>(slot);
-        // nchunks is kTile N / kAlign + (0 or 1) for full tiles: whole rounds at fixed offsets
-        const char *s0 = src + 16 * tid;
-        char *d0 = dst + 16 * tid;
-        const int rounds = nchunks / kThreads;
-        if (rounds == kTile * kN / kAlign / kThreads) {
-#pragma unroll
-          for (int r = 0; r < kTile * kN / kAlign / kThreads; ++r) cp_async16(d0 + 16 * kThreads * r, s0 + 16 * kThreads * r);
-        } else {
-          for (int r = 0; r < rounds; ++r) cp_async16(d0 + 16 * kThreads * r, s0 + 16 * kThreads * r);
-        }
-        const int i = rounds * kThreads + tid;
-        if (i < nchunks) cp_async16(dst + 16 * i, src + 16 * i);
-      } else {
-#pragma unroll
-        for (int q = 0; q < kTile; ++q)
-          if (q < nfr) cp_async(slot + q * kN + p, src_of(mt + q), (int)sizeof(word));
-      }
-    }
-    cp_async_commit();
-  };
-  issue_tile(0);
+  if (tid == 0) {
+    issue(0);
+    issue(1);
+  }
+
+  // per-item tables: pass-1 twiddles [k1][p2] and the epilogue gain of channel k1 + 16((k2+8)&15)
+  if (tid < kN) {
+    sm.tw[tid] = g.twiddle[(tid & 15) * (tid >> 4)];
+  } else if (MODE != MODE_CHAN) {
+    // Y = X * bp[c] * exp(+2 pi i (f0 tau_s + df_c (tau_s - n_s Ts))), phase in FP64 cycles
+    const int i = tid - kN, k1 = i >> 4, k2 = i & 15;
+    const int c = k1 + 16 * ((k2 + 8) & 15);
+    const double df = (double)(c - kN / 2) * (g.fs / kN);
+    const double phi = g.f0[f] * g.tau[s] + df * g.resid[s];
+    const float2 ph2 = unit_phasor_cycles(phi);
+    const float b = g.bandpass[c];
+    reinterpret_cast<float2 *>(sm.gain)[i] = make_float2(b * ph2.x, b * ph2.y);
+  }
 
   float2 h2[kL];   // (h, h): one packed FMA updates both components
 #pragma unroll
-  for (int t = 0; t < kL; ++t) { const float hv = g.taps[t * kN + p]; h2[t] = make_float2(hv, hv); }
-
-  float2 win[kL];   // frame r of this pol is kept in slot r & 15 (m0 is a multiple of 16)
+  for (int t = 0; t < kL; ++t) {
+    const float hv = g.taps[t * kN + p];
+    h2[t] = make_float2(hv, hv);
+  }
+  float2 win[kL];   // frame r of this polarisation is kept in slot r & 15 (m0 is a multiple of 16)
 #pragma unroll
-  for (int i = 0; i < kL - 1; ++i) win[i + 1] = SampleIO<BITS>::cvt_pol(*src_of(m0 - (kL - 1) + i), pol);
+  for (int i = 0; i < kL - 1; ++i) win[i + 1] = IO::cvt(gpair(m0 - (kL - 1) + i), pol);
+  __syncthreads();   // tables
 
-  const int j = tid & 15;          // lane within a 16-thread transform group
-  const int gq = tid >> 4;         // the group's spectrum within the tile
-  const int pv = 17 * (p >> 4) + (p & 15);   // point p in a padded row
+  float2(*wb)[kRowV] = sm.w[pol];
+  float2(*zb)[kRowV] = sm.z[pol];
+  const uint32_t bar_fir = 1 + pol, bar_p1 = 1 + kP + pol;   // this half's named barriers
+  // pass-1 thread (m1, c1 = p2); pass-2 thread (m2, k1)
+  const int m1 = p >> 4, c1 = p & 15;
+  const int m2 = p & 15, k1 = p >> 4;
 
   for (int t = 0; t < ntiles; ++t) {
     const int mt = m0 + t * kTile;
-    issue_tile(t + 1);
-    cp_async_wait<1>();            // this thread's copies of tile t have landed
-    __syncthreads();               // ... and everyone's
-    // ---- FIR: v_m[p] = sum_t h[tN + p] x'[(m - 15 + t) N + p], 16 spectra, this pol
-    const word *fr = sm.in[t % kStages] + slot_off(mt) + p;
-    float2 *vout = &sm.v[0][pv];
-    auto fir = [&](auto full) {
-#pragma unroll
-      for (int q = 0; q < kTile; ++q) {
-        if (decltype(full)::value || mt + q < m_end) win[q] = SampleIO<BITS>::cvt_pol(fr[q * kN], pol);
-        else win[q] = make_float2(0.f, 0.f);
-        // two partial sums per component halve the FMA dependency chain
-        float2 acc = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int tap = 0; tap < kL; tap += 2) {
-          acc = __ffma2_rn(h2[tap], win[(q + 1 + tap) & 15], acc);
-          acc1 = __ffma2_rn(h2[tap + 1], win[(q + 2 + tap) & 15], acc1);
-        }
-        vout[q * kRow] = __fadd2_rn(acc, acc1);
-      }
-    };
-    if (mt + kTile <= m_end) fir(std::true_type());
-    else fir(std::false_type());
-    __syncthreads();
+    const int nfr = min(kTile, m_end - mt);
+    const int st = t % kStages;
+    const bool bulk = is_bulk(mt);
+    bool failed = false;
+    if (bulk) {
+      failed = !mbar_wait(&sm.ctl.full[st], (ph >> st) & 1u, &sm.ctl.abort);
+      ph ^= 1u << st;
+      if (failed && atomicExch(&sm.ctl.abort, 1) == 0 && g.err) atomicCAS(g.err, 0, DERR_PPF_INPUT);
+    }
 
-    // ---- FFT-256 of the 16 transforms (spectra) of the tile, 16 threads each:
-    // n = 16 p1 + p2, k = k1 + 16 k2; thread j first owns column p2 = j, then row k1 = j
-    float2 *row = sm.v[gq];
-    float2 a[16];
+    // ---- FIR: v_m[p] = sum_t h[tN + p] x'[(m - 15 + t) N + p], 16 spectra, this polarisation
+    {
+      const long long e0 = (long long)mt * kN - dsh;
+      const word *slot = sm.in[st] + (bulk ? (int)(e0 & (kAlign - 1)) : 0) + p;
+      float2 *vout = &wb[0][p];
+      auto fir = [&](auto full, auto direct) {
 #pragma unroll
-    for (int p1 = 0; p1 < 16; ++p1) a[p1] = row[17 * p1 + j];
-    dft16(a);
+        for (int q = 0; q < kTile; ++q) {
+          if (decltype(full)::value || q < nfr)
+            win[q] = IO::cvt(decltype(direct)::value ? gpair(mt + q) : IO::pair(slot, (long long)q * kN, pol), pol);
+          else
+            win[q] = make_float2(0.f, 0.f);
+          // two partial sums per component halve the FMA dependency chain
+          float2 acc = __fmul2_rn(h2[0], win[(q + 1) & 15]);
+          float2 acc1 = __fmul2_rn(h2[1], win[(q + 2) & 15]);
 #pragma unroll
-    for (int k1 = 0; k1 < 16; ++k1) row[17 * k1 + j] = cmul(a[k1], sm.tw[16 * k1 + j]);
-    __syncwarp();
-#pragma unroll
-    for (int p2 = 0; p2 < 16; ++p2) a[p2] = row[17 * j + p2];
-    dft16(a);   // a[k2] = X[j + 16 k2]
-    const int m = mt + gq;
-    if (MODE == MODE_CT16) {
-      __syncthreads();   // every group has read its row: the buffer becomes staging [c][q]
-      float2 *stage = &sm.v[0][0];
-#pragma unroll
-      for (int k2 = 0; k2 < 16; ++k2) {
-        const int c = j + 16 * ((k2 + 8) & 15);
-        stage[c * kTile + (gq ^ (c & 15))] = cmul(a[k2], sm.gain[c]);
-      }
-      __syncthreads();
-      // [F*N][Mt][Kpad][P][32]: rows k = 2s (re) and 2s+1 (im).  Thread (channel c, h8) packs
-      // 8 consecutive spectra into one 16-byte store per plane and component; spectra at or past
-      // the block's end go out as zeros (the pad columns of the last tile).
-      const int mb = tc_tiles(g.M);
-      const bool full = mt + kTile <= m_end;
-      const int h8 = tid & 1;
-      const int m0 = mt + 8 * h8;
-#pragma unroll
-      for (int pass = 0; pass < kN / (kThreads / 2); ++pass) {
-        const int c = pass * (kThreads / 2) + (tid >> 1);
-        const float2 *srow = stage + c * kTile;
-        uint32_t hr[4], hm[4], lr[4], lm[4];
-#pragma unroll
-        for (int k = 0; k < 8; k += 2) {
-          float2 v0 = srow[(8 * h8 + k) ^ (c & 15)], v1 = srow[(8 * h8 + k + 1) ^ (c & 15)];
-          if (!full) {
-            if (m0 + k >= m_end) v0 = make_float2(0.f, 0.f);
-            if (m0 + k + 1 >= m_end) v1 = make_float2(0.f, 0.f);
+          for (int tap = 2; tap < kL; tap += 2) {
+            acc = __ffma2_rn(h2[tap], win[(q + 1 + tap) & 15], acc);
+            acc1 = __ffma2_rn(h2[tap + 1], win[(q + 2 + tap) & 15], acc1);
           }
-          const __half2 h_re = __floats2half2_rn(v0.x, v1.x), h_im = __floats2half2_rn(v0.y, v1.y);
-          const float2 f_re = __half22float2(h_re), f_im = __half22float2(h_im);
-          const __half2 l_re = __floats2half2_rn(v0.x - f_re.x, v1.x - f_re.y);
-          const __half2 l_im = __floats2half2_rn(v0.y - f_im.x, v1.y - f_im.y);
-          hr[k / 2] = *reinterpret_cast<const uint32_t *>(&h_re);
-          hm[k / 2] = *reinterpret_cast<const uint32_t *>(&h_im);
-          lr[k / 2] = *reinterpret_cast<const uint32_t *>(&l_re);
-          lm[k / 2] = *reinterpret_cast<const uint32_t *>(&l_im);
+          vout[q * kRowV] = __fadd2_rn(acc, acc1);
         }
-        const long long re = ((((long long)f * kN + c) * mb + (m0 >> 5)) * po.kpad + 2 * s) * 64 + pol * 32 + (m0 & 31);
-        *reinterpret_cast<uint4 *>(po.hi + re) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
-        *reinterpret_cast<uint4 *>(po.hi + re + 64) = make_uint4(hm[0], hm[1], hm[2], hm[3]);
-        if (po.lo) {
-          *reinterpret_cast<uint4 *>(po.lo + re) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
-          *reinterpret_cast<uint4 *>(po.lo + re + 64) = make_uint4(lm[0], lm[1], lm[2], lm[3]);
+      };
+      const bool full = nfr == kTile;
+      if (bulk) {
+        if (full) fir(std::true_type(), std::false_type());
+        else fir(std::false_type(), std::false_type());
+      } else {
+        if (full) fir(std::true_type(), std::true_type());
+        else fir(std::false_type(), std::true_type());
+      }
+    }
+    // the FIR buffer is complete; this half is done with the slot
+    if (half_sync_any(bar_fir, failed || *reinterpret_cast<volatile int *>(&sm.ctl.abort))) break;
+    if (p == 0 && atomicAdd(&sm.ctl.slot_done[st], 1) == kP - 1) {   // the second half refills it
+      atomicExch(&sm.ctl.slot_done[st], 0);
+      issue(t + kStages);
+    }
+
+    // ---- FFT pass 1: column p2 = c1 of spectrum m1, 16-point DFT over p1, twiddle W256^(p2 k1)
+    {
+      float2 a[16];
+      const float2 *src = &wb[m1][c1];
+#pragma unroll
+      for (int p1 = 0; p1 < 16; ++p1) a[p1] = src[16 * p1];
+      dft16(a);
+      float2 *dst = &zb[m1][c1];
+      dst[0] = a[0];
+#pragma unroll
+      for (int k = 1; k < 16; ++k) dst[16 * k] = cmul(a[k], sm.tw[16 * k + c1]);
+    }
+    half_sync(bar_p1);
+
+    // ---- FFT pass 2: row segment k1 of spectrum m2, 16-point DFT over p2: a[k2] = X[k1 + 16 k2],
+    // channel c = (k + N/2) mod N = k1 + 16 ((k2 + 8) & 15)
+    {
+      float2 a[16];
+      const float4 *src = reinterpret_cast<const float4 *>(&zb[m2][16 * k1]);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float4 v = src[i];
+        a[2 * i] = make_float2(v.x, v.y);
+        a[2 * i + 1] = make_float2(v.z, v.w);
+      }
+      dft16(a);
+      const int mg = mt + m2;
+      if (MODE == MODE_CHAN) {
+        if (mg < m_end) {
+          float2 *dst = po.f32 + ((((long long)f * g.S + s) * kP + pol) * g.M + mg) * kN + k1;
+#pragma unroll
+          for (int k2 = 0; k2 < 16; ++k2) dst[16 * ((k2 + 8) & 15)] = a[k2];
         }
-      }
-    } else if (!CT) {
-      if (m < m_end) {
-        float2 *dst = out + ((((long long)f * g.S + s) * kP + pol) * g.M + m) * kN;
+      } else {
+        const float4 *gp = &sm.gain[k1 * 8];
 #pragma unroll
-        for (int k2 = 0; k2 < 16; ++k2) dst[j + 16 * ((k2 + 8) & 15)] = a[k2];   // c = (k + N/2) mod N
-      }
-    } else {
-      __syncthreads();   // every group has read its row: the buffer becomes staging [c][q]
-      float2 *stage = &sm.v[0][0];
+        for (int i = 0; i < 8; ++i) {
+          const float4 gg = gp[i];
+          a[2 * i] = cmul(a[2 * i], make_float2(gg.x, gg.y));
+          a[2 * i + 1] = cmul(a[2 * i + 1], make_float2(gg.z, gg.w));
+        }
+        if (MODE == MODE_CT32) {
+          // ct[f][c][s][pol][m]: the 16 lanes of a channel write 16 consecutive spectra (128 B)
+          if (mg < m_end) {
+            float2 *dst = po.f32 + ((((long long)f * kN + k1) * g.S + s) * kP + pol) * g.M + mg;
+            const long long cstep = 16LL * g.S * kP * g.M;
 #pragma unroll
-      for (int k2 = 0; k2 < 16; ++k2) {
-        const int c = j + 16 * ((k2 + 8) & 15);
-        stage[c * kTile + (gq ^ (c & 15))] = cmul(a[k2], sm.gain[c]);
-      }
-      __syncthreads();
-      // ct[f][c][s][pol][m]: runs of 16 consecutive spectra (128 B) per channel.  Eight threads
-      // write a run, two spectra each as one 16-byte store (rows 16-byte aligned when M is even),
-      // so a warp's store covers four whole 128-byte runs.  Pass k writes channels 32 k + tid / 8.
-      const int pr = tid & 7;
-      const int m0 = mt + 2 * pr;
-      const bool vec = (g.M & 1) == 0 && m0 + 1 < m_end;
-      const int c0 = tid >> 3;
-      const float2 *srow = stage + c0 * kTile;
-      const int sw = c0 & 15;   // the swizzle of every channel this thread writes
-      float2 *dst = out + ((((long long)f * kN + c0) * g.S + s) * kP + pol) * g.M + m0;
-      const long long cstep = (long long)(kThreads / 8) * g.S * kP * g.M;
-#pragma unroll
-      for (int pass = 0; pass < kN / (kThreads / 8); ++pass, dst += cstep) {
-        const float2 v0 = srow[pass * (kThreads / 8) * kTile + ((2 * pr) ^ sw)];
-        const float2 v1 = srow[pass * (kThreads / 8) * kTile + ((2 * pr + 1) ^ sw)];
-        if (vec) {
-          *reinterpret_cast<float4 *>(dst) = make_float4(v0.x, v0.y, v1.x, v1.y);
+            for (int k2 = 0; k2 < 16; ++k2) dst[((k2 + 8) & 15) * cstep] = a[k2];
+          }
         } else {
-          if (m0 < m_end) dst[0] = v0;
-          if (m0 + 1 < m_end) dst[1] = v1;
+          // [F*N][Mt][Kpad][P][32] halves, rows k = 2s (re) and 2s+1 (im).  Lanes m and m^1 swap
+          // halves of their value: the even lane then holds Re of spectra (m, m+1), the odd lane
+          // Im of (m-1, m), each written as one half2 per plane.  Spectra at or past the block's
+          // end go out as zeros (pad columns of the last tile).
+          const int odd = m2 & 1;
+          const int me = mg & ~1;
+          const bool v0 = me < m_end, v1 = me + 1 < m_end;
+          const int mb = tc_tiles(g.M);
+          const long long rowbase = (long long)(me >> 5) * po.kpad + 2 * s + odd;
+          const long long cstride = (long long)mb * po.kpad * 64;
+          __half *hi0 = po.hi + (((long long)f * kN + k1) * mb * po.kpad + rowbase) * 64 + pol * 32 + (me & 31);
+          __half *lo0 = po.lo ? po.lo + (hi0 - po.hi) : nullptr;
+#pragma unroll
+          for (int k2 = 0; k2 < 16; ++k2) {
+            const float send = odd ? a[k2].x : a[k2].y;
+            const float recv = __shfl_xor_sync(0xffffffffu, send, 1);
+            float x0 = odd ? recv : a[k2].x;
+            float x1 = odd ? a[k2].y : recv;
+            if (!v0) x0 = 0.f;
+            if (!v1) x1 = 0.f;
+            const __half2 h = __floats2half2_rn(x0, x1);
+            const float2 hf = __half22float2(h);
+            const long long o = (long long)(16 * ((k2 + 8) & 15)) * cstride;
+            *reinterpret_cast<__half2 *>(hi0 + o) = h;
+            if (lo0) *reinterpret_cast<__half2 *>(lo0 + o) = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+          }
         }
       }
     }
-    __syncthreads();
   }
-  cp_async_wait<0>();
 }
 
-// Polarisation fastest in the CTA index: the two CTAs of a stream chunk read the same input run.
 template <int BITS, int MODE>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 1)
 ppf_kernel(Geometry g, const typename SampleIO<BITS>::word *__restrict__ in,
            const typename SampleIO<BITS>::word *__restrict__ hist, PpfOut po, int chunks, int spc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  PpfSmem<BITS> &sm = *reinterpret_cast<PpfSmem<BITS> *>(smem_raw);
   int s, f, chunk;
-  const int pol = (int)(blockIdx.x & 1);
-  const long long item = blockIdx.x >> 1;
-  if (MODE == MODE_CT16) {   // then stations: neighbouring CTAs fill neighbouring K rows of
-    s = (int)(item % g.S);                       // the same (channel) planes
+  const long long item = blockIdx.x;
+  if (MODE == MODE_CT16) {   // stations fastest: neighbouring CTAs fill neighbouring K rows of the
+    s = (int)(item % g.S);   // same (channel) planes
     const long long rest = item / g.S;
     chunk = (int)(rest % chunks);
     f = (int)(rest / chunks);
@@ -344,17 +436,28 @@ ppf_kernel(Geometry g, const typename SampleIO<BITS>::word *__restrict__ in,
     s = (int)(sf / g.F);
     f = (int)(sf - (long long)s * g.F);
   }
-  ppf_item<BITS, MODE>(g, in, hist, po, s, f, pol, chunk, spc, smem_raw);
+  ppf_setup(sm.ctl);
+  uint32_t ph = 0;
+  ppf_item<BITS, MODE>(g, in, hist, po, s, f, chunk, spc, sm, ph);
+  __syncthreads();
+  ppf_drain(sm.ctl);
 }
 
 // Persistent filter bank over the blocks of several observations (a batch): CTAs take work items
-// (stream, spectrum chunk, polarisation) from a shared counter until all groups are done.
-__global__ void __launch_bounds__(kThreads, 2)
+// (stream, spectrum chunk: both polarisations) from a shared counter until all groups are done.
+// The shared memory is laid out for the larger (16-bit) samples.
+__global__ void __launch_bounds__(kThreads, 1)
 ppf_group_kernel(const PpfGroup *__restrict__ grp, int ngrp, long long total, unsigned long long *counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ long long item_s;
+  PpfSmem<16> &sm16 = *reinterpret_cast<PpfSmem<16> *>(smem_raw);
+  PpfSmem<8> &sm8 = *reinterpret_cast<PpfSmem<8> *>(smem_raw);
+  static_assert(sizeof(PpfSmem<8>) <= sizeof(PpfSmem<16>), "the 16-bit layout is the larger");
+  PpfCtl &ctl = sm16.ctl;   // the same object in both layouts
+  ppf_setup(ctl);
+  uint32_t ph = 0;
   for (;;) {
-    if (threadIdx.x == 0) item_s = (long long)atomicAdd(counter, 1ull);
+    if (threadIdx.x == 0) item_s = ctl.abort ? total : (long long)atomicAdd(counter, 1ull);
     __syncthreads();
     const long long item = item_s;
     __syncthreads();
@@ -362,25 +465,26 @@ ppf_group_kernel(const PpfGroup *__restrict__ grp, int ngrp, long long total, un
     int o = 0;
     while (o + 1 < ngrp && grp[o + 1].first_item <= item) ++o;
     const PpfGroup &G = grp[o];
-    const long long local = (item - G.first_item) >> 1;
-    const int pol = (int)((item - G.first_item) & 1);
+    const long long local = item - G.first_item;
     const long long sf = local / G.chunks;
     const int chunk = (int)(local - sf * G.chunks);
     const int s = (int)(sf / G.g.F), f = (int)(sf - (long long)s * G.g.F);
     if (G.tc) {   // tensor-core plan: FP16 hi+lo planes
       PpfOut po{nullptr, reinterpret_cast<__half *>(G.ct16.hi), reinterpret_cast<__half *>(G.ct16.lo), G.ct16.kpad};
       if (G.bits == 16)
-        ppf_item<16, MODE_CT16>(G.g, (const uint2 *)G.in, (const uint2 *)G.hist, po, s, f, pol, chunk, G.spc, smem_raw);
+        ppf_item<16, MODE_CT16>(G.g, (const uint2 *)G.in, (const uint2 *)G.hist, po, s, f, chunk, G.spc, sm16, ph);
       else
-        ppf_item<8, MODE_CT16>(G.g, (const uint32_t *)G.in, (const uint32_t *)G.hist, po, s, f, pol, chunk, G.spc, smem_raw);
+        ppf_item<8, MODE_CT16>(G.g, (const uint32_t *)G.in, (const uint32_t *)G.hist, po, s, f, chunk, G.spc, sm8, ph);
     } else {
       PpfOut po{G.ct, nullptr, nullptr, 0};
       if (G.bits == 16)
-        ppf_item<16, MODE_CT32>(G.g, (const uint2 *)G.in, (const uint2 *)G.hist, po, s, f, pol, chunk, G.spc, smem_raw);
+        ppf_item<16, MODE_CT32>(G.g, (const uint2 *)G.in, (const uint2 *)G.hist, po, s, f, chunk, G.spc, sm16, ph);
       else
-        ppf_item<8, MODE_CT32>(G.g, (const uint32_t *)G.in, (const uint32_t *)G.hist, po, s, f, pol, chunk, G.spc, smem_raw);
+        ppf_item<8, MODE_CT32>(G.g, (const uint32_t *)G.in, (const uint32_t *)G.hist, po, s, f, chunk, G.spc, sm8, ph);
     }
   }
+  __syncthreads();
+  ppf_drain(ctl);
 }
 
 // History update of every observation of a batch: element i of the concatenated histories.
@@ -422,7 +526,7 @@ __global__ void hist_update_kernel(long long total, int H, int T,
 template <int BITS, int MODE>
 cudaError_t launch_ppf_t(const Geometry &g, const void *in, const void *hist, PpfOut po, cudaStream_t st) {
   using word = typename SampleIO<BITS>::word;
-  const long long streams = (long long)g.S * g.F * kP;
+  const long long streams = (long long)g.S * g.F;   // one CTA: both polarisations
   if (streams == 0 || g.M == 0) return cudaSuccess;
   const long long want = (kMinCtas + streams - 1) / streams;      // chunks per stream wanted
   const int spc = (int)((((long long)g.M + want - 1) / want + kTile - 1) / kTile) * kTile;
@@ -457,6 +561,9 @@ cudaError_t launch_ppf_bits(const Geometry &g, const void *in, const void *hist,
 
 }  // namespace
 
+int ppf_items_per_stream(int M, int spc) { return (M + spc - 1) / spc; }
+int ppf_ctas_per_sm() { return 1; }
+
 cudaError_t launch_ppf(const Geometry &g, int bits, const void *in, const void *hist, float2 *chan,
                        float2 *ct, cudaStream_t st, const Ct16Out *ct16) {
   return bits == 16 ? launch_ppf_bits<16>(g, in, hist, chan, ct, ct16, st)
@@ -466,7 +573,7 @@ cudaError_t launch_ppf(const Geometry &g, int bits, const void *in, const void *
 cudaError_t launch_ppf_group(const PpfGroup *d_groups, int ngrp, long long total, unsigned long long *counter,
                              int ctas, cudaStream_t st) {
   if (total == 0) return cudaSuccess;
-  const size_t smem = sizeof(PpfSmem<16>);
+  const size_t smem = sizeof(PpfSmem<16>);   // the larger layout: items of either width
   cudaError_t e = cudaFuncSetAttribute(ppf_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);

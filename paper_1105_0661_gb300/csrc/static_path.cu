@@ -58,12 +58,13 @@ bool on_device(const void *p, size_t align) {
 
 // Offsets of the tables inside the table region (host staging and device copy use the same map).
 struct TableMap {
-  size_t taps, tw, bp, dshift, tau, resid, f0, dtau, phase0, step, total;
+  size_t err, taps, tw, bp, dshift, tau, resid, f0, dtau, phase0, step, total;
 };
 
 TableMap table_map(int S, int F, int B) {
   TableMap m;
   size_t o = 0;
+  m.err = o;    o += align256(sizeof(int));   // device error word of bounded waits (cleared per call)
   m.taps = o;   o += align256(sizeof(float) * lbf::kL * lbf::kN);
   m.tw = o;     o += align256(sizeof(float2) * lbf::kN);
   m.bp = o;     o += align256(sizeof(float) * lbf::kN);
@@ -140,6 +141,7 @@ extern "C" lbf_status lbf_run_block_static(const lbf_config *c, const void *d_in
 
   // ---- host FP64 geometry into the static host staging area
   unsigned char *h = g_host_tables;
+  *reinterpret_cast<int *>(h + tm.err) = 0;
   std::memcpy(h + tm.taps, c->fir_taps, sizeof(float) * lbf::kL * lbf::kN);
   for (int n = 0; n < lbf::kN; ++n) {
     const double a = 2.0 * M_PI * (double)n / (double)lbf::kN;
@@ -179,6 +181,7 @@ extern "C" lbf_status lbf_run_block_static(const lbf_config *c, const void *d_in
   g.dtau = reinterpret_cast<const double *>(tab + tm.dtau);
   g.phase0 = reinterpret_cast<const float *>(tab + tm.phase0);
   g.step = reinterpret_cast<const float *>(tab + tm.step);
+  g.err = reinterpret_cast<int *>(tab + tm.err);
   const int out_kind = c->output == LBF_STOKES_I ? lbf::OUT_STOKES_I
                      : c->output == LBF_STOKES_IQUV ? lbf::OUT_STOKES_IQUV : lbf::OUT_VOLTAGES;
   if (e == cudaSuccess)
