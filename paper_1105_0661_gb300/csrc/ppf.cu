@@ -13,18 +13,20 @@
 //    shift d_s only moves the start inside the slot).  The slot of tile t is refilled with tile
 //    t + 2 by whichever half finishes reading it second.  A tile that reaches into the history
 //    (the first one of a stream) is read from global memory directly.
-//  * FIR: each thread converts its polarisation's samples exactly to float (2^23 magic-number
-//    method: integer ops and one packed add), slides a 16-frame window through registers and
+//  * FIR: each thread converts its polarisation's samples exactly to float (on the conversion
+//    pipe, which the FIR and FFT leave idle), slides a 16-frame window through registers and
 //    sums 16 taps (each held as an (h, h) pair for packed FP32x2 FMAs), writing v_m[p] for the
 //    tile's 16 spectra into the half's FIR buffer.
-//  * FFT-256 as 16 x 16 (n = 16 p1 + p2, k = k1 + 16 k2).  Pass 1: thread (m, p2) takes column p2
-//    of spectrum m, a 16-point DFT over p1 in registers, the twiddle exp(-2 pi i p2 k1 / 256), and
-//    writes row segment k1 of the half's second buffer.  Pass 2: thread (m = p & 15, k1 = p >> 4)
-//    reads 16 contiguous values, a 16-point DFT over p2 gives X[k1 + 16 k2]; sixteen lanes then
-//    hold sixteen consecutive spectra of one channel, so the corner-turned output is written
-//    straight from registers as whole 128-byte runs, with the delay phasor and bandpass applied.
-//  * Two buffers per half (FIR output, pass-1 output) leave two named barriers per tile: FIR ->
-//    pass 1 and pass 1 -> pass 2.
+//  * FFT-256 as 16 x 16 (n = 16 p1 + p2, k = k1 + 16 k2).  Pass 1, in place: thread (m, p2) takes
+//    column p2 of spectrum m, a 16-point DFT over p1 in registers and the twiddle
+//    exp(-2 pi i p2 k1 / 256), and writes the results back over its own 16 points.  Pass 2:
+//    thread (m = p & 15, k1 = p >> 4) reads 16 contiguous values, a 16-point DFT over p2 gives
+//    X[k1 + 16 k2]; sixteen lanes then hold sixteen consecutive spectra of one channel, so the
+//    corner-turned output is written straight from registers as whole 128-byte runs, with the
+//    delay phasor and bandpass applied.
+//  * Software pipeline over two tile buffers per half: the FIR of tile t + 1 runs inside the two
+//    FFT passes of tile t (half of its outputs in each), so FMA-bound and shared-memory-bound work
+//    are interleaved in every warp; two named barriers per tile.
 // Every wait on a copy is bounded: on expiry the CTA records DERR_PPF_INPUT in the device error
 // word, stops, waits (bounded) for its copies in flight and returns.
 #include <cuda_fp16.h>
@@ -48,8 +50,6 @@ constexpr long long kMinCtas = 152LL * 16;
 constexpr int kStages = 2;                 // input ring depth (tiles)
 constexpr int kRowV = 258;                 // float2 per transform row: 256 points + 2 of padding
 constexpr uint32_t kWaitIters = 1u << 20;  // polls before a wait on a copy gives up
-constexpr float kMagic16 = 8421376.0f;     // 2^23 + 2^15
-constexpr float kMagic8 = 8388736.0f;      // 2^23 + 2^7
 
 template <int BITS> struct SampleIO;
 template <> struct SampleIO<16> {   // X.re, X.im, Y.re, Y.im as four little-endian int16
@@ -59,25 +59,20 @@ template <> struct SampleIO<16> {   // X.re, X.im, Y.re, Y.im as four little-end
   __device__ static uint32_t pair(const word *base, long long i, int pol) {
     return reinterpret_cast<const uint32_t *>(base)[2 * i + pol];
   }
-  // (re, im) int16 pair to float: the bits 0x4B00 | (v + 2^15) are the float 2^23 + v + 2^15, so
-  // one packed subtract is exact.
+  // (re, im) int16 pair to float (exact): two conversions on the conversion pipe, leaving the FMA
+  // pipe to the FIR and the FFT
   __device__ static float2 cvt(uint32_t a, int) {
-    a ^= 0x80008000u;
-    return __fadd2_rn(make_float2(__uint_as_float(__byte_perm(a, 0x4B00u, 0x5410u)),
-                                  __uint_as_float(__byte_perm(a, 0x4B00u, 0x5432u))),
-                      make_float2(-kMagic16, -kMagic16));
+    return make_float2((float)(int16_t)(a & 0xffffu), (float)(int16_t)(a >> 16));
   }
 };
 template <> struct SampleIO<8> {    // X.re, X.im, Y.re, Y.im as four int8
   using word = uint32_t;
   static constexpr int kAlign = 4;
   __device__ static uint32_t pair(const word *base, long long i, int) { return base[i]; }
-  // polarisation pol's two int8 to float: 0x4B0000 | (v + 2^7) is the float 2^23 + v + 2^7
+  // polarisation pol's two int8 to float (exact)
   __device__ static float2 cvt(uint32_t w, int pol) {
-    const uint32_t a = (w ^ 0x80808080u) >> (16 * pol);
-    return __fadd2_rn(make_float2(__uint_as_float(__byte_perm(a, 0x4B00u, 0x5440u)),
-                                  __uint_as_float(__byte_perm(a, 0x4B00u, 0x5441u))),
-                      make_float2(-kMagic8, -kMagic8));
+    const uint32_t a = w >> (16 * pol);
+    return make_float2((float)(int8_t)(a & 0xffu), (float)(int8_t)((a >> 8) & 0xffu));
   }
 };
 
@@ -97,8 +92,7 @@ struct PpfSmem {
   PpfCtl ctl;
   alignas(16) float4 gain[kN / 2];             // [k1][k2 / 2]: bandpass x delay phasor, pairs of k2
   alignas(16) float2 tw[kN];                   // [k1][p2] = exp(-2 pi i k1 p2 / 256)
-  alignas(16) float2 w[kP][kTile][kRowV];      // FIR output v_m[p] per polarisation        (66 KB)
-  alignas(16) float2 z[kP][kTile][kRowV];      // pass-1 output: column DFTs x twiddles      (66 KB)
+  alignas(16) float2 w[kP][2][kTile][kRowV];   // per polarisation, two tiles of v_m[p] (132 KB)
   alignas(16) word in[kStages][kSlot];         // input ring of dual-pol samples (64 KB int16, 32 KB int8)
 };
 static_assert(offsetof(PpfSmem<16>, ctl) == 0 && offsetof(PpfSmem<8>, ctl) == 0, "ring control first");
@@ -277,143 +271,198 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
   for (int i = 0; i < kL - 1; ++i) win[i + 1] = IO::cvt(gpair(m0 - (kL - 1) + i), pol);
   __syncthreads();   // tables
 
-  float2(*wb)[kRowV] = sm.w[pol];
-  float2(*zb)[kRowV] = sm.z[pol];
-  const uint32_t bar_fir = 1 + pol, bar_p1 = 1 + kP + pol;   // this half's named barriers
-  // pass-1 thread (m1, c1 = p2); pass-2 thread (m2, k1)
-  const int m1 = p >> 4, c1 = p & 15;
-  const int m2 = p & 15, k1 = p >> 4;
+  // this half's two FIR buffers: tile t lives in wbuf[t & 1] (FIR output, transformed in place by
+  // pass 1, read by pass 2)
+  float2(*wbuf)[kTile][kRowV] = sm.w[pol];
+  const uint32_t bar_x = 1 + pol, bar_y = 1 + kP + pol;   // this half's named barriers
+  const int m1 = p >> 4, c1 = p & 15;   // pass-1 thread: spectrum m1, column p2 = c1
+  const int m2 = p & 15, k1 = p >> 4;   // pass-2 thread: spectrum m2, row segment k1
 
-  for (int t = 0; t < ntiles; ++t) {
-    const int mt = m0 + t * kTile;
-    const int nfr = min(kTile, m_end - mt);
+  // wait for tile t's copy (bulk tiles only); false if this thread's wait gave up
+  auto wait_tile = [&](int t) -> bool {
+    if (!is_bulk(m0 + t * kTile)) return true;
     const int st = t % kStages;
-    const bool bulk = is_bulk(mt);
-    bool failed = false;
-    if (bulk) {
-      failed = !mbar_wait(&sm.ctl.full[st], (ph >> st) & 1u, &sm.ctl.abort);
-      ph ^= 1u << st;
-      if (failed && atomicExch(&sm.ctl.abort, 1) == 0 && g.err) atomicCAS(g.err, 0, DERR_PPF_INPUT);
-    }
-
-    // ---- FIR: v_m[p] = sum_t h[tN + p] x'[(m - 15 + t) N + p], 16 spectra, this polarisation
-    {
-      const long long e0 = (long long)mt * kN - dsh;
-      const word *slot = sm.in[st] + (bulk ? (int)(e0 & (kAlign - 1)) : 0) + p;
-      float2 *vout = &wb[0][p];
-      auto fir = [&](auto full, auto direct) {
-#pragma unroll
-        for (int q = 0; q < kTile; ++q) {
-          if (decltype(full)::value || q < nfr)
-            win[q] = IO::cvt(decltype(direct)::value ? gpair(mt + q) : IO::pair(slot, (long long)q * kN, pol), pol);
-          else
-            win[q] = make_float2(0.f, 0.f);
-          // two partial sums per component halve the FMA dependency chain
-          float2 acc = __fmul2_rn(h2[0], win[(q + 1) & 15]);
-          float2 acc1 = __fmul2_rn(h2[1], win[(q + 2) & 15]);
-#pragma unroll
-          for (int tap = 2; tap < kL; tap += 2) {
-            acc = __ffma2_rn(h2[tap], win[(q + 1 + tap) & 15], acc);
-            acc1 = __ffma2_rn(h2[tap + 1], win[(q + 2 + tap) & 15], acc1);
-          }
-          vout[q * kRowV] = __fadd2_rn(acc, acc1);
-        }
-      };
-      const bool full = nfr == kTile;
-      if (bulk) {
-        if (full) fir(std::true_type(), std::false_type());
-        else fir(std::false_type(), std::false_type());
-      } else {
-        if (full) fir(std::true_type(), std::true_type());
-        else fir(std::false_type(), std::true_type());
-      }
-    }
-    // the FIR buffer is complete; this half is done with the slot
-    if (half_sync_any(bar_fir, failed || *reinterpret_cast<volatile int *>(&sm.ctl.abort))) break;
-    if (p == 0 && atomicAdd(&sm.ctl.slot_done[st], 1) == kP - 1) {   // the second half refills it
+    const bool ok = mbar_wait(&sm.ctl.full[st], (ph >> st) & 1u, &sm.ctl.abort);
+    ph ^= 1u << st;
+    if (!ok && atomicExch(&sm.ctl.abort, 1) == 0 && g.err) atomicCAS(g.err, 0, DERR_PPF_INPUT);
+    return ok;
+  };
+  // this half is done reading tile t's slot: the second half to get here refills it with t + 2
+  auto release_slot = [&](int t) {
+    const int st = t % kStages;
+    if (p == 0 && atomicAdd(&sm.ctl.slot_done[st], 1) == kP - 1) {
       atomicExch(&sm.ctl.slot_done[st], 0);
       issue(t + kStages);
     }
+  };
+  auto aborted = [&]() { return *reinterpret_cast<volatile int *>(&sm.ctl.abort) != 0; };
 
-    // ---- FFT pass 1: column p2 = c1 of spectrum m1, 16-point DFT over p1, twiddle W256^(p2 k1)
-    {
-      float2 a[16];
-      const float2 *src = &wb[m1][c1];
+  // FIR outputs [Q0, Q1) of tile t into wbuf[t & 1]:
+  // v_m[p] = sum_t h[tN + p] x'[(m - 15 + t) N + p], this polarisation
+  auto fir = [&](int t, auto q0c, auto q1c, auto fullc, auto directc) {
+    constexpr int Q0 = decltype(q0c)::value, Q1 = decltype(q1c)::value;
+    constexpr bool kFull = decltype(fullc)::value, kDirect = decltype(directc)::value;
+    const int mt = m0 + t * kTile;
+    const int nfr = min(kTile, m_end - mt);
+    const long long e0 = (long long)mt * kN - dsh;
+    const word *slot = sm.in[t % kStages] + (kDirect ? 0 : (int)(e0 & (kAlign - 1))) + p;
+    float2 *vout = &wbuf[t & 1][0][p];
 #pragma unroll
-      for (int p1 = 0; p1 < 16; ++p1) a[p1] = src[16 * p1];
-      dft16(a);
-      float2 *dst = &zb[m1][c1];
-      dst[0] = a[0];
+    for (int q = Q0; q < Q1; ++q) {
+      if (kFull || q < nfr)
+        win[q] = IO::cvt(kDirect ? gpair(mt + q) : IO::pair(slot, (long long)q * kN, pol), pol);
+      else
+        win[q] = make_float2(0.f, 0.f);
+      // two partial sums per component halve the FMA dependency chain
+      float2 acc = __fmul2_rn(h2[0], win[(q + 1) & 15]);
+      float2 acc1 = __fmul2_rn(h2[1], win[(q + 2) & 15]);
 #pragma unroll
-      for (int k = 1; k < 16; ++k) dst[16 * k] = cmul(a[k], sm.tw[16 * k + c1]);
+      for (int tap = 2; tap < kL; tap += 2) {
+        acc = __ffma2_rn(h2[tap], win[(q + 1 + tap) & 15], acc);
+        acc1 = __ffma2_rn(h2[tap + 1], win[(q + 2 + tap) & 15], acc1);
+      }
+      vout[q * kRowV] = __fadd2_rn(acc, acc1);
     }
-    half_sync(bar_p1);
+  };
+  // call body(full, direct) with the FIR variant of tile t as compile-time flags
+  auto with_variant = [&](int t, auto &&body) {
+    const int mt = m0 + t * kTile;
+    const bool full = m_end - mt >= kTile, bulk = is_bulk(mt);
+    if (bulk && full) body(std::true_type(), std::false_type());
+    else if (bulk) body(std::false_type(), std::false_type());
+    else if (full) body(std::true_type(), std::true_type());
+    else body(std::false_type(), std::true_type());
+  };
 
-    // ---- FFT pass 2: row segment k1 of spectrum m2, 16-point DFT over p2: a[k2] = X[k1 + 16 k2],
-    // channel c = (k + N/2) mod N = k1 + 16 ((k2 + 8) & 15)
-    {
-      float2 a[16];
-      const float4 *src = reinterpret_cast<const float4 *>(&zb[m2][16 * k1]);
+  // ---- FFT pass 1 of tile t, in place: column p2 = c1 of spectrum m1, 16-point DFT over p1,
+  // twiddle W256^(p2 k1); the thread reads and writes only its own 16 points
+  auto pass1 = [&](int t) {
+    float2 *col = &wbuf[t & 1][m1][c1];
+    float2 a[16];
+#pragma unroll
+    for (int p1 = 0; p1 < 16; ++p1) a[p1] = col[16 * p1];
+    dft16(a);
+    col[0] = a[0];
+#pragma unroll
+    for (int k = 1; k < 16; ++k) col[16 * k] = cmul(a[k], sm.tw[16 * k + c1]);
+  };
+
+  // ---- FFT pass 2 of tile t: row segment k1 of spectrum m2, 16-point DFT over p2:
+  // a[k2] = X[k1 + 16 k2], channel c = (k + N/2) mod N = k1 + 16 ((k2 + 8) & 15)
+  auto pass2 = [&](int t) {
+    const int mt = m0 + t * kTile;
+    float2 a[16];
+    const float4 *src = reinterpret_cast<const float4 *>(&wbuf[t & 1][m2][16 * k1]);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float4 v = src[i];
+      a[2 * i] = make_float2(v.x, v.y);
+      a[2 * i + 1] = make_float2(v.z, v.w);
+    }
+    dft16(a);
+    const int mg = mt + m2;
+    if (MODE == MODE_CHAN) {
+      if (mg < m_end) {
+        float2 *dst = po.f32 + ((((long long)f * g.S + s) * kP + pol) * g.M + mg) * kN + k1;
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) dst[16 * ((k2 + 8) & 15)] = a[k2];
+      }
+    } else {
+      const float4 *gp = &sm.gain[k1 * 8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const float4 v = src[i];
-        a[2 * i] = make_float2(v.x, v.y);
-        a[2 * i + 1] = make_float2(v.z, v.w);
+        const float4 gg = gp[i];
+        a[2 * i] = cmul(a[2 * i], make_float2(gg.x, gg.y));
+        a[2 * i + 1] = cmul(a[2 * i + 1], make_float2(gg.z, gg.w));
       }
-      dft16(a);
-      const int mg = mt + m2;
-      if (MODE == MODE_CHAN) {
+      if (MODE == MODE_CT32) {
+        // ct[f][c][s][pol][m]: the 16 lanes of a channel write 16 consecutive spectra (128 B)
         if (mg < m_end) {
-          float2 *dst = po.f32 + ((((long long)f * g.S + s) * kP + pol) * g.M + mg) * kN + k1;
+          float2 *dst = po.f32 + ((((long long)f * kN + k1) * g.S + s) * kP + pol) * g.M + mg;
+          const long long cstep = 16LL * g.S * kP * g.M;
 #pragma unroll
-          for (int k2 = 0; k2 < 16; ++k2) dst[16 * ((k2 + 8) & 15)] = a[k2];
+          for (int k2 = 0; k2 < 16; ++k2) dst[((k2 + 8) & 15) * cstep] = a[k2];
         }
       } else {
-        const float4 *gp = &sm.gain[k1 * 8];
+        // [F*N][Mt][Kpad][P][32] halves, rows k = 2s (re) and 2s+1 (im).  Lanes m and m^1 swap
+        // halves of their value: the even lane then holds Re of spectra (m, m+1), the odd lane
+        // Im of (m-1, m), each written as one half2 per plane.  Spectra at or past the block's
+        // end go out as zeros (pad columns of the last tile).
+        const int odd = m2 & 1;
+        const int me = mg & ~1;
+        const bool v0 = me < m_end, v1 = me + 1 < m_end;
+        const int mb = tc_tiles(g.M);
+        const long long rowbase = (long long)(me >> 5) * po.kpad + 2 * s + odd;
+        const long long cstride = (long long)mb * po.kpad * 64;
+        __half *hi0 = po.hi + (((long long)f * kN + k1) * mb * po.kpad + rowbase) * 64 + pol * 32 + (me & 31);
+        __half *lo0 = po.lo ? po.lo + (hi0 - po.hi) : nullptr;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const float4 gg = gp[i];
-          a[2 * i] = cmul(a[2 * i], make_float2(gg.x, gg.y));
-          a[2 * i + 1] = cmul(a[2 * i + 1], make_float2(gg.z, gg.w));
-        }
-        if (MODE == MODE_CT32) {
-          // ct[f][c][s][pol][m]: the 16 lanes of a channel write 16 consecutive spectra (128 B)
-          if (mg < m_end) {
-            float2 *dst = po.f32 + ((((long long)f * kN + k1) * g.S + s) * kP + pol) * g.M + mg;
-            const long long cstep = 16LL * g.S * kP * g.M;
-#pragma unroll
-            for (int k2 = 0; k2 < 16; ++k2) dst[((k2 + 8) & 15) * cstep] = a[k2];
-          }
-        } else {
-          // [F*N][Mt][Kpad][P][32] halves, rows k = 2s (re) and 2s+1 (im).  Lanes m and m^1 swap
-          // halves of their value: the even lane then holds Re of spectra (m, m+1), the odd lane
-          // Im of (m-1, m), each written as one half2 per plane.  Spectra at or past the block's
-          // end go out as zeros (pad columns of the last tile).
-          const int odd = m2 & 1;
-          const int me = mg & ~1;
-          const bool v0 = me < m_end, v1 = me + 1 < m_end;
-          const int mb = tc_tiles(g.M);
-          const long long rowbase = (long long)(me >> 5) * po.kpad + 2 * s + odd;
-          const long long cstride = (long long)mb * po.kpad * 64;
-          __half *hi0 = po.hi + (((long long)f * kN + k1) * mb * po.kpad + rowbase) * 64 + pol * 32 + (me & 31);
-          __half *lo0 = po.lo ? po.lo + (hi0 - po.hi) : nullptr;
-#pragma unroll
-          for (int k2 = 0; k2 < 16; ++k2) {
-            const float send = odd ? a[k2].x : a[k2].y;
-            const float recv = __shfl_xor_sync(0xffffffffu, send, 1);
-            float x0 = odd ? recv : a[k2].x;
-            float x1 = odd ? a[k2].y : recv;
-            if (!v0) x0 = 0.f;
-            if (!v1) x1 = 0.f;
-            const __half2 h = __floats2half2_rn(x0, x1);
-            const float2 hf = __half22float2(h);
-            const long long o = (long long)(16 * ((k2 + 8) & 15)) * cstride;
-            *reinterpret_cast<__half2 *>(hi0 + o) = h;
-            if (lo0) *reinterpret_cast<__half2 *>(lo0 + o) = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
-          }
+        for (int k2 = 0; k2 < 16; ++k2) {
+          const float send = odd ? a[k2].x : a[k2].y;
+          const float recv = __shfl_xor_sync(0xffffffffu, send, 1);
+          float x0 = odd ? recv : a[k2].x;
+          float x1 = odd ? a[k2].y : recv;
+          if (!v0) x0 = 0.f;
+          if (!v1) x1 = 0.f;
+          const __half2 h = __floats2half2_rn(x0, x1);
+          const float2 hf = __half22float2(h);
+          const long long o = (long long)(16 * ((k2 + 8) & 15)) * cstride;
+          *reinterpret_cast<__half2 *>(hi0 + o) = h;
+          if (lo0) *reinterpret_cast<__half2 *>(lo0 + o) = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
         }
       }
     }
+  };
+
+  using I0 = std::integral_constant<int, 0>;
+  using I8 = std::integral_constant<int, kTile / 2>;
+  using I16 = std::integral_constant<int, kTile>;
+  // Software pipeline: the FIR of tile t + 1 is split over the two FFT phases of tile t, so every
+  // warp has independent FMA work to issue while its shared-memory loads are in flight.
+  //   prologue:  FIR(0)                               | barrier x
+  //   tile t:    pass 1(t) + FIR(t + 1) outputs 0..7  | barrier x (pass 1 done; abort check)
+  //              pass 2(t) + FIR(t + 1) outputs 8..15 | barrier y (wbuf[t & 1] free, FIR done)
+  // The FP16-plane output keeps its pass 2 (shuffles and the hi/lo split) apart from the FIR:
+  // together they outgrow the registers.  Its schedule is sequential over the same two buffers:
+  //   tile t:    FIR(t) | barrier x (slot free) | pass 1(t) | barrier y | pass 2(t)
+  if constexpr (MODE == MODE_CT16) {
+    for (int t = 0; t < ntiles; ++t) {
+      const bool failed = !wait_tile(t);
+      with_variant(t, [&](auto full, auto direct) { fir(t, I0(), I16(), full, direct); });
+      if (half_sync_any(bar_x, failed || aborted())) return;
+      release_slot(t);
+      pass1(t);
+      half_sync(bar_y);
+      pass2(t);
+    }
+    return;
+  }
+  {
+    const bool failed = !wait_tile(0);
+    with_variant(0, [&](auto full, auto direct) { fir(0, I0(), I16(), full, direct); });
+    if (half_sync_any(bar_x, failed || aborted())) return;
+    release_slot(0);
+  }
+  for (int t = 0; t < ntiles; ++t) {
+    const bool next = t + 1 < ntiles;
+    const bool failed = next && !wait_tile(t + 1);
+    if (next)
+      with_variant(t + 1, [&](auto full, auto direct) {
+        pass1(t);
+        fir(t + 1, I0(), I8(), full, direct);
+      });
+    else
+      pass1(t);
+    if (half_sync_any(bar_x, failed || aborted())) return;
+    if (next)
+      with_variant(t + 1, [&](auto full, auto direct) {
+        pass2(t);
+        fir(t + 1, I8(), I16(), full, direct);
+      });
+    else
+      pass2(t);
+    half_sync(bar_y);
+    if (next) release_slot(t + 1);
   }
 }
 
