@@ -482,9 +482,17 @@ def run_ours(args):
         "parity": parity, "precision_compare": compare,
         "paper_context": "Blue Gene/P rack: up to 198 Gb/s = 3.1e9 station-samples/s (64 stations x 248 subbands)",
     }
+    plan.close()
+    del d_in, d_out
+    torch.cuda.empty_cache()
+    # the metric's other two parts on the same GPU, rank 0 at N = 1: the 1024-beam precision form
+    # (FP16 tensor cores vs plain FP32) and the serving loop's p99 block latency
+    if rank == 0 and world == 1 and not args.no_extras:
+        line["precision_form_1024beam"] = precision_form_1024(args, dev, stream, pk, smi_index)
+        line["serving"] = serve_measure(dev, args.serve_obs, args.serve_line_blocks, args.budget_gb,
+                                        args.serve_chunks, smi_index)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    plan.close()
     dist.barrier(dev)
     dist.finalize()
     return 0
@@ -511,111 +519,195 @@ def serving_observations(n: int, seed: int = 5):
     return out
 
 
-def run_serve(args):
+def serve_measure(dev, n_obs: int, n_blocks: int, budget_gb: float, n_chunks: int, smi_index: str = "0") -> dict:
+    """The streaming server on the serving workload: n_obs observations, n_blocks blocks each at
+    the real-time period with late-arrival jitter, each observation served in n_chunks subband
+    chunks.  Returns latencies, sustained throughput, the host link's copy rates, kernel time per
+    period and the clocks seen."""
     import numpy as np
     import torch
 
     from paper_1105_0661_gb300 import Plan
-    from paper_1105_0661_gb300.build_lib import build
-    from paper_1105_0661_gb300.serve import Server, latency_summary, poisson_schedule
+    from paper_1105_0661_gb300.serve import Server, latency_summary, poisson_schedule, subband_ranges
     from synth.device import make_block_device
 
-    build()
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
     period = 196608 / G.SUBBAND_RATE_HZ
-    specs = serving_observations(args.serve_obs)
-    budget = int(args.budget_gb * 1e9)
-    srv = Server(dev, budget)
-    plans = [Plan.from_workload(wl, precision=prec, external_workspace=True) for wl, prec in specs]
-    max_in = max(p.dims.in_bytes for p in plans)
-    max_out = max(p.dims.out_bytes for p in plans)
+    specs = serving_observations(n_obs)
+    srv = Server(dev, int(budget_gb * 1e9))
+    chunk_plans = []
+    for wl, prec in specs:
+        chunk_plans.append([(Plan.from_workload(wl.subset(list(range(f, f + n))), precision=prec,
+                                                external_workspace=True), f)
+                            for f, n in subband_ranges(wl.n_subbands, n_chunks)])
+    in_b = [sum(p.dims.in_bytes for p, _ in cp) for cp in chunk_plans]
+    out_b = [sum(p.dims.out_bytes for p, _ in cp) for cp in chunk_plans]
     # one pinned host input/output area serves every observation (block contents do not change
     # the work; they are synthetic noise of the right shape, copied in each step)
-    h_in = torch.empty(max_in, dtype=torch.uint8, pin_memory=True)
-    h_out = torch.empty(max_out, dtype=torch.uint8, pin_memory=True)
+    h_in = torch.empty(max(in_b), dtype=torch.uint8, pin_memory=True)
+    h_out = torch.empty(max(out_b), dtype=torch.uint8, pin_memory=True)
     big = max(specs, key=lambda x: x[0].station_samples())[0]
     blk = make_block_device(big, 0, dev)
     h_in[:blk.numel() * blk.element_size()].copy_(blk.view(torch.uint8).reshape(-1))
     del blk
     torch.cuda.empty_cache()
+
     # the host-copy rates of this process's pinned buffers (the server's copies are most of its
-    # per-block time), reported beside the latencies
-    copy_gbs = {}
-    nb = min(max_in, 4 << 30)
-    d_probe = torch.empty(nb, dtype=torch.uint8, device=dev)
-    for name, (dst, src) in {"h2d": (d_probe, h_in[:nb]), "d2h": (h_in[:nb], d_probe)}.items():
-        dst.copy_(src, non_blocking=True)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        dst.copy_(src, non_blocking=True)
-        torch.cuda.synchronize()
-        copy_gbs[name] = nb / (time.perf_counter() - t0) / 1e9
-    del d_probe
-    torch.cuda.empty_cache()
-    for oid, p in enumerate(plans):
-        srv.add(oid, p, h_in, h_out)
+    # per-block time), before and after the schedule
+    def copy_rates():
+        r = {}
+        nb = min(max(in_b), 4 << 30)
+        d_probe = torch.empty(nb, dtype=torch.uint8, device=dev)
+        for name, (dst, src) in {"h2d": (d_probe, h_in[:nb]), "d2h": (h_in[:nb], d_probe)}.items():
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            r[name] = nb / (time.perf_counter() - t0) / 1e9
+        del d_probe
+        torch.cuda.empty_cache()
+        return r
+    copy_before = copy_rates()
+    for oid, cp in enumerate(chunk_plans):
+        srv.add(oid, cp, specs[oid][0].n_subbands, h_in, h_out)
     # warm-up: one block per observation, outside the measured schedule
-    srv.run([(0.0, oid, -1) for oid in range(len(plans))])
+    srv.run([(0.0, oid, -1) for oid in range(len(specs))])
     for o in srv.obs.values():
         o.results.clear()
     rng = np.random.default_rng(11)
-    sched = poisson_schedule(len(plans), args.serve_blocks, period, rng)
-    # kernel times of every observation's blocks and the clocks while the schedule runs, so that
-    # a slow run can be told apart from a slow host link
+    sched = poisson_schedule(len(specs), n_blocks, period, rng)
+    # kernel times of every chunk plan and the clocks while the schedule runs, so that a slow run
+    # can be told apart from a slow host link
+    plans = [p for cp in chunk_plans for p, _ in cp]
     for p in plans:
-        p.trace_begin(8 * args.serve_blocks + 8)
-    with ClockSampler("0") as clk:
+        p.trace_begin(8 * n_blocks + 8)
+    with ClockSampler(smi_index) as clk:
         res, wall = srv.run(sched)
-    kernel_ms = {}
+    kernel_ms, launches = {}, 0
     for p in plans:
         for k, v in p.trace_end().items():
             if k.startswith("_") or not v[0]:
                 continue
             kernel_ms[k] = kernel_ms.get(k, 0.0) + v[1]
+            launches += v[0]
+    copy_after = copy_rates()
     summ = latency_summary(res, period)
     ss = sum(specs[r.obs][0].station_samples() for r in res)
-    line = {
-        "metric": "p99 block latency", "value": summ["p99_s"], "unit": "s", "n_gpus": 1,
-        "steps": len(res), "warmup": len(plans), "ms_per_step": 1e3 * summ["p50_s"],
-        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f16",
-        "data": "synthetic",
-        "config": {"workload": f"serving: {len(plans)} observations, 196608-sample int16 blocks at the "
-                               f"real-time period with late-arrival jitter (exponential, mean period/4)",
-                   "observations": [wl.name + f" ({prec})" for wl, prec in specs],
-                   "hbm_budget_gb": args.budget_gb, "period_s": period},
-        "latency": summ, "sustained_station_samples_per_s": ss / wall, "host_copy_gbs": copy_gbs,
-        "kernel_s_per_period": sum(kernel_ms.values()) / 1e3 / (wall / period), "kernels_ms_total": kernel_ms,
-        "clocks": clk.summary(),
+    first = min(r.arrival for r in res)
+    last = max(r.done for r in res)
+    out = {
+        "latency": summ,
+        # served station-samples over the span from the first arrival to the last completion
+        # (with few blocks per observation the span includes the ramp-up of the staggered
+        # observations and the drain of the last blocks, so it reads below the arrival rate)
+        "sustained_station_samples_per_s": ss / (last - first),
+        # fraction of that span with a block waiting or in flight: below 1 with no late block,
+        # the server keeps up with the arrivals and has capacity left
+        "busy_fraction": srv.busy_s / (last - first),
+        "capacity_station_samples_per_s": ss / srv.busy_s if srv.busy_s > 0 else None,
         "realtime_station_samples_per_s": sum(wl.station_samples() for wl, _ in specs) / period,
-        "e2e": {"value": summ["p99_s"], "unit": "s", "h2d_bytes_per_step": int(np.mean([p.dims.in_bytes for p in plans])),
-                "d2h_bytes_per_step": int(np.mean([p.dims.out_bytes for p in plans]))},
-        "gpu_launches": 3 * len(res),
+        "host_copy_gbs": {"before": copy_before, "after": copy_after},
+        "kernel_s_per_period": sum(kernel_ms.values()) / 1e3 / (wall / period), "kernels_ms_total": kernel_ms,
+        "clocks": clk.summary(), "period_s": period, "hbm_budget_gb": budget_gb, "chunks_per_observation": n_chunks,
+        "observations": [wl.name + f" ({'tensor cores' if p.dims.bf_kernel == 3 else 'fp32'})"
+                         for (wl, _), p in zip(specs, [cp[0][0] for cp in chunk_plans])],
+        "mean_h2d_bytes_per_block": int(np.mean(in_b)), "mean_d2h_bytes_per_block": int(np.mean(out_b)),
+        "gpu_launches": launches,
     }
-    print(json.dumps(line), flush=True)
     for p in plans:
         p.close()
+    del srv, h_in, h_out
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_serve(args):
+    import torch
+
+    from paper_1105_0661_gb300.build_lib import build
+
+    build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    r = serve_measure(dev, args.serve_obs, args.serve_blocks, args.budget_gb, args.serve_chunks)
+    summ = r["latency"]
+    line = {
+        "metric": "p99 block latency", "value": summ["p99_s"], "unit": "s", "n_gpus": 1,
+        "steps": summ["blocks"], "warmup": args.serve_obs, "ms_per_step": 1e3 * summ["p50_s"],
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f16",
+        "data": "synthetic",
+        "config": {"workload": f"serving: {args.serve_obs} observations, 196608-sample int16 blocks at the "
+                               f"real-time period with late-arrival jitter (exponential, mean period/4)",
+                   "observations": r["observations"], "hbm_budget_gb": args.budget_gb, "period_s": r["period_s"],
+                   "chunks_per_observation": args.serve_chunks},
+        **{k: v for k, v in r.items() if k not in ("observations",)},
+        "e2e": {"value": summ["p99_s"], "unit": "s", "h2d_bytes_per_step": r["mean_h2d_bytes_per_block"],
+                "d2h_bytes_per_step": r["mean_d2h_bytes_per_block"]},
+    }
+    print(json.dumps(line), flush=True)
     return 0
+
+
+def precision_form_1024(args, dev, stream, pk, smi_index):
+    """The precision form of the observation (1024 beams on a hexagonal grid, full Stokes IQUV
+    integrated over 16): FP16 tensor cores with int8 samples and with int16 samples, and the plain
+    FP32 path on the same int8 block."""
+    import torch
+
+    from paper_1105_0661_gb300 import Plan
+    from synth.device import make_block_device
+
+    res = {}
+    peak_tf = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+    with ClockSampler(smi_index) as clk:
+        for bits in (8, 16):
+            wl = G.workload_lofar_tc(bits, 0)
+            d_in = make_block_device(wl, seed=0, device=dev)
+            ss = wl.station_samples()
+            flop = 8.0 * wl.n_beams * ss * 2               # one complex product per MAC
+            forms = ("fp16tc", "fp32") if bits == 8 else ("fp16tc",)
+            for prec in forms:
+                plan = Plan.from_workload(wl, precision=prec)
+                d_out = torch.empty(plan.shape("stokes"), dtype=torch.float32, device=dev)
+                steps = args.steps if prec == "fp16tc" else 2
+                for _ in range(3):
+                    plan.run_block(d_in, d_out, stream)
+                stream.synchronize()
+                plan.trace_begin(4 * steps + 8)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(steps):
+                    plan.run_block(d_in, d_out, stream)
+                e1.record(stream)
+                stream.synchronize()
+                tr = plan.trace_end()
+                ms = e0.elapsed_time(e1) / steps
+                r = {"ms_per_step": ms, "value": ss / (ms / 1e3), "steps": steps, "warmup": 3,
+                     "kernels_ms": {k: v[1] / v[0] for k, v in tr.items() if not k.startswith("_") and v[0]}}
+                bf = "bf_tc" if prec == "fp16tc" else ("bf_many" if "bf_many" in r["kernels_ms"] else "bf_few")
+                bf_ms = r["kernels_ms"].get(bf)
+                if bf_ms:
+                    r["beamform_tflops"] = flop / (bf_ms / 1e3) / 1e12
+                    if prec == "fp16tc":
+                        r["bf_tc_frac_algorithmic"] = r["beamform_tflops"] / peak_tf
+                        r["bf_tc_frac_executed"] = 3 * r["beamform_tflops"] / peak_tf
+                        r["peak_tflops"] = peak_tf
+                res[f"{prec}_i{bits}"] = r
+                plan.close()
+                del d_out
+                torch.cuda.empty_cache()
+            del d_in
+            torch.cuda.empty_cache()
+    res["fp16tc_speedup_over_fp32_i8"] = res["fp32_i8"]["ms_per_step"] / res["fp16tc_i8"]["ms_per_step"]
+    res["workload"] = "48 st x 244 sb x 196608 samples, 1024 hex beams, Stokes IQUV over 16 spectra"
+    res["clocks"] = clk.summary()
+    return res
 
 
 # ----------------------------------------------------------------------------- batching
 def batch_observations(n: int = 16):
-    """The batched workload: n sub-observations with stations 12-64, subbands 8-244, beams 1-512
-    (log-uniform), int8 or int16, drawn from seeds 1..n, otherwise as the tiny observation (65536
-    samples, Stokes I over 4 spectra, tone at beam 0)."""
-    import numpy as np
-    out = []
-    for i in range(1, n + 1):
-        rng = np.random.default_rng(i)
-        S = int(rng.integers(12, 65))
-        F = int(rng.integers(8, 245))
-        B = int(np.exp(rng.uniform(0.0, np.log(512.0))))
-        bits = 8 if rng.random() < 0.5 else 16
-        xyz = G.lofar_positions(rng, S // 2, S - S // 2)
-        out.append(G.Workload(f"sub{i}-{S}st-{F}sb-{B}beam-i{bits}", xyz, G.subband_centres(F, 110e6),
-                              G.hex_beam_grid(B, 0.05), (0.3, 0.4), 65536, 4, "I", sample_bits=bits,
-                              sigma=8.0 if bits == 8 else 32.0, source="tone"))
-    return out
+    """The batched workload (16 uneven sub-observations, 65536-sample blocks; synth.generate)."""
+    return G.batch_workloads(n, 65536)
 
 
 # ----------------------------------------------------------------------------- pulsar pipeline
@@ -908,7 +1000,12 @@ def main():
     ap.add_argument("--incoherent", action="store_true", help="cost of the incoherent beam on both precision paths")
     ap.add_argument("--dm", type=float, default=13.8, help="dispersion measure, pc cm^-3")
     ap.add_argument("--serve-obs", type=int, default=8)
-    ap.add_argument("--serve-blocks", type=int, default=8)
+    ap.add_argument("--serve-blocks", type=int, default=16)
+    ap.add_argument("--serve-line-blocks", type=int, default=12,
+                    help="blocks per observation of the serving run inside the default bench line")
+    ap.add_argument("--serve-chunks", type=int, default=4, help="subband chunks per served observation")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default line without the 1024-beam precision form and the serving run")
     ap.add_argument("--budget-gb", type=float, default=120.0)
     args = ap.parse_args()
     if args.cpu_subbands <= 0:   # one oracle process per subband, one per host core

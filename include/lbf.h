@@ -245,6 +245,23 @@ lbf_status lbf_run_block_host(lbf_plan_t plan, const void *h_in, void *h_out, vo
 lbf_status lbf_run_blocks_host(lbf_plan_t plan, int32_t n, const void *const *h_in, void *const *h_out,
                                void *d_in0, void *d_in1, void *d_out, void *stream);
 
+/* Transport of a subband range between a whole block in HOST memory and a plan that covers only
+ * that range (a "chunk" plan: the same observation restricted to subbands [first_subband,
+ * first_subband + F) of n_subbands_full).  Subbands are independent given their own history, so a
+ * block processed as chunks gives exactly the beams of the whole block, and a serving loop can
+ * upload chunk k + 1 while chunk k is filtered and beam-formed.  Each call is one asynchronous
+ * strided copy on `stream` (h_in / h_out should be page-locked).
+ * lbf_upload_subbands: h_in [S][n_subbands_full][T][P][2] -> d_in, the chunk's `in` block
+ *   [S][F][T][P][2] (in_bytes of the chunk plan).
+ * lbf_download_subbands: d_out, the chunk's `out` (Stokes [B (+1)][nS][F][N][M/Q]) or `vol`
+ *   ([B][F][N][P][M]) -> the same rows of h_out, laid out for n_subbands_full subbands.
+ * Errors: LBF_EINVAL (range outside the full block, NULL or non-device buffers), LBF_ESTATE,
+ * LBF_ECUDA. */
+lbf_status lbf_upload_subbands(lbf_plan_t chunk, const void *h_in, int32_t n_subbands_full, int32_t first_subband,
+                               void *d_in, void *stream);
+lbf_status lbf_download_subbands(lbf_plan_t chunk, const void *d_out, int32_t n_subbands_full, int32_t first_subband,
+                                 void *h_out, void *stream);
+
 /* Kernel timing trace (CUDA events around every kernel the plan launches).
  * lbf_trace_begin allocates event pairs for up to `max_launches` launches and starts recording;
  * lbf_trace_end synchronises on the recorded events, writes per-kernel totals to `out` and frees

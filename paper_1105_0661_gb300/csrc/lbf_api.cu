@@ -622,6 +622,36 @@ lbf_status lbf_run_blocks_host(lbf_plan_t p, int32_t n, const void *const *h_in,
   return cuda_status(e);
 }
 
+lbf_status lbf_upload_subbands(lbf_plan_t p, const void *h_in, int32_t n_subbands_full, int32_t first_subband,
+                               void *d_in, void *stream) {
+  lbf_status s = check_call(p);
+  if (s != LBF_OK) return s;
+  if (!h_in || n_subbands_full < p->F || first_subband < 0 || first_subband > n_subbands_full - p->F) return LBF_EINVAL;
+  if (p->M == 0) return LBF_OK;
+  if (!device_ptr(d_in, p->word)) return LBF_EINVAL;
+  // rows: stations; a row of the full block holds n_subbands_full streams, the chunk's p->F of them
+  const size_t stream_bytes = (size_t)p->T * p->word;
+  const unsigned char *src = static_cast<const unsigned char *>(h_in) + (size_t)first_subband * stream_bytes;
+  return cuda_status(cudaMemcpy2DAsync(d_in, (size_t)p->F * stream_bytes, src, (size_t)n_subbands_full * stream_bytes,
+                                       (size_t)p->F * stream_bytes, (size_t)p->S, cudaMemcpyHostToDevice,
+                                       (cudaStream_t)stream));
+}
+
+lbf_status lbf_download_subbands(lbf_plan_t p, const void *d_out, int32_t n_subbands_full, int32_t first_subband,
+                                 void *h_out, void *stream) {
+  lbf_status s = check_call(p);
+  if (s != LBF_OK) return s;
+  if (!h_out || n_subbands_full < p->F || first_subband < 0 || first_subband > n_subbands_full - p->F) return LBF_EINVAL;
+  if (p->M == 0) return LBF_OK;
+  if (!device_ptr(d_out, p->nS ? 4 : 8)) return LBF_EINVAL;
+  // rows: (beam, Stokes parameter) of [B (+1)][nS][F][N][M/Q], or beams of [B][F][N][P][M]
+  const size_t rows = p->nS ? (size_t)(p->B + p->inc) * p->nS : (size_t)p->B;
+  const size_t sub_bytes = p->nS ? (size_t)p->N * (p->M / p->Q) * sizeof(float) : (size_t)p->N * lbf::kP * p->M * sizeof(float2);
+  unsigned char *dst = static_cast<unsigned char *>(h_out) + (size_t)first_subband * sub_bytes;
+  return cuda_status(cudaMemcpy2DAsync(dst, (size_t)n_subbands_full * sub_bytes, d_out, (size_t)p->F * sub_bytes,
+                                       (size_t)p->F * sub_bytes, rows, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+}
+
 lbf_status lbf_dedisperse(lbf_plan_t p, double dm, int32_t fft_len, const void *d_vol_in, void *d_vol_out,
                           void *stream) {
   lbf_status s = check_call(p);

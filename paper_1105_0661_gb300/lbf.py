@@ -25,7 +25,7 @@ BF_VARIANTS = {"auto": 0, "few": 1, "many": 2}
 EXPORTED = ("lbf_plan", "lbf_plan_destroy", "lbf_plan_dims", "lbf_plan_shifts", "lbf_reset_state",
             "lbf_ppf", "lbf_delay_correct", "lbf_beamform", "lbf_beamform_stokes", "lbf_stokes",
             "lbf_run_block", "lbf_run_block_ws", "lbf_run_block_host", "lbf_run_blocks_host",
-            "lbf_trace_begin", "lbf_trace_end",
+            "lbf_upload_subbands", "lbf_download_subbands", "lbf_trace_begin", "lbf_trace_end",
             "lbf_device_status", "lbf_debug_stall_next", "lbf_run_block_static", "lbf_superstation", "lbf_dedisperse",
             "lbf_batch_create", "lbf_batch_destroy",
             "lbf_batch_run", "lbf_batch_capture", "lbf_batch_launch", "lbf_batch_tune",
@@ -107,6 +107,8 @@ def load_library() -> ctypes.CDLL:
             "lbf_run_block_host": ([vp, vp, vp, vp, vp, vp], ctypes.c_int),
             "lbf_run_blocks_host": ([vp, ctypes.c_int32, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp, vp, vp],
                                     ctypes.c_int),
+            "lbf_upload_subbands": ([vp, vp, ctypes.c_int32, ctypes.c_int32, vp, vp], ctypes.c_int),
+            "lbf_download_subbands": ([vp, vp, ctypes.c_int32, ctypes.c_int32, vp, vp], ctypes.c_int),
             "lbf_trace_begin": ([vp, ctypes.c_int32], ctypes.c_int),
             "lbf_trace_end": ([vp, ctypes.POINTER(_Trace)], ctypes.c_int),
             "lbf_device_status": ([vp, i32p], ctypes.c_int),
@@ -321,6 +323,23 @@ class Plan:
         d1 = _ptr(d_in1, d.in_bytes) if d_in1 is not None else None
         _check(self._lib.lbf_run_blocks_host(self._h, n, arr_in, arr_out, _ptr(d_in0, d.in_bytes), d1,
                                              _ptr(d_out, d.out_bytes), _stream(stream)), "lbf_run_blocks_host")
+
+    def upload_subbands(self, h_in, n_subbands_full, first_subband, d_in, stream=None):
+        """Asynchronous strided copy of subbands [first, first + F) of a whole host block
+        [S][n_subbands_full][T][P][2] into this (chunk) plan's device input block."""
+        d = self.dims
+        full = d.in_bytes // d.n_subbands * int(n_subbands_full)
+        _check(self._lib.lbf_upload_subbands(self._h, _ptr(h_in, full), int(n_subbands_full), int(first_subband),
+                                             _ptr(d_in, d.in_bytes), _stream(stream)), "lbf_upload_subbands")
+
+    def download_subbands(self, d_out, n_subbands_full, first_subband, h_out, stream=None):
+        """Asynchronous strided copy of this (chunk) plan's output into the rows of a whole host
+        output laid out for n_subbands_full subbands."""
+        d = self.dims
+        full = d.out_bytes // d.n_subbands * int(n_subbands_full)
+        _check(self._lib.lbf_download_subbands(self._h, _ptr(d_out, d.out_bytes), int(n_subbands_full),
+                                               int(first_subband), _ptr(h_out, full), _stream(stream)),
+               "lbf_download_subbands")
 
     def dedisperse(self, dm, fft_len, d_vol_in, d_vol_out, stream=None):
         """Channel-level dedispersion (Section 4.4) of voltages [B][F][N][P][M] (may be in place)."""

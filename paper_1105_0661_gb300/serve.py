@@ -1,20 +1,27 @@
 """Streaming block server: continuous batching of concurrent observations on one GPU.
 
-Several observations (each its own plan: tables and device-resident FIR/shift history) deliver
-blocks over time.  The server admits a block as soon as
+Several observations deliver blocks over time.  Each observation is served by a few chunk plans,
+one per contiguous range of its subbands (subbands are independent given their own FIR/shift
+history, so the chunks together give exactly the beams of one plan over the whole block).  A block
+is admitted as soon as
 
-  * its observation has no block on the GPU (the FIR history makes an observation's blocks
-    sequential), and
-  * the device-memory budget has room for the block's working set (input staging, output, and
-    the corner-turned scratch, drawn from a shared pool so observations share memory),
+  * its observation has fewer than two blocks on the GPU (the FIR history makes an observation's
+    blocks sequential on its compute stream, but block k + 1 may already upload while block k is
+    being processed), and
+  * the device-memory budget has room for the block's input and output buffers (drawn from a
+    shared pool, so observations share memory); among the admissible blocks the one that arrived
+    first goes first.
 
-and then enqueues, on the observation's own CUDA stream, the host-to-device copy of the block, the
-fused path (lbf_run_block_ws) and the device-to-host copy of the beams.  Blocks of different
-observations therefore overlap on the device while others wait for memory; completions free their
-slot and the next waiting block is admitted.  Latency is measured per block from its arrival to the
-host seeing its completion event, and reported as p50/p99 against the real-time block period.
+An admitted block is pipelined over three streams of its observation: chunk c is uploaded (one
+strided copy out of the whole host block, lbf_upload_subbands), filtered and beam-formed
+(lbf_run_block_ws) and downloaded (lbf_download_subbands) while chunk c + 1 is uploading, so a
+block's latency is about one upload plus the last chunk's kernels and download, not the sum of
+the whole block's upload, kernels and download.  Blocks of different observations overlap on the
+device.  Latency is measured per block from its arrival to the host seeing its last download
+complete, and reported as p50/p99 against the real-time block period.
 
-All computation runs in the CUDA library; this module schedules and accounts memory.
+All computation runs in the CUDA library; this module schedules, accounts memory and orders the
+copies.
 """
 
 from __future__ import annotations
@@ -24,6 +31,8 @@ import time
 from dataclasses import dataclass, field
 
 import numpy as np
+
+MAX_INFLIGHT_PER_OBS = 2
 
 
 @dataclass
@@ -40,16 +49,30 @@ class BlockResult:
 
 
 @dataclass
+class _Chunk:
+    plan: object
+    first: int               # first subband of the chunk in the observation
+
+
+@dataclass
 class _Obs:
     oid: int
-    plan: object
-    stream: object
-    host_in: object          # pinned host tensor holding this observation's block bytes
-    host_out: object         # pinned host tensor receiving its beams
-    queue: list = field(default_factory=list)   # (arrival, index) waiting, in order
-    busy: bool = False
+    chunks: list
+    n_subbands: int
+    s_h2d: object            # upload stream
+    s_comp: object           # kernel stream (the chunks' histories advance in order here)
+    s_d2h: object            # download stream
+    ws: object               # device workspace shared by the chunks (they run one after another)
+    host_in: object          # default pinned host input / output of a block (whole observation)
+    host_out: object
+    queue: list = field(default_factory=list)   # (arrival, index, host_in, host_out) waiting, in order
+    inflight: int = 0
     results: list = field(default_factory=list)
     outputs: list = field(default_factory=list)
+
+    @property
+    def busy(self) -> bool:
+        return self.inflight > 0
 
 
 class Pool:
@@ -64,7 +87,7 @@ class Pool:
         self.device = device
         self.budget = int(budget_bytes)
         self.held = 0          # bytes of buffers currently handed out (in-flight blocks)
-        self.reserved = 0      # bytes owned permanently (plans)
+        self.reserved = 0      # bytes owned permanently (plans and workspaces)
         self.free = {}         # nbytes -> [tensor]
 
     def fits(self, nbytes: int) -> bool:
@@ -81,6 +104,13 @@ class Pool:
         self.free.setdefault(nbytes, []).append(t)
 
 
+def subband_ranges(n_subbands: int, n_chunks: int):
+    """n_chunks contiguous, nearly equal subband ranges (first, count) covering n_subbands."""
+    k = max(1, min(int(n_chunks), int(n_subbands)))
+    edges = [round(i * n_subbands / k) for i in range(k + 1)]
+    return [(edges[i], edges[i + 1] - edges[i]) for i in range(k)]
+
+
 class Server:
     """Continuous-batching server of observation blocks on one GPU."""
 
@@ -90,78 +120,117 @@ class Server:
         self.device = device
         self.pool = Pool(device, budget_bytes)
         self.obs: dict[int, _Obs] = {}
-        self.inflight = []          # (event, obs, index, arrival, admitted, buffers)
+        self.inflight = []          # (done event, obs, index, arrival, admitted, buffers, host_out)
         self.keep_outputs = keep_outputs
 
     # -- observations
-    def add(self, oid: int, plan, host_in, host_out):
-        d = plan.dims
-        plan_bytes = plan.device_bytes()
-        if self.pool.reserved + plan_bytes > self.pool.budget:
-            raise MemoryError(f"observation {oid}: plan needs {plan_bytes} B beyond the budget")
-        self.pool.reserved += plan_bytes
-        need = d.in_bytes + d.out_bytes + d.workspace_bytes
-        if self.pool.reserved + need > self.pool.budget:
-            raise MemoryError(f"observation {oid}: one block needs {need} B beyond the budget")
-        self.obs[oid] = _Obs(oid, plan, self.torch.cuda.Stream(device=self.device), host_in, host_out)
+    def add(self, oid: int, chunk_plans, n_subbands: int, host_in, host_out):
+        """Observation `oid` served by `chunk_plans`: a list of (plan, first_subband) covering its
+        n_subbands subbands in order (one plan is the whole observation as a single chunk).  Plans
+        are created with an external workspace; host_in / host_out are the default pinned host
+        buffers of a whole block."""
+        chunks = [_Chunk(p, int(f)) for p, f in chunk_plans]
+        assert sum(c.plan.dims.n_subbands for c in chunks) == n_subbands
+        plan_bytes = sum(c.plan.device_bytes() for c in chunks)
+        ws_bytes = max(c.plan.dims.workspace_bytes for c in chunks)
+        if self.pool.reserved + plan_bytes + ws_bytes > self.pool.budget:
+            raise MemoryError(f"observation {oid}: plans need {plan_bytes + ws_bytes} B beyond the budget")
+        self.pool.reserved += plan_bytes + ws_bytes
+        ws = self.torch.empty(max(ws_bytes, 256), dtype=self.torch.uint8, device=self.device)
+        o = _Obs(oid, chunks, int(n_subbands), *(self.torch.cuda.Stream(device=self.device) for _ in range(3)),
+                 ws, host_in, host_out)
+        self.obs[oid] = o
+        if self.pool.reserved + self.block_bytes(oid) > self.pool.budget:
+            raise MemoryError(f"observation {oid}: one block needs {self.block_bytes(oid)} B beyond the budget")
 
     def block_bytes(self, oid: int) -> int:
-        d = self.obs[oid].plan.dims
-        return d.in_bytes + d.out_bytes + d.workspace_bytes
+        """Pool bytes one block of observation oid holds while in flight (inputs and outputs)."""
+        return sum(c.plan.dims.in_bytes + c.plan.dims.out_bytes for c in self.obs[oid].chunks)
 
     # -- arrivals and scheduling
-    def arrive(self, oid: int, index: int, t: float):
-        self.obs[oid].queue.append((t, index))
+    def arrive(self, oid: int, index: int, t: float, host_in=None, host_out=None):
+        """Block `index` of observation oid arrived at time t (host buffers default to the
+        observation's own)."""
+        self.obs[oid].queue.append((t, index, host_in, host_out))
+
+    def _enqueue(self, o: _Obs, host_in, host_out):
+        torch = self.torch
+        bufs = []
+        for c in o.chunks:
+            d = c.plan.dims
+            d_in, d_out = self.pool.take(d.in_bytes), self.pool.take(d.out_bytes)
+            bufs += [(d_in, d.in_bytes), (d_out, d.out_bytes)]
+            c.plan.upload_subbands(host_in, o.n_subbands, c.first, d_in, o.s_h2d)
+            ev_in = torch.cuda.Event()
+            ev_in.record(o.s_h2d)
+            o.s_comp.wait_event(ev_in)
+            c.plan.run_block_ws(d_in, d_out, o.ws, o.s_comp)
+            ev_k = torch.cuda.Event()
+            ev_k.record(o.s_comp)
+            o.s_d2h.wait_event(ev_k)
+            c.plan.download_subbands(d_out, o.n_subbands, c.first, host_out, o.s_d2h)
+        done = torch.cuda.Event()
+        done.record(o.s_d2h)
+        return done, bufs
 
     def _admit(self, now: float):
-        # oldest waiting block first, across observations
-        cands = sorted((o.queue[0][0], o.oid) for o in self.obs.values() if o.queue and not o.busy)
+        # earliest arrival first, across observations
+        cands = sorted((o.queue[0][0], o.oid) for o in self.obs.values()
+                       if o.queue and o.inflight < MAX_INFLIGHT_PER_OBS)
         for _, oid in cands:
             o = self.obs[oid]
-            d = o.plan.dims
-            if not self.pool.fits(d.in_bytes + d.out_bytes + d.workspace_bytes):
+            if not self.pool.fits(self.block_bytes(oid)):
                 continue
-            arrival, index = o.queue.pop(0)
-            bufs = [(self.pool.take(n), n) for n in (d.in_bytes, d.out_bytes, d.workspace_bytes)]
-            d_in, d_out, d_ws = (b[0] for b in bufs)
-            with self.torch.cuda.stream(o.stream):
-                d_in[:d.in_bytes].copy_(o.host_in.view(self.torch.uint8)[:d.in_bytes], non_blocking=True)
-                o.plan.run_block_ws(d_in, d_out, d_ws, o.stream)
-                o.host_out.view(self.torch.uint8)[:d.out_bytes].copy_(d_out[:d.out_bytes], non_blocking=True)
-                ev = self.torch.cuda.Event()
-                ev.record(o.stream)
-            o.busy = True
-            self.inflight.append((ev, o, index, arrival, now, bufs))
+            arrival, index, h_in, h_out = o.queue.pop(0)
+            h_in = o.host_in if h_in is None else h_in
+            h_out = o.host_out if h_out is None else h_out
+            ev, bufs = self._enqueue(o, h_in, h_out)
+            o.inflight += 1
+            self.inflight.append((ev, o, index, arrival, now, bufs, h_out))
 
     def _reap(self, now: float):
         still = []
         for item in self.inflight:
-            ev, o, index, arrival, admitted, bufs = item
+            ev, o, index, arrival, admitted, bufs, h_out = item
             if ev.query():
                 done = time.perf_counter()
                 o.results.append(BlockResult(o.oid, index, arrival, admitted, done))
                 if self.keep_outputs:
-                    o.outputs.append(o.host_out.clone())
+                    o.outputs.append(h_out.clone())
                 for t, n in bufs:
                     self.pool.give(t, n)
-                o.busy = False
+                o.inflight -= 1
             else:
                 still.append(item)
         self.inflight = still
 
+    def idle(self) -> bool:
+        return not self.inflight and not any(o.queue for o in self.obs.values())
+
+    def step(self):
+        now = time.perf_counter()
+        self._reap(now)
+        self._admit(now)
+
     def run(self, schedule, poll_s: float = 2e-4):
-        """Serve a schedule of (arrival_offset_s, oid, index) in real time; returns the results."""
+        """Serve a schedule of (arrival_offset_s, oid, index) in real time; returns the results and
+        the wall time.  `busy_s` afterwards holds the time during which at least one block was
+        waiting or in flight (the GPU and its copy engines had work)."""
         events = list(schedule)
         heapq.heapify(events)
         t0 = time.perf_counter()
-        while events or self.inflight or any(o.queue for o in self.obs.values()):
+        self.busy_s = 0.0
+        last = t0
+        while events or not self.idle():
             now = time.perf_counter()
+            if not self.idle():
+                self.busy_s += now - last
+            last = now
             while events and t0 + events[0][0] <= now:
                 off, oid, index = heapq.heappop(events)
                 self.arrive(oid, index, t0 + off)
-            self._reap(now)
-            self._admit(now)
-            if not self.inflight and events and not any(o.queue for o in self.obs.values()):
+            self.step()
+            if self.idle() and events:
                 time.sleep(max(0.0, min(poll_s * 10, t0 + events[0][0] - time.perf_counter())))
             else:
                 time.sleep(poll_s)

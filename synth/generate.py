@@ -191,6 +191,24 @@ def workload_lofar_tc(sample_bits: int = 8, seed: int = 0) -> Workload:
 
 
 # ----------------------------------------------------------------------------- station signals
+def batch_workloads(n: int = 16, block_samples: int = 65536) -> list:
+    """The batched workload: n sub-observations with stations 12-64, subbands 8-244, beams 1-512
+    (log-uniform), int8 or int16 samples, drawn from numpy.random.default_rng(i) for i = 1..n,
+    otherwise as the tiny observation (Stokes I over 4 spectra, tone at beam 0)."""
+    out = []
+    for i in range(1, n + 1):
+        rng = np.random.default_rng(i)
+        S = int(rng.integers(12, 65))
+        F = int(rng.integers(8, 245))
+        B = int(np.exp(rng.uniform(0.0, np.log(512.0))))
+        bits = 8 if rng.random() < 0.5 else 16
+        xyz = lofar_positions(rng, S // 2, S - S // 2)
+        out.append(Workload(f"sub{i}-{S}st-{F}sb-{B}beam-i{bits}", xyz, subband_centres(F, 110e6),
+                            hex_beam_grid(B, 0.05), (0.3, 0.4), block_samples, 4, "I", sample_bits=bits,
+                            sigma=8.0 if bits == 8 else 32.0, source="tone"))
+    return out
+
+
 def _arrival_offset(xyz: np.ndarray, l: float, m: float) -> np.ndarray:
     """Arrival-time offset (s) of a plane wave from direction (l, m) at each station (sky model)."""
     n = np.sqrt(max(0.0, 1.0 - l * l - m * m))
