@@ -898,16 +898,18 @@ def run_incoherent(args):
 def batch_launches(wls, prec, tuning):
     """Kernel launches in one batch graph: the grouped filter bank and history update, one grouped
     FP32 beam former per shared-memory class in use (many-beam CTAs with more than 56 stations
-    need one SM each), and one tensor-core launch per tensor-core plan."""
+    need one SM each), and one grouped tensor-core launch per class of output kind and
+    integration length (all the batched observations are Stokes I over 4 spectra: one)."""
     classes = set()
     for wl, pr in zip(wls, prec):
-        if pr != "fp32":
+        if pr != "fp32" and wl.n_beams > 8:
             continue
         many = wl.n_beams > 8 and wl.n_stations <= 113
         if 8 < wl.n_beams <= 64 and wl.n_stations <= 113 and tuning.get("best_mid_variant"):
             many = not many
         classes.add(1 if many and wl.n_stations * 2048 > 113 * 1024 else 0)
-    return 2 + len(classes) + sum(1 for pr in prec if pr != "fp32")
+    tc = any(pr != "fp32" and wl.n_beams > 8 for wl, pr in zip(wls, prec))
+    return 2 + len(classes) + (1 if tc else 0)
 
 
 def run_batch(args):

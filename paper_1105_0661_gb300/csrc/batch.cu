@@ -6,8 +6,9 @@
 // not leave the GPU idle and large ones do not serialise the batch.
 //
 // Tensor-core plans join the grouped filter bank (writing their FP16 planes) and the grouped
-// history update; each then adds its own persistent tensor-core beam-former launch (one CTA per
-// SM already) after the grouped FP32 beam former.
+// history update; then one persistent tensor-core launch per class of output kind and integration
+// length serves all of the class's plans (their work items numbered one after the other), after
+// the grouped FP32 beam former.
 //
 // A batch can be captured as CUDA graphs (one per history parity: each block flips every plan's
 // history ping-pong) and replayed with a single graph launch per block, and its tile shapes --
@@ -15,6 +16,7 @@
 // beam former -- can be tuned by timing the candidates on the batch itself.
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "lbf.h"
@@ -146,6 +148,10 @@ cudaError_t enqueue(lbf_batch_t b, int par, cudaStream_t st) {
   if (e == cudaSuccess && b->bf_n[1])
     e = lbf::launch_bf_group(b->d_bf + par * n + b->bf_n[0], b->bf_n[1], b->bf_items[1], b->d_counter + 2, b->sms,
                              b->bf_smem[1], st);
+  // tensor-core plans: their incoherent beams, then ONE persistent tcgen05 launch per class of
+  // output kind and integration length (up to tc_max_plans_per_launch() plans each), whose CTAs
+  // walk the work items of all the class's plans
+  std::vector<std::pair<long long, lbf::TcPlanRef>> refs;
   for (int i = 0; i < n && e == cudaSuccess; ++i) {
     lbf_plan_t p = b->plans[i];
     if (!p->tc || p->M == 0) continue;
@@ -157,8 +163,20 @@ cudaError_t enqueue(lbf_batch_t b, int par, cudaStream_t st) {
       o.kpad = p->kpad;
       e = lbf::launch_incoherent_ct16(g, p->out_kind, o, static_cast<float *>(b->tc_out[i]), st);
     }
-    if (e == cudaSuccess)
-      e = lbf::launch_bf_tc(g, p->out_kind, &p->tmap[0], &p->tmap[1], static_cast<float *>(b->tc_out[i]), p->d_err, st);
+    const long long cls = (long long)p->out_kind * 64 + (p->out_kind == lbf::OUT_VOLTAGES ? 1 : p->Q);
+    refs.push_back({cls, lbf::TcPlanRef{g, &p->tmap[0], &p->tmap[1], static_cast<float *>(b->tc_out[i]), p->d_err}});
+  }
+  std::vector<bool> done(refs.size(), false);
+  const int cap = lbf::tc_max_plans_per_launch();
+  for (size_t i = 0; i < refs.size() && e == cudaSuccess; ++i) {
+    if (done[i]) continue;
+    std::vector<lbf::TcPlanRef> cls;
+    for (size_t j = i; j < refs.size() && (int)cls.size() < cap; ++j)
+      if (!done[j] && refs[j].first == refs[i].first) { cls.push_back(refs[j].second); done[j] = true; }
+    const int out_kind = (int)(refs[i].first / 64);
+    const int q = (int)(refs[i].first % 64);
+    // (a class of more than `cap` plans continues at its first plan not yet launched)
+    e = lbf::launch_bf_tc_group(cls.data(), (int)cls.size(), out_kind, q, st);
   }
   return e;
 }

@@ -60,16 +60,36 @@ constexpr uint32_t kWaitIters = 1u << 20;
 
 enum ErrCode { ERR_NONE = 0, ERR_PRODUCER = 1, ERR_MMA = 2, ERR_EPILOGUE = 3 };
 
+// One plan of a launch.
 struct TcParams {
   int S, F, B, M, Kpad, ntiles, items_per_fc;
   int items;                  // F * 256 * items_per_fc (< 2^31 for any plan that fits in memory)
-  int nstages, stage_bytes;   // B ring: stages of 2 planes x 2 tiles x Kpad K rows x 128 bytes
+  int first_item;             // the plan's first work item in the launch
+  int stage_bytes;            // its ring stage: 2 planes x 2 tiles x Kpad K rows x 128 bytes
   int vec;                    // output rows 16-byte aligned (M/Q % 4 == 0, aligned base)
-  long long stall_item;       // failure-detection test: the loads stop at this item (-1: never)
   const float *phase0, *step;
   float *out;
-  int *err;
+  int *err;                   // the plan's device error word
 };
+
+// A launch: up to kMaxPlans plans of the same output kind and integration length, whose work
+// items are numbered one after the other, so that one persistent grid walks all of them (a batch
+// of uneven observations shares the SMs).  The TMA descriptors of plan i are map[2i] (hi plane)
+// and map[2i + 1] (lo plane); the whole table is a grid-constant kernel parameter.
+constexpr int kMaxPlans = 32;
+struct TcLaunch {
+  CUtensorMap map[2 * kMaxPlans];
+  TcParams plan[kMaxPlans];
+  int nplans, items;          // plans, and work items of all plans
+  int nstages, stage_max;     // ring stages, sized for the plan with the largest stage
+  long long stall_item;       // failure-detection test: the loads stop at this item (-1: never)
+};
+
+__device__ __forceinline__ int plan_of(const TcLaunch &L, int item) {
+  int i = 0;
+  while (i + 1 < L.nplans && L.plan[i + 1].first_item <= item) ++i;
+  return i;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -429,9 +449,11 @@ __device__ __forceinline__ void flush_stage(const TcParams &p, const float *buf,
   }
 }
 
-template <int NS, int Q>
+// kMulti: the launch table holds several plans (a batch); otherwise plan 0 is the only one and
+// its parameters are compile-time offsets into the table.
+template <int NS, int Q, bool kMulti>
 __global__ void __launch_bounds__(kThreads, 1)
-bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo, TcParams p) {
+bf_tc_kernel(const __grid_constant__ TcLaunch L) {
   using St = Stage<NS, Q>;
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -448,8 +470,8 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
   const uint32_t drain_bar = bar0 + 208u;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sbase + 224);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(sbase + 228);
-  const int nst = p.nstages;
-  float *const stage_out = reinterpret_cast<float *>(sbase + kBarBytes + (size_t)nst * p.stage_bytes);
+  const int nst = L.nstages;
+  float *const stage_out = reinterpret_cast<float *>(sbase + kBarBytes + (size_t)nst * L.stage_max);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -478,24 +500,26 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t plane_bytes = (uint32_t)(2 * p.Kpad * 128);   // two tiles of one plane
 
   if (warp == 0) {
     // ---------------------------------------------------------------- TMA producer
     if (lane == 0) {
-      const uint32_t bytes = (uint32_t)p.stage_bytes;
       int s = 0, issued_n = 0;           // ring stage and the number of stages filled so far
       uint32_t ph = 0;                   // phase parity of stage s
       bool ok = true, stalled = false;
-      for (int item = blockIdx.x; item < p.items && ok; item += gridDim.x) {
-        if ((long long)item == p.stall_item) { stalled = true; break; }   // test hook: a barrier nothing fills
-        const int fc = item / p.items_per_fc;
+      for (int item = blockIdx.x; item < L.items && ok; item += gridDim.x) {
+        if ((long long)item == L.stall_item) { stalled = true; break; }   // test hook: a barrier nothing fills
+        const int pi = kMulti ? plan_of(L, item) : 0;
+        const TcParams &p = L.plan[pi];
+        const int fc = (item - p.first_item) / p.items_per_fc;
+        const uint32_t bytes = (uint32_t)p.stage_bytes;
+        const uint32_t plane_bytes = bytes / 2;    // two tiles of one plane
         for (int t = 0; t < p.ntiles; ++t) {
           if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag)) { fail(abort_flag, p.err, ERR_PRODUCER); ok = false; break; }
           mbar_expect_tx(full_bar(s), bytes);
-          const uint32_t dst = sB + (uint32_t)s * bytes;
-          tma_load_4d(dst, &tm_hi, 0, 0, 2 * t, fc, full_bar(s));
-          tma_load_4d(dst + plane_bytes, &tm_lo, 0, 0, 2 * t, fc, full_bar(s));
+          const uint32_t dst = sB + (uint32_t)s * (uint32_t)L.stage_max;
+          tma_load_4d(dst, &L.map[2 * pi], 0, 0, 2 * t, fc, full_bar(s));
+          tma_load_4d(dst + plane_bytes, &L.map[2 * pi + 1], 0, 0, 2 * t, fc, full_bar(s));
           ++issued_n;
           if (++s == nst) { s = 0; ph ^= 1u; }
         }
@@ -515,12 +539,16 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
-      const int ksteps = p.Kpad >> 4;
-      const uint64_t desc_b0 = smem_desc(sB, (uint32_t)(p.Kpad * 128));   // stage 0, hi plane, k step 0
       bool issued = false, ok = true;
       int s = 0, it = 0;
       uint32_t ph = 0, gpar = 0;         // ring stage and its phase parity; tile-pair parity
-      for (int item = blockIdx.x; item < p.items && ok; item += gridDim.x, ++it) {
+      int *err = L.plan[0].err;
+      for (int item = blockIdx.x; item < L.items && ok; item += gridDim.x, ++it) {
+        const TcParams &p = L.plan[kMulti ? plan_of(L, item) : 0];
+        err = p.err;
+        const int ksteps = p.Kpad >> 4;
+        const uint32_t plane_bytes = (uint32_t)p.stage_bytes / 2;
+        const uint64_t desc_b0 = smem_desc(sB, (uint32_t)(p.Kpad * 128));   // stage 0, hi plane, k step 0
         for (int t = 0; t < p.ntiles && ok; ++t, gpar ^= 1u) {
           if (!mbar_wait(full_bar(s), ph, abort_flag)) { fail(abort_flag, p.err, ERR_MMA); ok = false; break; }
           for (int mt = 0; mt < kMTiles; ++mt) {
@@ -535,7 +563,7 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
             uint32_t a_hi = tmem + kACol0 + (uint32_t)(2 * mt * 64);
             // descriptors advance by adding the byte offset / 16 to the start-address field (all
             // shared addresses are below 256 KB, so the 14-bit field never carries)
-            uint64_t b_hi = desc_b0 + (uint64_t)((s * p.stage_bytes) >> 4);
+            uint64_t b_hi = desc_b0 + (uint64_t)((s * L.stage_max) >> 4);
             for (int ks = 0; ks < ksteps; ++ks) {
               const uint64_t b_lo = b_hi + (uint64_t)(plane_bytes >> 4);
               umma(d, a_hi, b_hi, ks != 0);           // Whi Yhi
@@ -554,7 +582,7 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
       if (issued) {   // every MMA (and its barrier arrivals) retired before TMEM is released
         umma_commit(drain_bar);
         volatile int never = 0;
-        if (!mbar_wait(drain_bar, 0, &never)) fail(abort_flag, p.err, ERR_MMA);
+        if (!mbar_wait(drain_bar, 0, &never)) fail(abort_flag, err, ERR_MMA);
       }
     }
   } else {
@@ -565,15 +593,17 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
     const int ro = lane & 1;              // 0: Re V rows, 1: Im V rows
     const int jq = lane >> 1;             // beam within the quadrant (16 per M tile)
     const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
-    const int Mq = p.M / Q;
-    const long long pstride = (long long)p.F * kN * Mq;      // between Stokes parameters
     float *const qbuf = stage_out + quad * 2 * St::kBuf;
     uint32_t gpar = 0;                   // tile-pair parity
     int fl = 0;
     bool ok = true;
-    for (int item = blockIdx.x; item < p.items && ok; item += gridDim.x) {
-      const int fc = item / p.items_per_fc;
-      const int bb = item - fc * p.items_per_fc;
+    for (int item = blockIdx.x; item < L.items && ok; item += gridDim.x) {
+      const TcParams &p = L.plan[kMulti ? plan_of(L, item) : 0];
+      const int Mq = p.M / Q;
+      const long long pstride = (long long)p.F * kN * Mq;      // between Stokes parameters
+      const int li = item - p.first_item;
+      const int fc = li / p.items_per_fc;
+      const int bb = li - fc * p.items_per_fc;
       const int f = fc / kN, c = fc - f * kN;
       if (item == (int)blockIdx.x) {      // weights of the first item; later ones follow each last tile
         for (int mt = 0; mt < kMTiles; ++mt) {
@@ -586,19 +616,22 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
           if (lane == 0) mbar_arrive(afull_bar(mt));
         }
       }
+      // the next item of this CTA (possibly of another plan): its weights follow this item's last tile
       const int nitem = item + gridDim.x;
-      const int nfc = nitem / p.items_per_fc;
-      const int nbb = nitem - nfc * p.items_per_fc;
+      const TcParams &pn = L.plan[kMulti ? plan_of(L, nitem < L.items ? nitem : item) : 0];
+      const int nli = nitem - pn.first_item;
+      const int nfc = nli / pn.items_per_fc;
+      const int nbb = nli - nfc * pn.items_per_fc;
       FlushRows<NS, Q> frows;
       if constexpr (St::kOn) flush_rows<NS, Q>(p, frows, half * 32 + lane, quad, bb, f, c);
       for (int t = 0; t < p.ntiles && ok; ++t, gpar ^= 1u) {
         const int wbase = (t / St::kPeriod) * 8;
         float *const buf = qbuf + (fl & 1) * St::kBuf;
         for (int mt = 0; mt < kMTiles; ++mt) {
-          const bool boundary = t == p.ntiles - 1 && nitem < p.items;
+          const bool boundary = t == p.ntiles - 1 && nitem < L.items;
           WeightTables tab;
           if (boundary)   // the next item's table values, in flight while the last accumulator fills
-            load_weight_tables(p, nfc / kN, nbb * kBeamsPerItem + mt * (kRows / 2) + quad * 16 + jq, ro, half, tab);
+            load_weight_tables(pn, nfc / kN, nbb * kBeamsPerItem + mt * (kRows / 2) + quad * 16 + jq, ro, half, tab);
           if (!mbar_wait(accf_bar(mt), gpar, abort_flag)) { fail(abort_flag, p.err, ERR_EPILOGUE); ok = false; break; }
           tc_fence_after();
           const int b = bb * kBeamsPerItem + mt * (kRows / 2) + quad * 16 + jq;
@@ -621,7 +654,7 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
             // the MMAs that read this tile's weights are complete (its last accumulator was
             // committed): write the next item's
             const uint32_t ta_hi = tmem + lane_off + kACol0 + (uint32_t)(2 * mt * 64);
-            write_weights(p, ta_hi, ta_hi + 64u, nfc % kN, ro, half, tab);
+            write_weights(pn, ta_hi, ta_hi + 64u, nfc % kN, ro, half, tab);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(afull_bar(mt));
@@ -649,32 +682,32 @@ bf_tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ 
   }
 }
 
-template <int NS, int Q>
-cudaError_t launch_q(const CUtensorMap *hi, const CUtensorMap *lo, TcParams p, int grid, cudaStream_t st) {
-  // B ring: as many stages as shared memory leaves after the barriers and the output staging
-  p.nstages = (kRingBytes - Stage<NS, Q>::kBytes) / p.stage_bytes;
-  if (p.nstages > kMaxStages) p.nstages = kMaxStages;
-  if (p.nstages < 2) return cudaErrorInvalidValue;
-  int smem = 1024 + kBarBytes + p.nstages * p.stage_bytes + Stage<NS, Q>::kBytes;
+template <int NS, int Q, bool kMulti>
+cudaError_t launch_q(TcLaunch &L, int grid, cudaStream_t st) {
+  // B ring: as many stages of the largest plan as shared memory leaves after the barriers and
+  // the output staging
+  L.nstages = (kRingBytes - Stage<NS, Q>::kBytes) / L.stage_max;
+  if (L.nstages > kMaxStages) L.nstages = kMaxStages;
+  if (L.nstages < 2) return cudaErrorInvalidValue;
+  int smem = 1024 + kBarBytes + L.nstages * L.stage_max + Stage<NS, Q>::kBytes;
   // at least half of an SM's shared memory, so that no two CTAs share an SM (each holds all of
   // its TMEM columns)
   if (smem < kMinSmem) smem = kMinSmem;
-  cudaError_t e = cudaFuncSetAttribute(bf_tc_kernel<NS, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(bf_tc_kernel<NS, Q, kMulti>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  bf_tc_kernel<NS, Q><<<grid, kThreads, smem, st>>>(*hi, *lo, p);
+  bf_tc_kernel<NS, Q, kMulti><<<grid, kThreads, smem, st>>>(L);
   return cudaGetLastError();
 }
 
-template <int NS>
-cudaError_t launch_ns(int Q, const CUtensorMap *hi, const CUtensorMap *lo, const TcParams &p, int grid,
-                      cudaStream_t st) {
+template <int NS, bool kMulti>
+cudaError_t launch_ns(int Q, TcLaunch &L, int grid, cudaStream_t st) {
   switch (Q) {
-    case 1: return launch_q<NS, 1>(hi, lo, p, grid, st);
-    case 2: return launch_q<NS, 2>(hi, lo, p, grid, st);
-    case 4: return launch_q<NS, 4>(hi, lo, p, grid, st);
-    case 8: return launch_q<NS, 8>(hi, lo, p, grid, st);
-    case 16: return launch_q<NS, 16>(hi, lo, p, grid, st);
-    case 32: return launch_q<NS, 32>(hi, lo, p, grid, st);
+    case 1: return launch_q<NS, 1, kMulti>(L, grid, st);
+    case 2: return launch_q<NS, 2, kMulti>(L, grid, st);
+    case 4: return launch_q<NS, 4, kMulti>(L, grid, st);
+    case 8: return launch_q<NS, 8, kMulti>(L, grid, st);
+    case 16: return launch_q<NS, 16, kMulti>(L, grid, st);
+    case 32: return launch_q<NS, 32, kMulti>(L, grid, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -687,39 +720,75 @@ int sm_count() {
   return n[dev];
 }
 
+// Plan i of a launch: its parameters from the geometry, its work items after the previous plans'.
+bool fill_plan(TcLaunch &L, int i, const Geometry &g, int out_kind, const void *tm_hi, const void *tm_lo, float *out,
+               int *err) {
+  if (!tm_hi || !tm_lo || g.S > tc_max_stations()) return false;
+  TcParams &p = L.plan[i];
+  p.S = g.S; p.F = g.F; p.B = g.B; p.M = g.M;
+  p.Kpad = tc_kpad(g.S);
+  p.stage_bytes = 4 * p.Kpad * 128;
+  p.ntiles = tc_tiles(g.M) / 2;
+  p.items_per_fc = (g.B + kBeamsPerItem - 1) / kBeamsPerItem;
+  const long long items = (long long)g.F * kN * p.items_per_fc;
+  const long long first = i == 0 ? 0 : (long long)L.plan[i - 1].first_item + L.plan[i - 1].items;
+  if (items + first >= (1ll << 31)) return false;
+  p.items = (int)items;
+  p.first_item = (int)first;
+  p.phase0 = g.phase0; p.step = g.step; p.out = out; p.err = err;
+  const bool aligned = (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+  p.vec = out_kind == OUT_VOLTAGES ? (g.M % 2 == 0 && aligned) : ((g.M / g.Q) % 4 == 0 && aligned);
+  L.map[2 * i] = *reinterpret_cast<const CUtensorMap *>(tm_hi);
+  L.map[2 * i + 1] = *reinterpret_cast<const CUtensorMap *>(tm_lo);
+  L.items = p.first_item + p.items;
+  L.stage_max = p.stage_bytes > L.stage_max ? p.stage_bytes : L.stage_max;
+  L.nplans = i + 1;
+  return true;
+}
+
+template <bool kMulti>
+cudaError_t launch_table(TcLaunch &L, int out_kind, int Q, cudaStream_t st) {
+  if (L.items == 0) return cudaSuccess;
+  const int sms = sm_count();
+  if (sms <= 0) return cudaErrorInvalidDevice;
+  const int grid = L.items < sms ? L.items : sms;
+  if (out_kind == OUT_VOLTAGES) return launch_q<0, 1, kMulti>(L, grid, st);
+  if (out_kind == OUT_STOKES_IQUV) return launch_ns<4, kMulti>(Q, L, grid, st);
+  if (out_kind == OUT_STOKES_I) return launch_ns<1, kMulti>(Q, L, grid, st);
+  return cudaErrorInvalidValue;
+}
+
 }  // namespace
 
 int tc_max_stations() { return kMaxKpad / 2; }
 int tc_spectra_per_tile() { return kSpec; }
 int tc_kpad(int S) { return ((2 * S + 15) / 16) * 16; }
+int tc_max_plans_per_launch() { return kMaxPlans; }
 
 cudaError_t launch_bf_tc(const Geometry &g, int out_kind, const void *tm_hi, const void *tm_lo, float *out, int *err,
                          cudaStream_t st, long long stall_item) {
   if (g.M == 0 || g.B == 0) return cudaSuccess;
-  if (!tm_hi || !tm_lo || g.S > tc_max_stations()) return cudaErrorInvalidValue;
-  TcParams p;
-  p.S = g.S; p.F = g.F; p.B = g.B; p.M = g.M;
-  p.Kpad = tc_kpad(g.S);
-  p.stage_bytes = 4 * p.Kpad * 128;
-  p.nstages = 0;
-  p.ntiles = tc_tiles(g.M) / 2;
-  p.items_per_fc = (g.B + kBeamsPerItem - 1) / kBeamsPerItem;
-  const long long items = (long long)g.F * kN * p.items_per_fc;
-  if (items >= (1ll << 31)) return cudaErrorInvalidValue;
-  p.items = (int)items;
-  p.phase0 = g.phase0; p.step = g.step; p.out = out; p.err = err;
-  const bool aligned = (reinterpret_cast<uintptr_t>(out) & 15) == 0;
-  p.vec = out_kind == OUT_VOLTAGES ? (g.M % 2 == 0 && aligned) : ((g.M / g.Q) % 4 == 0 && aligned);
-  p.stall_item = stall_item;
-  const int sms = sm_count();
-  if (sms <= 0) return cudaErrorInvalidDevice;
-  const int grid = p.items < sms ? p.items : sms;
-  const CUtensorMap *hi = reinterpret_cast<const CUtensorMap *>(tm_hi);
-  const CUtensorMap *lo = reinterpret_cast<const CUtensorMap *>(tm_lo);
-  if (out_kind == OUT_VOLTAGES) return launch_q<0, 1>(hi, lo, p, grid, st);
-  if (out_kind == OUT_STOKES_IQUV) return launch_ns<4>(g.Q, hi, lo, p, grid, st);
-  if (out_kind == OUT_STOKES_I) return launch_ns<1>(g.Q, hi, lo, p, grid, st);
-  return cudaErrorInvalidValue;
+  TcLaunch L;
+  L.nplans = 0; L.items = 0; L.nstages = 0; L.stage_max = 0;
+  L.stall_item = stall_item;
+  if (!fill_plan(L, 0, g, out_kind, tm_hi, tm_lo, out, err)) return cudaErrorInvalidValue;
+  return launch_table<false>(L, out_kind, g.Q, st);
+}
+
+cudaError_t launch_bf_tc_group(const TcPlanRef *plans, int n, int out_kind, int Q, cudaStream_t st) {
+  if (n < 1 || n > kMaxPlans) return cudaErrorInvalidValue;
+  TcLaunch L;
+  L.nplans = 0; L.items = 0; L.nstages = 0; L.stage_max = 0;
+  L.stall_item = -1;
+  int k = 0;
+  for (int i = 0; i < n; ++i) {
+    const TcPlanRef &r = plans[i];
+    if (r.g.Q != Q && out_kind != OUT_VOLTAGES) return cudaErrorInvalidValue;
+    if (r.g.M == 0 || r.g.B == 0) continue;
+    if (!fill_plan(L, k, r.g, out_kind, r.tm_hi, r.tm_lo, r.out, r.err)) return cudaErrorInvalidValue;
+    ++k;
+  }
+  return k == 1 ? launch_table<false>(L, out_kind, Q, st) : launch_table<true>(L, out_kind, Q, st);
 }
 
 }  // namespace lbf

@@ -97,6 +97,16 @@ cudaError_t launch_incoherent_ct16(const Geometry &g, int out_kind, const Ct16Ou
 // stall_item >= 0: failure-detection test, the loads of that work item are never issued
 cudaError_t launch_bf_tc(const Geometry &g, int out_kind, const void *tm_hi, const void *tm_lo, float *out, int *err,
                          cudaStream_t st, long long stall_item = -1);
+// several tensor-core plans of one output kind and integration length in ONE persistent launch
+// (their work items numbered one after the other); n <= tc_max_plans_per_launch()
+struct TcPlanRef {
+  Geometry g;
+  const void *tm_hi, *tm_lo;   // CUtensorMap* of the plan's FP16 planes
+  float *out;
+  int *err;
+};
+cudaError_t launch_bf_tc_group(const TcPlanRef *plans, int n, int out_kind, int Q, cudaStream_t st);
+int tc_max_plans_per_launch();
 // channel-level dedispersion of vol [B][F][N][P][M] (in may equal out); K a power of two dividing M
 cudaError_t launch_dedisperse(const Geometry &g, double dm, int K, const float2 *in, float2 *out, cudaStream_t st);
 int tc_max_stations();

@@ -42,6 +42,7 @@ class BlockResult:
     arrival: float
     admitted: float
     done: float
+    upload_gbs: float = 0.0   # host-to-device rate of this block's own uploads (CUDA events)
 
     @property
     def latency(self) -> float:
@@ -120,7 +121,7 @@ class Server:
         self.device = device
         self.pool = Pool(device, budget_bytes)
         self.obs: dict[int, _Obs] = {}
-        self.inflight = []          # (done event, obs, index, arrival, admitted, buffers, host_out)
+        self.inflight = []          # (done event, obs, index, arrival, admitted, buffers, host_out, upload events)
         self.keep_outputs = keep_outputs
 
     # -- observations
@@ -156,6 +157,8 @@ class Server:
     def _enqueue(self, o: _Obs, host_in, host_out):
         torch = self.torch
         bufs = []
+        up0 = torch.cuda.Event(enable_timing=True)
+        up0.record(o.s_h2d)
         for c in o.chunks:
             d = c.plan.dims
             d_in, d_out = self.pool.take(d.in_bytes), self.pool.take(d.out_bytes)
@@ -169,9 +172,11 @@ class Server:
             ev_k.record(o.s_comp)
             o.s_d2h.wait_event(ev_k)
             c.plan.download_subbands(d_out, o.n_subbands, c.first, host_out, o.s_d2h)
+        up1 = torch.cuda.Event(enable_timing=True)
+        up1.record(o.s_h2d)
         done = torch.cuda.Event()
         done.record(o.s_d2h)
-        return done, bufs
+        return done, bufs, (up0, up1)
 
     def _admit(self, now: float):
         # earliest arrival first, across observations
@@ -184,17 +189,20 @@ class Server:
             arrival, index, h_in, h_out = o.queue.pop(0)
             h_in = o.host_in if h_in is None else h_in
             h_out = o.host_out if h_out is None else h_out
-            ev, bufs = self._enqueue(o, h_in, h_out)
+            ev, bufs, up = self._enqueue(o, h_in, h_out)
             o.inflight += 1
-            self.inflight.append((ev, o, index, arrival, now, bufs, h_out))
+            self.inflight.append((ev, o, index, arrival, now, bufs, h_out, up))
 
     def _reap(self, now: float):
         still = []
         for item in self.inflight:
-            ev, o, index, arrival, admitted, bufs, h_out = item
+            ev, o, index, arrival, admitted, bufs, h_out, up = item
             if ev.query():
                 done = time.perf_counter()
-                o.results.append(BlockResult(o.oid, index, arrival, admitted, done))
+                up_s = up[0].elapsed_time(up[1]) / 1e3
+                nbytes = sum(c.plan.dims.in_bytes for c in o.chunks)
+                o.results.append(BlockResult(o.oid, index, arrival, admitted, done,
+                                             nbytes / up_s / 1e9 if up_s > 0 else 0.0))
                 if self.keep_outputs:
                     o.outputs.append(h_out.clone())
                 for t, n in bufs:
@@ -253,6 +261,11 @@ def poisson_schedule(n_obs: int, n_blocks: int, period_s: float, rng: np.random.
 
 def latency_summary(results, period_s: float) -> dict:
     lat = np.array([r.latency for r in results])
-    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-            "max_s": float(lat.max()), "period_s": period_s, "blocks": int(lat.size),
-            "late_blocks": int(np.sum(lat > period_s))}
+    out = {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+           "max_s": float(lat.max()), "period_s": period_s, "blocks": int(lat.size),
+           "late_blocks": int(np.sum(lat > period_s))}
+    up = np.array([r.upload_gbs for r in results if r.upload_gbs > 0])
+    if up.size:   # the host link as the blocks' own uploads saw it (shared with other jobs)
+        out["block_upload_gbs"] = {"p50": float(np.percentile(up, 50)), "min": float(up.min()),
+                                   "max": float(up.max())}
+    return out

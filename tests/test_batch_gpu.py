@@ -80,8 +80,10 @@ def test_batch_equals_separate_runs():
 
 def test_batch_with_tensor_core_plans_equals_separate_runs():
     """Tensor-core plans (Stokes I, IQUV with the incoherent beam, voltages) and FP32 plans in one
-    batch: grouped filter bank writing the FP16 planes, then one tensor-core launch per plan;
-    every output equals the same plan run alone, block after block, also as graph replays."""
+    batch: grouped filter bank writing the FP16 planes, then one persistent tensor-core launch per
+    class of output kind and integration length (here the two IQUV plans, of 20 and 64 stations,
+    share one); every output equals the same plan run alone, block after block, also as graph
+    replays."""
     from paper_1105_0661_gb300 import Batch, Plan, build_lib
     build_lib.build()
     dev = torch.device("cuda:0")
