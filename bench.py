@@ -141,6 +141,7 @@ def algorithmic_work(wl, dims):
         "delay_ct": ("hbm", ss * 32),
         "bf_few": ("hbm", ss * 16 + out_bytes),  # read corner-turned cf32 once, write the output
         "bf_many": ("alu", 8.0 * B * ss * 2),   # 8 flop per complex MAC, B x S x 2 pols x T per subband
+        "bf_many64": ("alu", 8.0 * B * ss * 2),
         "stokes": ("hbm", B * F * T * 16 + out_bytes),
         # FP16 forms: hi and lo half2 planes per pol; one complex product is the algorithmic work
         "ppf_ct16": ("hbm", ss * (word + 2 * 4 * 2)),
@@ -156,7 +157,7 @@ def traffic_from_profiles(kernel: str, workload_name: str):
     path = os.path.join(ROOT, "profiles", "traffic.md")
     if not os.path.exists(path):
         return None
-    src = {"bf_many": "beamform.cu", "bf_few": "beamform.cu", "ppf_ct": "ppf.cu", "ppf": "ppf.cu",
+    src = {"bf_many": "beamform.cu", "bf_many64": "beamform.cu", "bf_few": "beamform.cu", "ppf_ct": "ppf.cu", "ppf": "ppf.cu",
            "ppf_ct16": "ppf.cu", "bf_tc": "bf_tc.cu", "hist_update": "ppf.cu", "delay_ct": "delay.cu",
            "dedisperse": "dedisperse.cu",
            "stokes": "stokes.cu", "superstation": "delay.cu"}.get(kernel)
@@ -895,23 +896,6 @@ def run_incoherent(args):
     return 0
 
 
-def batch_launches(wls, prec, tuning):
-    """Kernel launches in one batch graph: the grouped filter bank and history update, one grouped
-    FP32 beam former per shared-memory class in use (many-beam CTAs with more than 56 stations
-    need one SM each), and one grouped tensor-core launch per class of output kind and
-    integration length (all the batched observations are Stokes I over 4 spectra: one)."""
-    classes = set()
-    for wl, pr in zip(wls, prec):
-        if pr != "fp32" and wl.n_beams > 8:
-            continue
-        many = wl.n_beams > 8 and wl.n_stations <= 113
-        if 8 < wl.n_beams <= 64 and wl.n_stations <= 113 and tuning.get("best_mid_variant"):
-            many = not many
-        classes.add(1 if many and wl.n_stations * 2048 > 113 * 1024 else 0)
-    tc = any(pr != "fp32" and wl.n_beams > 8 for wl, pr in zip(wls, prec))
-    return 2 + len(classes) + (1 if tc else 0)
-
-
 def run_batch(args):
     import torch
 
@@ -966,7 +950,7 @@ def run_batch(args):
         "separate_launches": {"value": ss / (ms_sep / 1e3), "ms_per_step": ms_sep, "gpu_launches": 3 * len(plans)},
         "precision": args.precision,
         "speedup_vs_separate": ms_sep / ms_graph, "tuning": tuning,
-        "gpu_launches": batch_launches(wls, prec, tuning),
+        "gpu_launches": batch.launches(),
     }
     print(json.dumps(line), flush=True)
     batch.close()

@@ -71,9 +71,12 @@ typedef enum { LBF_VOLTAGES = 0, LBF_STOKES_I = 1, LBF_STOKES_IQUV = 4 } lbf_out
 
 typedef enum { LBF_FP32 = 0, LBF_FP16_TC = 1 } lbf_precision;
 
-/* Beam-former kernel choice: AUTO picks the bandwidth-bound few-beam kernel for B <= 8 and the
- * register-tiled many-beam kernel (FP32) or the tensor-core kernel (LBF_FP16_TC) otherwise. */
-typedef enum { LBF_BF_AUTO = 0, LBF_BF_FEW = 1, LBF_BF_MANY = 2 } lbf_bf_variant;
+/* Beam-former kernel choice: AUTO picks the bandwidth-bound few-beam kernel for B <= 8 and
+ * otherwise the tensor-core kernel (LBF_FP16_TC) or the register-tiled FP32 many-beam kernel with
+ * the beam tile -- 128 (MANY) or 64 (MANY64) beams per CTA -- that leaves the fewest tile slots
+ * empty (a 64-beam slot weighed as 1.15 of a 128-beam one).  With LBF_FP16_TC, MANY and MANY64
+ * both select the tensor-core kernel. */
+typedef enum { LBF_BF_AUTO = 0, LBF_BF_FEW = 1, LBF_BF_MANY = 2, LBF_BF_MANY64 = 3 } lbf_bf_variant;
 
 /* The plan does not allocate the run_block scratch; the caller passes one to lbf_run_block_ws
  * (several plans can then share scratch buffers, as a serving loop does). */
@@ -113,7 +116,8 @@ typedef struct lbf_dims {
   int32_t n_stokes;           /* nS: 1 (I), 4 (IQUV), 0 (voltages) */
   int32_t d_max;              /* largest integer shift d_s, in samples */
   int32_t history_samples;    /* H = (L-1) N + d_max samples kept per (station, subband) */
-  int32_t bf_kernel;          /* beam former the plan uses: 1 few-beam, 2 many-beam FP32, 3 tensor core */
+  int32_t bf_kernel;          /* beam former the plan uses: 1 few-beam, 2 many-beam FP32 (128-beam
+                                 tiles), 3 tensor core, 4 many-beam FP32 (64-beam tiles) */
   size_t in_bytes;            /* bytes of one input block */
   size_t chan_bytes;          /* bytes of a chan buffer */
   size_t ct_bytes;            /* bytes of a ct buffer */
@@ -326,21 +330,26 @@ lbf_status lbf_run_block_static(const lbf_config *cfg, const void *d_in, void *d
 /* ---- Batches: several observations processed together (Section 7: independent observations can
  * run in parallel as long as resources allow).  One block of every plan of
  * a batch runs as ONE persistent grouped launch per stage -- filter bank (with the delay / bandpass
- * / corner-turn epilogue), history update, beam former with its Stokes epilogue -- instead of
- * three launches per plan; CTAs take work items from a shared counter, so uneven observations
- * load-balance.  Tensor-core plans join the grouped filter bank and history update and then
- * run their own persistent tensor-core beam former (one launch per such plan, after the grouped
- * FP32 beam former).  Plans of a batch must use their own scratch (no
+ * / corner-turn epilogue), history update, beam former with its Stokes epilogue (one launch per
+ * FP32 beam-former kernel in use, each at its own residency) -- instead of three launches per
+ * plan; CTAs take work items from a shared counter, so uneven observations load-balance.
+ * Tensor-core plans join the grouped filter bank and history update; then ONE persistent
+ * tensor-core launch per class of output kind and integration length walks the work items of all
+ * the class's plans (up to 32 plans per launch).  Plans of a batch must use their own scratch (no
  * LBF_FLAG_EXTERNAL_WORKSPACE), be on the current device and be in at most one active batch;
  * their history advances exactly as with lbf_run_block.  d_in[i] / d_out[i] are plan i's device
  * `in` and `out` (or `vol`) buffers. */
 typedef struct lbf_batch_s *lbf_batch_t;
 
 typedef struct lbf_batch_tuning {
-  int32_t n_candidates;         /* candidates timed (3 or 6) */
-  int32_t spc[6];               /* spectra per filter-bank work item of each candidate */
-  int32_t mid_variant[6];       /* 1: plans with 9..64 beams switched to the other beam former */
-  double ms[6];                 /* mean time of one batch block per candidate */
+  int32_t n_candidates;         /* candidates timed (4, 7 or 10) */
+  int32_t spc[10];              /* spectra per filter-bank work item of each candidate; 0: the
+                                   per-plan mode (each plan's own filter bank and FP32 beam former
+                                   inside the batch graph, the tensor-core stage still grouped) */
+  int32_t mid_variant[10];      /* beam-former choice: 0 each plan's own; 1 plans with 9..64 beams
+                                   switched between the few- and many-beam kernels; 2 FP32 plans
+                                   with more than 8 beams switched between 128- and 64-beam tiles */
+  double ms[10];                /* mean time of one batch block per candidate */
   int32_t best_spc, best_mid_variant;
   double best_ms;
 } lbf_batch_tuning;
@@ -358,9 +367,19 @@ lbf_status lbf_batch_run(lbf_batch_t batch, const void *const *d_in, void *const
 lbf_status lbf_batch_capture(lbf_batch_t batch, const void *const *d_in, void *const *d_out, void *stream);
 lbf_status lbf_batch_launch(lbf_batch_t batch, void *stream);
 
-/* Autotune the batch's tile shapes on these buffers: spectra per filter-bank work item (64, 128,
- * 256) and, for plans with 9..64 beams, the few- or many-beam beam former; each candidate is timed
- * over `reps` blocks with CUDA events, the fastest is kept.  The candidate runs use the plans'
+/* Kernel launches of one batch block as the tables were last filled (by lbf_batch_run,
+ * lbf_batch_capture or lbf_batch_tune): one grouped filter-bank launch per class of sample width
+ * and output form, the grouped history update, one grouped FP32 beam-former launch per class of
+ * beam-former kernel, output kind and CTAs per SM, one tensor-core launch per class of output kind
+ * and integration length (per 32 plans), and one incoherent-beam kernel per tensor-core plan that
+ * forms it.  Host only. */
+lbf_status lbf_batch_launches(lbf_batch_t batch, int32_t *n_launches);
+
+/* Autotune the batch's tile shapes on these buffers: spectra per filter-bank work item (64, 256,
+ * 1024: a quarter, half or all of a stream's block) times the beam-former choice (each plan's own; for plans with 9..64 beams the few- or
+ * many-beam kernel; for FP32 plans with more than 8 beams the 128- or 64-beam tile) in grouped
+ * persistent launches, then the best of these as per-plan launches of the FP32 stages; each
+ * candidate is timed over `reps` blocks with CUDA events, the fastest is kept.  The candidate runs use the plans'
  * histories, so every plan's stream is restarted (history zeroed) afterwards.  `out` may be NULL. */
 lbf_status lbf_batch_tune(lbf_batch_t batch, const void *const *d_in, void *const *d_out, void *stream,
                           int32_t reps, lbf_batch_tuning *out);

@@ -12,8 +12,9 @@
 //
 // A batch can be captured as CUDA graphs (one per history parity: each block flips every plan's
 // history ping-pong) and replayed with a single graph launch per block, and its tile shapes --
-// spectra per filter-bank item and, for observations with 9..64 beams, the few- or many-beam
-// beam former -- can be tuned by timing the candidates on the batch itself.
+// spectra per filter-bank item, for observations with 9..64 beams the few- or many-beam beam
+// former, and the many-beam tile (128 or 64 beams per CTA) -- can be tuned by timing the
+// candidates on the batch itself.
 #include <cstring>
 #include <new>
 #include <utility>
@@ -26,7 +27,7 @@
 namespace {
 
 constexpr uint32_t kBatchMagic = 0x4c424642u;   // "LBFB"
-constexpr size_t kTwoPerSm = 113 * 1024;        // beam-former shared memory that still fits twice per SM
+constexpr int kMaxCounters = 64;                // >= 4 filter-bank + 3 x 3 x 3 beam-former classes
 
 bool plan_ok(lbf_plan_t p) { return p && p->magic == lbf::kPlanMagic; }
 
@@ -48,19 +49,23 @@ struct lbf_batch_s {
   uint32_t magic = kBatchMagic;
   int device = 0;
   std::vector<lbf_plan_t> plans;
-  int spc = 128;                       // spectra per filter-bank item
+  int spc = 256;                       // spectra per filter-bank item (tuned: 64, 256 or 1024)
+  bool per_plan = false;               // FP32 stages as each plan's own kernels (tuned)
   std::vector<int> variant;            // beam-former kernel per plan
   // group tables: [parity][plan]; parity p describes the plans' history state after p blocks
   lbf::PpfGroup *h_ppf = nullptr, *d_ppf = nullptr;   // pinned host / device, 2 * n
-  lbf::BfGroup *h_bf = nullptr, *d_bf = nullptr;     // plans of shared-memory class 0, then class 1
-  unsigned long long *d_counter = nullptr;            // [3] work counters
-  long long ppf_items = 0, hist_items = 0;
-  // beam-former classes: 0 fits two CTAs per SM, 1 needs one (large station counts)
-  int bf_n[2] = {0, 0};
-  long long bf_items[2] = {0, 0};
-  size_t bf_smem[2] = {0, 0};
+  lbf::BfGroup *h_bf = nullptr, *d_bf = nullptr;     // FP32 plans, class by class
+  unsigned long long *d_counter = nullptr;            // [kMaxCounters] work counters, one per launch
+  long long hist_items = 0;
+  // launch classes: filter bank per (sample width, FP32 or FP16 output); FP32 beam former per
+  // (variant, output kind, CTAs per SM) -- each class one persistent launch over its groups
+  struct PpfClass { int bits, tc, first, n; long long items; };
+  struct BfClass { int variant, out_kind, per_sm, first, n; long long items; size_t smem; };
+  std::vector<PpfClass> ppf_cls;
+  std::vector<BfClass> bf_cls;
   int ppf_ctas = 0, sms = 0;
-  std::vector<void *> tc_out;          // output of each plan's block (used by tensor-core plans)
+  std::vector<void *> tc_out;          // output of each plan's block
+  std::vector<const void *> d_in_cur;  // input of each plan's block (per-plan mode)
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int graph_parity = 0;                // which graph describes the current state
 };
@@ -75,61 +80,81 @@ void free_graphs(lbf_batch_t b) {
 }
 
 // Fill the group tables of parity `par` (par = 1: every plan's history one block ahead) for the
-// given block buffers.
+// given block buffers: filter-bank groups class by class (work items numbered from 0 within a
+// class; history elements numbered over the whole table), then the FP32 beam-former groups class
+// by class.
 void fill_tables(lbf_batch_t b, int par, const void *const *d_in, void *const *d_out) {
   const int n = (int)b->plans.size();
-  long long pi = 0, hi = 0;
-  for (int i = 0; i < n; ++i) {
-    lbf_plan_t p = b->plans[i];
-    const int cur = p->cur ^ par;
-    lbf::PpfGroup &G = b->h_ppf[par * n + i];
-    G.g = p->geometry();
-    G.in = d_in[i];
-    G.hist = p->hist[cur];
-    G.new_hist = p->hist[cur ^ 1];
-    G.ct = p->ws;
-    G.tc = p->tc ? 1 : 0;
-    G.ct16.hi = p->ct16[0];
-    G.ct16.lo = p->tc ? static_cast<unsigned char *>(p->ct16[0]) + p->ct16_bytes : nullptr;
-    G.ct16.kpad = p->kpad;
-    G.bits = p->bits;
-    G.spc = b->spc;
-    G.chunks = lbf::ppf_items_per_stream(p->M, b->spc);
-    G.first_item = pi;
-    G.first_hist = hi;
-    pi += (long long)p->S * p->F * G.chunks;   // one item: both polarisations of a chunk
-    hi += (long long)p->S * p->F * p->H;
-  }
-  b->ppf_items = pi;
+  long long hi = 0;
+  int slot = 0;
+  b->ppf_cls.clear();
+  for (int bits : {16, 8})
+    for (int tc = 0; tc < 2; ++tc) {
+      lbf_batch_s::PpfClass cls{bits, tc, slot, 0, 0};
+      for (int i = 0; i < n; ++i) {
+        lbf_plan_t p = b->plans[i];
+        if (p->bits != bits || (p->tc ? 1 : 0) != tc) continue;
+        const int cur = p->cur ^ par;
+        lbf::PpfGroup &G = b->h_ppf[par * n + slot++];
+        G.g = p->geometry();
+        G.in = d_in[i];
+        G.hist = p->hist[cur];
+        G.new_hist = p->hist[cur ^ 1];
+        G.ct = p->ws;
+        G.tc = tc;
+        G.ct16.hi = p->ct16[0];
+        G.ct16.lo = p->tc ? static_cast<unsigned char *>(p->ct16[0]) + p->ct16_bytes : nullptr;
+        G.ct16.kpad = p->kpad;
+        G.bits = p->bits;
+        G.spc = b->spc;
+        G.chunks = lbf::ppf_items_per_stream(p->M, b->spc);
+        G.first_item = cls.items;
+        G.first_hist = hi;
+        cls.items += (long long)p->S * p->F * G.chunks;   // one item: both polarisations of a chunk
+        hi += (long long)p->S * p->F * p->H;
+        ++cls.n;
+      }
+      if (cls.n) b->ppf_cls.push_back(cls);
+    }
   b->hist_items = hi;
   b->tc_out.assign(d_out, d_out + n);
-  // beam former: class 0 (two CTAs per SM fit) first, then class 1
-  int slot = par * n;
-  for (int cls = 0; cls < 2; ++cls) {
-    long long items = 0;
-    size_t smem = 0;
-    int cnt = 0;
-    for (int i = 0; i < n; ++i) {
-      lbf_plan_t p = b->plans[i];
-      if (p->tc) continue;                  // its own tensor-core launch
-      const size_t sm = lbf::bf_smem_bytes(b->variant[i], p->S);
-      if ((sm > kTwoPerSm) != (cls == 1)) continue;
-      lbf::BfGroup &Bg = b->h_bf[slot++];
+  b->d_in_cur.assign(d_in, d_in + n);
+  // FP32 beam former: plans of the same variant, output kind and residency share a launch
+  std::vector<int> per_sm(n, 0);
+  std::vector<size_t> smem_of(n, 0);
+  for (int i = 0; i < n; ++i) {
+    lbf_plan_t p = b->plans[i];
+    if (p->tc) continue;
+    smem_of[i] = lbf::bf_smem_bytes(b->variant[i], p->S);
+    per_sm[i] = lbf::bf_group_residency(b->variant[i], p->out_kind, smem_of[i]);
+  }
+  b->bf_cls.clear();
+  slot = 0;
+  std::vector<bool> placed(n, false);
+  for (int i = 0; i < n; ++i) {
+    lbf_plan_t pi = b->plans[i];
+    if (pi->tc || placed[i]) continue;
+    lbf_batch_s::BfClass cls{b->variant[i], pi->out_kind, per_sm[i], slot, 0, 0, 0};
+    for (int j = i; j < n; ++j) {
+      lbf_plan_t p = b->plans[j];
+      if (p->tc || placed[j] || b->variant[j] != cls.variant || p->out_kind != cls.out_kind ||
+          per_sm[j] != cls.per_sm)
+        continue;
+      placed[j] = true;
+      lbf::BfGroup &Bg = b->h_bf[par * n + slot++];
       Bg.g = p->geometry();
       Bg.ct = p->ws;
-      Bg.out = d_out[i];
-      Bg.variant = b->variant[i];
+      Bg.out = d_out[j];
+      Bg.variant = b->variant[j];
       Bg.out_kind = p->out_kind;
-      const int per = b->variant[i] == 1 ? lbf::few_beams_per_item() : lbf::many_beams_per_item();
+      const int per = b->variant[j] == 1 ? lbf::few_beams_per_item() : lbf::many_beams_per_item(b->variant[j]);
       Bg.per_fc = (p->B + per - 1) / per;
-      Bg.first_item = items;
-      items += (long long)p->F * lbf::kN * Bg.per_fc;
-      smem = sm > smem ? sm : smem;
-      ++cnt;
+      Bg.first_item = cls.items;
+      cls.items += (long long)p->F * lbf::kN * Bg.per_fc;
+      cls.smem = smem_of[j] > cls.smem ? smem_of[j] : cls.smem;
+      ++cls.n;
     }
-    b->bf_n[cls] = cnt;
-    b->bf_items[cls] = items;
-    b->bf_smem[cls] = smem;
+    b->bf_cls.push_back(cls);
   }
 }
 
@@ -140,14 +165,39 @@ cudaError_t enqueue(lbf_batch_t b, int par, cudaStream_t st) {
                                   cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->d_bf + par * n, b->h_bf + par * n, sizeof(lbf::BfGroup) * n, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = lbf::launch_ppf_group(b->d_ppf + par * n, n, b->ppf_items, b->d_counter, b->ppf_ctas, st);
-  if (e == cudaSuccess) e = lbf::launch_hist_group(b->d_ppf + par * n, n, b->hist_items, st);
-  if (e == cudaSuccess && b->bf_n[0])
-    e = lbf::launch_bf_group(b->d_bf + par * n, b->bf_n[0], b->bf_items[0], b->d_counter + 1, 2 * b->sms,
-                             b->bf_smem[0], st);
-  if (e == cudaSuccess && b->bf_n[1])
-    e = lbf::launch_bf_group(b->d_bf + par * n + b->bf_n[0], b->bf_n[1], b->bf_items[1], b->d_counter + 2, b->sms,
-                             b->bf_smem[1], st);
+  if (b->per_plan) {
+    // each plan's own filter bank, history update and FP32 beam former (the hardware schedules
+    // their CTAs; large observations each fill the GPU) -- the tensor-core stage stays grouped
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+      lbf_plan_t p = b->plans[i];
+      if (p->M == 0) continue;
+      const int cur = p->cur ^ par;
+      const lbf::Geometry g = p->geometry();
+      const void *din = b->d_in_cur[i];
+      if (p->tc) {
+        lbf::Ct16Out o;
+        o.hi = p->ct16[0];
+        o.lo = static_cast<unsigned char *>(p->ct16[0]) + p->ct16_bytes;
+        o.kpad = p->kpad;
+        e = lbf::launch_ppf(g, p->bits, din, p->hist[cur], nullptr, nullptr, st, &o);
+      } else {
+        e = lbf::launch_ppf(g, p->bits, din, p->hist[cur], nullptr, p->ws, st);
+      }
+      if (e == cudaSuccess) e = lbf::launch_hist_update(g, p->bits, din, p->hist[cur], p->hist[cur ^ 1], st);
+      if (e == cudaSuccess && !p->tc) e = lbf::launch_beamform(g, b->variant[i], p->out_kind, p->ws, b->tc_out[i], st);
+    }
+  } else {
+    int counter = 0;
+    for (const auto &c : b->ppf_cls)
+      if (e == cudaSuccess)
+        e = lbf::launch_ppf_group(c.bits, c.tc, b->d_ppf + par * n + c.first, c.n, c.items,
+                                  b->d_counter + counter++, b->ppf_ctas, st);
+    if (e == cudaSuccess) e = lbf::launch_hist_group(b->d_ppf + par * n, n, b->hist_items, st);
+    for (const auto &c : b->bf_cls)
+      if (e == cudaSuccess)
+        e = lbf::launch_bf_group(c.variant, c.out_kind, b->d_bf + par * n + c.first, c.n, c.items,
+                                 b->d_counter + counter++, c.smem, st);
+  }
   // tensor-core plans: their incoherent beams, then ONE persistent tcgen05 launch per class of
   // output kind and integration length (up to tc_max_plans_per_launch() plans each), whose CTAs
   // walk the work items of all the class's plans
@@ -226,7 +276,7 @@ lbf_status lbf_batch_create(const lbf_plan_t *plans, int32_t n, lbf_batch_t *out
   if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_bf, sizeof(lbf::BfGroup) * 2 * n);
   if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_ppf, sizeof(lbf::PpfGroup) * 2 * n);
   if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_bf, sizeof(lbf::BfGroup) * 2 * n);
-  if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_counter, 3 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_counter, kMaxCounters * sizeof(unsigned long long));
   if (e != cudaSuccess) {
     cudaFreeHost(b->h_ppf); cudaFreeHost(b->h_bf); cudaFree(b->d_ppf); cudaFree(b->d_bf); cudaFree(b->d_counter);
     delete b;
@@ -297,6 +347,42 @@ lbf_status lbf_batch_capture(lbf_batch_t b, const void *const *d_in, void *const
   return LBF_OK;
 }
 
+lbf_status lbf_batch_launches(lbf_batch_t b, int32_t *n_launches) {
+  if (!b || b->magic != kBatchMagic) return LBF_ESTATE;
+  if (!n_launches) return LBF_EINVAL;
+  // classes of the tables last filled (lbf_batch_run, lbf_batch_capture or lbf_batch_tune)
+  if (b->per_plan) {   // per plan: filter bank + history (+ FP32 beam former) each; grouped tensor cores
+    int k = 0;
+    for (lbf_plan_t p : b->plans) k += p->M ? (p->tc ? 2 : 3) : 0;
+    int tc_classes = 0;
+    std::vector<long long> seen;
+    for (lbf_plan_t p : b->plans) {
+      if (!p->tc || p->M == 0) continue;
+      const long long cls = (long long)p->out_kind * 64 + (p->out_kind == lbf::OUT_VOLTAGES ? 1 : p->Q);
+      int same = 0;
+      for (long long c : seen) same += c == cls;
+      if (same % lbf::tc_max_plans_per_launch() == 0) ++tc_classes;
+      seen.push_back(cls);
+      if (p->inc) ++tc_classes;
+    }
+    *n_launches = k + tc_classes;
+    return LBF_OK;
+  }
+  int tc_classes = 0;
+  std::vector<long long> seen;
+  for (lbf_plan_t p : b->plans) {
+    if (!p->tc || p->M == 0) continue;
+    const long long cls = (long long)p->out_kind * 64 + (p->out_kind == lbf::OUT_VOLTAGES ? 1 : p->Q);
+    int same = 0;
+    for (long long c : seen) same += c == cls;
+    if (same % lbf::tc_max_plans_per_launch() == 0) ++tc_classes;
+    seen.push_back(cls);
+    if (p->inc) ++tc_classes;   // its incoherent-beam kernel
+  }
+  *n_launches = (int32_t)(b->ppf_cls.size() + 1 + b->bf_cls.size()) + tc_classes;
+  return LBF_OK;
+}
+
 lbf_status lbf_batch_launch(lbf_batch_t b, void *stream) {
   if (!b || b->magic != kBatchMagic) return LBF_ESTATE;
   if (!b->graph[0] || !b->graph[1]) return LBF_ESTATE;
@@ -315,15 +401,23 @@ lbf_status lbf_batch_tune(lbf_batch_t b, const void *const *d_in, void *const *d
   if (s != LBF_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
   const int n = (int)b->plans.size();
-  const int spcs[3] = {64, 128, 256};
-  std::vector<int> base(n), alt(n);
-  bool has_mid = false;
+  // spectra per filter-bank item: a quarter, half, or all of a stream's block (1024 >= M here)
+  const int spcs[3] = {64, 256, 1024};
+  // beam-former choices: 0 each plan's own; 1 plans with 9..64 beams switched between the few- and
+  // many-beam kernels; 2 plans with more than 8 beams switched between the 128- and 64-beam tiles
+  std::vector<int> choice[3];
+  bool has[3] = {true, false, false};
+  for (int k = 0; k < 3; ++k) choice[k].resize(n);
   for (int i = 0; i < n; ++i) {
     lbf_plan_t p = b->plans[i];
-    base[i] = p->variant;
-    const bool mid = !p->tc && p->B > 8 && p->B <= 64 && p->S <= lbf::many_beam_max_stations();
-    alt[i] = mid ? (p->variant == 1 ? 2 : 1) : p->variant;
-    has_mid = has_mid || mid;
+    const int v = p->variant;
+    choice[0][i] = v;
+    const bool fp32_many_ok = !p->tc && p->B > 8 && p->S <= lbf::many_beam_max_stations();
+    const bool mid = fp32_many_ok && p->B <= 64;
+    choice[1][i] = mid ? (v == 1 ? 2 : 1) : v;
+    choice[2][i] = fp32_many_ok ? (v == 3 ? 2 : 3) : v;
+    has[1] = has[1] || mid;
+    has[2] = has[2] || fp32_many_ok;
   }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -333,8 +427,10 @@ lbf_status lbf_batch_tune(lbf_batch_t b, const void *const *d_in, void *const *d
   lbf_batch_tuning t;
   std::memset(&t, 0, sizeof(t));
   cudaError_t e = cudaSuccess;
-  for (int v = 0; v < (has_mid ? 2 : 1) && e == cudaSuccess; ++v) {
-    b->variant = v ? alt : base;
+  int idx = 0;
+  for (int v = 0; v < 3 && e == cudaSuccess; ++v) {
+    if (!has[v]) continue;
+    b->variant = choice[v];
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
       b->spc = spcs[k];
       e = cudaStreamSynchronize(st);
@@ -347,21 +443,44 @@ lbf_status lbf_batch_tune(lbf_batch_t b, const void *const *d_in, void *const *d
       float ms = 0.f;
       if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
       ms /= reps;
-      const int idx = v * 3 + k;
       t.ms[idx] = ms;
       t.spc[idx] = spcs[k];
-      t.mid_variant[idx] = v ? 1 : 0;
+      t.mid_variant[idx] = v;
+      ++idx;
       if (e == cudaSuccess && ms < best) { best = ms; best_spc = spcs[k]; best_v = v; }
     }
   }
-  t.n_candidates = has_mid ? 6 : 3;
-  t.best_spc = best_spc;
+  // the per-plan mode (each plan's own FP32 kernels in the graph), with the best beam-former choice
+  bool best_pp = false;
+  if (e == cudaSuccess) {
+    b->variant = choice[best_v];
+    b->per_plan = true;
+    e = cudaStreamSynchronize(st);
+    fill_tables(b, 0, d_in, d_out);
+    if (e == cudaSuccess) e = enqueue(b, 0, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = enqueue(b, 0, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    ms /= reps;
+    t.ms[idx] = ms;
+    t.spc[idx] = 0;
+    t.mid_variant[idx] = best_v;
+    ++idx;
+    if (e == cudaSuccess && ms < best) { best = ms; best_pp = true; }
+    b->per_plan = false;
+  }
+  t.n_candidates = idx;
+  t.best_spc = best_pp ? 0 : best_spc;
   t.best_mid_variant = best_v;
   t.best_ms = best;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   b->spc = best_spc;
-  b->variant = best_v ? alt : base;
+  b->variant = choice[best_v];
+  b->per_plan = best_pp;
   // the candidate runs advanced nothing (parity-0 tables, histories untouched by design of the
   // tables: each run read hist[cur] and wrote hist[cur^1]); restart every stream cleanly
   for (lbf_plan_t p : b->plans) {

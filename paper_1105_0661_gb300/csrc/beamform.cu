@@ -160,21 +160,30 @@ __device__ __forceinline__ void cp_async8(void *smem_dst, const void *gmem_src, 
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(gmem_src), "r"(src_bytes) : "memory");
 }
 
-// Thread tile: beams 4 bg .. 4 bg + 3 of the CTA's 128, spectra {2 mg, 2 mg + 1, 16 + 2 mg,
-// 17 + 2 mg} of the 32-spectrum pass (so each 16-byte shared load of a warp covers 128 contiguous
-// bytes), both pols: 32 complex accumulators, four scalar FMAs per complex multiply-add.
-// The station loop is not unrolled, walks two pointers, and has the beams innermost: measured on
-// the LOFAR block, this lowers the FP32 pipe's dispatch stalls (11 % faster than unrolling by 2
-// with the spectra innermost), as does the planar weight layout (another 4 %).
-// Work item: (subband, channel) fc, beams bt * 128 .. + 127.
-template <int OUT>
+// Two tile shapes, both 256 threads and 32-spectrum passes:
+//  * BT = 128 beams per CTA: thread tile beams 4 bg .. 4 bg + 3 (bg = tid / 8), spectra {2 mg,
+//    2 mg + 1, 16 + 2 mg, 17 + 2 mg} (mg = tid % 8) of the pass, both pols: 32 complex
+//    accumulators, 6 16-byte shared loads per station for 128 FFMAs;
+//  * BT = 64 beams per CTA: beams 4 bg .. +3 (bg = tid / 16), spectra {2 mg, 2 mg + 1}
+//    (mg = tid % 16): 16 complex accumulators, 4 loads per 64 FFMAs, a third of the shared memory
+//    per CTA (three CTAs per SM).  A plan whose beam count leaves most of a 128-beam tile empty
+//    (24, 154 or 269 beams) wastes less work in 64-beam tiles.
+// Each 16-byte shared load of a warp covers 128 contiguous bytes.  Four scalar FMAs per complex
+// multiply-add.  The station loop is not unrolled, walks two pointers, and has the beams
+// innermost: measured on the LOFAR block, this lowers the FP32 pipe's dispatch stalls (11 %
+// faster than unrolling by 2 with the spectra innermost), as does the planar weight layout
+// (another 4 %).
+// Work item: (subband, channel) fc, beams bt * BT .. + BT - 1.
+template <int OUT, int BT>
 __device__ __forceinline__ void bf_many_item(const Geometry &g, const float2 *__restrict__ ct, void *__restrict__ out,
                                              int fc, int bt, float2 *smem) {
-  float2 *wsm = smem;                      // [S][kBT / 4][re x4, im x4]
-  float2 *ysm = smem + (size_t)g.S * kBT;  // [2 buffers][S][kP][kMC]
+  constexpr int kJ = BT == 128 ? 4 : 2;   // spectra per thread in a pass
+  constexpr int kLanesM = kMC / kJ;       // threads sharing a beam group (8 or 16)
+  float2 *wsm = smem;                     // [S][BT / 4][re x4, im x4]
+  float2 *ysm = smem + (size_t)g.S * BT;  // [2 buffers][S][kP][kMC]
   const int tid = threadIdx.x;
   const int f = fc / kN, c = fc - f * kN;
-  const int bbase = bt * kBT;
+  const int bbase = bt * BT;
   const float2 *y = ct + (long long)fc * g.S * kP * g.M;
   const int rows = g.S * kP;
   const size_t ybuf = (size_t)rows * kMC;
@@ -204,15 +213,17 @@ __device__ __forceinline__ void bf_many_item(const Geometry &g, const float2 *__
 
   // weights of each group of four beams stored planar: re[4] then im[4], so that a beam's real
   // and imaginary parts land in registers of the same parity (see the inner loop)
-  for (int i = tid; i < g.S * kBT; i += kManyThreads) {
-    const int s = i / kBT, bl = i - s * kBT, b = bbase + bl;
+  for (int i = tid; i < g.S * BT; i += kManyThreads) {
+    const int s = i / BT, bl = i - s * BT, b = bbase + bl;
     const float2 w = (b < g.B) ? beam_weight(g, f, c, (long long)b * g.S + s) : make_float2(0.f, 0.f);
-    float *wg = reinterpret_cast<float *>(wsm + s * kBT + (bl & ~3));
+    float *wg = reinterpret_cast<float *>(wsm + s * BT + (bl & ~3));
     wg[bl & 3] = w.x;
     wg[4 + (bl & 3)] = w.y;
   }
-  const int bg = tid >> 3;   // beams bbase + 4 bg .. +3
-  const int mg = tid & 7;    // spectra 2 mg, 2 mg + 1, 16 + 2 mg, 17 + 2 mg of the pass
+  const int bg = tid / kLanesM;   // beams bbase + 4 bg .. +3
+  const int mg = tid % kLanesM;   // spectra 2 mg, 2 mg + 1 (and 16 + 2 mg, 17 + 2 mg for BT = 128)
+  // spectrum of accumulator jm within the pass
+  auto mof = [&](int jm) { return 16 * (jm >> 1) + 2 * mg + (jm & 1); };
   const int nS = (OUT == OUT_STOKES_IQUV) ? 4 : 1;
   const int Mq = (OUT == OUT_VOLTAGES) ? 0 : g.M / g.Q;
 
@@ -236,29 +247,34 @@ __device__ __forceinline__ void bf_many_item(const Geometry &g, const float2 *__
       }
     }
 
-    float2 acc[4][kP][4];
+    float2 acc[4][kP][kJ];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int pol = 0; pol < kP; ++pol)
 #pragma unroll
-        for (int jm = 0; jm < 4; ++jm) acc[i][pol][jm] = make_float2(0.f, 0.f);
+        for (int jm = 0; jm < kJ; ++jm) acc[i][pol][jm] = make_float2(0.f, 0.f);
 
     const float4 *wp = reinterpret_cast<const float4 *>(wsm + bg * 4);
     const float4 *yp = reinterpret_cast<const float4 *>(yb + 2 * mg);
 #pragma unroll 1
-    for (int s = 0; s < g.S; ++s, wp += kBT / 2, yp += kP * kMC / 2) {
+    for (int s = 0; s < g.S; ++s, wp += BT / 2, yp += kP * kMC / 2) {
       const float4 wre = wp[0], wim = wp[1];
       const float2 w[4] = {make_float2(wre.x, wim.x), make_float2(wre.y, wim.y),
                            make_float2(wre.z, wim.z), make_float2(wre.w, wim.w)};
 #pragma unroll
       for (int pol = 0; pol < kP; ++pol) {
+        float2 yv[kJ];
         const float4 ya = yp[pol * (kMC / 2)];
-        const float4 yc = yp[pol * (kMC / 2) + 8];
-        const float2 yv[4] = {make_float2(ya.x, ya.y), make_float2(ya.z, ya.w),
-                              make_float2(yc.x, yc.y), make_float2(yc.z, yc.w)};
+        yv[0] = make_float2(ya.x, ya.y);
+        yv[1] = make_float2(ya.z, ya.w);
+        if constexpr (kJ == 4) {
+          const float4 yc = yp[pol * (kMC / 2) + 8];
+          yv[2] = make_float2(yc.x, yc.y);
+          yv[3] = make_float2(yc.z, yc.w);
+        }
 #pragma unroll
-        for (int jm = 0; jm < 4; ++jm)
+        for (int jm = 0; jm < kJ; ++jm)
 #pragma unroll
           for (int i = 0; i < 4; ++i) cmac(acc[i][pol][jm], w[i], yv[jm]);
       }
@@ -273,8 +289,8 @@ __device__ __forceinline__ void bf_many_item(const Geometry &g, const float2 *__
 #pragma unroll
         for (int pol = 0; pol < kP; ++pol)
 #pragma unroll
-          for (int jm = 0; jm < 4; ++jm) {
-            const int m = mc + 16 * (jm >> 1) + 2 * mg + (jm & 1);
+          for (int jm = 0; jm < kJ; ++jm) {
+            const int m = mc + mof(jm);
             if (m < g.M) vol[((((long long)b * g.F + f) * kN + c) * kP + pol) * g.M + m] = acc[i][pol][jm];
           }
       }
@@ -285,27 +301,29 @@ __device__ __forceinline__ void bf_many_item(const Geometry &g, const float2 *__
         const int b = bbase + bg * 4 + i;
 #pragma unroll
         for (int st = 0; st < nS; ++st) {
-          float v[4];
+          float v[kJ];
 #pragma unroll
-          for (int jm = 0; jm < 4; ++jm) v[jm] = stokes_param(st, acc[i][0][jm], acc[i][1][jm]);
+          for (int jm = 0; jm < kJ; ++jm) v[jm] = stokes_param(st, acc[i][0][jm], acc[i][1][jm]);
           float *orow = o + ((((long long)b * nS + st) * g.F + f) * kN + c) * Mq;
           if (g.Q == 1) {
 #pragma unroll
-            for (int jm = 0; jm < 4; ++jm) {
-              const int m = mc + 16 * (jm >> 1) + 2 * mg + (jm & 1);
+            for (int jm = 0; jm < kJ; ++jm) {
+              const int m = mc + mof(jm);
               if (b < g.B && m < g.M) orow[m] = v[jm];
             }
-          } else if (g.Q == 32) {
-            float sum = (v[0] + v[1]) + (v[2] + v[3]);
-            for (int o2 = 1; o2 < 8; o2 <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o2);
+          } else if (kJ == 4 && g.Q == 32) {
+            float sum = (v[0] + v[1]) + (v[kJ - 2] + v[kJ - 1]);
+            for (int o2 = 1; o2 < kLanesM; o2 <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o2);
             if (b < g.B && mg == 0 && mc < g.M) orow[mc / 32] = sum;
           } else {
-            // windows of Q consecutive spectra: pair sums, then across Q/2 lanes of mg
+            // windows of Q consecutive spectra: pair sums, then across the Q/2 lanes of mg that
+            // hold the window's other pairs (BT = 64: all 32 spectra of the pass are in one run
+            // of 16 lanes, so Q = 32 is this case too)
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < kJ / 2; ++h) {
               float sum = v[2 * h] + v[2 * h + 1];
 #pragma unroll
-              for (int o2 = 1; o2 < 8; o2 <<= 1)
+              for (int o2 = 1; o2 < kLanesM; o2 <<= 1)
                 if (o2 < g.Q / 2) sum += __shfl_xor_sync(0xffffffffu, sum, o2);
               const int m = mc + 16 * h + 2 * mg;
               if (b < g.B && m < g.M && (mg & (g.Q / 2 - 1)) == 0) orow[m / g.Q] = sum;
@@ -319,18 +337,23 @@ __device__ __forceinline__ void bf_many_item(const Geometry &g, const float2 *__
   asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
-template <int OUT>
-__global__ void __launch_bounds__(kManyThreads, 2)
+// Three 64-beam CTAs per SM fit the shared memory; the IQUV epilogue needs more than the 85
+// registers per thread that three CTAs leave, so that form runs two.
+template <int OUT, int BT>
+__global__ void __launch_bounds__(kManyThreads, (BT == 128 || OUT == OUT_STOKES_IQUV) ? 2 : 3)
 bf_many_kernel(Geometry g, const float2 *__restrict__ ct, void *__restrict__ out, int nbt) {
   extern __shared__ __align__(16) float2 smem[];
   const int fc = blockIdx.x / nbt;
-  bf_many_item<OUT>(g, ct, out, fc, blockIdx.x - fc * nbt, smem);
+  bf_many_item<OUT, BT>(g, ct, out, fc, blockIdx.x - fc * nbt, smem);
 }
 
 // Persistent beam former over the blocks of several observations (a batch): CTAs take work items
-// (subband-channel, beam group) from a shared counter; each item runs the few- or many-beam body
-// its observation was tuned to, with that observation's output kind.
-__global__ void __launch_bounds__(kManyThreads, 2)
+// (subband-channel, beam group) from a shared counter; each item runs the body of variant V (1 few,
+// 2 many with 128-beam tiles, 3 many with 64-beam tiles) for output kind OUT.  One launch per
+// (variant, output kind, residency) class, so that each body keeps its own registers and shared
+// memory footprint, as when its observation runs alone.
+template <int V, int OUT>
+__global__ void __launch_bounds__(kManyThreads, (V == 3 && OUT != OUT_STOKES_IQUV) ? 3 : 2)
 bf_group_kernel(const BfGroup *__restrict__ grp, int ngrp, long long total, unsigned long long *counter) {
   extern __shared__ __align__(16) float2 smem[];
   __shared__ long long item_s;
@@ -345,15 +368,27 @@ bf_group_kernel(const BfGroup *__restrict__ grp, int ngrp, long long total, unsi
     const BfGroup &G = grp[o];
     const long long local = item - G.first_item;
     const int fc = (int)(local / G.per_fc), sub = (int)(local - (long long)fc * G.per_fc);
-    if (G.variant == 1) {
-      if (G.out_kind == OUT_STOKES_I) bf_few_item<OUT_STOKES_I>(G.g, G.ct, G.out, fc, sub, smem);
-      else if (G.out_kind == OUT_STOKES_IQUV) bf_few_item<OUT_STOKES_IQUV>(G.g, G.ct, G.out, fc, sub, smem);
-      else bf_few_item<OUT_VOLTAGES>(G.g, G.ct, G.out, fc, sub, smem);
-    } else {
-      if (G.out_kind == OUT_STOKES_I) bf_many_item<OUT_STOKES_I>(G.g, G.ct, G.out, fc, sub, smem);
-      else if (G.out_kind == OUT_STOKES_IQUV) bf_many_item<OUT_STOKES_IQUV>(G.g, G.ct, G.out, fc, sub, smem);
-      else bf_many_item<OUT_VOLTAGES>(G.g, G.ct, G.out, fc, sub, smem);
-    }
+    if constexpr (V == 1) bf_few_item<OUT>(G.g, G.ct, G.out, fc, sub, smem);
+    else if constexpr (V == 3) bf_many_item<OUT, 64>(G.g, G.ct, G.out, fc, sub, smem);
+    else bf_many_item<OUT, 128>(G.g, G.ct, G.out, fc, sub, smem);
+  }
+}
+
+template <int BT>
+cudaError_t launch_many(const Geometry &g, int out_kind, const float2 *ct, void *out, cudaStream_t st) {
+  const int nbt = (g.B + BT - 1) / BT;
+  const long long ctas = (long long)g.F * kN * nbt;
+  const size_t smem = (size_t)g.S * (BT + 2 * kP * kMC) * sizeof(float2);
+  auto go = [&](auto kern) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)ctas, kManyThreads, smem, st>>>(g, ct, out, nbt);
+    return cudaGetLastError();
+  };
+  switch (out_kind) {
+    case OUT_VOLTAGES: return go(bf_many_kernel<OUT_VOLTAGES, BT>);
+    case OUT_STOKES_I: return go(bf_many_kernel<OUT_STOKES_I, BT>);
+    default: return go(bf_many_kernel<OUT_STOKES_IQUV, BT>);
   }
 }
 
@@ -385,45 +420,92 @@ cudaError_t launch_beamform(const Geometry &g, int variant, int out_kind, const 
     }
     return cudaGetLastError();
   }
-  const int nbt = (g.B + kBT - 1) / kBT;
-  const long long ctas = (long long)g.F * kN * nbt;
-  const size_t smem = (size_t)g.S * (kBT + 2 * kP * kMC) * sizeof(float2);
-  cudaError_t e;
-  switch (out_kind) {
-    case OUT_VOLTAGES:
-      e = cudaFuncSetAttribute(bf_many_kernel<OUT_VOLTAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      bf_many_kernel<OUT_VOLTAGES><<<(unsigned)ctas, kManyThreads, smem, st>>>(g, ct, out, nbt);
-      break;
-    case OUT_STOKES_I:
-      e = cudaFuncSetAttribute(bf_many_kernel<OUT_STOKES_I>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      bf_many_kernel<OUT_STOKES_I><<<(unsigned)ctas, kManyThreads, smem, st>>>(g, ct, out, nbt);
-      break;
-    default:
-      e = cudaFuncSetAttribute(bf_many_kernel<OUT_STOKES_IQUV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      bf_many_kernel<OUT_STOKES_IQUV><<<(unsigned)ctas, kManyThreads, smem, st>>>(g, ct, out, nbt);
-      break;
-  }
+  if (variant == 3) return launch_many<64>(g, out_kind, ct, out, st);
+  return launch_many<128>(g, out_kind, ct, out, st);
+}
+
+namespace {
+
+template <int V, int OUT>
+cudaError_t launch_group_t(const BfGroup *d_groups, int ngrp, long long total, unsigned long long *counter,
+                           size_t smem, cudaStream_t st) {
+  auto kern = bf_group_kernel<V, OUT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  // persistent: as many CTAs as are resident at once (registers and this launch's shared memory)
+  int per_sm = 0, dev = 0, sms = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kManyThreads, smem);
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  kern<<<per_sm * sms, kManyThreads, smem, st>>>(d_groups, ngrp, total, counter);
   return cudaGetLastError();
 }
 
-cudaError_t launch_bf_group(const BfGroup *d_groups, int ngrp, long long total, unsigned long long *counter,
-                            int ctas, size_t smem, cudaStream_t st) {
+template <int V>
+cudaError_t launch_group_v(int out_kind, const BfGroup *d_groups, int ngrp, long long total,
+                           unsigned long long *counter, size_t smem, cudaStream_t st) {
+  if (out_kind == OUT_STOKES_I) return launch_group_t<V, OUT_STOKES_I>(d_groups, ngrp, total, counter, smem, st);
+  if (out_kind == OUT_STOKES_IQUV) return launch_group_t<V, OUT_STOKES_IQUV>(d_groups, ngrp, total, counter, smem, st);
+  return launch_group_t<V, OUT_VOLTAGES>(d_groups, ngrp, total, counter, smem, st);
+}
+
+template <int V, int OUT>
+int residency_t(size_t smem) {
+  auto kern = bf_group_kernel<V, OUT>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kManyThreads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm;
+}
+
+template <int V>
+int residency_v(int out_kind, size_t smem) {
+  if (out_kind == OUT_STOKES_I) return residency_t<V, OUT_STOKES_I>(smem);
+  if (out_kind == OUT_STOKES_IQUV) return residency_t<V, OUT_STOKES_IQUV>(smem);
+  return residency_t<V, OUT_VOLTAGES>(smem);
+}
+
+}  // namespace
+
+cudaError_t launch_bf_group(int variant, int out_kind, const BfGroup *d_groups, int ngrp, long long total,
+                            unsigned long long *counter, size_t smem, cudaStream_t st) {
   if (total == 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(bf_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
-  if (e != cudaSuccess) return e;
-  bf_group_kernel<<<ctas, kManyThreads, smem, st>>>(d_groups, ngrp, total, counter);
-  return cudaGetLastError();
+  if (variant == 1) return launch_group_v<1>(out_kind, d_groups, ngrp, total, counter, smem, st);
+  if (variant == 3) return launch_group_v<3>(out_kind, d_groups, ngrp, total, counter, smem, st);
+  return launch_group_v<2>(out_kind, d_groups, ngrp, total, counter, smem, st);
+}
+
+int bf_group_residency(int variant, int out_kind, size_t smem) {
+  if (variant == 1) return residency_v<1>(out_kind, smem);
+  if (variant == 3) return residency_v<3>(out_kind, smem);
+  return residency_v<2>(out_kind, smem);
 }
 
 int few_beams_per_item() { return kFewBeams; }
-int many_beams_per_item() { return kBT; }
+int many_beams_per_item(int variant) { return variant == 3 ? 64 : kBT; }
 size_t bf_smem_bytes(int variant, int S) {
-  return variant == 1 ? (size_t)S * kFewBeams * sizeof(float2) : (size_t)S * (kBT + 2 * kP * kMC) * sizeof(float2);
+  if (variant == 1) return (size_t)S * kFewBeams * sizeof(float2);
+  return (size_t)S * ((variant == 3 ? 64 : kBT) + 2 * kP * kMC) * sizeof(float2);
+}
+
+// Beam-former choice for AUTO: the few-beam kernel up to 8 beams; beyond, the many-beam tile
+// (128 or 64 beams per CTA) that leaves the fewest tile slots empty, a 64-beam slot counted as
+// 1.15 of a 128-beam one (the narrower tile issues more shared loads per FMA).
+int auto_bf_variant(int B, int S) {
+  if (B <= 8 || S > many_beam_max_stations()) return 1;
+  const double slots128 = (double)((B + 127) / 128) * 128.0;
+  const double slots64 = (double)((B + 63) / 64) * 64.0 * 1.15;
+  return slots64 < slots128 ? 3 : 2;
 }
 
 // Largest station count the many-beam kernel accepts (its shared memory holds S x (128 + 64) cf32).

@@ -73,7 +73,7 @@ lbf_status validate(const lbf_config *c) {
   if (c->sample_bits != 16 && c->sample_bits != 8) return LBF_EINVAL;
   if (c->output != LBF_VOLTAGES && c->output != LBF_STOKES_I && c->output != LBF_STOKES_IQUV) return LBF_EINVAL;
   if (c->precision != LBF_FP32 && c->precision != LBF_FP16_TC) return LBF_EINVAL;
-  if (c->bf_variant < LBF_BF_AUTO || c->bf_variant > LBF_BF_MANY) return LBF_EINVAL;
+  if (c->bf_variant < LBF_BF_AUTO || c->bf_variant > LBF_BF_MANY64) return LBF_EINVAL;
   if ((c->flags & ~(LBF_FLAG_EXTERNAL_WORKSPACE | LBF_FLAG_INCOHERENT_BEAM)) != 0) return LBF_EINVAL;
   if ((c->flags & LBF_FLAG_INCOHERENT_BEAM) && c->output == LBF_VOLTAGES) return LBF_EINVAL;
   if (!is_pow2_upto32(c->int_factor)) return LBF_EINVAL;
@@ -87,7 +87,9 @@ lbf_status validate(const lbf_config *c) {
   for (int i = 0; i < 2 * c->n_beams; ++i) if (!std::isfinite(c->beam_dlm[i])) return LBF_EINVAL;
   if (c->n_channels != lbf::kN || c->n_taps != lbf::kL) return LBF_EUNSUPPORTED;
   if (c->precision == LBF_FP16_TC && c->n_stations > lbf::tc_max_stations()) return LBF_EUNSUPPORTED;
-  if (c->bf_variant == LBF_BF_MANY && c->n_stations > lbf::many_beam_max_stations()) return LBF_EUNSUPPORTED;
+  if ((c->bf_variant == LBF_BF_MANY || c->bf_variant == LBF_BF_MANY64) && c->precision == LBF_FP32 &&
+      c->n_stations > lbf::many_beam_max_stations())
+    return LBF_EUNSUPPORTED;
   // index arithmetic: per-plan sizes must keep grid dimensions in range
   const long long ctas = (long long)c->n_subbands * lbf::kN * ((c->n_beams + 7) / 8);
   if (ctas >= (1LL << 31)) return LBF_EUNSUPPORTED;
@@ -154,11 +156,11 @@ lbf_status check_call(lbf_plan_t p) {
 }
 
 enum KernelId { K_PPF = 0, K_PPF_CT, K_HIST, K_DELAY, K_BF_FEW, K_BF_MANY, K_STOKES, K_PPF_CT16, K_BF_TC,
-                K_CT16, K_INC16, K_DEDISP, K_SS, K_COUNT };
+                K_CT16, K_INC16, K_DEDISP, K_SS, K_BF_MANY64, K_COUNT };
 static_assert(K_COUNT <= 16, "lbf_trace holds 16 kernels");
 const char *const kKernelNames[K_COUNT] = {"ppf", "ppf_ct", "hist_update", "delay_ct", "bf_few", "bf_many",
                                            "stokes", "ppf_ct16", "bf_tc", "ct_to_ct16", "incoherent_ct16",
-                                           "dedisperse", "superstation"};
+                                           "dedisperse", "superstation", "bf_many64"};
 
 // Launch through `fn`, bracketed by trace events when a trace is active.
 template <typename Fn>
@@ -185,7 +187,7 @@ void trace_free(lbf_plan_t p) {
   p->tracing = false;
 }
 
-int bf_kernel_id(lbf_plan_t p) { return p->variant == 1 ? K_BF_FEW : K_BF_MANY; }
+int bf_kernel_id(lbf_plan_t p) { return p->variant == 1 ? K_BF_FEW : p->variant == 3 ? K_BF_MANY64 : K_BF_MANY; }
 
 // The fused path on device buffers (a1-a7).  `ws` is the scratch of this call: the FP32
 // corner-turned block, or the FP16 planes of a tensor-core plan (with `maps` their descriptors).
@@ -265,7 +267,7 @@ lbf_status lbf_plan(const lbf_config *cfg, lbf_plan_t *out) {
               : cfg->output == LBF_STOKES_IQUV ? lbf::OUT_STOKES_IQUV : lbf::OUT_VOLTAGES;
   p->nS = cfg->output == LBF_STOKES_I ? 1 : cfg->output == LBF_STOKES_IQUV ? 4 : 0;
   if (cfg->bf_variant == LBF_BF_AUTO)
-    p->variant = (p->B <= 8 || p->S > lbf::many_beam_max_stations()) ? 1 : 2;
+    p->variant = lbf::auto_bf_variant(p->B, p->S);
   else
     p->variant = cfg->bf_variant;
   // Tensor cores only where the beam count makes the beam former a dense contraction: a
@@ -381,7 +383,8 @@ lbf_status lbf_plan_dims(lbf_plan_t p, lbf_dims *d) {
   std::memset(d, 0, sizeof(*d));
   d->n_stations = p->S; d->n_subbands = p->F; d->n_channels = p->N; d->n_taps = p->L;
   d->n_beams = p->B; d->block_samples = p->T; d->int_factor = p->Q; d->n_spectra = p->M;
-  d->n_stokes = p->nS; d->d_max = p->d_max; d->history_samples = p->H; d->bf_kernel = p->tc ? 3 : p->variant;
+  d->n_stokes = p->nS; d->d_max = p->d_max; d->history_samples = p->H;
+  d->bf_kernel = p->tc ? 3 : p->variant == 3 ? 4 : p->variant;
   const size_t cplx = (size_t)p->S * p->F * lbf::kP * p->T * sizeof(float2);
   d->in_bytes = (size_t)p->S * p->F * p->T * p->word;
   d->chan_bytes = cplx;

@@ -64,7 +64,7 @@ struct BfGroup {
   Geometry g;
   const float2 *ct;
   void *out;
-  int variant;                // 1 few-beam, 2 many-beam
+  int variant;                // 1 few-beam, 2 many-beam (128-beam tiles), 3 many-beam (64-beam tiles)
   int out_kind;
   int per_fc;                 // work items per (subband, channel): beam groups or beam tiles
   long long first_item;
@@ -75,16 +75,23 @@ struct BfGroup {
 cudaError_t launch_ppf(const Geometry &g, int bits, const void *in, const void *hist,
                        float2 *chan, float2 *ct, cudaStream_t st, const Ct16Out *ct16 = nullptr);
 // batch: persistent grouped filter bank (FP32 corner-turned output), history update, beam former
-cudaError_t launch_ppf_group(const PpfGroup *d_groups, int ngrp, long long total, unsigned long long *counter,
-                             int ctas, cudaStream_t st);
+// one persistent launch for the groups of one sample width and output form (FP32 corner turn or
+// FP16 planes); items numbered from 0 within the class
+cudaError_t launch_ppf_group(int bits, int tc, const PpfGroup *d_groups, int ngrp, long long total,
+                             unsigned long long *counter, int ctas, cudaStream_t st);
 cudaError_t launch_hist_group(const PpfGroup *d_groups, int ngrp, long long total, cudaStream_t st);
 // filter-bank work items (both polarisations of one stream chunk) per (station, subband) stream
 int ppf_items_per_stream(int M, int spc);
 int ppf_ctas_per_sm();
-cudaError_t launch_bf_group(const BfGroup *d_groups, int ngrp, long long total, unsigned long long *counter,
-                            int ctas, size_t smem, cudaStream_t st);
+// one persistent launch for groups of one beam-former variant (1, 2 or 3) and output kind, sized to
+// the residency of that kernel with `smem` bytes of shared memory (bf_group_residency)
+cudaError_t launch_bf_group(int variant, int out_kind, const BfGroup *d_groups, int ngrp, long long total,
+                            unsigned long long *counter, size_t smem, cudaStream_t st);
+int bf_group_residency(int variant, int out_kind, size_t smem);
 int few_beams_per_item();
-int many_beams_per_item();
+int many_beams_per_item(int variant);   // 128 (variant 2) or 64 (variant 3)
+// AUTO beam-former choice: 1 few-beam, 2 many-beam 128-beam tiles, 3 many-beam 64-beam tiles
+int auto_bf_variant(int B, int S);
 size_t bf_smem_bytes(int variant, int S);
 // FP32 corner-turned [F][N][S][P][M] -> FP16 [F][N][P][M][kpad] hi/lo planes (split-call TC path)
 cudaError_t launch_ct_to_ct16(const Geometry &g, const float2 *ct, const Ct16Out &o, cudaStream_t st);
@@ -118,6 +125,7 @@ cudaError_t launch_hist_update(const Geometry &g, int bits, const void *in, cons
 // a4 standalone: chan -> ct
 cudaError_t launch_delay_ct(const Geometry &g, const float2 *chan, float2 *ct, cudaStream_t st);
 // a5-a6 (+ a7): beam former; out_kind selects voltages or fused Stokes; variant 1 few, 2 many
+// (128-beam tiles), 3 many (64-beam tiles)
 cudaError_t launch_beamform(const Geometry &g, int variant, int out_kind, const float2 *ct,
                             void *out, cudaStream_t st);
 // plan-time FP64 tables of the weight phases (tables.cu)

@@ -494,19 +494,19 @@ ppf_kernel(Geometry g, const typename SampleIO<BITS>::word *__restrict__ in,
 
 // Persistent filter bank over the blocks of several observations (a batch): CTAs take work items
 // (stream, spectrum chunk: both polarisations) from a shared counter until all groups are done.
-// The shared memory is laid out for the larger (16-bit) samples.
+// One launch per class of sample width and output form, so each body keeps the registers it has
+// when its observation runs alone.
+template <int BITS, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
 ppf_group_kernel(const PpfGroup *__restrict__ grp, int ngrp, long long total, unsigned long long *counter) {
+  using word = typename SampleIO<BITS>::word;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ long long item_s;
-  PpfSmem<16> &sm16 = *reinterpret_cast<PpfSmem<16> *>(smem_raw);
-  PpfSmem<8> &sm8 = *reinterpret_cast<PpfSmem<8> *>(smem_raw);
-  static_assert(sizeof(PpfSmem<8>) <= sizeof(PpfSmem<16>), "the 16-bit layout is the larger");
-  PpfCtl &ctl = sm16.ctl;   // the same object in both layouts
-  ppf_setup(ctl);
+  PpfSmem<BITS> &sm = *reinterpret_cast<PpfSmem<BITS> *>(smem_raw);
+  ppf_setup(sm.ctl);
   uint32_t ph = 0;
   for (;;) {
-    if (threadIdx.x == 0) item_s = ctl.abort ? total : (long long)atomicAdd(counter, 1ull);
+    if (threadIdx.x == 0) item_s = sm.ctl.abort ? total : (long long)atomicAdd(counter, 1ull);
     __syncthreads();
     const long long item = item_s;
     __syncthreads();
@@ -518,22 +518,26 @@ ppf_group_kernel(const PpfGroup *__restrict__ grp, int ngrp, long long total, un
     const long long sf = local / G.chunks;
     const int chunk = (int)(local - sf * G.chunks);
     const int s = (int)(sf / G.g.F), f = (int)(sf - (long long)s * G.g.F);
-    if (G.tc) {   // tensor-core plan: FP16 hi+lo planes
-      PpfOut po{nullptr, reinterpret_cast<__half *>(G.ct16.hi), reinterpret_cast<__half *>(G.ct16.lo), G.ct16.kpad};
-      if (G.bits == 16)
-        ppf_item<16, MODE_CT16>(G.g, (const uint2 *)G.in, (const uint2 *)G.hist, po, s, f, chunk, G.spc, sm16, ph);
-      else
-        ppf_item<8, MODE_CT16>(G.g, (const uint32_t *)G.in, (const uint32_t *)G.hist, po, s, f, chunk, G.spc, sm8, ph);
-    } else {
-      PpfOut po{G.ct, nullptr, nullptr, 0};
-      if (G.bits == 16)
-        ppf_item<16, MODE_CT32>(G.g, (const uint2 *)G.in, (const uint2 *)G.hist, po, s, f, chunk, G.spc, sm16, ph);
-      else
-        ppf_item<8, MODE_CT32>(G.g, (const uint32_t *)G.in, (const uint32_t *)G.hist, po, s, f, chunk, G.spc, sm8, ph);
-    }
+    const PpfOut po = MODE == MODE_CT16
+        ? PpfOut{nullptr, reinterpret_cast<__half *>(G.ct16.hi), reinterpret_cast<__half *>(G.ct16.lo), G.ct16.kpad}
+        : PpfOut{G.ct, nullptr, nullptr, 0};
+    ppf_item<BITS, MODE>(G.g, (const word *)G.in, (const word *)G.hist, po, s, f, chunk, G.spc, sm, ph);
   }
   __syncthreads();
-  ppf_drain(ctl);
+  ppf_drain(sm.ctl);
+}
+
+template <int BITS, int MODE>
+cudaError_t launch_group_t(const PpfGroup *d_groups, int ngrp, long long total, unsigned long long *counter, int ctas,
+                           cudaStream_t st) {
+  const size_t smem = sizeof(PpfSmem<BITS>);
+  auto kern = ppf_group_kernel<BITS, MODE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  kern<<<ctas, kThreads, smem, st>>>(d_groups, ngrp, total, counter);
+  return cudaGetLastError();
 }
 
 // History update of every observation of a batch: element i of the concatenated histories.
@@ -619,16 +623,13 @@ cudaError_t launch_ppf(const Geometry &g, int bits, const void *in, const void *
                     : launch_ppf_bits<8>(g, in, hist, chan, ct, ct16, st);
 }
 
-cudaError_t launch_ppf_group(const PpfGroup *d_groups, int ngrp, long long total, unsigned long long *counter,
-                             int ctas, cudaStream_t st) {
+cudaError_t launch_ppf_group(int bits, int tc, const PpfGroup *d_groups, int ngrp, long long total,
+                             unsigned long long *counter, int ctas, cudaStream_t st) {
   if (total == 0) return cudaSuccess;
-  const size_t smem = sizeof(PpfSmem<16>);   // the larger layout: items of either width
-  cudaError_t e = cudaFuncSetAttribute(ppf_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
-  if (e != cudaSuccess) return e;
-  ppf_group_kernel<<<ctas, kThreads, smem, st>>>(d_groups, ngrp, total, counter);
-  return cudaGetLastError();
+  if (bits == 16) return tc ? launch_group_t<16, MODE_CT16>(d_groups, ngrp, total, counter, ctas, st)
+                            : launch_group_t<16, MODE_CT32>(d_groups, ngrp, total, counter, ctas, st);
+  return tc ? launch_group_t<8, MODE_CT16>(d_groups, ngrp, total, counter, ctas, st)
+            : launch_group_t<8, MODE_CT32>(d_groups, ngrp, total, counter, ctas, st);
 }
 
 cudaError_t launch_hist_group(const PpfGroup *d_groups, int ngrp, long long total, cudaStream_t st) {

@@ -115,9 +115,10 @@ extern "C" lbf_status lbf_run_block_static(const lbf_config *c, const void *d_in
   if ((size_t)S * F * lbf::kP * (size_t)T * sizeof(float2) > kCtBytes) return LBF_ETOOBIG;
   if ((size_t)S * F * (size_t)H * word > kHistBytes) return LBF_ETOOBIG;
   if (tm.total > kTableBytes) return LBF_ETOOBIG;
-  if (c->bf_variant == LBF_BF_MANY && S > lbf::many_beam_max_stations()) return LBF_EUNSUPPORTED;
-  const int variant = c->bf_variant == LBF_BF_AUTO ? ((B <= 8 || S > lbf::many_beam_max_stations()) ? 1 : 2)
-                                                   : c->bf_variant;
+  if (c->bf_variant < LBF_BF_AUTO || c->bf_variant > LBF_BF_MANY64) return LBF_EINVAL;
+  if ((c->bf_variant == LBF_BF_MANY || c->bf_variant == LBF_BF_MANY64) && S > lbf::many_beam_max_stations())
+    return LBF_EUNSUPPORTED;
+  const int variant = c->bf_variant == LBF_BF_AUTO ? lbf::auto_bf_variant(B, S) : c->bf_variant;
   if (!on_device(d_in, word) || !on_device(d_out, c->output == LBF_VOLTAGES ? 8 : 4)) return LBF_EINVAL;
 
   // From here to the last enqueue the host-side state is in use: one caller at a time.  The lock

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liblbf.so")
 LBF_OK, LBF_EINVAL, LBF_ENOMEM, LBF_ECUDA, LBF_ESTATE, LBF_ETIMEOUT, LBF_EBUSY, LBF_EUNSUPPORTED, LBF_ETOOBIG = range(9)
 OUTPUTS = {"V": 0, "I": 1, "IQUV": 4}
 PRECISIONS = {"fp32": 0, "fp16tc": 1}
-BF_VARIANTS = {"auto": 0, "few": 1, "many": 2}
+BF_VARIANTS = {"auto": 0, "few": 1, "many": 2, "many64": 3}
 
 # Every symbol include/lbf.h declares; the test suite checks the library exports all of them.
 EXPORTED = ("lbf_plan", "lbf_plan_destroy", "lbf_plan_dims", "lbf_plan_shifts", "lbf_reset_state",
@@ -28,7 +28,7 @@ EXPORTED = ("lbf_plan", "lbf_plan_destroy", "lbf_plan_dims", "lbf_plan_shifts", 
             "lbf_upload_subbands", "lbf_download_subbands", "lbf_trace_begin", "lbf_trace_end",
             "lbf_device_status", "lbf_debug_stall_next", "lbf_run_block_static", "lbf_superstation", "lbf_dedisperse",
             "lbf_batch_create", "lbf_batch_destroy",
-            "lbf_batch_run", "lbf_batch_capture", "lbf_batch_launch", "lbf_batch_tune",
+            "lbf_batch_run", "lbf_batch_capture", "lbf_batch_launch", "lbf_batch_launches", "lbf_batch_tune",
             "lbf_measure_fp32_peak", "lbf_status_string", "lbf_version")
 
 
@@ -61,8 +61,8 @@ class _Trace(ctypes.Structure):
 
 
 class _Tuning(ctypes.Structure):
-    _fields_ = [("n_candidates", ctypes.c_int32), ("spc", ctypes.c_int32 * 6), ("mid_variant", ctypes.c_int32 * 6),
-                ("ms", ctypes.c_double * 6), ("best_spc", ctypes.c_int32), ("best_mid_variant", ctypes.c_int32),
+    _fields_ = [("n_candidates", ctypes.c_int32), ("spc", ctypes.c_int32 * 10), ("mid_variant", ctypes.c_int32 * 10),
+                ("ms", ctypes.c_double * 10), ("best_spc", ctypes.c_int32), ("best_mid_variant", ctypes.c_int32),
                 ("best_ms", ctypes.c_double)]
 
 
@@ -121,6 +121,7 @@ def load_library() -> ctypes.CDLL:
             "lbf_batch_run": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp], ctypes.c_int),
             "lbf_batch_capture": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp], ctypes.c_int),
             "lbf_batch_launch": ([vp, vp], ctypes.c_int),
+            "lbf_batch_launches": ([vp, i32p], ctypes.c_int),
             "lbf_batch_tune": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, ctypes.c_int32,
                                 ctypes.POINTER(_Tuning)], ctypes.c_int),
             "lbf_measure_fp32_peak": ([ctypes.c_int32, vp, ctypes.POINTER(_AluPeak)], ctypes.c_int),
@@ -425,6 +426,12 @@ class Batch:
 
     def launch(self, stream=None):
         _check(self._lib.lbf_batch_launch(self._h, _stream(stream)), "lbf_batch_launch")
+
+    def launches(self) -> int:
+        """Kernel launches of one batch block (as the tables were last filled)."""
+        n = ctypes.c_int32(0)
+        _check(self._lib.lbf_batch_launches(self._h, ctypes.byref(n)), "lbf_batch_launches")
+        return n.value
 
     def tune(self, d_ins, d_outs, reps=3, stream=None) -> dict:
         ins, outs = self._bufs(d_ins, d_outs)

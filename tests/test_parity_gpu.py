@@ -162,7 +162,8 @@ def test_corner_turn_is_exact_transpose(dev):
 
 
 # ----------------------------------------------------------------------------- a5-a6 beam former
-@pytest.mark.parametrize("variant,B", [("few", 5), ("many", 5), ("many", 133), ("few", 19)])
+@pytest.mark.parametrize("variant,B", [("few", 5), ("many", 5), ("many", 133), ("few", 19), ("many64", 5),
+                                       ("many64", 64), ("many64", 133)])
 def test_beamform_voltages_match_oracle(dev, variant, B):
     wl = _wl(B=B, out="V")
     p = _plan(wl, bf_variant=variant)
@@ -175,6 +176,17 @@ def test_beamform_voltages_match_oracle(dev, variant, B):
     ref = ob.beamform(ct.astype(np.complex128))
     err = _rel_rms(vol.cpu().numpy().astype(np.complex128), ref, (2, 3, 4))
     assert err.max() <= TOL, err.max()
+    p.close()
+
+
+@pytest.mark.parametrize("B,kernel", [(8, 1), (9, 4), (24, 4), (64, 4), (65, 2), (127, 2), (154, 4), (200, 2),
+                                      (269, 4), (472, 2)])
+def test_automatic_beam_former_choice(dev, B, kernel):
+    """AUTO: the few-beam kernel up to 8 beams, then the many-beam tile (128 beams: kernel 2, 64
+    beams: kernel 4) that leaves the fewest tile slots empty (a 64-beam slot weighed 1.15)."""
+    wl = _wl(B=B, F=1, T=16 * N)
+    p = _plan(wl)
+    assert p.dims.bf_kernel == kernel
     p.close()
 
 
@@ -197,8 +209,8 @@ def test_stokes_matches_oracle(dev, out, Q, M):
     p.close()
 
 
-@pytest.mark.parametrize("variant", ["few", "many"])
-@pytest.mark.parametrize("out,Q", [("I", 4), ("IQUV", 16), ("I", 1), ("IQUV", 2)])
+@pytest.mark.parametrize("variant", ["few", "many", "many64"])
+@pytest.mark.parametrize("out,Q", [("I", 4), ("IQUV", 16), ("I", 1), ("IQUV", 2), ("I", 32), ("IQUV", 8)])
 def test_beamform_stokes_epilogue_matches_oracle(dev, variant, out, Q):
     wl = _wl(T=64 * N, out=out, Q=Q, B=6)
     p = _plan(wl, bf_variant=variant)
@@ -213,7 +225,7 @@ def test_beamform_stokes_epilogue_matches_oracle(dev, variant, out, Q):
 
 
 # ----------------------------------------------------------------------------- a1-a7 fused
-@pytest.mark.parametrize("variant", ["few", "many"])
+@pytest.mark.parametrize("variant", ["few", "many", "many64"])
 @pytest.mark.parametrize("out,bits", [("I", 16), ("IQUV", 16), ("V", 16), ("I", 8)])
 def test_run_block_matches_oracle(dev, variant, out, bits):
     wl = _wl(out=out, bits=bits, Q=4 if out != "V" else 1)
@@ -261,7 +273,7 @@ def test_fused_equals_split_chain(dev):
 def test_degenerate_single_everything(dev):
     """S = 1, B = 1, one spectrum per block (T = N), Q = 1."""
     wl = _wl(S=1, F=1, T=N, B=1, Q=1, long_baselines=False)
-    for variant in ("few", "many"):
+    for variant in ("few", "many", "many64"):
         p = _plan(wl, bf_variant=variant)
         ob = O.observation_from_workload(wl)
         o = torch.empty(p.shape("stokes"), dtype=torch.float32, device=dev)
@@ -316,6 +328,7 @@ def test_maximum_paper_geometry(dev):
 # last group of 8 spectra that runs past M (M = 36)
 @pytest.mark.parametrize("variant,prec,bits,out,tol,M,Q", [
     ("few", "fp32", 16, "IQUV", TOL, 64, 4), ("many", "fp32", 8, "I", TOL, 64, 4),
+    ("many64", "fp32", 16, "IQUV", TOL, 64, 4),
     ("auto", "fp16tc", 16, "IQUV", 1e-3, 64, 4), ("auto", "fp16tc", 8, "I", 1e-3, 64, 4),
     ("auto", "fp16tc", 16, "I", 1e-3, 96, 32), ("auto", "fp16tc", 16, "IQUV", 1e-3, 36, 2),
     ("auto", "fp16tc", 8, "I", 1e-3, 80, 16)])
