@@ -71,11 +71,11 @@ typedef enum { LBF_VOLTAGES = 0, LBF_STOKES_I = 1, LBF_STOKES_IQUV = 4 } lbf_out
 
 typedef enum { LBF_FP32 = 0, LBF_FP16_TC = 1 } lbf_precision;
 
-/* Beam-former kernel choice: AUTO picks the bandwidth-bound few-beam kernel for B <= 8 and
- * otherwise the tensor-core kernel (LBF_FP16_TC) or the register-tiled FP32 many-beam kernel with
- * the beam tile -- 128 (MANY) or 64 (MANY64) beams per CTA -- that leaves the fewest tile slots
- * empty (a 64-beam slot weighed as 1.15 of a 128-beam one).  With LBF_FP16_TC, MANY and MANY64
- * both select the tensor-core kernel. */
+/* Beam-former kernel choice: AUTO picks the bandwidth-bound few-beam kernel for B <= 8 (FP16_TC)
+ * or B <= 32 (FP32), and otherwise the tensor-core kernel (LBF_FP16_TC) or the register-tiled FP32
+ * many-beam kernel with the beam tile -- 128 (MANY) or 64 (MANY64) beams per CTA -- that leaves
+ * the fewest tile slots empty (a 64-beam slot weighed as 1.15 of a 128-beam one).  With
+ * LBF_FP16_TC, MANY and MANY64 both select the tensor-core kernel. */
 typedef enum { LBF_BF_AUTO = 0, LBF_BF_FEW = 1, LBF_BF_MANY = 2, LBF_BF_MANY64 = 3 } lbf_bf_variant;
 
 /* The plan does not allocate the run_block scratch; the caller passes one to lbf_run_block_ws

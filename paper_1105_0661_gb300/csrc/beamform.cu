@@ -498,11 +498,12 @@ size_t bf_smem_bytes(int variant, int S) {
   return (size_t)S * ((variant == 3 ? 64 : kBT) + 2 * kP * kMC) * sizeof(float2);
 }
 
-// Beam-former choice for AUTO: the few-beam kernel up to 8 beams; beyond, the many-beam tile
-// (128 or 64 beams per CTA) that leaves the fewest tile slots empty, a 64-beam slot counted as
-// 1.15 of a 128-beam one (the narrower tile issues more shared loads per FMA).
+// Beam-former choice for AUTO: the few-beam kernel up to 32 beams (it reads the block once per 8
+// beams at HBM speed; a 64-beam FP32 tile costs about as much as 6 such passes); beyond, the
+// many-beam tile (128 or 64 beams per CTA) that leaves the fewest tile slots empty, a 64-beam slot
+// counted as 1.15 of a 128-beam one (the narrower tile issues more shared loads per FMA).
 int auto_bf_variant(int B, int S) {
-  if (B <= 8 || S > many_beam_max_stations()) return 1;
+  if (B <= 32 || S > many_beam_max_stations()) return 1;
   const double slots128 = (double)((B + 127) / 128) * 128.0;
   const double slots64 = (double)((B + 63) / 64) * 64.0 * 1.15;
   return slots64 < slots128 ? 3 : 2;

@@ -179,10 +179,10 @@ def test_beamform_voltages_match_oracle(dev, variant, B):
     p.close()
 
 
-@pytest.mark.parametrize("B,kernel", [(8, 1), (9, 4), (24, 4), (64, 4), (65, 2), (127, 2), (154, 4), (200, 2),
+@pytest.mark.parametrize("B,kernel", [(8, 1), (32, 1), (33, 4), (64, 4), (65, 2), (127, 2), (154, 4), (200, 2),
                                       (269, 4), (472, 2)])
 def test_automatic_beam_former_choice(dev, B, kernel):
-    """AUTO: the few-beam kernel up to 8 beams, then the many-beam tile (128 beams: kernel 2, 64
+    """AUTO: the few-beam kernel up to 32 beams, then the many-beam tile (128 beams: kernel 2, 64
     beams: kernel 4) that leaves the fewest tile slots empty (a 64-beam slot weighed 1.15)."""
     wl = _wl(B=B, F=1, T=16 * N)
     p = _plan(wl)
