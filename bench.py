@@ -479,7 +479,8 @@ def run_ours(args):
         "config": config_dict(wl, args), "e2e": e2e, "gpu_launches": launches, "roofline": roof,
         "cpu_baseline": cpu, "clocks": clocks, "kernels": kernels, "fp32_peak": alu_peak,
         "beamform_tflops": bf_flop * args.steps / (sum(v[1] for k, v in trace.items() if k.startswith("bf_")) / 1e3) / 1e12,
-        "dtype_detail": "fp16 tensor-core operands, fp32 accumulation" if args.precision == "fp16tc" else "fp32",
+        "dtype_detail": {"fp16tc": "fp16 tensor-core operands (three products), fp32 accumulation",
+                         "fp16tc2": "fp16 tensor-core operands (two products), fp32 accumulation"}.get(args.precision, "fp32"),
         "parity": parity, "precision_compare": compare,
         "paper_context": "Blue Gene/P rack: up to 198 Gb/s = 3.1e9 station-samples/s (64 stations x 248 subbands)",
     }
@@ -651,8 +652,9 @@ def run_serve(args):
 
 def precision_form_1024(args, dev, stream, pk, smi_index):
     """The precision form of the observation (1024 beams on a hexagonal grid, full Stokes IQUV
-    integrated over 16): FP16 tensor cores with int8 samples and with int16 samples, and the plain
-    FP32 path on the same int8 block."""
+    integrated over 16): FP16 tensor cores with int8 samples and with int16 samples, in the
+    three-product form and the two-product form (FP16 weights), and the plain FP32 path on the same
+    int8 block."""
     import torch
 
     from paper_1105_0661_gb300 import Plan
@@ -666,11 +668,11 @@ def precision_form_1024(args, dev, stream, pk, smi_index):
             d_in = make_block_device(wl, seed=0, device=dev)
             ss = wl.station_samples()
             flop = 8.0 * wl.n_beams * ss * 2               # one complex product per MAC
-            forms = ("fp16tc", "fp32") if bits == 8 else ("fp16tc",)
+            forms = ("fp16tc", "fp16tc2", "fp32") if bits == 8 else ("fp16tc", "fp16tc2")
             for prec in forms:
                 plan = Plan.from_workload(wl, precision=prec)
                 d_out = torch.empty(plan.shape("stokes"), dtype=torch.float32, device=dev)
-                steps = args.steps if prec == "fp16tc" else 2
+                steps = args.steps if prec != "fp32" else 2
                 for _ in range(3):
                     plan.run_block(d_in, d_out, stream)
                 stream.synchronize()
@@ -685,13 +687,13 @@ def precision_form_1024(args, dev, stream, pk, smi_index):
                 ms = e0.elapsed_time(e1) / steps
                 r = {"ms_per_step": ms, "value": ss / (ms / 1e3), "steps": steps, "warmup": 3,
                      "kernels_ms": {k: v[1] / v[0] for k, v in tr.items() if not k.startswith("_") and v[0]}}
-                bf = "bf_tc" if prec == "fp16tc" else ("bf_many" if "bf_many" in r["kernels_ms"] else "bf_few")
+                bf = "bf_tc" if prec != "fp32" else ("bf_many" if "bf_many" in r["kernels_ms"] else "bf_few")
                 bf_ms = r["kernels_ms"].get(bf)
                 if bf_ms:
                     r["beamform_tflops"] = flop / (bf_ms / 1e3) / 1e12
-                    if prec == "fp16tc":
+                    if prec != "fp32":   # executed: three (fp16tc) or two (fp16tc2) FP16 products
                         r["bf_tc_frac_algorithmic"] = r["beamform_tflops"] / peak_tf
-                        r["bf_tc_frac_executed"] = 3 * r["beamform_tflops"] / peak_tf
+                        r["bf_tc_frac_executed"] = (3 if prec == "fp16tc" else 2) * r["beamform_tflops"] / peak_tf
                         r["peak_tflops"] = peak_tf
                 res[f"{prec}_i{bits}"] = r
                 plan.close()
@@ -700,6 +702,7 @@ def precision_form_1024(args, dev, stream, pk, smi_index):
             del d_in
             torch.cuda.empty_cache()
     res["fp16tc_speedup_over_fp32_i8"] = res["fp32_i8"]["ms_per_step"] / res["fp16tc_i8"]["ms_per_step"]
+    res["fp16tc2_speedup_over_fp32_i8"] = res["fp32_i8"]["ms_per_step"] / res["fp16tc2_i8"]["ms_per_step"]
     res["workload"] = "48 st x 244 sb x 196608 samples, 1024 hex beams, Stokes IQUV over 16 spectra"
     res["clocks"] = clk.summary()
     return res
@@ -967,7 +970,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="lofar", choices=["lofar", "lofar1024", "lofar8", "tiny"])
     ap.add_argument("--bits", type=int, default=0, choices=[0, 8, 16], help="sample width override")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16tc"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16tc", "fp16tc2"])
     ap.add_argument("--subbands", type=int, default=0,
                     help="use only the first N subbands (small profiling cases; 0 = all)")
     ap.add_argument("--cpu-subbands", type=int, default=0,

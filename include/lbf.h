@@ -69,13 +69,20 @@ typedef enum { LBF_I8 = 8, LBF_I16 = 16 } lbf_sample_bits;
 /* Pipelines of Section 3: complex voltages, Stokes I, Stokes IQUV. */
 typedef enum { LBF_VOLTAGES = 0, LBF_STOKES_I = 1, LBF_STOKES_IQUV = 4 } lbf_output;
 
-typedef enum { LBF_FP32 = 0, LBF_FP16_TC = 1 } lbf_precision;
+/* Arithmetic of the beam former (the precision form of the beam former, Section 4.3 computed on
+ * tensor cores): FP32 SIMT; FP16 tensor cores with three products (spectrum and weights both split
+ * hi + lo: Whi Yhi + Wlo Yhi + Whi Ylo, FP32 accumulation, errors ~1e-6 relative); or FP16 tensor
+ * cores with two products (spectrum split hi + lo, weights rounded to FP16 once: Whi Yhi + Whi Ylo,
+ * two thirds of the MMA work; the weight rounding, <= 2^-12 per component, limits Stokes I to
+ * ~1e-4 relative RMS, more on single elements of beams that cancel a strong source). */
+typedef enum { LBF_FP32 = 0, LBF_FP16_TC = 1, LBF_FP16_TC2 = 2 } lbf_precision;
 
-/* Beam-former kernel choice: AUTO picks the bandwidth-bound few-beam kernel for B <= 8 (FP16_TC)
- * or B <= 32 (FP32), and otherwise the tensor-core kernel (LBF_FP16_TC) or the register-tiled FP32
- * many-beam kernel with the beam tile -- 128 (MANY) or 64 (MANY64) beams per CTA -- that leaves
- * the fewest tile slots empty (a 64-beam slot weighed as 1.15 of a 128-beam one).  With
- * LBF_FP16_TC, MANY and MANY64 both select the tensor-core kernel. */
+/* Beam-former kernel choice: AUTO picks the bandwidth-bound few-beam kernel for B <= 8 (tensor-core
+ * precisions) or B <= 32 (FP32), and otherwise the tensor-core kernel (LBF_FP16_TC, LBF_FP16_TC2)
+ * or the register-tiled FP32 many-beam kernel with the beam tile -- 128 (MANY) or 64 (MANY64)
+ * beams per CTA -- that leaves the fewest tile slots empty (a 64-beam slot weighed as 1.15 of a
+ * 128-beam one).  With
+ * LBF_FP16_TC or LBF_FP16_TC2, MANY and MANY64 both select the tensor-core kernel. */
 typedef enum { LBF_BF_AUTO = 0, LBF_BF_FEW = 1, LBF_BF_MANY = 2, LBF_BF_MANY64 = 3 } lbf_bf_variant;
 
 /* The plan does not allocate the run_block scratch; the caller passes one to lbf_run_block_ws
@@ -140,12 +147,13 @@ typedef struct lbf_plan_s *lbf_plan_t;
  * With precision LBF_FP16_TC the many-beam beam former runs on the tensor cores (tcgen05, FP16
  * operands, FP32 accumulation): the filtered spectrum Y of either sample width feeds it as two
  * FP16 planes (hi = fp16(Y), lo = fp16(Y - hi)) and the weights are split the same way, three
- * products per tile, writing Stokes or beam voltages; it needs S <= 64.  The tensor cores are used
+ * products per tile, writing Stokes or beam voltages; it needs S <= 64.  LBF_FP16_TC2 is the same
+ * with FP16 weights only (two products per tile).  The tensor cores are used
  * only where the beam count makes the beam former a dense contraction: with bf_variant AUTO and
- * B <= 8 beams, or bf_variant FEW, an LBF_FP16_TC plan runs the bandwidth-bound FP32 few-beam
+ * B <= 8 beams, or bf_variant FEW, a tensor-core plan runs the bandwidth-bound FP32 few-beam
  * kernel on the FP32 corner-turned block instead (lbf_plan_dims reports bf_kernel 1); with MANY,
  * or AUTO and B > 8, it runs the tensor-core kernel (bf_kernel 3).
- * Errors: LBF_EINVAL (bad config), LBF_EUNSUPPORTED (N != 256, L != 16, or an FP16_TC plan with
+ * Errors: LBF_EINVAL (bad config), LBF_EUNSUPPORTED (N != 256, L != 16, or a tensor-core plan with
  * S > 64), LBF_ENOMEM, LBF_ECUDA. */
 lbf_status lbf_plan(const lbf_config *cfg, lbf_plan_t *out);
 

@@ -8,7 +8,9 @@
 // split into FP16 hi and lo = fp16(x - hi) parts; the products Whi Yhi + Wlo Yhi + Whi Ylo
 // accumulate in FP32 into the same TMEM tile, which keeps the error at the level of the FP32 path
 // rather than of FP16 rounding (the filtered spectrum Y is not exact in FP16 for either sample
-// width, and beams summed with cancellation magnify its rounding).
+// width, and beams summed with cancellation magnify its rounding).  The two-product form drops
+// Wlo Yhi: FP16 weights (rounding error <= 2^-12 per component) against the hi+lo spectrum, two
+// thirds of the MMA work.
 //
 // Operands.  A (the weights) lives in tensor memory: the epilogue warps compute it from the
 // FP64-reduced phase tables with the hardware sincos of the reduced phase and write it with
@@ -67,6 +69,7 @@ struct TcParams {
   int first_item;             // the plan's first work item in the launch
   int stage_bytes;            // its ring stage: 2 planes x 2 tiles x Kpad K rows x 128 bytes
   int vec;                    // output rows 16-byte aligned (M/Q % 4 == 0, aligned base)
+  int wlo;                    // 1: three products (Wlo Yhi too); 0: two products
   const float *phase0, *step;
   float *out;
   int *err;                   // the plan's device error word
@@ -223,7 +226,7 @@ __device__ __forceinline__ void load_weight_tables(const TcParams &p, int f, int
 }
 
 __device__ __forceinline__ void write_weights(const TcParams &p, uint32_t ta_hi, uint32_t ta_lo, int c, int ro,
-                                              int half, const WeightTables &tab) {
+                                              int half, const WeightTables &tab, bool wlo) {
   const float dc = (float)(c - kN / 2);
 #pragma unroll
   for (int gi = 0; gi < kWStations / 4; ++gi) {
@@ -256,7 +259,7 @@ __device__ __forceinline__ void write_weights(const TcParams &p, uint32_t ta_hi,
       }
     }
     tmem_st8(ta_hi + (uint32_t)(g8 * 8), vh);
-    tmem_st8(ta_lo + (uint32_t)(g8 * 8), vl);
+    if (wlo) tmem_st8(ta_lo + (uint32_t)(g8 * 8), vl);
   }
   tmem_wait_st();
 }
@@ -449,11 +452,16 @@ __device__ __forceinline__ void flush_stage(const TcParams &p, const float *buf,
   }
 }
 
-// kMulti: the launch table holds several plans (a batch); otherwise plan 0 is the only one and
-// its parameters are compile-time offsets into the table.
-template <int NS, int Q, bool kMulti>
+// kForm: kMultiPlan (the launch table holds several plans, a batch, each with its own product count)
+// or a single plan -- plan 0, its parameters at compile-time offsets into the table -- with three
+// (kSingle3) or two (kSingle2) products; a run-time product count costs the single plan ~3 %.
+constexpr int kSingle3 = 0, kSingle2 = 1, kMultiPlan = 2;
+template <int NS, int Q, int kForm>
 __global__ void __launch_bounds__(kThreads, 1)
 bf_tc_kernel(const __grid_constant__ TcLaunch L) {
+  constexpr bool kMulti = kForm == kMultiPlan;
+  // whether plan p adds the Wlo Yhi product
+  auto wlo_of = [](const TcParams &p) { return kMulti ? p.wlo != 0 : kForm == kSingle3; };
   using St = Stage<NS, Q>;
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -547,6 +555,7 @@ bf_tc_kernel(const __grid_constant__ TcLaunch L) {
         const TcParams &p = L.plan[kMulti ? plan_of(L, item) : 0];
         err = p.err;
         const int ksteps = p.Kpad >> 4;
+        const bool wlo = wlo_of(p);     // read once: the MMA asm clobbers memory
         const uint32_t plane_bytes = (uint32_t)p.stage_bytes / 2;
         const uint64_t desc_b0 = smem_desc(sB, (uint32_t)(p.Kpad * 128));   // stage 0, hi plane, k step 0
         for (int t = 0; t < p.ntiles && ok; ++t, gpar ^= 1u) {
@@ -567,7 +576,7 @@ bf_tc_kernel(const __grid_constant__ TcLaunch L) {
             for (int ks = 0; ks < ksteps; ++ks) {
               const uint64_t b_lo = b_hi + (uint64_t)(plane_bytes >> 4);
               umma(d, a_hi, b_hi, ks != 0);           // Whi Yhi
-              umma(d, a_hi + 64u, b_hi, 1);           // Wlo Yhi
+              if (wlo) umma(d, a_hi + 64u, b_hi, 1);     // Wlo Yhi
               umma(d, a_hi, b_lo, 1);                 // Whi Ylo
               a_hi += 8u;                             // 16 K elements = 8 TMEM columns
               b_hi += (uint64_t)((16 * 128) >> 4);    // 16 K rows of 128 bytes
@@ -610,7 +619,7 @@ bf_tc_kernel(const __grid_constant__ TcLaunch L) {
           const uint32_t ta_hi = tmem + lane_off + kACol0 + (uint32_t)(2 * mt * 64);
           WeightTables tab;
           load_weight_tables(p, f, bb * kBeamsPerItem + mt * (kRows / 2) + quad * 16 + jq, ro, half, tab);
-          write_weights(p, ta_hi, ta_hi + 64u, c, ro, half, tab);
+          write_weights(p, ta_hi, ta_hi + 64u, c, ro, half, tab, wlo_of(p));
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(afull_bar(mt));
@@ -654,7 +663,7 @@ bf_tc_kernel(const __grid_constant__ TcLaunch L) {
             // the MMAs that read this tile's weights are complete (its last accumulator was
             // committed): write the next item's
             const uint32_t ta_hi = tmem + lane_off + kACol0 + (uint32_t)(2 * mt * 64);
-            write_weights(pn, ta_hi, ta_hi + 64u, nfc % kN, ro, half, tab);
+            write_weights(pn, ta_hi, ta_hi + 64u, nfc % kN, ro, half, tab, wlo_of(pn));
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(afull_bar(mt));
@@ -682,7 +691,7 @@ bf_tc_kernel(const __grid_constant__ TcLaunch L) {
   }
 }
 
-template <int NS, int Q, bool kMulti>
+template <int NS, int Q, int kForm>
 cudaError_t launch_q(TcLaunch &L, int grid, cudaStream_t st) {
   // B ring: as many stages of the largest plan as shared memory leaves after the barriers and
   // the output staging
@@ -693,21 +702,21 @@ cudaError_t launch_q(TcLaunch &L, int grid, cudaStream_t st) {
   // at least half of an SM's shared memory, so that no two CTAs share an SM (each holds all of
   // its TMEM columns)
   if (smem < kMinSmem) smem = kMinSmem;
-  cudaError_t e = cudaFuncSetAttribute(bf_tc_kernel<NS, Q, kMulti>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(bf_tc_kernel<NS, Q, kForm>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  bf_tc_kernel<NS, Q, kMulti><<<grid, kThreads, smem, st>>>(L);
+  bf_tc_kernel<NS, Q, kForm><<<grid, kThreads, smem, st>>>(L);
   return cudaGetLastError();
 }
 
-template <int NS, bool kMulti>
+template <int NS, int kForm>
 cudaError_t launch_ns(int Q, TcLaunch &L, int grid, cudaStream_t st) {
   switch (Q) {
-    case 1: return launch_q<NS, 1, kMulti>(L, grid, st);
-    case 2: return launch_q<NS, 2, kMulti>(L, grid, st);
-    case 4: return launch_q<NS, 4, kMulti>(L, grid, st);
-    case 8: return launch_q<NS, 8, kMulti>(L, grid, st);
-    case 16: return launch_q<NS, 16, kMulti>(L, grid, st);
-    case 32: return launch_q<NS, 32, kMulti>(L, grid, st);
+    case 1: return launch_q<NS, 1, kForm>(L, grid, st);
+    case 2: return launch_q<NS, 2, kForm>(L, grid, st);
+    case 4: return launch_q<NS, 4, kForm>(L, grid, st);
+    case 8: return launch_q<NS, 8, kForm>(L, grid, st);
+    case 16: return launch_q<NS, 16, kForm>(L, grid, st);
+    case 32: return launch_q<NS, 32, kForm>(L, grid, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -736,6 +745,7 @@ bool fill_plan(TcLaunch &L, int i, const Geometry &g, int out_kind, const void *
   p.items = (int)items;
   p.first_item = (int)first;
   p.phase0 = g.phase0; p.step = g.step; p.out = out; p.err = err;
+  p.wlo = g.tc_wlo ? 1 : 0;
   const bool aligned = (reinterpret_cast<uintptr_t>(out) & 15) == 0;
   p.vec = out_kind == OUT_VOLTAGES ? (g.M % 2 == 0 && aligned) : ((g.M / g.Q) % 4 == 0 && aligned);
   L.map[2 * i] = *reinterpret_cast<const CUtensorMap *>(tm_hi);
@@ -746,16 +756,22 @@ bool fill_plan(TcLaunch &L, int i, const Geometry &g, int out_kind, const void *
   return true;
 }
 
-template <bool kMulti>
+template <int kForm>
+cudaError_t launch_form(TcLaunch &L, int out_kind, int Q, int grid, cudaStream_t st) {
+  if (out_kind == OUT_VOLTAGES) return launch_q<0, 1, kForm>(L, grid, st);
+  if (out_kind == OUT_STOKES_IQUV) return launch_ns<4, kForm>(Q, L, grid, st);
+  if (out_kind == OUT_STOKES_I) return launch_ns<1, kForm>(Q, L, grid, st);
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_table(TcLaunch &L, int out_kind, int Q, cudaStream_t st) {
   if (L.items == 0) return cudaSuccess;
   const int sms = sm_count();
   if (sms <= 0) return cudaErrorInvalidDevice;
   const int grid = L.items < sms ? L.items : sms;
-  if (out_kind == OUT_VOLTAGES) return launch_q<0, 1, kMulti>(L, grid, st);
-  if (out_kind == OUT_STOKES_IQUV) return launch_ns<4, kMulti>(Q, L, grid, st);
-  if (out_kind == OUT_STOKES_I) return launch_ns<1, kMulti>(Q, L, grid, st);
-  return cudaErrorInvalidValue;
+  if (L.nplans > 1) return launch_form<kMultiPlan>(L, out_kind, Q, grid, st);
+  return L.plan[0].wlo ? launch_form<kSingle3>(L, out_kind, Q, grid, st)
+                       : launch_form<kSingle2>(L, out_kind, Q, grid, st);
 }
 
 }  // namespace
@@ -772,7 +788,7 @@ cudaError_t launch_bf_tc(const Geometry &g, int out_kind, const void *tm_hi, con
   L.nplans = 0; L.items = 0; L.nstages = 0; L.stage_max = 0;
   L.stall_item = stall_item;
   if (!fill_plan(L, 0, g, out_kind, tm_hi, tm_lo, out, err)) return cudaErrorInvalidValue;
-  return launch_table<false>(L, out_kind, g.Q, st);
+  return launch_table(L, out_kind, g.Q, st);
 }
 
 cudaError_t launch_bf_tc_group(const TcPlanRef *plans, int n, int out_kind, int Q, cudaStream_t st) {
@@ -788,7 +804,7 @@ cudaError_t launch_bf_tc_group(const TcPlanRef *plans, int n, int out_kind, int 
     if (!fill_plan(L, k, r.g, out_kind, r.tm_hi, r.tm_lo, r.out, r.err)) return cudaErrorInvalidValue;
     ++k;
   }
-  return k == 1 ? launch_table<false>(L, out_kind, Q, st) : launch_table<true>(L, out_kind, Q, st);
+  return launch_table(L, out_kind, Q, st);
 }
 
 }  // namespace lbf

@@ -72,7 +72,7 @@ lbf_status validate(const lbf_config *c) {
   if (c->block_samples < 0 || c->block_samples % c->n_channels != 0) return LBF_EINVAL;
   if (c->sample_bits != 16 && c->sample_bits != 8) return LBF_EINVAL;
   if (c->output != LBF_VOLTAGES && c->output != LBF_STOKES_I && c->output != LBF_STOKES_IQUV) return LBF_EINVAL;
-  if (c->precision != LBF_FP32 && c->precision != LBF_FP16_TC) return LBF_EINVAL;
+  if (c->precision != LBF_FP32 && c->precision != LBF_FP16_TC && c->precision != LBF_FP16_TC2) return LBF_EINVAL;
   if (c->bf_variant < LBF_BF_AUTO || c->bf_variant > LBF_BF_MANY64) return LBF_EINVAL;
   if ((c->flags & ~(LBF_FLAG_EXTERNAL_WORKSPACE | LBF_FLAG_INCOHERENT_BEAM)) != 0) return LBF_EINVAL;
   if ((c->flags & LBF_FLAG_INCOHERENT_BEAM) && c->output == LBF_VOLTAGES) return LBF_EINVAL;
@@ -86,7 +86,7 @@ lbf_status validate(const lbf_config *c) {
   for (int i = 0; i < c->n_subbands; ++i) if (!std::isfinite(c->subband_centre_hz[i])) return LBF_EINVAL;
   for (int i = 0; i < 2 * c->n_beams; ++i) if (!std::isfinite(c->beam_dlm[i])) return LBF_EINVAL;
   if (c->n_channels != lbf::kN || c->n_taps != lbf::kL) return LBF_EUNSUPPORTED;
-  if (c->precision == LBF_FP16_TC && c->n_stations > lbf::tc_max_stations()) return LBF_EUNSUPPORTED;
+  if (c->precision != LBF_FP32 && c->n_stations > lbf::tc_max_stations()) return LBF_EUNSUPPORTED;
   if ((c->bf_variant == LBF_BF_MANY || c->bf_variant == LBF_BF_MANY64) && c->precision == LBF_FP32 &&
       c->n_stations > lbf::many_beam_max_stations())
     return LBF_EUNSUPPORTED;
@@ -274,7 +274,7 @@ lbf_status lbf_plan(const lbf_config *cfg, lbf_plan_t *out) {
   // tensor-core plan with few beams (AUTO and B <= 8, or FEW asked for) runs the bandwidth-bound
   // few-beam kernel on the FP32 corner-turned block instead (Section 4.3: few beams stream the
   // stations once; many beams reuse each station sample across beams).
-  const bool tc_asked = cfg->precision == LBF_FP16_TC;
+  const bool tc_asked = cfg->precision != LBF_FP32;
   const bool tc_few = tc_asked && (cfg->bf_variant == LBF_BF_FEW || (cfg->bf_variant == LBF_BF_AUTO && p->B <= 8));
   if (tc_few) p->variant = 1;
 
@@ -329,6 +329,7 @@ lbf_status lbf_plan(const lbf_config *cfg, lbf_plan_t *out) {
     if (e == cudaSuccess) e = cudaMemset(p->hist[i], 0, p->hist_bytes ? p->hist_bytes : 16);
   }
   p->tc = tc_asked && !tc_few;
+  p->tc_wlo = cfg->precision == LBF_FP16_TC2 ? 0 : 1;
   p->external_ws = (cfg->flags & LBF_FLAG_EXTERNAL_WORKSPACE) != 0;
   p->inc = (cfg->flags & LBF_FLAG_INCOHERENT_BEAM) ? 1 : 0;
   if (e == cudaSuccess) e = cudaMalloc((void **)&p->ss_members, sizeof(int) * p->S);

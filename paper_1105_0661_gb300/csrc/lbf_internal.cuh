@@ -16,6 +16,8 @@ struct Geometry {
                                                         // spectra, integration factor, Stokes
   int H = 0;                  // history samples per (station, subband)
   int inc = 0;                // 1: the Stokes output also holds the incoherent beam at index B
+  int tc_wlo = 1;             // tensor-core beam former: 1 adds the Wlo Yhi product (three
+                              // products), 0 keeps FP16 weights only (two products)
   double fs = 0.0;            // subband sample rate
   const float *taps = nullptr;          // [L*N]
   const float2 *twiddle = nullptr;      // [N] exp(-2 pi i n / N)

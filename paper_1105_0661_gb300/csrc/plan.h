@@ -27,6 +27,7 @@ struct lbf_plan_s {
   float *phase0 = nullptr, *step = nullptr;
   // tensor-core precision: FP16 corner-turned planes and their TMA descriptors
   bool tc = false;
+  int tc_wlo = 1;               // three products (LBF_FP16_TC) or two (LBF_FP16_TC2)
   int kpad = 0, planes = 0;
   void *ct16[2] = {nullptr, nullptr};
   alignas(64) CUtensorMap tmap[2];
@@ -64,6 +65,7 @@ struct lbf_plan_s {
     g.taps = taps; g.twiddle = twiddle; g.bandpass = bandpass; g.dshift = dshift;
     g.tau = tau; g.resid = resid; g.f0 = f0; g.dtau = dtau; g.phase0 = phase0; g.step = step;
     g.inc = inc;
+    g.tc_wlo = tc_wlo;
     g.err = d_err;
     return g;
   }

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liblbf.so")
 
 LBF_OK, LBF_EINVAL, LBF_ENOMEM, LBF_ECUDA, LBF_ESTATE, LBF_ETIMEOUT, LBF_EBUSY, LBF_EUNSUPPORTED, LBF_ETOOBIG = range(9)
 OUTPUTS = {"V": 0, "I": 1, "IQUV": 4}
-PRECISIONS = {"fp32": 0, "fp16tc": 1}
+PRECISIONS = {"fp32": 0, "fp16tc": 1, "fp16tc2": 2}
 BF_VARIANTS = {"auto": 0, "few": 1, "many": 2, "many64": 3}
 
 # Every symbol include/lbf.h declares; the test suite checks the library exports all of them.

@@ -83,15 +83,15 @@ def test_batch_with_tensor_core_plans_equals_separate_runs():
     """Tensor-core plans (Stokes I, IQUV with the incoherent beam, voltages) and FP32 plans in one
     batch: grouped filter bank writing the FP16 planes, then one persistent tensor-core launch per
     class of output kind and integration length (here the two IQUV plans, of 20 and 64 stations,
-    share one); every output equals the same plan run alone, block after block, also as graph
-    replays."""
+    share one, the second in the two-product form); every output equals the same plan run alone,
+    block after block, also as graph replays."""
     from paper_1105_0661_gb300 import Batch, Plan, build_lib
     build_lib.build()
     dev = torch.device("cuda:0")
     torch.cuda.set_device(dev)
     wls = _specs()
     kinds = [dict(), dict(precision="fp16tc"), dict(precision="fp16tc", incoherent_beam=True),
-             dict(precision="fp16tc"), dict(precision="fp16tc")]
+             dict(precision="fp16tc"), dict(precision="fp16tc2")]
     solo = [Plan.from_workload(wl, **kw) for wl, kw in zip(wls, kinds)]
     grouped = [Plan.from_workload(wl, **kw) for wl, kw in zip(wls, kinds)]
     batch = Batch(grouped)

@@ -219,3 +219,65 @@ def test_tc_split_beamform_voltages(dev):
     print(f"TC split beamform: max rel RMS {err:.2e}")
     assert err <= 1e-4
     p.close()
+
+
+def test_tc2_voltages_within_the_weight_rounding_bound(dev):
+    """Two-product form (weights rounded to FP16 once, spectrum split hi + lo): every beam voltage
+    lies within the bound its arithmetic sets,
+        |V - V_ref| <= (sqrt(2) 2^-12 + 1e-5) sum_s |Y_s|,
+    i.e. the FP16 rounding of each weight component (at most 2^-12 for |x| < 1) plus 1e-5 for the
+    sincos of the reduced phase and the FP32 accumulation; the three-product form of the same plan
+    stays far inside it."""
+    from paper_1105_0661_gb300 import Plan
+    wl = _wl(S=48, B=130, out="I", T=64 * N, Q=16)
+    ob = O.observation_from_workload(wl)
+    rng = np.random.default_rng(6)
+    ratios = {}
+    for prec in ("fp16tc2", "fp16tc"):
+        p = Plan.from_workload(wl, precision=prec)
+        assert p.dims.bf_kernel == 3
+        shp = p.shape("ct")                                   # [F][N][S][P][M]
+        if not ratios:
+            ct = (rng.standard_normal(shp) + 1j * rng.standard_normal(shp)).astype(np.complex64)
+            y = ct.astype(np.complex128)
+            ref = ob.beamform(y)                              # [B][F][N][P][M]
+            bound = (np.sqrt(2.0) * 2.0 ** -12 + 1e-5) * np.abs(y).sum(axis=2)[None]
+        vol = torch.empty(p.shape("vol"), dtype=torch.complex64, device=dev)
+        p.beamform(torch.from_numpy(ct).to(dev), vol)
+        assert p.device_status() == 0
+        err = np.abs(vol.cpu().numpy().astype(np.complex128) - ref)
+        ratios[prec] = float((err / bound).max())
+        p.close()
+    print(f"voltage error / weight-rounding bound: two products {ratios['fp16tc2']:.3f}, "
+          f"three products {ratios['fp16tc']:.2e}")
+    assert ratios["fp16tc2"] <= 1.0
+    assert ratios["fp16tc"] <= 0.05
+
+
+@pytest.mark.parametrize("bits,out", [(16, "I"), (8, "IQUV")])
+def test_tc2_run_block_matches_oracle(dev, bits, out):
+    """Two-product form against the FP64 oracle over two blocks: Stokes I within 1e-3 relative RMS
+    per (beam, subband) row, Q, U, V within 1e-3 of I's RMS; the per-element maximum is printed
+    (the weight rounding is not scaled down on single elements of beams that cancel a source)."""
+    from paper_1105_0661_gb300 import Plan
+    wl = _wl(bits=bits, out=out, T=96 * N)
+    p = Plan.from_workload(wl, precision="fp16tc2")
+    assert p.dims.bf_kernel == 3
+    ob = O.observation_from_workload(wl)
+    o = torch.empty(p.shape("stokes"), dtype=torch.float32, device=dev)
+    for bi in range(2):
+        blk = G.make_block(wl, seed=2, block_index=bi)
+        p.run_block(torch.from_numpy(blk).to(dev), o)
+        assert p.device_status() == 0
+        got, ref = o.cpu().numpy().astype(np.float64), ob.run_block(blk)   # [B][nS][F][N][M/Q]
+        I = ref[:, 0]
+        rms_I = np.sqrt(np.sum((got[:, 0] - I) ** 2, axis=(2, 3)) / np.sum(I ** 2, axis=(2, 3)))
+        rms_q = 0.0
+        if ref.shape[1] == 4:
+            num = np.sqrt(np.sum((got[:, 1:] - ref[:, 1:]) ** 2, axis=(3, 4)))
+            rms_q = float((num / np.sqrt(np.sum(I ** 2, axis=(2, 3)))[:, None]).max())
+        eI, eq = _errors(got, ref)
+        print(f"TC2 run_block bits={bits} {out} block {bi}: I rel RMS {rms_I.max():.2e} (per element max {eI:.2e}), "
+              f"QUV/I rel RMS {rms_q:.2e} (max {eq:.2e})")
+        assert rms_I.max() <= TOL and rms_q <= TOL
+    p.close()
