@@ -1,20 +1,19 @@
 // Batches: several observations (plans) processed together, one block each, by persistent grouped
-// kernels -- one filter-bank launch, one history launch and one beam-former launch for the whole
-// batch -- instead of three launches per observation.  Uneven observations share the GPU through a
-// work counter: CTAs (one or two per SM) take (observation, stream, spectrum chunk) and
-// (observation, subband-channel, beam group) items until all are done, so small observations do
-// not leave the GPU idle and large ones do not serialise the batch.
-//
-// Tensor-core plans join the grouped filter bank (writing their FP16 planes) and the grouped
-// history update; then one persistent tensor-core launch per class of output kind and integration
-// length serves all of the class's plans (their work items numbered one after the other), after
-// the grouped FP32 beam former.
+// kernels instead of three launches per observation.  Uneven observations share the GPU through
+// work counters: CTAs take (observation, stream, spectrum chunk) and (observation, subband-channel,
+// beam group) items until all are done, so small observations do not leave the GPU idle and large
+// ones do not serialise the batch.  There is one launch per class of plans whose bodies need the
+// same registers and shared memory, so that each body runs as it does alone: the filter bank per
+// (sample width, FP32 or FP16-plane output), one history launch, the FP32 beam former per
+// (kernel variant, output kind, CTAs per SM), and one tensor-core launch per (output kind,
+// integration length), whose work items number the class's plans one after the other.
 //
 // A batch can be captured as CUDA graphs (one per history parity: each block flips every plan's
-// history ping-pong) and replayed with a single graph launch per block, and its tile shapes --
-// spectra per filter-bank item, for observations with 9..64 beams the few- or many-beam beam
-// former, and the many-beam tile (128 or 64 beams per CTA) -- can be tuned by timing the
-// candidates on the batch itself.
+// history ping-pong) and replayed with a single graph launch per block.  Its shapes -- spectra per
+// filter-bank item, for observations with 9..64 beams the few- or many-beam beam former, and the
+// many-beam tile (128 or 64 beams per CTA) -- and its mode are tuned by timing the candidates on
+// the batch itself.  The per-plan mode runs each FP32 stage as the plan's own kernel (the tensor
+// cores stay grouped); it wins where the observations are large enough to fill the GPU alone.
 #include <cstring>
 #include <new>
 #include <utility>
