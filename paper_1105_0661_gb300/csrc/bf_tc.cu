@@ -298,47 +298,74 @@ __device__ __forceinline__ void drain_tile(uint32_t taddr, int m0, int ro, int j
     tmem_ld16(taddr + (uint32_t)(kSpec + ch * 16), y[ch]);
   }
   tmem_wait_ld();
-  float sxx = 0.f, syy = 0.f, sxy = 0.f, sv = 0.f;
-#pragma unroll
-  for (int ml = 0; ml < kSpec; ++ml) {
-    const float xv = x[ml >> 4][ml & 15], yv = y[ml >> 4][ml & 15];
-    sxx = fmaf(xv, xv, sxx);
-    syy = fmaf(yv, yv, syy);
-    if (NS == 4) {
-      sxy = fmaf(xv, yv, sxy);
-      sv = fmaf(xv, __shfl_xor_sync(0xffffffffu, yv, 1), sv);   // Im X Re Y (ro 1) or Re X Im Y (ro 0)
-    }
-    if ((ml + 1) % Q == 0) {             // a window ends here (compile-time)
-      const int m = m0 + ml;
-      const bool ok = beam_ok && m < M;
-      const int w = m / Q;
-      if (NS == 1) {
-        const float i_own = sxx + syy;
-        const float I = i_own + __shfl_xor_sync(0xffffffffu, i_own, 1);
-        if (ok && ro == 0) {
-          if (Stage<NS, Q>::kOn) srow[Stage<NS, Q>::index(jq, 0, w - wbase)] = I;
-          else orow[w] = I;
-        }
-      } else {
-        // lane ro 0 ends with (I, Q), lane ro 1 with (U, V): each sends what its partner keeps
-        const float i_own = sxx + syy, q_own = sxx - syy, u_own = sxy, v_own = ro ? sv : -sv;
-        float k0 = ro ? u_own : i_own, k1 = ro ? v_own : q_own;
-        const float s0 = ro ? i_own : u_own, s1 = ro ? q_own : v_own;
-        k0 += __shfl_xor_sync(0xffffffffu, s0, 1);
-        k1 += __shfl_xor_sync(0xffffffffu, s1, 1);
-        if (ro) { k0 *= 2.f; k1 *= 2.f; }
-        if (ok) {
-          const int p0 = ro ? 2 : 0;
-          if (Stage<NS, Q>::kOn) {
-            srow[Stage<NS, Q>::index(jq, p0, w - wbase)] = k0;
-            srow[Stage<NS, Q>::index(jq, p0 + 1, w - wbase)] = k1;
-          } else {
-            orow[p0 * pstride + w] = k0;
-            orow[(p0 + 1) * pstride + w] = k1;
-          }
+  // window end: Stokes parameters of the sums, to the staging row or the output rows
+  auto window = [&](int ml, float sxx, float syy, float sxy, float sv) {
+    const int m = m0 + ml;
+    const bool ok = beam_ok && m < M;
+    const int w = m / Q;
+    if (NS == 1) {
+      const float i_own = sxx + syy;
+      const float I = i_own + __shfl_xor_sync(0xffffffffu, i_own, 1);
+      if (ok && ro == 0) {
+        if (Stage<NS, Q>::kOn) srow[Stage<NS, Q>::index(jq, 0, w - wbase)] = I;
+        else orow[w] = I;
+      }
+    } else {
+      // lane ro 0 ends with (I, Q), lane ro 1 with (U, V): each sends what its partner keeps
+      const float i_own = sxx + syy, q_own = sxx - syy, u_own = sxy, v_own = ro ? sv : -sv;
+      float k0 = ro ? u_own : i_own, k1 = ro ? v_own : q_own;
+      const float s0 = ro ? i_own : u_own, s1 = ro ? q_own : v_own;
+      k0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+      k1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+      if (ro) { k0 *= 2.f; k1 *= 2.f; }
+      if (ok) {
+        const int p0 = ro ? 2 : 0;
+        if (Stage<NS, Q>::kOn) {
+          srow[Stage<NS, Q>::index(jq, p0, w - wbase)] = k0;
+          srow[Stage<NS, Q>::index(jq, p0 + 1, w - wbase)] = k1;
+        } else {
+          orow[p0 * pstride + w] = k0;
+          orow[(p0 + 1) * pstride + w] = k1;
         }
       }
-      sxx = syy = sxy = sv = 0.f;
+    }
+  };
+  if constexpr (Q <= 2) {   // short windows: scalar sums (the pair form spills here)
+    float sxx = 0.f, syy = 0.f, sxy = 0.f, sv = 0.f;
+#pragma unroll
+    for (int ml = 0; ml < kSpec; ++ml) {
+      const float xv = x[ml >> 4][ml & 15], yv = y[ml >> 4][ml & 15];
+      sxx = fmaf(xv, xv, sxx);
+      syy = fmaf(yv, yv, syy);
+      if (NS == 4) {
+        sxy = fmaf(xv, yv, sxy);
+        sv = fmaf(xv, __shfl_xor_sync(0xffffffffu, yv, 1), sv);   // Im X Re Y (ro 1) or Re X Im Y (ro 0)
+      }
+      if ((ml + 1) % Q == 0) {
+        window(ml, sxx, syy, sxy, sv);
+        sxx = syy = sxy = sv = 0.f;
+      }
+    }
+  } else {
+    // spectra in pairs: packed FP32x2 FMAs, one per pair and sum (half the instructions and half
+    // the dependency chain of scalar sums); the two halves meet at the window's end
+    float2 pxx = make_float2(0.f, 0.f), pyy = pxx, pxy = pxx, pv = pxx;
+#pragma unroll
+    for (int ml = 0; ml < kSpec; ml += 2) {
+      const float2 xv = make_float2(x[ml >> 4][ml & 15], x[ml >> 4][(ml & 15) + 1]);
+      const float2 yv = make_float2(y[ml >> 4][ml & 15], y[ml >> 4][(ml & 15) + 1]);
+      pxx = __ffma2_rn(xv, xv, pxx);
+      pyy = __ffma2_rn(yv, yv, pyy);
+      if (NS == 4) {
+        pxy = __ffma2_rn(xv, yv, pxy);
+        // Im X Re Y (ro 1) or Re X Im Y (ro 0)
+        const float2 yp = make_float2(__shfl_xor_sync(0xffffffffu, yv.x, 1), __shfl_xor_sync(0xffffffffu, yv.y, 1));
+        pv = __ffma2_rn(xv, yp, pv);
+      }
+      if ((ml + 2) % Q == 0) {             // a window ends here (compile-time)
+        window(ml + 1, pxx.x + pxx.y, pyy.x + pyy.y, pxy.x + pxy.y, pv.x + pv.y);
+        pxx = pyy = pxy = pv = make_float2(0.f, 0.f);
+      }
     }
   }
 }
