@@ -57,7 +57,7 @@ constexpr int kRingBytes = kSmemLimit - 1024 /* alignment slack */ - kBarBytes;
 constexpr int kMinSmem = 120 * 1024;
 constexpr uint32_t kTmemCols = 512;         // 2 accumulators of 128 + 2 x 2 weight planes of <= 64
 constexpr uint32_t kAccCols = kCols;
-constexpr uint32_t kACol0 = kMTiles * kAccCols;   // weights: tile mt plane pl at kACol0 + (2 mt + pl) 64
+constexpr uint32_t kACol0 = kMTiles * kAccCols;   // first weight column (wcol)
 constexpr uint32_t kWaitIters = 1u << 20;
 
 enum ErrCode { ERR_NONE = 0, ERR_PRODUCER = 1, ERR_MMA = 2, ERR_EPILOGUE = 3 };
@@ -483,6 +483,15 @@ __device__ __forceinline__ void flush_stage(const TcParams &p, const float *buf,
 // or a single plan -- plan 0, its parameters at compile-time offsets into the table -- with three
 // (kSingle3) or two (kSingle2) products; a run-time product count costs the single plan ~3 %.
 constexpr int kSingle3 = 0, kSingle2 = 1, kMultiPlan = 2;
+
+// TMEM column of the weights of M tile mt: the hi plane (lo = hi + 64 with three products).  The
+// single-plan two-product form needs no lo planes, which leaves room for two weight sets used by
+// alternate items (set = item parity): the next item's weights are written early in the current
+// item, and the MMAs never wait for them at an item boundary.
+template <int kForm>
+__device__ __forceinline__ uint32_t wcol(int mt, int set) {
+  return kForm == kSingle2 ? kACol0 + (uint32_t)(set * 128 + mt * 64) : kACol0 + (uint32_t)(2 * mt * 64);
+}
 template <int NS, int Q, int kForm>
 __global__ void __launch_bounds__(kThreads, 1)
 bf_tc_kernel(const __grid_constant__ TcLaunch L) {
@@ -596,7 +605,7 @@ bf_tc_kernel(const __grid_constant__ TcLaunch L) {
             }
             tc_fence_after();
             const uint32_t d = tmem + (uint32_t)(mt * kAccCols);
-            uint32_t a_hi = tmem + kACol0 + (uint32_t)(2 * mt * 64);
+            uint32_t a_hi = tmem + wcol<kForm>(mt, it & 1);
             // descriptors advance by adding the byte offset / 16 to the start-address field (all
             // shared addresses are below 256 KB, so the 14-bit field never carries)
             uint64_t b_hi = desc_b0 + (uint64_t)((s * L.stage_max) >> 4);
@@ -631,9 +640,10 @@ bf_tc_kernel(const __grid_constant__ TcLaunch L) {
     const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
     float *const qbuf = stage_out + quad * 2 * St::kBuf;
     uint32_t gpar = 0;                   // tile-pair parity
-    int fl = 0;
+    int fl = 0, eit = 0;                 // staging flushes; items of this CTA so far
     bool ok = true;
-    for (int item = blockIdx.x; item < L.items && ok; item += gridDim.x) {
+    constexpr bool kTwoSets = kForm == kSingle2;
+    for (int item = blockIdx.x; item < L.items && ok; item += gridDim.x, ++eit) {
       const TcParams &p = L.plan[kMulti ? plan_of(L, item) : 0];
       const int Mq = p.M / Q;
       const long long pstride = (long long)p.F * kN * Mq;      // between Stokes parameters
@@ -641,9 +651,9 @@ bf_tc_kernel(const __grid_constant__ TcLaunch L) {
       const int fc = li / p.items_per_fc;
       const int bb = li - fc * p.items_per_fc;
       const int f = fc / kN, c = fc - f * kN;
-      if (item == (int)blockIdx.x) {      // weights of the first item; later ones follow each last tile
-        for (int mt = 0; mt < kMTiles; ++mt) {
-          const uint32_t ta_hi = tmem + lane_off + kACol0 + (uint32_t)(2 * mt * 64);
+      if (item == (int)blockIdx.x) {      // weights of the first item; later ones are written during the
+        for (int mt = 0; mt < kMTiles; ++mt) {   // item before (its first or last tile pair)
+          const uint32_t ta_hi = tmem + lane_off + wcol<kForm>(mt, 0);
           WeightTables tab;
           load_weight_tables(p, f, bb * kBeamsPerItem + mt * (kRows / 2) + quad * 16 + jq, ro, half, tab);
           write_weights(p, ta_hi, ta_hi + 64u, c, ro, half, tab, wlo_of(p));
@@ -664,7 +674,10 @@ bf_tc_kernel(const __grid_constant__ TcLaunch L) {
         const int wbase = (t / St::kPeriod) * 8;
         float *const buf = qbuf + (fl & 1) * St::kBuf;
         for (int mt = 0; mt < kMTiles; ++mt) {
-          const bool boundary = t == p.ntiles - 1 && nitem < L.items;
+          // write the next item's weights after this tile pair: with one weight set, after the
+          // last (the MMAs reading this tile's weights are then complete); with two, after the
+          // first (the other set's last reader, the previous item, is then complete)
+          const bool boundary = (kTwoSets ? t == 0 : t == p.ntiles - 1) && nitem < L.items;
           WeightTables tab;
           if (boundary)   // the next item's table values, in flight while the last accumulator fills
             load_weight_tables(pn, nfc / kN, nbb * kBeamsPerItem + mt * (kRows / 2) + quad * 16 + jq, ro, half, tab);
@@ -687,9 +700,7 @@ bf_tc_kernel(const __grid_constant__ TcLaunch L) {
           __syncwarp();
           if (lane == 0) mbar_arrive(acce_bar(mt));
           if (boundary) {
-            // the MMAs that read this tile's weights are complete (its last accumulator was
-            // committed): write the next item's
-            const uint32_t ta_hi = tmem + lane_off + kACol0 + (uint32_t)(2 * mt * 64);
+            const uint32_t ta_hi = tmem + lane_off + wcol<kForm>(mt, (eit + 1) & 1);
             write_weights(pn, ta_hi, ta_hi + 64u, nfc % kN, ro, half, tab, wlo_of(pn));
             tc_fence_before();
             __syncwarp();
