@@ -24,8 +24,9 @@
 // Work.  A persistent CTA per SM walks the work items (f, c, block of 128 beams) with a stride of
 // the grid, so the CTAs that run together share the (f, c) B tiles in L2.  An item is two UMMA M
 // tiles of 128 rows (64 beams each) by ceil(M/64) N tiles.  Warp roles: warp 0 issues the TMA
-// loads into a ring of stages, warp 1 issues the MMAs (M 128 x N 128 x K 16), warps 2-9 are the
-// epilogue: warp w serves M tile (w-2)/4 and the TMEM lane quadrant w%4.  Each M tile has one
+// loads into a ring of stages, warp 1 issues the MMAs (M 128 x N 128 x K 16), the other warps are
+// the epilogue: warp w serves the TMEM lane quadrant w%4 of both M tiles, 2 or 4 warps per
+// quadrant (epi_split), each draining its share of the spectra of every accumulator.  Each M tile has one
 // accumulator of 128 columns; the two tiles ping-pong, so that the epilogue drains one while the
 // MMAs fill the other.  At an item boundary the epilogue warps of an M tile write that tile's new
 // weights as soon as its last accumulator has been committed (the MMAs that read the old weights
@@ -43,7 +44,6 @@
 namespace lbf {
 namespace {
 
-constexpr int kThreads = 320;               // 10 warps: TMA, MMA, 8 epilogue
 constexpr int kRows = 128;                  // UMMA M
 constexpr int kMTiles = 2;                  // 128 beams per work item
 constexpr int kBeamsPerItem = kMTiles * kRows / 2;
@@ -59,6 +59,14 @@ constexpr uint32_t kTmemCols = 512;         // 2 accumulators of 128 + 2 x 2 wei
 constexpr uint32_t kAccCols = kCols;
 constexpr uint32_t kACol0 = kMTiles * kAccCols;   // first weight column (wcol)
 constexpr uint32_t kWaitIters = 1u << 20;
+
+// Epilogue warps per TMEM lane quadrant: 4 for Stokes outputs whose windows fit in 16 spectra (each
+// warp drains 16 spectra of an accumulator), else 2 (32 spectra each).  The epilogue is the longer
+// side of a work item, so more warps per accumulator shorten it.
+template <int NS, int Q>
+__host__ __device__ constexpr int epi_split() { return (NS != 0 && Q <= 16) ? 4 : 2; }
+template <int NS, int Q>
+__host__ __device__ constexpr int tc_threads() { return 64 + 4 * 32 * epi_split<NS, Q>(); }
 
 enum ErrCode { ERR_NONE = 0, ERR_PRODUCER = 1, ERR_MMA = 2, ERR_EPILOGUE = 3 };
 
@@ -204,19 +212,22 @@ __device__ __forceinline__ uint32_t pack_half2(float lo_k, float hi_k) {
 // evaluate every other station and swap the results; the two warps of a lane quadrant take
 // alternate groups of 8 columns (`half`).  The phase-table values are loaded first
 // (load_weight_tables), so that their latency hides behind an accumulator wait.
-constexpr int kWStations = kMaxKpad / 32 * 4;   // stations one thread evaluates per M tile (16)
-
+// With KS warps per quadrant, warp `sub` takes the groups of 8 columns g8 = sub (mod KS).
+template <int KS>
 struct WeightTables {
-  float ph[kWStations], st[kWStations];   // FP64-reduced phase of the subband, phase step per channel
-  uint32_t ok;                            // bit i: station i of this thread exists (else weight 0)
+  static constexpr int kN8 = kMaxKpad / 16 / KS;   // groups of 8 stations per warp
+  static constexpr int kSt = 4 * kN8;              // stations one thread evaluates per M tile
+  float ph[kSt], st[kSt];   // FP64-reduced phase of the subband, phase step per channel
+  uint32_t ok;              // bit i: station i of this thread exists (else weight 0)
 };
 
+template <int KS>
 __device__ __forceinline__ void load_weight_tables(const TcParams &p, int f, int b, int ro, int half,
-                                                   WeightTables &w) {
+                                                   WeightTables<KS> &w) {
   w.ok = 0;
 #pragma unroll
-  for (int i = 0; i < kWStations; ++i) {
-    const int s = (half + 2 * (i >> 2)) * 8 + 2 * (i & 3) + ro;
+  for (int i = 0; i < WeightTables<KS>::kSt; ++i) {
+    const int s = (half + KS * (i >> 2)) * 8 + 2 * (i & 3) + ro;
     const bool ok = b < p.B && s < p.S;
     const long long bs = (long long)b * p.S + s;
     w.ph[i] = ok ? __ldg(&p.phase0[(long long)f * p.B * p.S + bs]) : 0.f;
@@ -225,12 +236,13 @@ __device__ __forceinline__ void load_weight_tables(const TcParams &p, int f, int
   }
 }
 
+template <int KS>
 __device__ __forceinline__ void write_weights(const TcParams &p, uint32_t ta_hi, uint32_t ta_lo, int c, int ro,
-                                              int half, const WeightTables &tab, bool wlo) {
+                                              int half, const WeightTables<KS> &tab, bool wlo) {
   const float dc = (float)(c - kN / 2);
 #pragma unroll
-  for (int gi = 0; gi < kWStations / 4; ++gi) {
-    const int g8 = half + 2 * gi;                    // 8 stations per store
+  for (int gi = 0; gi < WeightTables<KS>::kN8; ++gi) {
+    const int g8 = half + KS * gi;                   // 8 stations per store
     if (g8 >= p.Kpad / 16) break;
     uint32_t vh[8], vl[8];
 #pragma unroll
@@ -285,15 +297,16 @@ struct Stage {
   }
 };
 
-// One 32-spectrum tile of an accumulator (pol X at `taddr`, pol Y 32 columns on; spectra m0 ..
-// m0 + 31): integrate over windows of Q spectra and store the Stokes parameters, to the staging
-// row `srow` (window wl = w - wbase) or, when staging is off, to the output rows at `orow`.
-template <int NS, int Q>
+// kSpecW spectra (32 or 16) of one 32-spectrum tile of an accumulator (pol X at `taddr`, pol Y
+// 32 columns on; spectra m0 .. m0 + kSpecW - 1): integrate over windows of Q <= kSpecW spectra and
+// store the Stokes parameters, to the staging row `srow` (window wl = w - wbase) or, when staging
+// is off, to the output rows at `orow`.
+template <int NS, int Q, int kSpecW>
 __device__ __forceinline__ void drain_tile(uint32_t taddr, int m0, int ro, int jq, int M, bool beam_ok, float *orow,
                                            long long pstride, float *srow, int wbase) {
-  float x[2][16], y[2][16];
+  float x[kSpecW / 16][16], y[kSpecW / 16][16];
 #pragma unroll
-  for (int ch = 0; ch < 2; ++ch) {
+  for (int ch = 0; ch < kSpecW / 16; ++ch) {
     tmem_ld16(taddr + (uint32_t)(ch * 16), x[ch]);
     tmem_ld16(taddr + (uint32_t)(kSpec + ch * 16), y[ch]);
   }
@@ -333,7 +346,7 @@ __device__ __forceinline__ void drain_tile(uint32_t taddr, int m0, int ro, int j
   if constexpr (Q <= 2) {   // short windows: scalar sums (the pair form spills here)
     float sxx = 0.f, syy = 0.f, sxy = 0.f, sv = 0.f;
 #pragma unroll
-    for (int ml = 0; ml < kSpec; ++ml) {
+    for (int ml = 0; ml < kSpecW; ++ml) {
       const float xv = x[ml >> 4][ml & 15], yv = y[ml >> 4][ml & 15];
       sxx = fmaf(xv, xv, sxx);
       syy = fmaf(yv, yv, syy);
@@ -351,7 +364,7 @@ __device__ __forceinline__ void drain_tile(uint32_t taddr, int m0, int ro, int j
     // the dependency chain of scalar sums); the two halves meet at the window's end
     float2 pxx = make_float2(0.f, 0.f), pyy = pxx, pxy = pxx, pv = pxx;
 #pragma unroll
-    for (int ml = 0; ml < kSpec; ml += 2) {
+    for (int ml = 0; ml < kSpecW; ml += 2) {
       const float2 xv = make_float2(x[ml >> 4][ml & 15], x[ml >> 4][(ml & 15) + 1]);
       const float2 yv = make_float2(y[ml >> 4][ml & 15], y[ml >> 4][(ml & 15) + 1]);
       pxx = __ffma2_rn(xv, xv, pxx);
@@ -429,26 +442,27 @@ __device__ __forceinline__ void drain_tile_v(uint32_t taddr, int m0, int ro, int
   }
 }
 
-// The rows a thread writes in every flush of a work item (64 threads per quadrant: thread t64 of
-// the quadrant's two epilogue warps): rows (beam, Stokes parameter) i = t64 + 64 k, each written
-// as the 16-byte part `part` of a 32-byte segment.  Their addresses depend only on the item, so
-// they are formed once per item (null for beams past B).
+// The rows a thread writes in every flush of a work item (kQT threads per quadrant: thread tq of
+// the quadrant's epilogue warps): rows (beam, Stokes parameter) i = tq + kQT k, each written as the
+// 16-byte part `part` of a 32-byte segment.  Their addresses depend only on the item, so they are
+// formed once per item (null for beams past B, and for threads past the quadrant's 64 NS parts).
 template <int NS, int Q>
 struct FlushRows {
-  static constexpr int kRowsPer = NS * 2 * 32 / 64 > 0 ? NS * 2 * 32 / 64 : 1;   // rows per thread
+  static constexpr int kQT = 32 * epi_split<NS, Q>();
+  static constexpr int kRowsPer = NS * 2 * 32 / kQT > 0 ? NS * 2 * 32 / kQT : 1;   // rows per thread
   float *row[kRowsPer];
   int soff[kRowsPer];     // float offset of the row's part within the quadrant buffer
   int part;
 };
 
 template <int NS, int Q>
-__device__ __forceinline__ void flush_rows(const TcParams &p, FlushRows<NS, Q> &fr, int t64, int quad, int bb, int f,
+__device__ __forceinline__ void flush_rows(const TcParams &p, FlushRows<NS, Q> &fr, int tq, int quad, int bb, int f,
                                            int c) {
   const int Mq = p.M / Q;
-  fr.part = t64 & 1;
+  fr.part = tq & 1;
 #pragma unroll
   for (int k = 0; k < FlushRows<NS, Q>::kRowsPer; ++k) {
-    const int i = t64 + 64 * k;
+    const int i = tq + FlushRows<NS, Q>::kQT * k;
     const int param = (i >> 1) % NS, bq = (i >> 1) / NS;
     const int jq = bq & 15, mt = bq >> 4;
     const int b = bb * kBeamsPerItem + mt * (kRows / 2) + quad * 16 + jq;
@@ -493,9 +507,11 @@ __device__ __forceinline__ uint32_t wcol(int mt, int set) {
   return kForm == kSingle2 ? kACol0 + (uint32_t)(set * 128 + mt * 64) : kACol0 + (uint32_t)(2 * mt * 64);
 }
 template <int NS, int Q, int kForm>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(tc_threads<NS, Q>(), 1)
 bf_tc_kernel(const __grid_constant__ TcLaunch L) {
   constexpr bool kMulti = kForm == kMultiPlan;
+  constexpr int KS = epi_split<NS, Q>();          // epilogue warps per TMEM lane quadrant
+  constexpr int kSpecW = 2 * kSpec / KS;          // spectra of a tile one epilogue warp drains
   // whether plan p adds the Wlo Yhi product
   auto wlo_of = [](const TcParams &p) { return kMulti ? p.wlo != 0 : kForm == kSingle3; };
   using St = Stage<NS, Q>;
@@ -526,10 +542,10 @@ bf_tc_kernel(const __grid_constant__ TcLaunch L) {
     }
     for (int mt = 0; mt < kMTiles; ++mt) {
       mbar_init(accf_bar(mt), 1);
-      mbar_init(acce_bar(mt), 8);     // one arrival per epilogue warp
-      mbar_init(afull_bar(mt), 8);
+      mbar_init(acce_bar(mt), 4 * KS);     // one arrival per epilogue warp
+      mbar_init(afull_bar(mt), 4 * KS);
     }
-    for (int q = 0; q < 4; ++q) mbar_init(pair_bar(q), 2);
+    for (int q = 0; q < 4; ++q) mbar_init(pair_bar(q), KS);
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -633,8 +649,9 @@ bf_tc_kernel(const __grid_constant__ TcLaunch L) {
   } else {
     // ---------------------------------------------------------------- epilogue: weights, TMEM -> Stokes
     // warp (quad, half): TMEM lanes 32 quad .. +31 of both M tiles; weight columns of groups
-    // g8 = half (mod 2); accumulator tile 2t + half of every tile pair t
+    // g8 = half (mod KS); of every tile pair t, spectra q2 kSpecW .. + kSpecW - 1 of tile 2t + h
     const int quad = warp & 3, half = (warp - 2) >> 2;
+    const int h = half / (KS / 2), q2 = half % (KS / 2);
     const int ro = lane & 1;              // 0: Re V rows, 1: Im V rows
     const int jq = lane >> 1;             // beam within the quadrant (16 per M tile)
     const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
@@ -654,7 +671,7 @@ bf_tc_kernel(const __grid_constant__ TcLaunch L) {
       if (item == (int)blockIdx.x) {      // weights of the first item; later ones are written during the
         for (int mt = 0; mt < kMTiles; ++mt) {   // item before (its first or last tile pair)
           const uint32_t ta_hi = tmem + lane_off + wcol<kForm>(mt, 0);
-          WeightTables tab;
+          WeightTables<KS> tab;
           load_weight_tables(p, f, bb * kBeamsPerItem + mt * (kRows / 2) + quad * 16 + jq, ro, half, tab);
           write_weights(p, ta_hi, ta_hi + 64u, c, ro, half, tab, wlo_of(p));
           tc_fence_before();
@@ -669,7 +686,7 @@ bf_tc_kernel(const __grid_constant__ TcLaunch L) {
       const int nfc = nli / pn.items_per_fc;
       const int nbb = nli - nfc * pn.items_per_fc;
       FlushRows<NS, Q> frows;
-      if constexpr (St::kOn) flush_rows<NS, Q>(p, frows, half * 32 + lane, quad, bb, f, c);
+      if constexpr (St::kOn) flush_rows<NS, Q>(p, frows, half * 32 + lane, quad, bb, f, c);   // tq
       for (int t = 0; t < p.ntiles && ok; ++t, gpar ^= 1u) {
         const int wbase = (t / St::kPeriod) * 8;
         float *const buf = qbuf + (fl & 1) * St::kBuf;
@@ -678,14 +695,14 @@ bf_tc_kernel(const __grid_constant__ TcLaunch L) {
           // last (the MMAs reading this tile's weights are then complete); with two, after the
           // first (the other set's last reader, the previous item, is then complete)
           const bool boundary = (kTwoSets ? t == 0 : t == p.ntiles - 1) && nitem < L.items;
-          WeightTables tab;
+          WeightTables<KS> tab;
           if (boundary)   // the next item's table values, in flight while the last accumulator fills
             load_weight_tables(pn, nfc / kN, nbb * kBeamsPerItem + mt * (kRows / 2) + quad * 16 + jq, ro, half, tab);
           if (!mbar_wait(accf_bar(mt), gpar, abort_flag)) { fail(abort_flag, p.err, ERR_EPILOGUE); ok = false; break; }
           tc_fence_after();
           const int b = bb * kBeamsPerItem + mt * (kRows / 2) + quad * 16 + jq;
-          const uint32_t taddr = tmem + lane_off + (uint32_t)(mt * kAccCols + half * 2 * kSpec);
-          const int m0 = t * 2 * kSpec + half * kSpec;
+          const uint32_t taddr = tmem + lane_off + (uint32_t)(mt * kAccCols + h * 2 * kSpec + q2 * kSpecW);
+          const int m0 = t * 2 * kSpec + h * kSpec + q2 * kSpecW;
           if constexpr (NS == 0) {
             const int b0 = bb * kBeamsPerItem + mt * (kRows / 2) + quad * 16;   // beam of lanes 0, 1
             const long long bstride = (long long)p.F * kN * kP * p.M;             // between beams
@@ -694,7 +711,8 @@ bf_tc_kernel(const __grid_constant__ TcLaunch L) {
                          reinterpret_cast<float2 *>(stage_out) + (warp - 2) * (kVStageBytes / 8));
           } else {
             float *const orow = p.out + (((long long)b * NS * p.F + f) * kN + c) * Mq;
-            drain_tile<NS, Q>(taddr, m0, ro, jq, p.M, b < p.B, orow, pstride, buf + (mt * 16 + jq) * St::kRow, wbase);
+            drain_tile<NS, Q, kSpecW>(taddr, m0, ro, jq, p.M, b < p.B, orow, pstride, buf + (mt * 16 + jq) * St::kRow,
+                                      wbase);
           }
           tc_fence_before();
           __syncwarp();
@@ -742,7 +760,7 @@ cudaError_t launch_q(TcLaunch &L, int grid, cudaStream_t st) {
   if (smem < kMinSmem) smem = kMinSmem;
   cudaError_t e = cudaFuncSetAttribute(bf_tc_kernel<NS, Q, kForm>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  bf_tc_kernel<NS, Q, kForm><<<grid, kThreads, smem, st>>>(L);
+  bf_tc_kernel<NS, Q, kForm><<<grid, tc_threads<NS, Q>(), smem, st>>>(L);
   return cudaGetLastError();
 }
 
