@@ -26,11 +26,11 @@
 // tiles of 128 rows (64 beams each) by ceil(M/64) N tiles.  Warp roles: warp 0 issues the TMA
 // loads into a ring of stages, warp 1 issues the MMAs (M 128 x N 128 x K 16), the other warps are
 // the epilogue: warp w serves the TMEM lane quadrant w%4 of both M tiles, 2 or 4 warps per
-// quadrant (epi_split), each draining its share of the spectra of every accumulator.  Each M tile has one
-// accumulator of 128 columns; the two tiles ping-pong, so that the epilogue drains one while the
-// MMAs fill the other.  At an item boundary the epilogue warps of an M tile write that tile's new
-// weights as soon as its last accumulator has been committed (the MMAs that read the old weights
-// are then complete), while the other tile's MMAs still run.
+// quadrant (epi_split), each draining its share of the spectra of every accumulator.  Each M tile
+// has one accumulator of 128 columns; the two tiles ping-pong, so that the epilogue drains one
+// while the MMAs fill the other.  The epilogue warps of an M tile write its next item's weights as
+// soon as the MMAs that read the weights they replace are complete: at the item's last tile pair
+// with one weight set (three products), at its first with two (the two-product form).
 //
 // The epilogue integrates each polarisation component over the window in registers (one shuffle
 // per spectrum for Stokes V) and combines the (Re, Im) row pair with two shuffles per window.
