@@ -26,7 +26,9 @@
 namespace {
 
 constexpr uint32_t kBatchMagic = 0x4c424642u;   // "LBFB"
-constexpr int kMaxCounters = 64;                // >= 4 filter-bank + 3 x 3 x 3 beam-former classes
+// work counters, one per grouped launch: at most one filter-bank and one beam-former launch per
+// plan, plus the partly filled launches of each class
+int max_counters(int n) { return 2 * n + 64; }
 
 bool plan_ok(lbf_plan_t p) { return p && p->magic == lbf::kPlanMagic; }
 
@@ -53,8 +55,8 @@ struct lbf_batch_s {
   std::vector<int> variant;            // beam-former kernel per plan
   // group tables: [parity][plan]; parity p describes the plans' history state after p blocks
   lbf::PpfGroup *h_ppf = nullptr, *d_ppf = nullptr;   // pinned host / device, 2 * n
-  lbf::BfGroup *h_bf = nullptr, *d_bf = nullptr;     // FP32 plans, class by class
-  unsigned long long *d_counter = nullptr;            // [kMaxCounters] work counters, one per launch
+  lbf::BfGroup *h_bf = nullptr;                      // pinned host, 2 * n: FP32 plans, class by class
+  unsigned long long *d_counter = nullptr;            // [max_counters(n)] work counters, one per launch
   long long hist_items = 0;
   // launch classes: filter bank per (sample width, FP32 or FP16 output); FP32 beam former per
   // (variant, output kind, CTAs per SM) -- each class one persistent launch over its groups
@@ -93,6 +95,10 @@ void fill_tables(lbf_batch_t b, int par, const void *const *d_in, void *const *d
       for (int i = 0; i < n; ++i) {
         lbf_plan_t p = b->plans[i];
         if (p->bits != bits || (p->tc ? 1 : 0) != tc) continue;
+        if (cls.n == lbf::kMaxGroups) {   // one launch holds at most kMaxGroups groups
+          b->ppf_cls.push_back(cls);
+          cls = lbf_batch_s::PpfClass{bits, tc, slot, 0, 0};
+        }
         const int cur = p->cur ^ par;
         lbf::PpfGroup &G = b->h_ppf[par * n + slot++];
         G.g = p->geometry();
@@ -137,7 +143,7 @@ void fill_tables(lbf_batch_t b, int par, const void *const *d_in, void *const *d
     for (int j = i; j < n; ++j) {
       lbf_plan_t p = b->plans[j];
       if (p->tc || placed[j] || b->variant[j] != cls.variant || p->out_kind != cls.out_kind ||
-          per_sm[j] != cls.per_sm)
+          per_sm[j] != cls.per_sm || cls.n == lbf::kMaxGroups)
         continue;
       placed[j] = true;
       lbf::BfGroup &Bg = b->h_bf[par * n + slot++];
@@ -160,10 +166,10 @@ void fill_tables(lbf_batch_t b, int par, const void *const *d_in, void *const *d
 // Enqueue one batch block with the tables of parity `par` (already filled).
 cudaError_t enqueue(lbf_batch_t b, int par, cudaStream_t st) {
   const int n = (int)b->plans.size();
+  // the history update reads the filter-bank table from device memory; the grouped filter bank
+  // and beam former take theirs as kernel parameters
   cudaError_t e = cudaMemcpyAsync(b->d_ppf + par * n, b->h_ppf + par * n, sizeof(lbf::PpfGroup) * n,
                                   cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b->d_bf + par * n, b->h_bf + par * n, sizeof(lbf::BfGroup) * n, cudaMemcpyHostToDevice, st);
   if (b->per_plan) {
     // each plan's own filter bank, history update and FP32 beam former (the hardware schedules
     // their CTAs; large observations each fill the GPU) -- the tensor-core stage stays grouped
@@ -189,12 +195,12 @@ cudaError_t enqueue(lbf_batch_t b, int par, cudaStream_t st) {
     int counter = 0;
     for (const auto &c : b->ppf_cls)
       if (e == cudaSuccess)
-        e = lbf::launch_ppf_group(c.bits, c.tc, b->d_ppf + par * n + c.first, c.n, c.items,
+        e = lbf::launch_ppf_group(c.bits, c.tc, b->h_ppf + par * n + c.first, c.n, c.items,
                                   b->d_counter + counter++, b->ppf_ctas, st);
     if (e == cudaSuccess) e = lbf::launch_hist_group(b->d_ppf + par * n, n, b->hist_items, st);
     for (const auto &c : b->bf_cls)
       if (e == cudaSuccess)
-        e = lbf::launch_bf_group(c.variant, c.out_kind, b->d_bf + par * n + c.first, c.n, c.items,
+        e = lbf::launch_bf_group(c.variant, c.out_kind, b->h_bf + par * n + c.first, c.n, c.items,
                                  b->d_counter + counter++, c.smem, st);
   }
   // tensor-core plans: their incoherent beams, then ONE persistent tcgen05 launch per class of
@@ -274,10 +280,9 @@ lbf_status lbf_batch_create(const lbf_plan_t *plans, int32_t n, lbf_batch_t *out
   cudaError_t e = cudaMallocHost((void **)&b->h_ppf, sizeof(lbf::PpfGroup) * 2 * n);
   if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_bf, sizeof(lbf::BfGroup) * 2 * n);
   if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_ppf, sizeof(lbf::PpfGroup) * 2 * n);
-  if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_bf, sizeof(lbf::BfGroup) * 2 * n);
-  if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_counter, kMaxCounters * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_counter, max_counters(n) * sizeof(unsigned long long));
   if (e != cudaSuccess) {
-    cudaFreeHost(b->h_ppf); cudaFreeHost(b->h_bf); cudaFree(b->d_ppf); cudaFree(b->d_bf); cudaFree(b->d_counter);
+    cudaFreeHost(b->h_ppf); cudaFreeHost(b->h_bf); cudaFree(b->d_ppf); cudaFree(b->d_counter);
     delete b;
     cudaGetLastError();
     return status_of(e);
@@ -291,7 +296,7 @@ lbf_status lbf_batch_destroy(lbf_batch_t b) {
   if (b->magic != kBatchMagic) return LBF_ESTATE;
   cudaDeviceSynchronize();
   free_graphs(b);
-  cudaFreeHost(b->h_ppf); cudaFreeHost(b->h_bf); cudaFree(b->d_ppf); cudaFree(b->d_bf); cudaFree(b->d_counter);
+  cudaFreeHost(b->h_ppf); cudaFreeHost(b->h_bf); cudaFree(b->d_ppf); cudaFree(b->d_counter);
   b->magic = 0;
   delete b;
   return LBF_OK;

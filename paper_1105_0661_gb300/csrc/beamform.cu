@@ -354,18 +354,22 @@ bf_many_kernel(Geometry g, const float2 *__restrict__ ct, void *__restrict__ out
 // memory footprint, as when its observation runs alone.
 template <int V, int OUT>
 __global__ void __launch_bounds__(kManyThreads, (V == 3 && OUT != OUT_STOKES_IQUV) ? 3 : 2)
-bf_group_kernel(const BfGroup *__restrict__ grp, int ngrp, long long total, unsigned long long *counter) {
+bf_group_kernel(const __grid_constant__ BfTable T, long long total, unsigned long long *counter) {
   extern __shared__ __align__(16) float2 smem[];
   __shared__ long long item_s;
+  __shared__ int grp_s;
   for (;;) {
-    if (threadIdx.x == 0) item_s = (long long)atomicAdd(counter, 1ull);
+    if (threadIdx.x == 0) {
+      const long long it = (long long)atomicAdd(counter, 1ull);
+      item_s = it;
+      grp_s = it < total ? group_of(T, it) : 0;
+    }
     __syncthreads();
     const long long item = item_s;
+    const int o = grp_s;
     __syncthreads();
     if (item >= total) break;
-    int o = 0;
-    while (o + 1 < ngrp && grp[o + 1].first_item <= item) ++o;
-    const BfGroup &G = grp[o];
+    const BfGroup &G = T.grp[o];
     const long long local = item - G.first_item;
     const int fc = (int)(local / G.per_fc), sub = (int)(local - (long long)fc * G.per_fc);
     if constexpr (V == 1) bf_few_item<OUT>(G.g, G.ct, G.out, fc, sub, smem);
@@ -427,8 +431,8 @@ cudaError_t launch_beamform(const Geometry &g, int variant, int out_kind, const 
 namespace {
 
 template <int V, int OUT>
-cudaError_t launch_group_t(const BfGroup *d_groups, int ngrp, long long total, unsigned long long *counter,
-                           size_t smem, cudaStream_t st) {
+cudaError_t launch_group_t(const BfTable &T, long long total, unsigned long long *counter, size_t smem,
+                           cudaStream_t st) {
   auto kern = bf_group_kernel<V, OUT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -441,16 +445,16 @@ cudaError_t launch_group_t(const BfGroup *d_groups, int ngrp, long long total, u
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
-  kern<<<per_sm * sms, kManyThreads, smem, st>>>(d_groups, ngrp, total, counter);
+  kern<<<per_sm * sms, kManyThreads, smem, st>>>(T, total, counter);
   return cudaGetLastError();
 }
 
 template <int V>
-cudaError_t launch_group_v(int out_kind, const BfGroup *d_groups, int ngrp, long long total,
-                           unsigned long long *counter, size_t smem, cudaStream_t st) {
-  if (out_kind == OUT_STOKES_I) return launch_group_t<V, OUT_STOKES_I>(d_groups, ngrp, total, counter, smem, st);
-  if (out_kind == OUT_STOKES_IQUV) return launch_group_t<V, OUT_STOKES_IQUV>(d_groups, ngrp, total, counter, smem, st);
-  return launch_group_t<V, OUT_VOLTAGES>(d_groups, ngrp, total, counter, smem, st);
+cudaError_t launch_group_v(int out_kind, const BfTable &T, long long total, unsigned long long *counter, size_t smem,
+                           cudaStream_t st) {
+  if (out_kind == OUT_STOKES_I) return launch_group_t<V, OUT_STOKES_I>(T, total, counter, smem, st);
+  if (out_kind == OUT_STOKES_IQUV) return launch_group_t<V, OUT_STOKES_IQUV>(T, total, counter, smem, st);
+  return launch_group_t<V, OUT_VOLTAGES>(T, total, counter, smem, st);
 }
 
 template <int V, int OUT>
@@ -477,12 +481,16 @@ int residency_v(int out_kind, size_t smem) {
 
 }  // namespace
 
-cudaError_t launch_bf_group(int variant, int out_kind, const BfGroup *d_groups, int ngrp, long long total,
+cudaError_t launch_bf_group(int variant, int out_kind, const BfGroup *h_groups, int ngrp, long long total,
                             unsigned long long *counter, size_t smem, cudaStream_t st) {
   if (total == 0) return cudaSuccess;
-  if (variant == 1) return launch_group_v<1>(out_kind, d_groups, ngrp, total, counter, smem, st);
-  if (variant == 3) return launch_group_v<3>(out_kind, d_groups, ngrp, total, counter, smem, st);
-  return launch_group_v<2>(out_kind, d_groups, ngrp, total, counter, smem, st);
+  if (ngrp < 1 || ngrp > kMaxGroups) return cudaErrorInvalidValue;
+  BfTable T;
+  T.n = ngrp;
+  for (int i = 0; i < ngrp; ++i) T.grp[i] = h_groups[i];
+  if (variant == 1) return launch_group_v<1>(out_kind, T, total, counter, smem, st);
+  if (variant == 3) return launch_group_v<3>(out_kind, T, total, counter, smem, st);
+  return launch_group_v<2>(out_kind, T, total, counter, smem, st);
 }
 
 int bf_group_residency(int variant, int out_kind, size_t smem) {

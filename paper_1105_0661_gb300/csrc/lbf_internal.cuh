@@ -76,18 +76,37 @@ struct BfGroup {
 // a1-a3 (+ a4 when ct or ct16 is given): filter bank; reads history `hist`, block `in`.
 cudaError_t launch_ppf(const Geometry &g, int bits, const void *in, const void *hist,
                        float2 *chan, float2 *ct, cudaStream_t st, const Ct16Out *ct16 = nullptr);
-// batch: persistent grouped filter bank (FP32 corner-turned output), history update, beam former
+// batch: persistent grouped filter bank (FP32 corner-turned output), history update, beam former.
+// A grouped launch takes its groups (HOST array, at most kMaxGroups) as a grid-constant kernel
+// parameter, so that a work item reads its observation's geometry from the constant bank, as a
+// kernel of one observation does.
+constexpr int kMaxGroups = 64;
+struct PpfTable { PpfGroup grp[kMaxGroups]; int n; };
+struct BfTable { BfGroup grp[kMaxGroups]; int n; };
+// The group of work item `item` in a grouped launch: the last group whose first item is <= item
+// (binary search, by one thread per item; the others read the result from shared memory).
+template <class Table>
+__device__ __forceinline__ int group_of(const Table &T, long long item) {
+  int lo = 0, hi = T.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (T.grp[mid].first_item <= item) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
 // one persistent launch for the groups of one sample width and output form (FP32 corner turn or
-// FP16 planes); items numbered from 0 within the class
-cudaError_t launch_ppf_group(int bits, int tc, const PpfGroup *d_groups, int ngrp, long long total,
+// FP16 planes); items numbered from 0 within the launch
+cudaError_t launch_ppf_group(int bits, int tc, const PpfGroup *h_groups, int ngrp, long long total,
                              unsigned long long *counter, int ctas, cudaStream_t st);
+// history update of all groups (DEVICE table: each thread looks up its own element's group)
 cudaError_t launch_hist_group(const PpfGroup *d_groups, int ngrp, long long total, cudaStream_t st);
 // filter-bank work items (both polarisations of one stream chunk) per (station, subband) stream
 int ppf_items_per_stream(int M, int spc);
 int ppf_ctas_per_sm();
 // one persistent launch for groups of one beam-former variant (1, 2 or 3) and output kind, sized to
 // the residency of that kernel with `smem` bytes of shared memory (bf_group_residency)
-cudaError_t launch_bf_group(int variant, int out_kind, const BfGroup *d_groups, int ngrp, long long total,
+cudaError_t launch_bf_group(int variant, int out_kind, const BfGroup *h_groups, int ngrp, long long total,
                             unsigned long long *counter, size_t smem, cudaStream_t st);
 int bf_group_residency(int variant, int out_kind, size_t smem);
 int few_beams_per_item();

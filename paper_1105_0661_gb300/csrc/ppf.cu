@@ -498,22 +498,26 @@ ppf_kernel(Geometry g, const typename SampleIO<BITS>::word *__restrict__ in,
 // when its observation runs alone.
 template <int BITS, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
-ppf_group_kernel(const PpfGroup *__restrict__ grp, int ngrp, long long total, unsigned long long *counter) {
+ppf_group_kernel(const __grid_constant__ PpfTable T, long long total, unsigned long long *counter) {
   using word = typename SampleIO<BITS>::word;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ long long item_s;
+  __shared__ int grp_s;
   PpfSmem<BITS> &sm = *reinterpret_cast<PpfSmem<BITS> *>(smem_raw);
   ppf_setup(sm.ctl);
   uint32_t ph = 0;
   for (;;) {
-    if (threadIdx.x == 0) item_s = sm.ctl.abort ? total : (long long)atomicAdd(counter, 1ull);
+    if (threadIdx.x == 0) {
+      const long long it = sm.ctl.abort ? total : (long long)atomicAdd(counter, 1ull);
+      item_s = it;
+      grp_s = it < total ? group_of(T, it) : 0;
+    }
     __syncthreads();
     const long long item = item_s;
+    const int o = grp_s;
     __syncthreads();
     if (item >= total) break;
-    int o = 0;
-    while (o + 1 < ngrp && grp[o + 1].first_item <= item) ++o;
-    const PpfGroup &G = grp[o];
+    const PpfGroup &G = T.grp[o];
     const long long local = item - G.first_item;
     const long long sf = local / G.chunks;
     const int chunk = (int)(local - sf * G.chunks);
@@ -528,7 +532,7 @@ ppf_group_kernel(const PpfGroup *__restrict__ grp, int ngrp, long long total, un
 }
 
 template <int BITS, int MODE>
-cudaError_t launch_group_t(const PpfGroup *d_groups, int ngrp, long long total, unsigned long long *counter, int ctas,
+cudaError_t launch_group_t(const PpfTable &T, long long total, unsigned long long *counter, int ctas,
                            cudaStream_t st) {
   const size_t smem = sizeof(PpfSmem<BITS>);
   auto kern = ppf_group_kernel<BITS, MODE>;
@@ -536,7 +540,7 @@ cudaError_t launch_group_t(const PpfGroup *d_groups, int ngrp, long long total, 
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
-  kern<<<ctas, kThreads, smem, st>>>(d_groups, ngrp, total, counter);
+  kern<<<ctas, kThreads, smem, st>>>(T, total, counter);
   return cudaGetLastError();
 }
 
@@ -623,13 +627,17 @@ cudaError_t launch_ppf(const Geometry &g, int bits, const void *in, const void *
                     : launch_ppf_bits<8>(g, in, hist, chan, ct, ct16, st);
 }
 
-cudaError_t launch_ppf_group(int bits, int tc, const PpfGroup *d_groups, int ngrp, long long total,
+cudaError_t launch_ppf_group(int bits, int tc, const PpfGroup *h_groups, int ngrp, long long total,
                              unsigned long long *counter, int ctas, cudaStream_t st) {
   if (total == 0) return cudaSuccess;
-  if (bits == 16) return tc ? launch_group_t<16, MODE_CT16>(d_groups, ngrp, total, counter, ctas, st)
-                            : launch_group_t<16, MODE_CT32>(d_groups, ngrp, total, counter, ctas, st);
-  return tc ? launch_group_t<8, MODE_CT16>(d_groups, ngrp, total, counter, ctas, st)
-            : launch_group_t<8, MODE_CT32>(d_groups, ngrp, total, counter, ctas, st);
+  if (ngrp < 1 || ngrp > kMaxGroups) return cudaErrorInvalidValue;
+  PpfTable T;
+  T.n = ngrp;
+  for (int i = 0; i < ngrp; ++i) T.grp[i] = h_groups[i];
+  if (bits == 16) return tc ? launch_group_t<16, MODE_CT16>(T, total, counter, ctas, st)
+                            : launch_group_t<16, MODE_CT32>(T, total, counter, ctas, st);
+  return tc ? launch_group_t<8, MODE_CT16>(T, total, counter, ctas, st)
+            : launch_group_t<8, MODE_CT32>(T, total, counter, ctas, st);
 }
 
 cudaError_t launch_hist_group(const PpfGroup *d_groups, int ngrp, long long total, cudaStream_t st) {
