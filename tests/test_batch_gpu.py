@@ -175,3 +175,38 @@ def test_batch_of_sixteen_uneven_observations_matches_the_oracle():
     check("tuned")
     print(f"batch of 16 vs oracle: max Stokes I rel err FP32 {worst['fp32']:.2e}, tensor cores {worst['fp16tc']:.2e}")
     batch.close()
+
+
+def test_batch_larger_than_one_launch_table():
+    """70 small observations of one class (int16, FP32, Stokes I, few-beam): a grouped launch
+    holds at most 64 observations, so the class runs as two launches each numbering its own work
+    items; every output equals the same plan run alone, over two blocks."""
+    from paper_1105_0661_gb300 import Batch, Plan, build_lib
+    build_lib.build()
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    rng = np.random.default_rng(7)
+    wls = []
+    for i in range(70):
+        S, F, B = 2 + i % 5, 1 + i % 3, 1 + i % 4
+        xyz = G.lofar_positions(rng, S // 2, S - S // 2)
+        wls.append(G.Workload(f"m{i}", xyz, G.subband_centres(F, 120e6 + 1e6 * i), G.hex_beam_grid(B, 0.05),
+                              (0.3, 0.4), 32 * N, 4, "I", sample_bits=16, sigma=32.0, source="tone"))
+    solo = [Plan.from_workload(wl) for wl in wls]
+    grouped = [Plan.from_workload(wl) for wl in wls]
+    assert {p.dims.bf_kernel for p in grouped} == {1}
+    batch = Batch(grouped)
+    d_in = [torch.empty((wl.n_stations, wl.n_subbands, wl.block_samples, 2, 2), dtype=torch.int16, device=dev)
+            for wl in wls]
+    so = [_out(p, dev) for p in solo]
+    bo = [_out(p, dev) for p in grouped]
+    for k in range(2):
+        for i, wl in enumerate(wls):
+            d_in[i].copy_(torch.from_numpy(G.make_block(wl, seed=i, block_index=k)))
+            solo[i].run_block(d_in[i], so[i])
+        batch.run(d_in, bo)
+        torch.cuda.synchronize()
+        for i in range(len(wls)):
+            assert torch.equal(so[i], bo[i]), (k, i)
+    assert batch.launches() < 70
+    batch.close()
