@@ -210,7 +210,8 @@ cudaError_t enqueue(lbf_batch_t b, int par, cudaStream_t st) {
   for (int i = 0; i < n && e == cudaSuccess; ++i) {
     lbf_plan_t p = b->plans[i];
     if (!p->tc || p->M == 0) continue;
-    const lbf::Geometry g = p->geometry();
+    lbf::Geometry g = p->geometry();
+    g.ct16_raw = 1;   // planes from the grouped filter bank: delay and bandpass go with the weights
     if (p->inc) {
       lbf::Ct16Out o;
       o.hi = p->ct16[0];

@@ -79,6 +79,7 @@ struct TcParams {
   int vec;                    // output rows 16-byte aligned (M/Q % 4 == 0, aligned base)
   int wlo;                    // 1: three products (Wlo Yhi too); 0: two products
   const float *phase0, *step;
+  const float *bp;            // bandpass folded into the weights (raw FP16 planes), or null
   float *out;
   int *err;                   // the plan's device error word
 };
@@ -240,6 +241,7 @@ template <int KS>
 __device__ __forceinline__ void write_weights(const TcParams &p, uint32_t ta_hi, uint32_t ta_lo, int c, int ro,
                                               int half, const WeightTables<KS> &tab, bool wlo) {
   const float dc = (float)(c - kN / 2);
+  const float bpc = p.bp ? __ldg(&p.bp[c]) : 1.f;   // bandpass of the channel (raw planes)
 #pragma unroll
   for (int gi = 0; gi < WeightTables<KS>::kN8; ++gi) {
     const int g8 = half + KS * gi;                   // 8 stations per store
@@ -256,6 +258,8 @@ __device__ __forceinline__ void write_weights(const TcParams &p, uint32_t ta_hi,
         float phi = fmaf(dc, tab.st[i], tab.ph[i]);
         phi -= rintf(phi);
         __sincosf(6.283185307179586f * phi, &w.y, &w.x);
+        w.x *= bpc;
+        w.y *= bpc;
       }
       float2 o;
       o.x = __shfl_xor_sync(0xffffffffu, w.x, 1);
@@ -800,7 +804,12 @@ bool fill_plan(TcLaunch &L, int i, const Geometry &g, int out_kind, const void *
   if (items + first >= (1ll << 31)) return false;
   p.items = (int)items;
   p.first_item = (int)first;
-  p.phase0 = g.phase0; p.step = g.step; p.out = out; p.err = err;
+  // raw planes (the fused path): weights with the delay compensation and the bandpass folded in
+  p.phase0 = g.ct16_raw ? g.phase0g : g.phase0;
+  p.step = g.ct16_raw ? g.stepg : g.step;
+  p.bp = g.ct16_raw ? g.bandpass : nullptr;
+  if (!p.phase0 || !p.step) return false;
+  p.out = out; p.err = err;
   p.wlo = g.tc_wlo ? 1 : 0;
   const bool aligned = (reinterpret_cast<uintptr_t>(out) & 15) == 0;
   p.vec = out_kind == OUT_VOLTAGES ? (g.M % 2 == 0 && aligned) : ((g.M / g.Q) % 4 == 0 && aligned);

@@ -79,7 +79,9 @@ ct_to_ct16_kernel(Geometry g, const float2 *__restrict__ ct, Ct16Out o, long lon
 
 // Incoherent beam of a tensor-core plan (Section 3) from its FP16 planes [F*N][Mt][kpad][P][32]:
 // thread per (subband-channel, spectrum), summing over stations the Stokes parameters of
-// Y = hi (+ lo); writes beam index B of the Stokes output.  Lane l of a warp holds spectrum
+// Y = hi (+ lo); writes beam index B of the Stokes output.  Planes written before the delay phase
+// and bandpass (g.ct16_raw) get the bandpass here: the unit delay phasor leaves the powers alone,
+// the bandpass scales every Stokes parameter by bp[c]^2.  Lane l of a warp holds spectrum
 // 32 w + l, so the integration over Q <= 32 spectra is a warp-shuffle reduction.
 template <int NS>
 __global__ void __launch_bounds__(256)
@@ -112,9 +114,10 @@ incoherent_ct16_kernel(Geometry g, Ct16Out o, float *__restrict__ out) {
         im = fmaf(xi, yr, fmaf(-xr, yi, im));
       }
     }
+    const float b2 = g.ct16_raw ? g.bandpass[c] * g.bandpass[c] : 1.f;
 #pragma unroll
     for (int st = 0; st < NS; ++st) {
-      float v = st == 0 ? xx + yy : st == 1 ? xx - yy : st == 2 ? 2.f * re : 2.f * im;
+      float v = b2 * (st == 0 ? xx + yy : st == 1 ? xx - yy : st == 2 ? 2.f * re : 2.f * im);
       for (int o2 = 1; o2 < g.Q; o2 <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o2);
       if (active && (m & (g.Q - 1)) == 0)
         out[((((long long)g.B * NS + st) * g.F + f) * kN + c) * Mq + m / g.Q] = v;

@@ -55,7 +55,7 @@ void release(lbf_plan_s *p) {
   cudaFree(p->taps); cudaFree(p->twiddle); cudaFree(p->bandpass); cudaFree(p->dshift);
   cudaFree(p->tau); cudaFree(p->resid); cudaFree(p->f0); cudaFree(p->dtau);
   cudaFree(p->hist[0]); cudaFree(p->hist[1]); cudaFree(p->ws);
-  cudaFree(p->phase0); cudaFree(p->step);
+  cudaFree(p->phase0); cudaFree(p->step); cudaFree(p->phase0g); cudaFree(p->stepg);
   cudaFree(p->ct16[0]); cudaFree(p->d_err); cudaFree(p->ss_members); cudaFree(p->ss_offs);
   if (p->h2d) cudaStreamDestroy(p->h2d);
   if (p->d2h) cudaStreamDestroy(p->d2h);
@@ -195,10 +195,13 @@ int bf_kernel_id(lbf_plan_t p) { return p->variant == 1 ? K_BF_FEW : p->variant 
 // waits for out_free (optional).
 cudaError_t run_block_device(lbf_plan_t p, const void *d_in, void *d_out, void *ws, const CUtensorMap *maps,
                              cudaStream_t st, cudaEvent_t input_read = nullptr, cudaEvent_t out_free = nullptr) {
-  const lbf::Geometry g = p->geometry();
+  lbf::Geometry g = p->geometry();
   const void *h = p->hist[p->cur];
   void *nh = p->hist[p->cur ^ 1];
   if (p->tc) {
+    // the filter bank writes the FP16 planes before the delay phase and bandpass; the
+    // tensor-core weights carry both (folded tables), the incoherent beam the bandpass
+    g.ct16_raw = 1;
     lbf::Ct16Out o;
     o.hi = ws;
     o.lo = p->planes > 1 ? static_cast<unsigned char *>(ws) + p->ct16_bytes : nullptr;
@@ -330,6 +333,13 @@ lbf_status lbf_plan(const lbf_config *cfg, lbf_plan_t *out) {
   }
   p->tc = tc_asked && !tc_few;
   p->tc_wlo = cfg->precision == LBF_FP16_TC2 ? 0 : 1;
+  if (p->tc) {   // weight tables with the delay compensation folded in, for the fused path
+    if (e == cudaSuccess) e = upload<float>(&p->phase0g, nullptr, (size_t)p->F * p->B * p->S);
+    if (e == cudaSuccess) e = upload<float>(&p->stepg, nullptr, (size_t)p->B * p->S);
+    if (e == cudaSuccess)
+      e = lbf::launch_phase_tables(p->F, p->B, p->S, p->fs, p->f0, p->dtau, p->phase0g, p->stepg, 0, p->tau,
+                                   p->resid);
+  }
   p->external_ws = (cfg->flags & LBF_FLAG_EXTERNAL_WORKSPACE) != 0;
   p->inc = (cfg->flags & LBF_FLAG_INCOHERENT_BEAM) ? 1 : 0;
   if (e == cudaSuccess) e = cudaMalloc((void **)&p->ss_members, sizeof(int) * p->S);

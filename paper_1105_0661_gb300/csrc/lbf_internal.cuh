@@ -29,6 +29,12 @@ struct Geometry {
   const double *dtau = nullptr;         // [B][S] beam delay difference
   const float *phase0 = nullptr;        // [F][B][S] f0_f dtau[b,s] reduced to [-1/2, 1/2] cycle (FP64 -> FP32)
   const float *step = nullptr;          // [B][S] fs/N * dtau[b,s], cycles per channel
+  // the same two tables with the delay compensation folded in (tensor-core plans): phase
+  // f0_f (dtau[b,s] + tau_s) reduced, step fs/N (dtau[b,s] + tau_s - n_s Ts)
+  const float *phase0g = nullptr;
+  const float *stepg = nullptr;
+  int ct16_raw = 0;           // 1: the FP16 planes hold the filtered spectrum before the delay phase
+                              // and bandpass, which the tensor-core weights then carry
   int *err = nullptr;                   // device error word: a bounded wait that gave up records here
 };
 
@@ -151,7 +157,8 @@ cudaError_t launch_beamform(const Geometry &g, int variant, int out_kind, const 
                             void *out, cudaStream_t st);
 // plan-time FP64 tables of the weight phases (tables.cu)
 cudaError_t launch_phase_tables(int F, int B, int S, double fs, const double *f0, const double *dtau,
-                                float *phase0, float *step, cudaStream_t st);
+                                float *phase0, float *step, cudaStream_t st, const double *tau = nullptr,
+                                const double *resid = nullptr);
 // largest S the many-beam kernel accepts (shared-memory bound)
 int many_beam_max_stations();
 // a7 standalone: vol -> Stokes

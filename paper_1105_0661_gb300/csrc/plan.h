@@ -25,6 +25,7 @@ struct lbf_plan_s {
   int *dshift = nullptr;
   double *tau = nullptr, *resid = nullptr, *f0 = nullptr, *dtau = nullptr;
   float *phase0 = nullptr, *step = nullptr;
+  float *phase0g = nullptr, *stepg = nullptr;   // with the delay folded in (tensor-core plans)
   // tensor-core precision: FP16 corner-turned planes and their TMA descriptors
   bool tc = false;
   int tc_wlo = 1;               // three products (LBF_FP16_TC) or two (LBF_FP16_TC2)
@@ -64,6 +65,7 @@ struct lbf_plan_s {
     g.S = S; g.F = F; g.B = B; g.T = T; g.M = M; g.Q = Q; g.nS = nS; g.H = H; g.fs = fs;
     g.taps = taps; g.twiddle = twiddle; g.bandpass = bandpass; g.dshift = dshift;
     g.tau = tau; g.resid = resid; g.f0 = f0; g.dtau = dtau; g.phase0 = phase0; g.step = step;
+    g.phase0g = phase0g; g.stepg = stepg;
     g.inc = inc;
     g.tc_wlo = tc_wlo;
     g.err = d_err;

@@ -1,6 +1,8 @@
 // Poly-phase filter bank of Section 4.2: integer sample shift (Section 3), int->float conversion,
-// 16-tap FIR and 256-point FFT into channels, with an optional fused epilogue that applies the
-// sub-sample delay phase and bandpass (Sections 3, 4.3) and writes a corner-turned layout.
+// 16-tap FIR and 256-point FFT into channels, with an optional fused epilogue that writes a
+// corner-turned layout: in FP32 with the sub-sample delay phase and bandpass applied (Sections 3,
+// 4.3), or as the FP16 planes of the tensor-core beam former, whose weights carry that phase and
+// the bandpass instead (the phase has the weight phase's form; tables.cu folds it in).
 //
 // One 512-thread CTA filters both polarisations of up to `spc` consecutive spectra of one
 // (station, subband) stream, in tiles of 16 spectra.  Each half of the CTA (256 threads) owns one
@@ -247,9 +249,11 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
   }
 
   // per-item tables: pass-1 twiddles [k1][p2] and the epilogue gain of channel k1 + 16((k2+8)&15)
+  // (FP32 corner turn only: the FP16 planes leave the delay phase and bandpass to the tensor-core
+  // weights)
   if (tid < kN) {
     sm.tw[tid] = g.twiddle[(tid & 15) * (tid >> 4)];
-  } else if (MODE != MODE_CHAN) {
+  } else if (MODE == MODE_CT32) {
     // Y = X * bp[c] * exp(+2 pi i (f0 tau_s + df_c (tau_s - n_s Ts))), phase in FP64 cycles
     const int i = tid - kN, k1 = i >> 4, k2 = i & 15;
     const int c = k1 + 16 * ((k2 + 8) & 15);
@@ -368,14 +372,14 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
         for (int k2 = 0; k2 < 16; ++k2) dst[16 * ((k2 + 8) & 15)] = a[k2];
       }
     } else {
-      const float4 *gp = &sm.gain[k1 * 8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const float4 gg = gp[i];
-        a[2 * i] = cmul(a[2 * i], make_float2(gg.x, gg.y));
-        a[2 * i + 1] = cmul(a[2 * i + 1], make_float2(gg.z, gg.w));
-      }
       if (MODE == MODE_CT32) {
+        const float4 *gp = &sm.gain[k1 * 8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float4 gg = gp[i];
+          a[2 * i] = cmul(a[2 * i], make_float2(gg.x, gg.y));
+          a[2 * i + 1] = cmul(a[2 * i + 1], make_float2(gg.z, gg.w));
+        }
         // ct[f][c][s][pol][m]: the 16 lanes of a channel write 16 consecutive spectra (128 B)
         if (mg < m_end) {
           float2 *dst = po.f32 + ((((long long)f * kN + k1) * g.S + s) * kP + pol) * g.M + mg;
@@ -422,8 +426,9 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
   //   prologue:  FIR(0)                               | barrier x
   //   tile t:    pass 1(t) + FIR(t + 1) outputs 0..7  | barrier x (pass 1 done; abort check)
   //              pass 2(t) + FIR(t + 1) outputs 8..15 | barrier y (wbuf[t & 1] free, FIR done)
-  // The FP16-plane output keeps its pass 2 (shuffles and the hi/lo split) apart from the FIR:
-  // together they outgrow the registers.  Its schedule is sequential over the same two buffers:
+  // The FP16-plane output keeps its pass 2 (shuffles and the hi/lo split) apart from the FIR: the
+  // pipelined schedule measured 8 % slower for it (spilling with 16-bit samples, and slower
+  // without spills with 8-bit ones).  Its schedule is sequential over the same two buffers:
   //   tile t:    FIR(t) | barrier x (slot free) | pass 1(t) | barrier y | pass 2(t)
   if constexpr (MODE == MODE_CT16) {
     for (int t = 0; t < ntiles; ++t) {

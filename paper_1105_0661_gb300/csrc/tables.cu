@@ -12,8 +12,13 @@
 namespace lbf {
 namespace {
 
+// With tau and resid given, station s's delay compensation (Sections 3, 4.3) is folded in: the
+// phase of Y_s = X_s exp(+2 pi i (f0_f tau_s + df_c (tau_s - n_s Ts))) has the same form (a
+// subband term plus (c - N/2) times a per-channel step), so w Y_s = w' X_s with the tables of
+// dtau[b,s] + tau_s and dtau[b,s] + resid_s.
 __global__ void phase_table_kernel(int F, int B, int S, double fs, const double *__restrict__ f0,
-                                   const double *__restrict__ dtau, float *__restrict__ phase0,
+                                   const double *__restrict__ dtau, const double *__restrict__ tau,
+                                   const double *__restrict__ resid, float *__restrict__ phase0,
                                    float *__restrict__ step) {
   const long long n = (long long)F * B * S;
   const double df = fs / kN;
@@ -21,20 +26,23 @@ __global__ void phase_table_kernel(int F, int B, int S, double fs, const double 
        i += (long long)gridDim.x * blockDim.x) {
     const long long bs = i % ((long long)B * S);
     const int f = (int)(i / ((long long)B * S));
-    const double phi = f0[f] * dtau[bs];
+    const int s = (int)(bs % S);
+    const double phi = f0[f] * (dtau[bs] + (tau ? tau[s] : 0.0));
     phase0[i] = (float)(phi - rint(phi));
-    if (f == 0) step[bs] = (float)(df * dtau[bs]);
+    if (f == 0) step[bs] = (float)(df * (dtau[bs] + (resid ? resid[s] : 0.0)));
   }
 }
 
 }  // namespace
 
 cudaError_t launch_phase_tables(int F, int B, int S, double fs, const double *f0, const double *dtau,
-                                float *phase0, float *step, cudaStream_t st) {
+                                float *phase0, float *step, cudaStream_t st, const double *tau,
+                                const double *resid) {
   const long long n = (long long)F * B * S;
   if (n == 0) return cudaSuccess;
   const long long want = (n + 255) / 256;
-  phase_table_kernel<<<(unsigned)(want < 4096 ? want : 4096), 256, 0, st>>>(F, B, S, fs, f0, dtau, phase0, step);
+  phase_table_kernel<<<(unsigned)(want < 4096 ? want : 4096), 256, 0, st>>>(F, B, S, fs, f0, dtau, tau, resid,
+                                                                             phase0, step);
   return cudaGetLastError();
 }
 
