@@ -351,7 +351,8 @@ bf_many_kernel(Geometry g, const float2 *__restrict__ ct, void *__restrict__ out
 // (subband-channel, beam group) from a shared counter; each item runs the body of variant V (1 few,
 // 2 many with 128-beam tiles, 3 many with 64-beam tiles) for output kind OUT.  One launch per
 // (variant, output kind, residency) class, so that each body keeps its own registers and shared
-// memory footprint, as when its observation runs alone.
+// memory footprint, as when its observation runs alone.  The observations' geometry comes in a
+// grid-constant table (constant bank); thread 0 finds each item's observation.
 template <int V, int OUT>
 __global__ void __launch_bounds__(kManyThreads, (V == 3 && OUT != OUT_STOKES_IQUV) ? 3 : 2)
 bf_group_kernel(const __grid_constant__ BfTable T, long long total, unsigned long long *counter) {

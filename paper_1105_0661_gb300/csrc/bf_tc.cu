@@ -210,9 +210,9 @@ __device__ __forceinline__ uint32_t pack_half2(float lo_k, float hi_k) {
 
 // Weights of this thread's A row for work item (f, c) into its TMEM lane: column s of plane hi/lo
 // holds (Re w, -Im w) for a Re row and (Im w, Re w) for an Im row.  The two lanes of a beam each
-// evaluate every other station and swap the results; the two warps of a lane quadrant take
-// alternate groups of 8 columns (`half`).  The phase-table values are loaded first
-// (load_weight_tables), so that their latency hides behind an accumulator wait.
+// evaluate every other station and swap the results; the KS warps of a lane quadrant take every
+// KS-th group of 8 columns (`half` = the warp's index in its quadrant).  The phase-table values
+// are loaded first (load_weight_tables), so that their latency hides behind an accumulator wait.
 // With KS warps per quadrant, warp `sub` takes the groups of 8 columns g8 = sub (mod KS).
 template <int KS>
 struct WeightTables {

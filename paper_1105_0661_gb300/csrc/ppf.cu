@@ -500,7 +500,8 @@ ppf_kernel(Geometry g, const typename SampleIO<BITS>::word *__restrict__ in,
 // Persistent filter bank over the blocks of several observations (a batch): CTAs take work items
 // (stream, spectrum chunk: both polarisations) from a shared counter until all groups are done.
 // One launch per class of sample width and output form, so each body keeps the registers it has
-// when its observation runs alone.
+// when its observation runs alone.  The observations' geometry comes in a grid-constant table
+// (constant bank); thread 0 finds each item's observation.
 template <int BITS, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
 ppf_group_kernel(const __grid_constant__ PpfTable T, long long total, unsigned long long *counter) {
