@@ -12,8 +12,9 @@
 // history ping-pong) and replayed with a single graph launch per block.  Its shapes -- spectra per
 // filter-bank item, for observations with 9..64 beams the few- or many-beam beam former, and the
 // many-beam tile (128 or 64 beams per CTA) -- and its mode are tuned by timing the candidates on
-// the batch itself.  The per-plan mode runs each FP32 stage as the plan's own kernel (the tensor
-// cores stay grouped); it wins where the observations are large enough to fill the GPU alone.
+// the batch itself.  The per-plan mode runs each stage as the plan's own kernel, as separate
+// launches would (still one graph launch per block); it wins where the observations are large
+// enough to fill the GPU alone.
 #include <cstring>
 #include <new>
 #include <utility>
@@ -51,7 +52,7 @@ struct lbf_batch_s {
   int device = 0;
   std::vector<lbf_plan_t> plans;
   int spc = 256;                       // spectra per filter-bank item (tuned: 64, 256 or 1024)
-  bool per_plan = false;               // FP32 stages as each plan's own kernels (tuned)
+  bool per_plan = false;               // every stage as each plan's own kernels (tuned)
   std::vector<int> variant;            // beam-former kernel per plan
   // group tables: [parity][plan]; parity p describes the plans' history state after p blocks
   lbf::PpfGroup *h_ppf = nullptr, *d_ppf = nullptr;   // pinned host / device, 2 * n
@@ -172,7 +173,8 @@ cudaError_t enqueue(lbf_batch_t b, int par, cudaStream_t st) {
                                   cudaMemcpyHostToDevice, st);
   if (b->per_plan) {
     // each plan's own filter bank, history update and FP32 beam former (the hardware schedules
-    // their CTAs; large observations each fill the GPU) -- the tensor-core stage stays grouped
+    // their CTAs; large observations each fill the GPU); the tensor-core plans follow, one
+    // launch each
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
       lbf_plan_t p = b->plans[i];
       if (p->M == 0) continue;
@@ -223,7 +225,9 @@ cudaError_t enqueue(lbf_batch_t b, int par, cudaStream_t st) {
     refs.push_back({cls, lbf::TcPlanRef{g, &p->tmap[0], &p->tmap[1], static_cast<float *>(b->tc_out[i]), p->d_err}});
   }
   std::vector<bool> done(refs.size(), false);
-  const int cap = lbf::tc_max_plans_per_launch();
+  // per-plan mode: each tensor-core plan in its own launch (the single-plan kernel, with the plan
+  // and its product count compiled in); grouped mode: one launch per class
+  const int cap = b->per_plan ? 1 : lbf::tc_max_plans_per_launch();
   for (size_t i = 0; i < refs.size() && e == cudaSuccess; ++i) {
     if (done[i]) continue;
     std::vector<lbf::TcPlanRef> cls;
@@ -356,21 +360,10 @@ lbf_status lbf_batch_launches(lbf_batch_t b, int32_t *n_launches) {
   if (!b || b->magic != kBatchMagic) return LBF_ESTATE;
   if (!n_launches) return LBF_EINVAL;
   // classes of the tables last filled (lbf_batch_run, lbf_batch_capture or lbf_batch_tune)
-  if (b->per_plan) {   // per plan: filter bank + history (+ FP32 beam former) each; grouped tensor cores
+  if (b->per_plan) {   // per plan: filter bank, history and beam former (+ incoherent beam) each
     int k = 0;
-    for (lbf_plan_t p : b->plans) k += p->M ? (p->tc ? 2 : 3) : 0;
-    int tc_classes = 0;
-    std::vector<long long> seen;
-    for (lbf_plan_t p : b->plans) {
-      if (!p->tc || p->M == 0) continue;
-      const long long cls = (long long)p->out_kind * 64 + (p->out_kind == lbf::OUT_VOLTAGES ? 1 : p->Q);
-      int same = 0;
-      for (long long c : seen) same += c == cls;
-      if (same % lbf::tc_max_plans_per_launch() == 0) ++tc_classes;
-      seen.push_back(cls);
-      if (p->inc) ++tc_classes;
-    }
-    *n_launches = k + tc_classes;
+    for (lbf_plan_t p : b->plans) k += p->M ? 3 + (p->tc && p->inc ? 1 : 0) : 0;
+    *n_launches = k;
     return LBF_OK;
   }
   int tc_classes = 0;
@@ -455,7 +448,7 @@ lbf_status lbf_batch_tune(lbf_batch_t b, const void *const *d_in, void *const *d
       if (e == cudaSuccess && ms < best) { best = ms; best_spc = spcs[k]; best_v = v; }
     }
   }
-  // the per-plan mode (each plan's own FP32 kernels in the graph), with the best beam-former choice
+  // the per-plan mode (each plan's own kernels in the graph), with the best beam-former choice
   bool best_pp = false;
   if (e == cudaSuccess) {
     b->variant = choice[best_v];
