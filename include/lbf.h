@@ -145,9 +145,12 @@ typedef struct lbf_plan_s *lbf_plan_t;
  * stream starts with zero samples) and the run_block scratch.  Synchronous.  The config's host
  * arrays are copied; the caller keeps ownership.  On error *out is set to NULL.
  * With precision LBF_FP16_TC the many-beam beam former runs on the tensor cores (tcgen05, FP16
- * operands, FP32 accumulation): the filtered spectrum Y of either sample width feeds it as two
- * FP16 planes (hi = fp16(Y), lo = fp16(Y - hi)) and the weights are split the same way, three
- * products per tile, writing Stokes or beam voltages; it needs S <= 64.  LBF_FP16_TC2 is the same
+ * operands, FP32 accumulation): the filtered spectrum of either sample width feeds it as two FP16
+ * planes (hi = fp16(X), lo = fp16(X - hi)) and the weights are split the same way, three products
+ * per tile, writing Stokes or beam voltages; it needs S <= 64.  In lbf_run_block the planes hold
+ * the spectrum before the delay phase and bandpass, which the weights carry instead (the same
+ * linear map; Section 4.3's correction, applied once per weight); lbf_beamform and
+ * lbf_beamform_stokes take an already corrected block.  LBF_FP16_TC2 is the same
  * with FP16 weights only (two products per tile).  The tensor cores are used
  * only where the beam count makes the beam former a dense contraction: with bf_variant AUTO and
  * B <= 8 beams, or bf_variant FEW, a tensor-core plan runs the bandwidth-bound FP32 few-beam
