@@ -89,6 +89,8 @@ cudaError_t launch_ppf(const Geometry &g, int bits, const void *in, const void *
 constexpr int kMaxGroups = 64;
 struct PpfTable { PpfGroup grp[kMaxGroups]; int n; };
 struct BfTable { BfGroup grp[kMaxGroups]; int n; };
+// a kernel's parameters (the table, a count and a counter pointer) must fit in 32764 bytes
+static_assert(sizeof(PpfTable) + 16 <= 32764 && sizeof(BfTable) + 16 <= 32764, "grouped launch table too large");
 // The group of work item `item` in a grouped launch: the last group whose first item is <= item
 // (binary search, by one thread per item; the others read the result from shared memory).
 template <class Table>
