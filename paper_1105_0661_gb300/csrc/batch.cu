@@ -195,6 +195,7 @@ cudaError_t enqueue(lbf_batch_t b, int par, cudaStream_t st) {
     }
   } else {
     int counter = 0;
+    if ((int)(b->ppf_cls.size() + b->bf_cls.size()) > max_counters(n)) return cudaErrorInvalidValue;
     for (const auto &c : b->ppf_cls)
       if (e == cudaSuccess)
         e = lbf::launch_ppf_group(c.bits, c.tc, b->h_ppf + par * n + c.first, c.n, c.items,
