@@ -73,8 +73,9 @@ typedef enum { LBF_VOLTAGES = 0, LBF_STOKES_I = 1, LBF_STOKES_IQUV = 4 } lbf_out
  * tensor cores): FP32 SIMT; FP16 tensor cores with three products (spectrum and weights both split
  * hi + lo: Whi Yhi + Wlo Yhi + Whi Ylo, FP32 accumulation, errors ~1e-6 relative); or FP16 tensor
  * cores with two products (spectrum split hi + lo, weights rounded to FP16 once: Whi Yhi + Whi Ylo,
- * two thirds of the MMA work; the weight rounding, <= 2^-12 per component, limits Stokes I to
- * ~1e-4 relative RMS, more on single elements of beams that cancel a strong source). */
+ * two thirds of the MMA work; the weight rounding, <= 2^-12 per component, leaves Stokes I within
+ * ~7e-4 relative RMS on the test observations, more on single elements of beams that cancel a
+ * strong source). */
 typedef enum { LBF_FP32 = 0, LBF_FP16_TC = 1, LBF_FP16_TC2 = 2 } lbf_precision;
 
 /* Beam-former kernel choice: AUTO picks the bandwidth-bound few-beam kernel for B <= 8 (tensor-core

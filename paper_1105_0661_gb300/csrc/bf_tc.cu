@@ -79,7 +79,7 @@ struct TcParams {
   int vec;                    // output rows 16-byte aligned (M/Q % 4 == 0, aligned base)
   int wlo;                    // 1: three products (Wlo Yhi too); 0: two products
   const float *phase0, *step;
-  const float *bp;            // bandpass folded into the weights (raw FP16 planes), or null
+  const float *bp;            // bandpass applied to the outputs (raw FP16 planes), or null
   float *out;
   int *err;                   // the plan's device error word
 };
@@ -241,7 +241,6 @@ template <int KS>
 __device__ __forceinline__ void write_weights(const TcParams &p, uint32_t ta_hi, uint32_t ta_lo, int c, int ro,
                                               int half, const WeightTables<KS> &tab, bool wlo) {
   const float dc = (float)(c - kN / 2);
-  const float bpc = p.bp ? __ldg(&p.bp[c]) : 1.f;   // bandpass of the channel (raw planes)
 #pragma unroll
   for (int gi = 0; gi < WeightTables<KS>::kN8; ++gi) {
     const int g8 = half + KS * gi;                   // 8 stations per store
@@ -258,8 +257,6 @@ __device__ __forceinline__ void write_weights(const TcParams &p, uint32_t ta_hi,
         float phi = fmaf(dc, tab.st[i], tab.ph[i]);
         phi -= rintf(phi);
         __sincosf(6.283185307179586f * phi, &w.y, &w.x);
-        w.x *= bpc;
-        w.y *= bpc;
       }
       float2 o;
       o.x = __shfl_xor_sync(0xffffffffu, w.x, 1);
@@ -304,10 +301,11 @@ struct Stage {
 // kSpecW spectra (32 or 16) of one 32-spectrum tile of an accumulator (pol X at `taddr`, pol Y
 // 32 columns on; spectra m0 .. m0 + kSpecW - 1): integrate over windows of Q <= kSpecW spectra and
 // store the Stokes parameters, to the staging row `srow` (window wl = w - wbase) or, when staging
-// is off, to the output rows at `orow`.
+// is off, to the output rows at `orow`; every parameter is scaled by `osc` (the squared bandpass
+// of the channel when the weights leave it out).
 template <int NS, int Q, int kSpecW>
 __device__ __forceinline__ void drain_tile(uint32_t taddr, int m0, int ro, int jq, int M, bool beam_ok, float *orow,
-                                           long long pstride, float *srow, int wbase) {
+                                           long long pstride, float *srow, int wbase, float osc) {
   float x[kSpecW / 16][16], y[kSpecW / 16][16];
 #pragma unroll
   for (int ch = 0; ch < kSpecW / 16; ++ch) {
@@ -322,7 +320,7 @@ __device__ __forceinline__ void drain_tile(uint32_t taddr, int m0, int ro, int j
     const int w = m / Q;
     if (NS == 1) {
       const float i_own = sxx + syy;
-      const float I = i_own + __shfl_xor_sync(0xffffffffu, i_own, 1);
+      const float I = osc * (i_own + __shfl_xor_sync(0xffffffffu, i_own, 1));
       if (ok && ro == 0) {
         if (Stage<NS, Q>::kOn) srow[Stage<NS, Q>::index(jq, 0, w - wbase)] = I;
         else orow[w] = I;
@@ -334,7 +332,9 @@ __device__ __forceinline__ void drain_tile(uint32_t taddr, int m0, int ro, int j
       const float s0 = ro ? i_own : u_own, s1 = ro ? q_own : v_own;
       k0 += __shfl_xor_sync(0xffffffffu, s0, 1);
       k1 += __shfl_xor_sync(0xffffffffu, s1, 1);
-      if (ro) { k0 *= 2.f; k1 *= 2.f; }
+      const float sc = ro ? 2.f * osc : osc;
+      k0 *= sc;
+      k1 *= sc;
       if (ok) {
         const int p0 = ro ? 2 : 0;
         if (Stage<NS, Q>::kOn) {
@@ -396,7 +396,7 @@ __device__ __forceinline__ void drain_tile(uint32_t taddr, int m0, int ro, int j
 // shared memory, 8 beams at a time (spectrum index XOR 2 x beam, so the writes hit distinct
 // banks), and out as whole 256-byte rows: 16 lanes per (beam, pol) row, two rows per store.
 __device__ __forceinline__ void drain_tile_v(uint32_t taddr, int m0, int ro, int jq, int lane, int M, int B, int b0,
-                                             float2 *vrow0, long long bstride, bool vec, float2 *stage) {
+                                             float2 *vrow0, long long bstride, bool vec, float2 *stage, float osc) {
   float v[2][2][16];   // [pol][spectrum half][16]
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
@@ -429,8 +429,8 @@ __device__ __forceinline__ void drain_tile_v(uint32_t taddr, int m0, int ro, int
       const int bl = row >> 1, pol = row & 1;
       const int b = b0 + 8 * r + bl;
       const int s0 = 2 * j2;                 // spectrum within the tile (even)
-      const float4 val = *reinterpret_cast<const float4 *>(
-          stage + row * kSpec + (s0 & 16) + ((s0 & 15) ^ (2 * bl)));
+      float4 val = *reinterpret_cast<const float4 *>(stage + row * kSpec + (s0 & 16) + ((s0 & 15) ^ (2 * bl)));
+      val.x *= osc; val.y *= osc; val.z *= osc; val.w *= osc;
       const int m = m0 + s0;
       if (b < B) {
         float2 *dst = vrow0 + (long long)(8 * r + bl) * bstride + (long long)pol * M + m;
@@ -672,6 +672,9 @@ bf_tc_kernel(const __grid_constant__ TcLaunch L) {
       const int fc = li / p.items_per_fc;
       const int bb = li - fc * p.items_per_fc;
       const int f = fc / kN, c = fc - f * kN;
+      // bandpass of the channel when the planes precede it (applied to the outputs: the weights
+      // stay unit phasors, whose FP16 rounding is finest below 1)
+      const float bpc = p.bp ? __ldg(&p.bp[c]) : 1.f;
       if (item == (int)blockIdx.x) {      // weights of the first item; later ones are written during the
         for (int mt = 0; mt < kMTiles; ++mt) {   // item before (its first or last tile pair)
           const uint32_t ta_hi = tmem + lane_off + wcol<kForm>(mt, 0);
@@ -712,11 +715,11 @@ bf_tc_kernel(const __grid_constant__ TcLaunch L) {
             const long long bstride = (long long)p.F * kN * kP * p.M;             // between beams
             float2 *const v0 = reinterpret_cast<float2 *>(p.out) + (((long long)b0 * p.F + f) * kN + c) * kP * p.M;
             drain_tile_v(taddr, m0, ro, jq, lane, p.M, p.B, b0, v0, bstride, p.vec != 0,
-                         reinterpret_cast<float2 *>(stage_out) + (warp - 2) * (kVStageBytes / 8));
+                         reinterpret_cast<float2 *>(stage_out) + (warp - 2) * (kVStageBytes / 8), bpc);
           } else {
             float *const orow = p.out + (((long long)b * NS * p.F + f) * kN + c) * Mq;
             drain_tile<NS, Q, kSpecW>(taddr, m0, ro, jq, p.M, b < p.B, orow, pstride, buf + (mt * 16 + jq) * St::kRow,
-                                      wbase);
+                                      wbase, bpc * bpc);
           }
           tc_fence_before();
           __syncwarp();
@@ -804,7 +807,8 @@ bool fill_plan(TcLaunch &L, int i, const Geometry &g, int out_kind, const void *
   if (items + first >= (1ll << 31)) return false;
   p.items = (int)items;
   p.first_item = (int)first;
-  // raw planes (the fused path): weights with the delay compensation and the bandpass folded in
+  // raw planes (the fused path): weights with the delay compensation folded in, outputs scaled by
+  // the bandpass
   p.phase0 = g.ct16_raw ? g.phase0g : g.phase0;
   p.step = g.ct16_raw ? g.stepg : g.step;
   p.bp = g.ct16_raw ? g.bandpass : nullptr;

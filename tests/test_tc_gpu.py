@@ -281,3 +281,41 @@ def test_tc2_run_block_matches_oracle(dev, bits, out):
               f"QUV/I rel RMS {rms_q:.2e} (max {eq:.2e})")
         assert rms_I.max() <= TOL and rms_q <= TOL
     p.close()
+
+
+@pytest.mark.parametrize("S,out,Q,B,M", [(64, "I", 16, 130, 48), (48, "V", 1, 70, 47), (24, "IQUV", 32, 64, 96),
+                                         (8, "IQUV", 1, 9, 40), (33, "I", 8, 200, 64)])
+def test_tc2_shapes_match_oracle(dev, S, out, Q, B, M):
+    """Two-product form over the kernel's corners: 64 stations (the two weight sets then fill all
+    512 TMEM columns), voltages and 32-spectrum windows (two epilogue warps per lane quadrant),
+    single-spectrum windows (scalar sums), ragged beam blocks and spectra.  Voltages within 1e-3
+    relative RMS per (beam, subband); Stokes I within 1e-3 relative RMS per (beam, subband) row,
+    Q, U, V within 1e-3 of I's RMS."""
+    from paper_1105_0661_gb300 import Plan
+    wl = _wl(S=S, B=B, out=out, Q=Q, T=M * N)
+    p = Plan.from_workload(wl, precision="fp16tc2", bf_variant="many")
+    assert p.dims.bf_kernel == 3
+    ob = O.observation_from_workload(wl)
+    blk = G.make_block(wl, seed=12)
+    ref = ob.run_block(blk)
+    if out == "V":
+        vol = torch.empty(p.shape("vol"), dtype=torch.complex64, device=dev)
+        p.run_block(torch.from_numpy(blk).to(dev), vol)
+        assert p.device_status() == 0
+        err = _vol_rel_rms(vol.cpu().numpy().astype(np.complex128), ref)
+        print(f"TC2 voltages S={S} B={B} M={M}: max rel RMS {err:.2e}")
+        assert err <= TOL
+    else:
+        o = torch.empty(p.shape("stokes"), dtype=torch.float32, device=dev)
+        p.run_block(torch.from_numpy(blk).to(dev), o)
+        assert p.device_status() == 0
+        got = o.cpu().numpy().astype(np.float64)
+        I = ref[:, 0]
+        rms_I = np.sqrt(np.sum((got[:, 0] - I) ** 2, axis=(2, 3)) / np.sum(I ** 2, axis=(2, 3)))
+        rms_q = 0.0
+        if ref.shape[1] == 4:
+            num = np.sqrt(np.sum((got[:, 1:] - ref[:, 1:]) ** 2, axis=(3, 4)))
+            rms_q = float((num / np.sqrt(np.sum(I ** 2, axis=(2, 3)))[:, None]).max())
+        print(f"TC2 S={S} {out} Q={Q} B={B} M={M}: I rel RMS {rms_I.max():.2e}, QUV/I {rms_q:.2e}")
+        assert rms_I.max() <= TOL and rms_q <= TOL
+    p.close()
