@@ -19,7 +19,7 @@ namespace lbf {
 namespace {
 
 constexpr int kFewThreads = 256;
-constexpr int kFewBeams = 8;     // beams per few-beam CTA (grid.y covers more)
+constexpr int kFewBeams = 8;     // beams per few-beam CTA (grid.y covers more; 16 for some B)
 constexpr int kManyThreads = 256;
 constexpr int kBT = 128;         // beams per many-beam CTA
 constexpr int kMC = 32;          // spectra per many-beam pass
@@ -64,15 +64,16 @@ struct IncAcc {
 };
 
 // ------------------------------------------------------------------------------- few beams
-// Work item: (subband, channel) fc, beams bgrp * 8 .. + 7.
-template <int OUT>
+// Work item: (subband, channel) fc, beams bgrp * FB .. + FB - 1.  FB = 16 reads the corner-turned
+// block half as often for 9 to 32 beams (16 FP32 flop per byte, about the FP32/HBM ridge).
+template <int OUT, int FB = kFewBeams>
 __device__ __forceinline__ void bf_few_item(const Geometry &g, const float2 *__restrict__ ct, void *__restrict__ out,
-                                            int fc, int bgrp, float2 *wsm /* [S][kFewBeams] */) {
+                                            int fc, int bgrp, float2 *wsm /* [S][FB] */) {
   const int f = fc / kN, c = fc - f * kN;
-  const int b0 = bgrp * kFewBeams;
+  const int b0 = bgrp * FB;
   const int tid = threadIdx.x;
-  for (int i = tid; i < g.S * kFewBeams; i += kFewThreads) {
-    const int s = i / kFewBeams, b = b0 + (i - s * kFewBeams);
+  for (int i = tid; i < g.S * FB; i += kFewThreads) {
+    const int s = i / FB, b = b0 + (i - s * FB);
     wsm[i] = (b < g.B) ? beam_weight(g, f, c, (long long)b * g.S + s) : make_float2(0.f, 0.f);
   }
   __syncthreads();
@@ -82,9 +83,9 @@ __device__ __forceinline__ void bf_few_item(const Geometry &g, const float2 *__r
   for (int mb = 0; mb < g.M; mb += kFewThreads) {
     const int m = mb + tid;
     const bool active = m < g.M;
-    float2 acc[kFewBeams][kP];
+    float2 acc[FB][kP];
 #pragma unroll
-    for (int b = 0; b < kFewBeams; ++b) acc[b][0] = acc[b][1] = make_float2(0.f, 0.f);
+    for (int b = 0; b < FB; ++b) acc[b][0] = acc[b][1] = make_float2(0.f, 0.f);
     const bool inc = OUT != OUT_VOLTAGES && g.inc && bgrp == 0;   // this item also forms beam B
     IncAcc ia;
     if (active) {
@@ -95,9 +96,9 @@ __device__ __forceinline__ void bf_few_item(const Geometry &g, const float2 *__r
         const float2 yx = y[((long long)s * kP + 0) * g.M + m];
         const float2 yy = y[((long long)s * kP + 1) * g.M + m];
         if (inc) ia.add(yx, yy);
-        const float4 *w4 = reinterpret_cast<const float4 *>(wsm + s * kFewBeams);
+        const float4 *w4 = reinterpret_cast<const float4 *>(wsm + s * FB);
 #pragma unroll
-        for (int b2 = 0; b2 < kFewBeams / 2; ++b2) {
+        for (int b2 = 0; b2 < FB / 2; ++b2) {
           const float4 w = w4[b2];
           cmac(acc[2 * b2][0], make_float2(w.x, w.y), yx);
           cmac(acc[2 * b2][1], make_float2(w.x, w.y), yy);
@@ -110,7 +111,7 @@ __device__ __forceinline__ void bf_few_item(const Geometry &g, const float2 *__r
       if (active) {
         float2 *vol = reinterpret_cast<float2 *>(out);
 #pragma unroll
-        for (int b = 0; b < kFewBeams; ++b)
+        for (int b = 0; b < FB; ++b)
           if (b0 + b < g.B)
 #pragma unroll
             for (int pol = 0; pol < kP; ++pol)
@@ -119,7 +120,7 @@ __device__ __forceinline__ void bf_few_item(const Geometry &g, const float2 *__r
     } else {
       float *o = reinterpret_cast<float *>(out);
 #pragma unroll
-      for (int b = 0; b < kFewBeams; ++b) {
+      for (int b = 0; b < FB; ++b) {
         if (b0 + b >= g.B) break;   // uniform across the CTA
 #pragma unroll
         for (int st = 0; st < nS; ++st) {
@@ -143,11 +144,28 @@ __device__ __forceinline__ void bf_few_item(const Geometry &g, const float2 *__r
   __syncthreads();   // the weights in shared memory are rewritten by the next work item
 }
 
-template <int OUT>
+template <int OUT, int FB>
 __global__ void __launch_bounds__(kFewThreads)
 bf_few_kernel(Geometry g, const float2 *__restrict__ ct, void *__restrict__ out) {
   extern __shared__ __align__(16) float2 wsm[];
-  bf_few_item<OUT>(g, ct, out, blockIdx.x, blockIdx.y, wsm);
+  bf_few_item<OUT, FB>(g, ct, out, blockIdx.x, blockIdx.y, wsm);
+}
+
+template <int FB>
+cudaError_t launch_few(const Geometry &g, int out_kind, const float2 *ct, void *out, cudaStream_t st) {
+  dim3 grid((unsigned)(g.F * kN), (unsigned)((g.B + FB - 1) / FB));
+  const size_t smem = (size_t)g.S * FB * sizeof(float2);
+  auto go = [&](auto kern) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, kFewThreads, smem, st>>>(g, ct, out);
+    return cudaGetLastError();
+  };
+  switch (out_kind) {
+    case OUT_VOLTAGES: return go(bf_few_kernel<OUT_VOLTAGES, FB>);
+    case OUT_STOKES_I: return go(bf_few_kernel<OUT_STOKES_I, FB>);
+    default: return go(bf_few_kernel<OUT_STOKES_IQUV, 8>);
+  }
 }
 
 // ------------------------------------------------------------------------------- many beams
@@ -402,28 +420,12 @@ cudaError_t launch_many(const Geometry &g, int out_kind, const float2 *ct, void 
 cudaError_t launch_beamform(const Geometry &g, int variant, int out_kind, const float2 *ct, void *out,
                             cudaStream_t st) {
   if ((long long)g.F * kN == 0 || g.M == 0 || g.B == 0) return cudaSuccess;
+  // 16 beams per CTA where that makes fewer passes per cost: a 16-beam CTA costs ~1.84 of an
+  // 8-beam one (measured on the LOFAR block; it reads the same data but does twice the arithmetic),
+  // so 9-16 and 25-32 beams gain ~7 % and 17-24 would lose; the IQUV epilogue would spill at 16
   if (variant == 1) {
-    dim3 grid((unsigned)(g.F * kN), (unsigned)((g.B + kFewBeams - 1) / kFewBeams));
-    const size_t smem = (size_t)g.S * kFewBeams * sizeof(float2);
-    cudaError_t e;
-    switch (out_kind) {
-      case OUT_VOLTAGES:
-        e = cudaFuncSetAttribute(bf_few_kernel<OUT_VOLTAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        bf_few_kernel<OUT_VOLTAGES><<<grid, kFewThreads, smem, st>>>(g, ct, out);
-        break;
-      case OUT_STOKES_I:
-        e = cudaFuncSetAttribute(bf_few_kernel<OUT_STOKES_I>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        bf_few_kernel<OUT_STOKES_I><<<grid, kFewThreads, smem, st>>>(g, ct, out);
-        break;
-      default:
-        e = cudaFuncSetAttribute(bf_few_kernel<OUT_STOKES_IQUV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        bf_few_kernel<OUT_STOKES_IQUV><<<grid, kFewThreads, smem, st>>>(g, ct, out);
-        break;
-    }
-    return cudaGetLastError();
+    const bool wide = out_kind != OUT_STOKES_IQUV && 184 * ((g.B + 15) / 16) < 100 * ((g.B + 7) / 8);
+    return wide ? launch_few<16>(g, out_kind, ct, out, st) : launch_few<8>(g, out_kind, ct, out, st);
   }
   if (variant == 3) return launch_many<64>(g, out_kind, ct, out, st);
   return launch_many<128>(g, out_kind, ct, out, st);

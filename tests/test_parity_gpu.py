@@ -163,7 +163,7 @@ def test_corner_turn_is_exact_transpose(dev):
 
 # ----------------------------------------------------------------------------- a5-a6 beam former
 @pytest.mark.parametrize("variant,B", [("few", 5), ("many", 5), ("many", 133), ("few", 19), ("many64", 5),
-                                       ("many64", 64), ("many64", 133)])
+                                       ("many64", 64), ("many64", 133), ("few", 12), ("few", 28), ("few", 44)])
 def test_beamform_voltages_match_oracle(dev, variant, B):
     wl = _wl(B=B, out="V")
     p = _plan(wl, bf_variant=variant)
@@ -235,6 +235,29 @@ def test_run_block_matches_oracle(dev, variant, out, bits):
     o = torch.empty(shape, dtype=torch.float32 if out != "V" else torch.complex64, device=dev)
     for bi in range(2):
         blk = G.make_block(wl, seed=10, block_index=bi)
+        p.run_block(_to_dev(blk, dev), o)
+        ref = ob.run_block(blk)
+        got = o.cpu().numpy().astype(np.float64 if out != "V" else np.complex128)
+        if out == "V":
+            assert _rel_rms(got, ref, (2, 3, 4)).max() <= TOL
+        else:
+            _check_stokes(got, ref)
+    p.close()
+
+
+@pytest.mark.parametrize("B,out", [(12, "I"), (20, "I"), (30, "I"), (12, "IQUV"), (16, "V")])
+def test_few_beam_kernel_beam_counts_match_oracle(dev, B, out):
+    """The few-beam kernel takes 16 beams per CTA for 9-16 and 25-32 beams (Stokes I and
+    voltages) and 8 otherwise: both forms, with a partly filled last beam group, against the
+    oracle over two blocks."""
+    wl = _wl(B=B, out=out, Q=4 if out != "V" else 1)
+    p = _plan(wl, bf_variant="few")
+    assert p.dims.bf_kernel == 1
+    ob = O.observation_from_workload(wl)
+    shape = p.shape("stokes") if out != "V" else p.shape("vol")
+    o = torch.empty(shape, dtype=torch.float32 if out != "V" else torch.complex64, device=dev)
+    for bi in range(2):
+        blk = G.make_block(wl, seed=14, block_index=bi)
         p.run_block(_to_dev(blk, dev), o)
         ref = ob.run_block(blk)
         got = o.cpu().numpy().astype(np.float64 if out != "V" else np.complex128)
