@@ -144,8 +144,11 @@ __device__ __forceinline__ void bf_few_item(const Geometry &g, const float2 *__r
   __syncthreads();   // the weights in shared memory are rewritten by the next work item
 }
 
+// at least two CTAs per SM (three for the 8-beam Stokes I form): a bandwidth-bound kernel needs
+// the warps; left to itself the compiler gave the IQUV form 194 registers, one CTA per SM and 2.6x
+// the Stokes I time
 template <int OUT, int FB>
-__global__ void __launch_bounds__(kFewThreads)
+__global__ void __launch_bounds__(kFewThreads, (OUT == OUT_STOKES_I && FB == 8) ? 3 : 2)
 bf_few_kernel(Geometry g, const float2 *__restrict__ ct, void *__restrict__ out) {
   extern __shared__ __align__(16) float2 wsm[];
   bf_few_item<OUT, FB>(g, ct, out, blockIdx.x, blockIdx.y, wsm);
@@ -162,7 +165,7 @@ cudaError_t launch_few(const Geometry &g, int out_kind, const float2 *ct, void *
     return cudaGetLastError();
   };
   switch (out_kind) {
-    case OUT_VOLTAGES: return go(bf_few_kernel<OUT_VOLTAGES, FB>);
+    case OUT_VOLTAGES: return go(bf_few_kernel<OUT_VOLTAGES, 8>);
     case OUT_STOKES_I: return go(bf_few_kernel<OUT_STOKES_I, FB>);
     default: return go(bf_few_kernel<OUT_STOKES_IQUV, 8>);
   }
@@ -420,11 +423,12 @@ cudaError_t launch_many(const Geometry &g, int out_kind, const float2 *ct, void 
 cudaError_t launch_beamform(const Geometry &g, int variant, int out_kind, const float2 *ct, void *out,
                             cudaStream_t st) {
   if ((long long)g.F * kN == 0 || g.M == 0 || g.B == 0) return cudaSuccess;
-  // 16 beams per CTA where that makes fewer passes per cost: a 16-beam CTA costs ~1.84 of an
-  // 8-beam one (measured on the LOFAR block; it reads the same data but does twice the arithmetic),
-  // so 9-16 and 25-32 beams gain ~7 % and 17-24 would lose; the IQUV epilogue would spill at 16
+  // Stokes I: 16 beams per CTA where that makes fewer passes per cost -- a 16-beam CTA costs ~1.91
+  // of an 8-beam one (measured on the LOFAR block: the same reads, twice the arithmetic), so 9-16
+  // and 25-32 beams gain 4-9 % and 17-24 would lose.  Voltages and IQUV keep 8 (their 16-beam
+  // forms spill within two CTAs' registers per SM and lose to two 8-beam passes).
   if (variant == 1) {
-    const bool wide = out_kind != OUT_STOKES_IQUV && 184 * ((g.B + 15) / 16) < 100 * ((g.B + 7) / 8);
+    const bool wide = out_kind == OUT_STOKES_I && 191 * ((g.B + 15) / 16) < 100 * ((g.B + 7) / 8);
     return wide ? launch_few<16>(g, out_kind, ct, out, st) : launch_few<8>(g, out_kind, ct, out, st);
   }
   if (variant == 3) return launch_many<64>(g, out_kind, ct, out, st);

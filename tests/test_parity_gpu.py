@@ -247,9 +247,9 @@ def test_run_block_matches_oracle(dev, variant, out, bits):
 
 @pytest.mark.parametrize("B,out", [(12, "I"), (20, "I"), (30, "I"), (12, "IQUV"), (16, "V")])
 def test_few_beam_kernel_beam_counts_match_oracle(dev, B, out):
-    """The few-beam kernel takes 16 beams per CTA for 9-16 and 25-32 beams (Stokes I and
-    voltages) and 8 otherwise: both forms, with a partly filled last beam group, against the
-    oracle over two blocks."""
+    """The few-beam kernel takes 16 beams per CTA for 9-16 and 25-32 beams of Stokes I and 8
+    otherwise: both forms, with a partly filled last beam group, against the oracle over two
+    blocks."""
     wl = _wl(B=B, out=out, Q=4 if out != "V" else 1)
     p = _plan(wl, bf_variant="few")
     assert p.dims.bf_kernel == 1
