@@ -909,7 +909,7 @@ def run_batch(args):
     build()
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    wls = batch_observations(16)
+    wls = G.small_batch_workloads() if args.batch_small else batch_observations(16)
     # --precision fp16tc: observations with >= 64 beams and <= 64 stations on the tensor cores (as
     # the serving path chooses), the rest FP32; the separate launches use the same plans
     prec = ["fp16tc" if (args.precision == "fp16tc" and wl.n_beams >= 64 and wl.n_stations <= 64) else "fp32"
@@ -946,8 +946,10 @@ def run_batch(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f32+f16",
         "data": "synthetic",
-        "config": {"workload": "batched: 16 sub-observations (stations 12-64, subbands 8-244, beams 1-512, "
-                               "int8/int16, seeds 1-16), 65536-sample blocks, Stokes I over 4",
+        "config": {"workload": ("batched: 64 small observations (stations 8-16, subbands 2-8, beams 1-8, int16, "
+                                "seed 5), 16384-sample blocks, Stokes I over 4") if args.batch_small else
+                               ("batched: 16 sub-observations (stations 12-64, subbands 8-244, beams 1-512, "
+                                "int8/int16, seeds 1-16), 65536-sample blocks, Stokes I over 4"),
                    "observations": [f"{wl.name} ({pr})" for wl, pr in zip(wls, prec)],
                    "l2": "inputs larger than L2 (%.1f GB per step)" % (sum(p.dims.in_bytes for p in plans) / 1e9)},
         "separate_launches": {"value": ss / (ms_sep / 1e3), "ms_per_step": ms_sep, "gpu_launches": 3 * len(plans)},
@@ -982,6 +984,8 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the other precision form on the same block")
     ap.add_argument("--serve", action="store_true", help="streaming serving run (p50/p99 block latency)")
     ap.add_argument("--batch", action="store_true", help="16 uneven sub-observations, grouped graph vs separate")
+    ap.add_argument("--batch-small", action="store_true",
+                    help="with --batch: 64 small observations instead (where grouped launches pay)")
     ap.add_argument("--dedisperse", action="store_true",
                     help="voltages -> channel-level dedispersion -> Stokes (pulsar pipeline)")
     ap.add_argument("--dd-fft", type=int, default=256, help="dedispersion FFT length (spectra)")

@@ -209,6 +209,21 @@ def batch_workloads(n: int = 16, block_samples: int = 65536) -> list:
     return out
 
 
+def small_batch_workloads(n: int = 64, block_samples: int = 16384, seed: int = 5) -> list:
+    """Many small observations (the regime where one grouped launch beats per-observation
+    launches): stations 8-16, subbands 2-8, beams 1-8, int16, Stokes I over 4, drawn in turn from
+    numpy.random.default_rng(seed)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        S, F, B = int(rng.integers(8, 17)), int(rng.integers(2, 9)), int(rng.integers(1, 9))
+        xyz = lofar_positions(rng, S // 2, S - S // 2)
+        out.append(Workload(f"small{i}-{S}st-{F}sb-{B}beam", xyz, subband_centres(F, 120e6 + 1e6 * i),
+                            hex_beam_grid(B, 0.05), (0.3, 0.4), block_samples, 4, "I", sample_bits=16,
+                            sigma=32.0, source="tone"))
+    return out
+
+
 def _arrival_offset(xyz: np.ndarray, l: float, m: float) -> np.ndarray:
     """Arrival-time offset (s) of a plane wave from direction (l, m) at each station (sky model)."""
     n = np.sqrt(max(0.0, 1.0 - l * l - m * m))
