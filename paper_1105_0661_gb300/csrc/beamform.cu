@@ -380,11 +380,14 @@ bf_group_kernel(const __grid_constant__ BfTable T, long long total, unsigned lon
   extern __shared__ __align__(16) float2 smem[];
   __shared__ long long item_s;
   __shared__ int grp_s;
+  // thread 0 takes the next item while the current one runs (the counter's latency stays hidden)
+  long long nxt = threadIdx.x == 0 ? (long long)atomicAdd(counter, 1ull) : 0;
   for (;;) {
     if (threadIdx.x == 0) {
-      const long long it = (long long)atomicAdd(counter, 1ull);
+      const long long it = nxt;
       item_s = it;
       grp_s = it < total ? group_of(T, it) : 0;
+      if (it < total) nxt = (long long)atomicAdd(counter, 1ull);
     }
     __syncthreads();
     const long long item = item_s;

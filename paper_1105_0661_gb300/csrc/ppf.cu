@@ -512,11 +512,14 @@ ppf_group_kernel(const __grid_constant__ PpfTable T, long long total, unsigned l
   PpfSmem<BITS> &sm = *reinterpret_cast<PpfSmem<BITS> *>(smem_raw);
   ppf_setup(sm.ctl);
   uint32_t ph = 0;
+  // thread 0 takes the next item while the current one runs (the counter's latency stays hidden)
+  long long nxt = threadIdx.x == 0 ? (long long)atomicAdd(counter, 1ull) : 0;
   for (;;) {
     if (threadIdx.x == 0) {
-      const long long it = sm.ctl.abort ? total : (long long)atomicAdd(counter, 1ull);
+      const long long it = sm.ctl.abort ? total : nxt;
       item_s = it;
       grp_s = it < total ? group_of(T, it) : 0;
+      if (it < total) nxt = (long long)atomicAdd(counter, 1ull);
     }
     __syncthreads();
     const long long item = item_s;
