@@ -189,7 +189,11 @@ class Dims:
 
 
 class Plan:
-    """One observation: tables, device-resident FIR/shift history and run_block scratch."""
+    """One observation: tables, device-resident FIR/shift history and run_block scratch.
+
+    precision: "fp32" (SIMT), "fp16tc" (tensor cores, three FP16 products) or "fp16tc2" (tensor
+    cores, two products: FP16 weights); bf_variant: "auto", "few", "many" (128-beam tiles) or
+    "many64" (lbf_config's fields of the same names)."""
 
     def __init__(self, station_xyz, subband_hz, beam_dlm, phase_centre, taps, block_samples,
                  int_factor=1, output="I", sample_bits=16, bandpass=None, n_channels=256, n_taps=16,
