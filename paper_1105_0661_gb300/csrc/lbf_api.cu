@@ -17,7 +17,43 @@ namespace {
 constexpr uint32_t kMagic = lbf::kPlanMagic;
 constexpr double kC = 299792458.0;         // m/s
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return nullptr;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  return encode;
+}
+
 }  // namespace
+
+namespace lbf {
+
+// The filter bank's store boxes over a plane [F*N][Mt][kpad][P][32]: dims (64 halves of a K row,
+// kpad rows, Mt tiles, F*N channel rows); a box is 16 spectra of one pol (32 bytes) x the two rows
+// of a station x 1 tile x the 256 channels of a subband, laid out [channel][row][spectrum] in
+// shared memory.
+cudaError_t encode_ct16_store_map(void *map, void *base, int kpad, int M, long long fc_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  if (!encode) return cudaErrorNotSupported;
+  const cuuint64_t mb = (cuuint64_t)tc_tiles(M);
+  const cuuint64_t dims[4] = {64, (cuuint64_t)kpad, mb, (cuuint64_t)fc_rows};
+  const cuuint64_t strides[3] = {128, (cuuint64_t)kpad * 128, mb * kpad * 128};
+  const cuuint32_t box[4] = {16, 2, 1, (cuuint32_t)kN};
+  const cuuint32_t elem[4] = {1, 1, 1, 1};
+  CUresult r = encode(static_cast<CUtensorMap *>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4, base, dims, strides, box,
+                      elem, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace lbf
 
 namespace {
 
@@ -102,15 +138,8 @@ bool valid_plan(lbf_plan_t p) { return p && p->magic == kMagic; }
 // tiles of 32 spectra; a tile's kpad K rows hold the two pols side by side, 128 bytes per row, so
 // a tile is one contiguous kpad x 128-byte region): boxes of two tiles, 128-byte swizzle.
 cudaError_t encode_ct16_map(CUtensorMap *map, void *base, int kpad, int M, long long fc_rows) {
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  if (!encode) {
-    void *fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn)
-      return cudaErrorNotSupported;
-    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  }
+  PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  if (!encode) return cudaErrorNotSupported;
   const cuuint64_t mb = (cuuint64_t)lbf::tc_tiles(M);
   const cuuint64_t dims[4] = {64, (cuuint64_t)kpad, mb, (cuuint64_t)fc_rows};
   const cuuint64_t strides[3] = {128, (cuuint64_t)kpad * 128, mb * kpad * 128};

@@ -51,6 +51,9 @@ struct Ct16Out {
   int kpad;        // 2 S rounded up to a multiple of 16
 };
 __host__ __device__ inline int tc_tiles(int M) { return ((M + 63) / 64) * 2; }
+// Tensor map (CUtensorMap, 128 bytes, written to `map`) of one FP16 plane at `base` for the filter
+// bank's tensor stores: boxes of 16 spectra of one pol x 2 K rows x 256 channels, no swizzle.
+cudaError_t encode_ct16_store_map(void *map, void *base, int kpad, int M, long long fc_rows);
 
 // One observation of a batch (grouped persistent launches, batch.cu): its geometry, this
 // block's buffers, and its range of work items in the grouped filter bank and beam former.

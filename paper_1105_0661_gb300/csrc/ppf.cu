@@ -24,13 +24,21 @@
 //    exp(-2 pi i p2 k1 / 256), and writes the results back over its own 16 points.  Pass 2:
 //    thread (m = p & 15, k1 = p >> 4) reads 16 contiguous values, a 16-point DFT over p2 gives
 //    X[k1 + 16 k2]; sixteen lanes then hold sixteen consecutive spectra of one channel, so the
-//    corner-turned output is written straight from registers as whole 128-byte runs, with the
-//    delay phasor and bandpass applied.
-//  * Software pipeline over two tile buffers per half: the FIR of tile t + 1 runs inside the two
-//    FFT passes of tile t (half of its outputs in each), so FMA-bound and shared-memory-bound work
-//    are interleaved in every warp; two named barriers per tile.
+//    FP32 corner-turned output is written straight from registers as whole 128-byte runs, with
+//    the delay phasor and bandpass applied.  The FP16 planes are staged instead, in the tile's own
+//    (by then consumed) FIR buffer in the layout of a tensor-map box (16 spectra x the station's
+//    two K rows x 256 channels), and one thread per half writes them with two tensor stores that
+//    drain while the next tile is filtered: written from the lanes, the tile's 64 KB left each SM
+//    in one burst at the end of the tile and stalled its warps (a runtime switch that dropped the
+//    stores cut pass 2 from ~3.8k to ~2.6k cycles per tile).
+//  * Software pipeline over two tile buffers per half (FP32 outputs): the FIR of tile t + 1 runs
+//    inside the two FFT passes of tile t (half of its outputs in each), so FMA-bound and
+//    shared-memory-bound work are interleaved in every warp; two named barriers per tile.  The
+//    FP16 planes run FIR, pass 1 and pass 2 in sequence, with two more barriers around the
+//    staging; a tile's stores must have read its buffer before the FIR two tiles later refills it.
 // Every wait on a copy is bounded: on expiry the CTA records DERR_PPF_INPUT in the device error
 // word, stops, waits (bounded) for its copies in flight and returns.
+#include <cuda.h>
 #include <cuda_fp16.h>
 
 #include <cstddef>
@@ -94,12 +102,18 @@ struct PpfSmem {
   PpfCtl ctl;
   alignas(16) float4 gain[kN / 2];             // [k1][k2 / 2]: bandpass x delay phasor, pairs of k2
   alignas(16) float2 tw[kN];                   // [k1][p2] = exp(-2 pi i k1 p2 / 256)
-  alignas(16) float2 w[kP][2][kTile][kRowV];   // per polarisation, two tiles of v_m[p] (132 KB)
+  // per polarisation, two tiles of v_m[p] (132 KB); each tile buffer (258 x 128 bytes) also stages
+  // the FP16 planes of its tile for the tensor stores, so it starts on a 128-byte boundary
+  alignas(128) float2 w[kP][2][kTile][kRowV];
   alignas(16) word in[kStages][kSlot];         // input ring of dual-pol samples (64 KB int16, 32 KB int8)
 };
 static_assert(offsetof(PpfSmem<16>, ctl) == 0 && offsetof(PpfSmem<8>, ctl) == 0, "ring control first");
 static_assert((PpfSmem<16>::kSlot * sizeof(uint2)) % 16 == 0 && (PpfSmem<8>::kSlot * sizeof(uint32_t)) % 16 == 0,
               "ring slots 16-byte aligned");
+static_assert(sizeof(PpfSmem<16>) + 128 <= 232448 && sizeof(PpfSmem<8>) + 128 <= 232448, "one CTA's shared memory");
+static_assert(offsetof(PpfSmem<16>, w) % 128 == 0 && offsetof(PpfSmem<8>, w) % 128 == 0 &&
+                  (kTile * kRowV * sizeof(float2)) % 128 == 0 && 2 * kN * 64 <= kTile * kRowV * sizeof(float2),
+              "tile buffers 128-byte aligned and large enough to stage both FP16 planes of a tile");
 
 // Output modes: the channelised layout, the FP32 corner-turned layout, or the FP16 layout of the
 // tensor-core beam former ([F*N][M/32][Kpad][P][32] with station s in rows k = 2s (re), 2s+1 (im);
@@ -172,6 +186,24 @@ __device__ __forceinline__ void half_sync(uint32_t id) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(kHalf) : "memory");
 }
 
+// Tensor maps of the FP16 planes for the filter bank's stores: boxes of 16 spectra (one pol) x the
+// two K rows of a station x 256 channels (encode_ct16_store_map).
+struct PpfMaps {
+  CUtensorMap hi, lo;
+  int has_lo;
+};
+
+// Bulk tensor store of one box from this CTA's shared memory (completion tracked by bulk groups).
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap *map, uint32_t src, int x, int y, int z, int w) {
+  asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];"
+               ::"l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(src)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// this thread's bulk stores have finished reading shared memory / have completed
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // Barriers and counters of the ring, once per kernel (thread 0; the caller synchronises).
 __device__ __forceinline__ void ppf_setup(PpfCtl &c) {
   if (threadIdx.x == 0) {
@@ -200,10 +232,14 @@ __device__ __forceinline__ void ppf_drain(PpfCtl &c) {
 // One work item: both polarisations of spectra [chunk * spc, (chunk + 1) * spc) of stream (s, f),
 // spc a multiple of 16.  On entry every thread of the CTA is done with the previous item (if any);
 // `ph` holds this thread's parity bit per ring slot.
-template <int BITS, int MODE>
+// kTmaSt (FP16 planes only): pass 2 stages each tile's planes in the tile's own buffer and one
+// thread per half stores them with tensor stores (maps), which drain while the next tile is filtered;
+// otherwise every thread stores its values directly.
+template <int BITS, int MODE, bool kTmaSt>
 __device__ __forceinline__ void ppf_item(const Geometry &g, const typename SampleIO<BITS>::word *__restrict__ in,
                                          const typename SampleIO<BITS>::word *__restrict__ hist, const PpfOut &po,
-                                         int s, int f, int chunk, int spc, PpfSmem<BITS> &sm, uint32_t &ph) {
+                                         int s, int f, int chunk, int spc, PpfSmem<BITS> &sm, uint32_t &ph,
+                                         const PpfMaps *maps) {
   using word = typename SampleIO<BITS>::word;
   using IO = SampleIO<BITS>;
   constexpr int kAlign = IO::kAlign;
@@ -279,6 +315,7 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
   // pass 1, read by pass 2)
   float2(*wbuf)[kTile][kRowV] = sm.w[pol];
   const uint32_t bar_x = 1 + pol, bar_y = 1 + kP + pol;   // this half's named barriers
+  const uint32_t bar_z = 1 + 2 * kP + pol, bar_w = 1 + 3 * kP + pol;   // pass 2 staging (kTmaSt)
   const int m1 = p >> 4, c1 = p & 15;   // pass-1 thread: spectrum m1, column p2 = c1
   const int m2 = p & 15, k1 = p >> 4;   // pass-2 thread: spectrum m2, row segment k1
 
@@ -363,6 +400,7 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
       a[2 * i] = make_float2(v.x, v.y);
       a[2 * i + 1] = make_float2(v.z, v.w);
     }
+    if constexpr (MODE == MODE_CT16 && kTmaSt) half_sync(bar_z);   // the buffer is read: staging may overwrite it
     dft16(a);
     const int mg = mt + m2;
     if (MODE == MODE_CHAN) {
@@ -395,6 +433,36 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
         const int odd = m2 & 1;
         const int me = mg & ~1;
         const bool v0 = me < m_end, v1 = me + 1 < m_end;
+        if constexpr (kTmaSt) {
+          // staging = the tensor store's box: [256 channels][row 2s, 2s+1][16 spectra] halves per
+          // plane (64 bytes per channel), hi plane then lo plane, in this tile's buffer
+          unsigned char *stg = reinterpret_cast<unsigned char *>(&wbuf[t & 1][0][0]);
+          const int col = odd * 32 + (m2 & ~1) * 2;
+#pragma unroll
+          for (int k2 = 0; k2 < 16; ++k2) {
+            const float send = odd ? a[k2].x : a[k2].y;
+            const float recv = __shfl_xor_sync(0xffffffffu, send, 1);
+            float x0 = odd ? recv : a[k2].x;
+            float x1 = odd ? a[k2].y : recv;
+            if (!v0) x0 = 0.f;
+            if (!v1) x1 = 0.f;
+            const __half2 h = __floats2half2_rn(x0, x1);
+            const float2 hf = __half22float2(h);
+            const int o = (k1 + 16 * ((k2 + 8) & 15)) * 64 + col;
+            *reinterpret_cast<__half2 *>(stg + o) = h;
+            *reinterpret_cast<__half2 *>(stg + 16384 + o) = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // staging visible to the tensor stores
+          if (p == 0) bulk_wait_read();   // the previous tile's stores have read their staging
+          half_sync(bar_w);
+          if (p == 0) {
+            const uint32_t src = smem_u32(stg);
+            tma_store_4d(&maps->hi, src, pol * 32 + (mt & 31), 2 * s, mt >> 5, f * kN);
+            if (maps->has_lo) tma_store_4d(&maps->lo, src + 16384, pol * 32 + (mt & 31), 2 * s, mt >> 5, f * kN);
+            bulk_commit();
+          }
+          return;
+        }
         const int mb = tc_tiles(g.M);
         const long long rowbase = (long long)(me >> 5) * po.kpad + 2 * s + odd;
         const long long cstride = (long long)mb * po.kpad * 64;
@@ -429,7 +497,10 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
   // The FP16-plane output keeps its pass 2 (shuffles and the hi/lo split) apart from the FIR: the
   // pipelined schedule measured 8 % slower for it (spilling with 16-bit samples, and slower
   // without spills with 8-bit ones).  Its schedule is sequential over the same two buffers:
-  //   tile t:    FIR(t) | barrier x (slot free) | pass 1(t) | barrier y | pass 2(t)
+  //   tile t:    FIR(t) | barrier x (slot free) | pass 1(t) | barrier y | pass 2(t) loads |
+  //              barrier z (buffer read) | staging | barrier w | tensor stores of tile t
+  // (thread 0 of the half waits, before barrier w, until the stores of tile t - 1 have read their
+  // buffer, which FIR(t + 1) refills next)
   if constexpr (MODE == MODE_CT16) {
     for (int t = 0; t < ntiles; ++t) {
       const bool failed = !wait_tile(t);
@@ -474,9 +545,14 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
 template <int BITS, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
 ppf_kernel(Geometry g, const typename SampleIO<BITS>::word *__restrict__ in,
-           const typename SampleIO<BITS>::word *__restrict__ hist, PpfOut po, int chunks, int spc) {
+           const typename SampleIO<BITS>::word *__restrict__ hist, PpfOut po, int chunks, int spc,
+           const __grid_constant__ PpfMaps maps) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  PpfSmem<BITS> &sm = *reinterpret_cast<PpfSmem<BITS> *>(smem_raw);
+  // with tensor stores (FP16 planes) the layout starts on a 128-byte boundary, so that the staging
+  // buffers are 128-byte aligned; the launch adds 128 bytes of slack
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t pad = MODE == MODE_CT16 ? ((128u - (raw & 127u)) & 127u) : 0u;
+  PpfSmem<BITS> &sm = *reinterpret_cast<PpfSmem<BITS> *>(smem_raw + pad);
   int s, f, chunk;
   const long long item = blockIdx.x;
   if (MODE == MODE_CT16) {   // stations fastest: neighbouring CTAs fill neighbouring K rows of the
@@ -492,7 +568,10 @@ ppf_kernel(Geometry g, const typename SampleIO<BITS>::word *__restrict__ in,
   }
   ppf_setup(sm.ctl);
   uint32_t ph = 0;
-  ppf_item<BITS, MODE>(g, in, hist, po, s, f, chunk, spc, sm, ph);
+  ppf_item<BITS, MODE, MODE == MODE_CT16>(g, in, hist, po, s, f, chunk, spc, sm, ph, &maps);
+  // the tensor stores of the last tiles complete (read and written) before the CTA's shared
+  // memory is released; only thread 0 of each half issued any
+  if (MODE == MODE_CT16 && threadIdx.x % kHalf == 0) bulk_wait_all();
   __syncthreads();
   ppf_drain(sm.ctl);
 }
@@ -534,7 +613,8 @@ ppf_group_kernel(const __grid_constant__ PpfTable T, long long total, unsigned l
     const PpfOut po = MODE == MODE_CT16
         ? PpfOut{nullptr, reinterpret_cast<__half *>(G.ct16.hi), reinterpret_cast<__half *>(G.ct16.lo), G.ct16.kpad}
         : PpfOut{G.ct, nullptr, nullptr, 0};
-    ppf_item<BITS, MODE>(G.g, (const word *)G.in, (const word *)G.hist, po, s, f, chunk, G.spc, sm, ph);
+    ppf_item<BITS, MODE, false>(G.g, (const word *)G.in, (const word *)G.hist, po, s, f, chunk, G.spc, sm, ph,
+                                nullptr);
   }
   __syncthreads();
   ppf_drain(sm.ctl);
@@ -590,7 +670,8 @@ __global__ void hist_update_kernel(long long total, int H, int T,
 }
 
 template <int BITS, int MODE>
-cudaError_t launch_ppf_t(const Geometry &g, const void *in, const void *hist, PpfOut po, cudaStream_t st) {
+cudaError_t launch_ppf_t(const Geometry &g, const void *in, const void *hist, PpfOut po, const PpfMaps &maps,
+                         cudaStream_t st) {
   using word = typename SampleIO<BITS>::word;
   const long long streams = (long long)g.S * g.F;   // one CTA: both polarisations
   if (streams == 0 || g.M == 0) return cudaSuccess;
@@ -599,11 +680,11 @@ cudaError_t launch_ppf_t(const Geometry &g, const void *in, const void *hist, Pp
   const int chunks = (g.M + spc - 1) / spc;
   const long long ctas = streams * chunks;
   if (ctas == 0) return cudaSuccess;
-  const size_t smem = sizeof(PpfSmem<BITS>);
+  const size_t smem = sizeof(PpfSmem<BITS>) + 128;   // + alignment slack
   auto kern = ppf_kernel<BITS, MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<(unsigned)ctas, kThreads, smem, st>>>(g, (const word *)in, (const word *)hist, po, chunks, spc);
+  kern<<<(unsigned)ctas, kThreads, smem, st>>>(g, (const word *)in, (const word *)hist, po, chunks, spc, maps);
   return cudaGetLastError();
 }
 
@@ -611,18 +692,25 @@ template <int BITS>
 cudaError_t launch_ppf_bits(const Geometry &g, const void *in, const void *hist, float2 *chan, float2 *ct,
                             const Ct16Out *ct16, cudaStream_t st) {
   PpfOut po{nullptr, nullptr, nullptr, 0};
+  PpfMaps maps{};
   if (ct16) {
     po.hi = reinterpret_cast<__half *>(ct16->hi);
     po.lo = reinterpret_cast<__half *>(ct16->lo);
     po.kpad = ct16->kpad;
-    return launch_ppf_t<BITS, MODE_CT16>(g, in, hist, po, st);
+    if ((long long)g.S * g.F == 0 || g.M == 0) return cudaSuccess;
+    const long long fc_rows = (long long)g.F * kN;
+    cudaError_t e = encode_ct16_store_map(&maps.hi, ct16->hi, ct16->kpad, g.M, fc_rows);
+    if (e == cudaSuccess && ct16->lo) e = encode_ct16_store_map(&maps.lo, ct16->lo, ct16->kpad, g.M, fc_rows);
+    if (e != cudaSuccess) return e;
+    maps.has_lo = ct16->lo != nullptr;
+    return launch_ppf_t<BITS, MODE_CT16>(g, in, hist, po, maps, st);
   }
   if (ct) {
     po.f32 = ct;
-    return launch_ppf_t<BITS, MODE_CT32>(g, in, hist, po, st);
+    return launch_ppf_t<BITS, MODE_CT32>(g, in, hist, po, maps, st);
   }
   po.f32 = chan;
-  return launch_ppf_t<BITS, MODE_CHAN>(g, in, hist, po, st);
+  return launch_ppf_t<BITS, MODE_CHAN>(g, in, hist, po, maps, st);
 }
 
 }  // namespace
