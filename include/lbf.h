@@ -297,8 +297,9 @@ lbf_status lbf_trace_end(lbf_plan_t plan, lbf_trace *out);
 /* Synchronises the device and reports whether a bounded device-side wait (tensor-core pipeline
  * barriers) gave up since the last call: LBF_ETIMEOUT (the results of the affected launch are
  * invalid; *code, if given, receives the role that gave up: 1 tensor-core loads, 2 MMA, 3 epilogue,
- * 4 the filter bank's input copies), else
- * LBF_OK.  The error word is cleared. */
+ * 4 the filter bank's input copies).  Code 5 (returned as LBF_ECUDA) means the filter bank found
+ * its dynamic shared memory not 128-byte aligned for its tensor stores and wrote no output.
+ * Otherwise LBF_OK.  The error word is cleared. */
 lbf_status lbf_device_status(lbf_plan_t plan, int32_t *code);
 
 /* Failure-detection test hook for the bounded waits of the tensor-core beam former.  The next

@@ -53,6 +53,24 @@ cudaError_t encode_ct16_store_map(void *map, void *base, int kpad, int M, long l
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// The FP32 corner turn as FP32 elements: dims (2M re/im values of a (station, pol) row, P, S,
+// F*N channel rows); a box is 16 spectra (128 bytes) x 1 x 1 x nch channels, laid out
+// [channel][spectrum] in shared memory.  The strides are multiples of 16 bytes only for even M.
+cudaError_t encode_ct32_store_map(void *map, void *base, int S, int M, long long fc_rows, int nch) {
+  PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  if (!encode) return cudaErrorNotSupported;
+  if (M % 2 != 0 || nch < 1 || nch > kN) return cudaErrorInvalidValue;
+  const cuuint64_t row = (cuuint64_t)M * 8;   // bytes of one (station, pol) row
+  const cuuint64_t dims[4] = {(cuuint64_t)M * 2, 2, (cuuint64_t)S, (cuuint64_t)fc_rows};
+  const cuuint64_t strides[3] = {row, 2 * row, 2 * row * (cuuint64_t)S};
+  const cuuint32_t box[4] = {32, 1, 1, (cuuint32_t)nch};
+  const cuuint32_t elem[4] = {1, 1, 1, 1};
+  CUresult r = encode(static_cast<CUtensorMap *>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box,
+                      elem, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 }  // namespace lbf
 
 namespace {
@@ -728,7 +746,7 @@ lbf_status lbf_device_status(lbf_plan_t p, int32_t *code) {
   if (h != 0) {
     e = cudaMemset(p->d_err, 0, sizeof(int));
     if (e != cudaSuccess) return cuda_status(e);
-    return LBF_ETIMEOUT;
+    return h == lbf::DERR_PPF_ALIGN ? LBF_ECUDA : LBF_ETIMEOUT;
   }
   return LBF_OK;
 }

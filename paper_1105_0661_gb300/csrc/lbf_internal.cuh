@@ -39,7 +39,10 @@ struct Geometry {
 };
 
 // Codes of the device error word (lbf_device_status): the role whose bounded wait expired.
-enum DeviceErr { DERR_NONE = 0, DERR_TC_LOADS = 1, DERR_TC_MMA = 2, DERR_TC_EPILOGUE = 3, DERR_PPF_INPUT = 4 };
+// DERR_PPF_ALIGN is not a wait: the filter bank's shared memory was not 128-byte aligned for its
+// tensor stores, and it wrote nothing.
+enum DeviceErr { DERR_NONE = 0, DERR_TC_LOADS = 1, DERR_TC_MMA = 2, DERR_TC_EPILOGUE = 3, DERR_PPF_INPUT = 4,
+                 DERR_PPF_ALIGN = 5 };
 
 enum OutKind { OUT_VOLTAGES = 0, OUT_STOKES_I = 1, OUT_STOKES_IQUV = 4 };
 
@@ -54,6 +57,9 @@ __host__ __device__ inline int tc_tiles(int M) { return ((M + 63) / 64) * 2; }
 // Tensor map (CUtensorMap, 128 bytes, written to `map`) of one FP16 plane at `base` for the filter
 // bank's tensor stores: boxes of 16 spectra of one pol x 2 K rows x 256 channels, no swizzle.
 cudaError_t encode_ct16_store_map(void *map, void *base, int kpad, int M, long long fc_rows);
+// The same for the FP32 corner turn [F*N][S][P][M] float2 (M even): boxes of 16 spectra of one
+// (station, pol) x `nch` consecutive channels.
+cudaError_t encode_ct32_store_map(void *map, void *base, int S, int M, long long fc_rows, int nch);
 
 // One observation of a batch (grouped persistent launches, batch.cu): its geometry, this
 // block's buffers, and its range of work items in the grouped filter bank and beam former.

@@ -60,6 +60,17 @@ constexpr long long kMinCtas = 152LL * 16;
 constexpr int kStages = 2;                 // input ring depth (tiles)
 constexpr int kRowV = 258;                 // float2 per transform row: 256 points + 2 of padding
 constexpr uint32_t kWaitIters = 1u << 20;  // polls before a wait on a copy gives up
+// FP32 corner turn with tensor stores: the FIR outputs of tile t + 1 computed during pass 1 of
+// tile t (the rest during pass 2).  Rows [kFirA, 16) of a tile's buffer are refilled only in the
+// pass-2 phase of the next tile, so they stage the channels [256 - kCtTma, 256) of the tile's
+// output for the tensor store, from a 128-byte-aligned offset; the other channels are stored from
+// the lanes.  Measured on the LOFAR block (FP32 filter bank 13.54 ms with every value stored from
+// the lanes and 8 FIR outputs in each phase): kFirA = 8 (128 channels staged) 14.36 ms, 4 (192,
+// spilling) 15.19 ms, 0 (all 256 staged, the whole FIR of the next tile inside pass 2) 13.14 ms.
+constexpr int kFirA = 0;
+constexpr int kCtStageOff = ((kFirA * kRowV * 8 + 127) / 128) * 128;                 // bytes
+constexpr int kCtTma = (((kTile * kRowV * 8 - kCtStageOff) / 128) / 16) * 16 > kN
+                           ? kN : (((kTile * kRowV * 8 - kCtStageOff) / 128) / 16) * 16;   // channels
 
 template <int BITS> struct SampleIO;
 template <> struct SampleIO<16> {   // X.re, X.im, Y.re, Y.im as four little-endian int16
@@ -110,7 +121,7 @@ struct PpfSmem {
 static_assert(offsetof(PpfSmem<16>, ctl) == 0 && offsetof(PpfSmem<8>, ctl) == 0, "ring control first");
 static_assert((PpfSmem<16>::kSlot * sizeof(uint2)) % 16 == 0 && (PpfSmem<8>::kSlot * sizeof(uint32_t)) % 16 == 0,
               "ring slots 16-byte aligned");
-static_assert(sizeof(PpfSmem<16>) + 128 <= 232448 && sizeof(PpfSmem<8>) + 128 <= 232448, "one CTA's shared memory");
+static_assert(sizeof(PpfSmem<16>) <= 232448 && sizeof(PpfSmem<8>) <= 232448, "one CTA's shared memory");
 static_assert(offsetof(PpfSmem<16>, w) % 128 == 0 && offsetof(PpfSmem<8>, w) % 128 == 0 &&
                   (kTile * kRowV * sizeof(float2)) % 128 == 0 && 2 * kN * 64 <= kTile * kRowV * sizeof(float2),
               "tile buffers 128-byte aligned and large enough to stage both FP16 planes of a tile");
@@ -190,6 +201,7 @@ __device__ __forceinline__ void half_sync(uint32_t id) {
 // two K rows of a station x 256 channels (encode_ct16_store_map).
 struct PpfMaps {
   CUtensorMap hi, lo;
+  CUtensorMap ct;   // FP32 corner turn [F*N][S][P][M] float2: boxes of 16 spectra x kCtTma channels
   int has_lo;
 };
 
@@ -232,9 +244,10 @@ __device__ __forceinline__ void ppf_drain(PpfCtl &c) {
 // One work item: both polarisations of spectra [chunk * spc, (chunk + 1) * spc) of stream (s, f),
 // spc a multiple of 16.  On entry every thread of the CTA is done with the previous item (if any);
 // `ph` holds this thread's parity bit per ring slot.
-// kTmaSt (FP16 planes only): pass 2 stages each tile's planes in the tile's own buffer and one
-// thread per half stores them with tensor stores (maps), which drain while the next tile is filtered;
-// otherwise every thread stores its values directly.
+// kTmaSt: pass 2 stages each tile's FP16 planes (all of them) or FP32 corner turn (channels
+// [256 - kCtTma, 256)) in the tile's own buffer and one thread per half stores them with tensor
+// stores (maps), which drain while the next tile is filtered; otherwise every thread stores its
+// values directly.
 template <int BITS, int MODE, bool kTmaSt>
 __device__ __forceinline__ void ppf_item(const Geometry &g, const typename SampleIO<BITS>::word *__restrict__ in,
                                          const typename SampleIO<BITS>::word *__restrict__ hist, const PpfOut &po,
@@ -400,7 +413,7 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
       a[2 * i] = make_float2(v.x, v.y);
       a[2 * i + 1] = make_float2(v.z, v.w);
     }
-    if constexpr (MODE == MODE_CT16 && kTmaSt) half_sync(bar_z);   // the buffer is read: staging may overwrite it
+    if constexpr (MODE != MODE_CHAN && kTmaSt) half_sync(bar_z);   // the buffer is read: staging may overwrite it
     dft16(a);
     const int mg = mt + m2;
     if (MODE == MODE_CHAN) {
@@ -419,6 +432,29 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
           a[2 * i + 1] = cmul(a[2 * i + 1], make_float2(gg.z, gg.w));
         }
         // ct[f][c][s][pol][m]: the 16 lanes of a channel write 16 consecutive spectra (128 B)
+        if constexpr (kTmaSt) {
+          // channel c = k1 + 16 j (j = (k2 + 8) & 15): j >= 16 - kCtTma / 16 goes to the staging
+          // box [kCtTma channels][16 spectra] float2, the rest straight to global memory
+          constexpr int kJ0 = 16 - kCtTma / 16;
+          unsigned char *stg = reinterpret_cast<unsigned char *>(&wbuf[t & 1][0][0]) + kCtStageOff;
+          float2 *dst = po.f32 + ((((long long)f * kN + k1) * g.S + s) * kP + pol) * g.M + mg;
+          const long long cstep = 16LL * g.S * kP * g.M;
+#pragma unroll
+          for (int k2 = 0; k2 < 16; ++k2) {
+            const int j = (k2 + 8) & 15;
+            if (j >= kJ0)
+              *reinterpret_cast<float2 *>(stg + ((j - kJ0) * 16 + k1) * 128 + m2 * 8) = a[k2];
+            else if (mg < m_end)
+              dst[j * cstep] = a[k2];
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // staging visible to the tensor store
+          half_sync(bar_w);
+          if (p == 0) {
+            tma_store_4d(&maps->ct, smem_u32(stg), 2 * mt, pol, s, f * kN + kN - kCtTma);
+            bulk_commit();
+          }
+          return;
+        }
         if (mg < m_end) {
           float2 *dst = po.f32 + ((((long long)f * kN + k1) * g.S + s) * kP + pol) * g.M + mg;
           const long long cstep = 16LL * g.S * kP * g.M;
@@ -489,11 +525,14 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
   using I0 = std::integral_constant<int, 0>;
   using I8 = std::integral_constant<int, kTile / 2>;
   using I16 = std::integral_constant<int, kTile>;
-  // Software pipeline: the FIR of tile t + 1 is split over the two FFT phases of tile t, so every
-  // warp has independent FMA work to issue while its shared-memory loads are in flight.
+  // Software pipeline: the FIR of tile t + 1 runs inside the FFT phases of tile t, so every warp
+  // has independent FMA work to issue while its shared-memory loads are in flight.  Direct stores:
   //   prologue:  FIR(0)                               | barrier x
   //   tile t:    pass 1(t) + FIR(t + 1) outputs 0..7  | barrier x (pass 1 done; abort check)
   //              pass 2(t) + FIR(t + 1) outputs 8..15 | barrier y (wbuf[t & 1] free, FIR done)
+  // With tensor stores (kFirA = 0) the whole FIR of tile t + 1 runs in the pass-2 phase, which
+  // stages tile t in wbuf[t & 1] between barriers z and w; before barrier x thread 0 of the half
+  // waits until the store of tile t - 1 has read wbuf[(t + 1) & 1], which that FIR refills.
   // The FP16-plane output keeps its pass 2 (shuffles and the hi/lo split) apart from the FIR: the
   // pipelined schedule measured 8 % slower for it (spilling with 16-bit samples, and slower
   // without spills with 8-bit ones).  Its schedule is sequential over the same two buffers:
@@ -519,21 +558,25 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
     if (half_sync_any(bar_x, failed || aborted())) return;
     release_slot(0);
   }
+  using IA = std::integral_constant<int, kTmaSt ? kFirA : kTile / 2>;
   for (int t = 0; t < ntiles; ++t) {
     const bool next = t + 1 < ntiles;
     const bool failed = next && !wait_tile(t + 1);
     if (next)
       with_variant(t + 1, [&](auto full, auto direct) {
         pass1(t);
-        fir(t + 1, I0(), I8(), full, direct);
+        fir(t + 1, I0(), IA(), full, direct);
       });
     else
       pass1(t);
+    // the tensor store of tile t - 1 has read its staging rows, which pass 2 below refills with
+    // FIR outputs of tile t + 1
+    if (kTmaSt && p == 0) bulk_wait_read();
     if (half_sync_any(bar_x, failed || aborted())) return;
     if (next)
       with_variant(t + 1, [&](auto full, auto direct) {
         pass2(t);
-        fir(t + 1, I8(), I16(), full, direct);
+        fir(t + 1, IA(), I16(), full, direct);
       });
     else
       pass2(t);
@@ -542,17 +585,21 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
   }
 }
 
-template <int BITS, int MODE>
+template <int BITS, int MODE, bool kTma>
 __global__ void __launch_bounds__(kThreads, 1)
 ppf_kernel(Geometry g, const typename SampleIO<BITS>::word *__restrict__ in,
            const typename SampleIO<BITS>::word *__restrict__ hist, PpfOut po, int chunks, int spc,
            const __grid_constant__ PpfMaps maps) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  // with tensor stores (FP16 planes) the layout starts on a 128-byte boundary, so that the staging
-  // buffers are 128-byte aligned; the launch adds 128 bytes of slack
-  const uint32_t raw = smem_u32(smem_raw);
-  const uint32_t pad = MODE == MODE_CT16 ? ((128u - (raw & 127u)) & 127u) : 0u;
-  PpfSmem<BITS> &sm = *reinterpret_cast<PpfSmem<BITS> *>(smem_raw + pad);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  // The tensor stores read 128-byte-aligned staging buffers: the layout aligns them within itself
+  // and the base is declared 128-byte aligned (this kernel has no static shared memory).  Rounding
+  // the base up at run time instead cost the FP32 form registers (spills); a base that is not
+  // aligned after all is reported (device error 5) and the CTA writes nothing.
+  if (kTma && (smem_u32(smem_raw) & 127u) != 0) {
+    if (threadIdx.x == 0 && g.err) atomicCAS(g.err, 0, DERR_PPF_ALIGN);
+    return;
+  }
+  PpfSmem<BITS> &sm = *reinterpret_cast<PpfSmem<BITS> *>(smem_raw);
   int s, f, chunk;
   const long long item = blockIdx.x;
   if (MODE == MODE_CT16) {   // stations fastest: neighbouring CTAs fill neighbouring K rows of the
@@ -568,10 +615,10 @@ ppf_kernel(Geometry g, const typename SampleIO<BITS>::word *__restrict__ in,
   }
   ppf_setup(sm.ctl);
   uint32_t ph = 0;
-  ppf_item<BITS, MODE, MODE == MODE_CT16>(g, in, hist, po, s, f, chunk, spc, sm, ph, &maps);
+  ppf_item<BITS, MODE, kTma>(g, in, hist, po, s, f, chunk, spc, sm, ph, &maps);
   // the tensor stores of the last tiles complete (read and written) before the CTA's shared
   // memory is released; only thread 0 of each half issued any
-  if (MODE == MODE_CT16 && threadIdx.x % kHalf == 0) bulk_wait_all();
+  if (kTma && threadIdx.x % kHalf == 0) bulk_wait_all();
   __syncthreads();
   ppf_drain(sm.ctl);
 }
@@ -669,7 +716,7 @@ __global__ void hist_update_kernel(long long total, int H, int T,
   }
 }
 
-template <int BITS, int MODE>
+template <int BITS, int MODE, bool kTma>
 cudaError_t launch_ppf_t(const Geometry &g, const void *in, const void *hist, PpfOut po, const PpfMaps &maps,
                          cudaStream_t st) {
   using word = typename SampleIO<BITS>::word;
@@ -680,8 +727,8 @@ cudaError_t launch_ppf_t(const Geometry &g, const void *in, const void *hist, Pp
   const int chunks = (g.M + spc - 1) / spc;
   const long long ctas = streams * chunks;
   if (ctas == 0) return cudaSuccess;
-  const size_t smem = sizeof(PpfSmem<BITS>) + 128;   // + alignment slack
-  auto kern = ppf_kernel<BITS, MODE>;
+  const size_t smem = sizeof(PpfSmem<BITS>);
+  auto kern = ppf_kernel<BITS, MODE, kTma>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)ctas, kThreads, smem, st>>>(g, (const word *)in, (const word *)hist, po, chunks, spc, maps);
@@ -703,14 +750,20 @@ cudaError_t launch_ppf_bits(const Geometry &g, const void *in, const void *hist,
     if (e == cudaSuccess && ct16->lo) e = encode_ct16_store_map(&maps.lo, ct16->lo, ct16->kpad, g.M, fc_rows);
     if (e != cudaSuccess) return e;
     maps.has_lo = ct16->lo != nullptr;
-    return launch_ppf_t<BITS, MODE_CT16>(g, in, hist, po, maps, st);
+    return launch_ppf_t<BITS, MODE_CT16, true>(g, in, hist, po, maps, st);
   }
   if (ct) {
     po.f32 = ct;
-    return launch_ppf_t<BITS, MODE_CT32>(g, in, hist, po, maps, st);
+    // a tensor map over [F*N][S][P][M] float2 needs 16-byte strides (M even) and base
+    if ((long long)g.S * g.F > 0 && g.M > 0 && g.M % 2 == 0 && (reinterpret_cast<uintptr_t>(ct) & 15) == 0) {
+      cudaError_t e = encode_ct32_store_map(&maps.ct, ct, g.S, g.M, (long long)g.F * kN, kCtTma);
+      if (e != cudaSuccess) return e;
+      return launch_ppf_t<BITS, MODE_CT32, true>(g, in, hist, po, maps, st);
+    }
+    return launch_ppf_t<BITS, MODE_CT32, false>(g, in, hist, po, maps, st);
   }
   po.f32 = chan;
-  return launch_ppf_t<BITS, MODE_CHAN>(g, in, hist, po, maps, st);
+  return launch_ppf_t<BITS, MODE_CHAN, false>(g, in, hist, po, maps, st);
 }
 
 }  // namespace
