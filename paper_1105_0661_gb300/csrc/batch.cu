@@ -56,12 +56,14 @@ struct lbf_batch_s {
   std::vector<int> variant;            // beam-former kernel per plan
   // group tables: [parity][plan]; parity p describes the plans' history state after p blocks
   lbf::PpfGroup *h_ppf = nullptr, *d_ppf = nullptr;   // pinned host / device, 2 * n
+  unsigned char *h_maps = nullptr, *d_maps = nullptr; // their tensor maps (2 * n entries of
+                                                      // ppf_group_maps_bytes()), pinned host / device
   lbf::BfGroup *h_bf = nullptr;                      // pinned host, 2 * n: FP32 plans, class by class
   unsigned long long *d_counter = nullptr;            // [max_counters(n)] work counters, one per launch
   long long hist_items = 0;
   // launch classes: filter bank per (sample width, FP32 or FP16 output); FP32 beam former per
   // (variant, output kind, CTAs per SM) -- each class one persistent launch over its groups
-  struct PpfClass { int bits, tc, first, n; long long items; };
+  struct PpfClass { int bits, tc, tma, first, n; long long items; };
   struct BfClass { int variant, out_kind, per_sm, first, n; long long items; size_t smem; };
   std::vector<PpfClass> ppf_cls;
   std::vector<BfClass> bf_cls;
@@ -90,17 +92,25 @@ void fill_tables(lbf_batch_t b, int par, const void *const *d_in, void *const *d
   long long hi = 0;
   int slot = 0;
   b->ppf_cls.clear();
+  const size_t mb = lbf::ppf_group_maps_bytes();
   for (int bits : {16, 8})
-    for (int tc = 0; tc < 2; ++tc) {
-      lbf_batch_s::PpfClass cls{bits, tc, slot, 0, 0};
+    for (int tc = 0; tc < 2; ++tc)
+    for (int tma = 1; tma >= 0; --tma) {   // tensor-store output (FP16 planes; FP32 with even M) or not
+      lbf_batch_s::PpfClass cls{bits, tc, tma, slot, 0, 0};
       for (int i = 0; i < n; ++i) {
         lbf_plan_t p = b->plans[i];
         if (p->bits != bits || (p->tc ? 1 : 0) != tc) continue;
+        lbf::PpfGroup probe;
+        probe.g = p->geometry();
+        probe.tc = tc;
+        probe.ct = p->ws;
+        if ((lbf::ppf_group_tma(probe) ? 1 : 0) != tma) continue;
         if (cls.n == lbf::kMaxGroups) {   // one launch holds at most kMaxGroups groups
           b->ppf_cls.push_back(cls);
-          cls = lbf_batch_s::PpfClass{bits, tc, slot, 0, 0};
+          cls = lbf_batch_s::PpfClass{bits, tc, tma, slot, 0, 0};
         }
         const int cur = p->cur ^ par;
+        const int at = par * n + slot;
         lbf::PpfGroup &G = b->h_ppf[par * n + slot++];
         G.g = p->geometry();
         G.in = d_in[i];
@@ -116,6 +126,9 @@ void fill_tables(lbf_batch_t b, int par, const void *const *d_in, void *const *d
         G.chunks = lbf::ppf_items_per_stream(p->M, b->spc);
         G.first_item = cls.items;
         G.first_hist = hi;
+        G.maps = nullptr;
+        if (tma && lbf::ppf_group_maps(G, b->h_maps + (size_t)at * mb) == cudaSuccess)
+          G.maps = b->d_maps + (size_t)at * mb;
         cls.items += (long long)p->S * p->F * G.chunks;   // one item: both polarisations of a chunk
         hi += (long long)p->S * p->F * p->H;
         ++cls.n;
@@ -171,6 +184,10 @@ cudaError_t enqueue(lbf_batch_t b, int par, cudaStream_t st) {
   // and beam former take theirs as kernel parameters
   cudaError_t e = cudaMemcpyAsync(b->d_ppf + par * n, b->h_ppf + par * n, sizeof(lbf::PpfGroup) * n,
                                   cudaMemcpyHostToDevice, st);
+  const size_t mb = lbf::ppf_group_maps_bytes();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_maps + (size_t)par * n * mb, b->h_maps + (size_t)par * n * mb, mb * n,
+                        cudaMemcpyHostToDevice, st);
   if (b->per_plan) {
     // each plan's own filter bank, history update and FP32 beam former (the hardware schedules
     // their CTAs; large observations each fill the GPU); the tensor-core plans follow, one
@@ -198,7 +215,7 @@ cudaError_t enqueue(lbf_batch_t b, int par, cudaStream_t st) {
     if ((int)(b->ppf_cls.size() + b->bf_cls.size()) > max_counters(n)) return cudaErrorInvalidValue;
     for (const auto &c : b->ppf_cls)
       if (e == cudaSuccess)
-        e = lbf::launch_ppf_group(c.bits, c.tc, b->h_ppf + par * n + c.first, c.n, c.items,
+        e = lbf::launch_ppf_group(c.bits, c.tc, c.tma, b->h_ppf + par * n + c.first, c.n, c.items,
                                   b->d_counter + counter++, b->ppf_ctas, st);
     if (e == cudaSuccess) e = lbf::launch_hist_group(b->d_ppf + par * n, n, b->hist_items, st);
     for (const auto &c : b->bf_cls)
@@ -285,10 +302,13 @@ lbf_status lbf_batch_create(const lbf_plan_t *plans, int32_t n, lbf_batch_t *out
   b->ppf_ctas = lbf::ppf_ctas_per_sm() * b->sms;   // persistent filter-bank CTAs
   cudaError_t e = cudaMallocHost((void **)&b->h_ppf, sizeof(lbf::PpfGroup) * 2 * n);
   if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_bf, sizeof(lbf::BfGroup) * 2 * n);
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_maps, lbf::ppf_group_maps_bytes() * 2 * n);
   if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_ppf, sizeof(lbf::PpfGroup) * 2 * n);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_maps, lbf::ppf_group_maps_bytes() * 2 * n);
   if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_counter, max_counters(n) * sizeof(unsigned long long));
   if (e != cudaSuccess) {
-    cudaFreeHost(b->h_ppf); cudaFreeHost(b->h_bf); cudaFree(b->d_ppf); cudaFree(b->d_counter);
+    cudaFreeHost(b->h_ppf); cudaFreeHost(b->h_bf); cudaFreeHost(b->h_maps);
+    cudaFree(b->d_ppf); cudaFree(b->d_maps); cudaFree(b->d_counter);
     delete b;
     cudaGetLastError();
     return status_of(e);
@@ -302,7 +322,8 @@ lbf_status lbf_batch_destroy(lbf_batch_t b) {
   if (b->magic != kBatchMagic) return LBF_ESTATE;
   cudaDeviceSynchronize();
   free_graphs(b);
-  cudaFreeHost(b->h_ppf); cudaFreeHost(b->h_bf); cudaFree(b->d_ppf); cudaFree(b->d_counter);
+  cudaFreeHost(b->h_ppf); cudaFreeHost(b->h_bf); cudaFreeHost(b->h_maps);
+  cudaFree(b->d_ppf); cudaFree(b->d_maps); cudaFree(b->d_counter);
   b->magic = 0;
   delete b;
   return LBF_OK;

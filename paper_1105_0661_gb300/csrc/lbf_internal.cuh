@@ -76,6 +76,8 @@ struct PpfGroup {
   int chunks;                 // ceil(M / spc)
   long long first_item;       // first filter-bank work item of this group
   long long first_hist;       // first history element of this group
+  const void *maps;           // device copy of its output's tensor maps (ppf_group_maps), when
+                              // the group is in a tensor-store launch class
 };
 struct BfGroup {
   Geometry g;
@@ -114,7 +116,13 @@ __device__ __forceinline__ int group_of(const Table &T, long long item) {
 }
 // one persistent launch for the groups of one sample width and output form (FP32 corner turn or
 // FP16 planes); items numbered from 0 within the launch
-cudaError_t launch_ppf_group(int bits, int tc, const PpfGroup *h_groups, int ngrp, long long total,
+// Tensor-store output of a group's filter bank: whether its output allows it (FP16 planes always;
+// the FP32 corner turn for even M), and the bytes and host encoding of its tensor maps, which the
+// caller copies to device memory and points G.maps at.
+bool ppf_group_tma(const PpfGroup &G);
+size_t ppf_group_maps_bytes();
+cudaError_t ppf_group_maps(const PpfGroup &G, void *host_dst);
+cudaError_t launch_ppf_group(int bits, int tc, int tma, const PpfGroup *h_groups, int ngrp, long long total,
                              unsigned long long *counter, int ctas, cudaStream_t st);
 // history update of all groups (DEVICE table: each thread looks up its own element's group)
 cudaError_t launch_hist_group(const PpfGroup *d_groups, int ngrp, long long total, cudaStream_t st);

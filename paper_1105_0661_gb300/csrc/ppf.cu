@@ -42,6 +42,7 @@
 #include <cuda_fp16.h>
 
 #include <cstddef>
+#include <cstring>
 #include <type_traits>
 
 #include "fft16.cuh"
@@ -550,6 +551,8 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
       half_sync(bar_y);
       pass2(t);
     }
+    // the last tile's stores have read their buffer before another item's FIR refills it
+    if (kTmaSt && p == 0) bulk_wait_read();
     return;
   }
   {
@@ -583,6 +586,7 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
     half_sync(bar_y);
     if (next) release_slot(t + 1);
   }
+  if (kTmaSt && p == 0) bulk_wait_read();   // as above
 }
 
 template <int BITS, int MODE, bool kTma>
@@ -628,13 +632,17 @@ ppf_kernel(Geometry g, const typename SampleIO<BITS>::word *__restrict__ in,
 // One launch per class of sample width and output form, so each body keeps the registers it has
 // when its observation runs alone.  The observations' geometry comes in a grid-constant table
 // (constant bank); thread 0 finds each item's observation.
-template <int BITS, int MODE>
+template <int BITS, int MODE, bool kTma>
 __global__ void __launch_bounds__(kThreads, 1)
 ppf_group_kernel(const __grid_constant__ PpfTable T, long long total, unsigned long long *counter) {
   using word = typename SampleIO<BITS>::word;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ long long item_s;
   __shared__ int grp_s;
+  if (kTma && (smem_u32(smem_raw) & 127u) != 0) {   // staging buffers must be 128-byte aligned
+    if (threadIdx.x == 0 && T.grp[0].g.err) atomicCAS(T.grp[0].g.err, 0, DERR_PPF_ALIGN);
+    return;
+  }
   PpfSmem<BITS> &sm = *reinterpret_cast<PpfSmem<BITS> *>(smem_raw);
   ppf_setup(sm.ctl);
   uint32_t ph = 0;
@@ -660,18 +668,19 @@ ppf_group_kernel(const __grid_constant__ PpfTable T, long long total, unsigned l
     const PpfOut po = MODE == MODE_CT16
         ? PpfOut{nullptr, reinterpret_cast<__half *>(G.ct16.hi), reinterpret_cast<__half *>(G.ct16.lo), G.ct16.kpad}
         : PpfOut{G.ct, nullptr, nullptr, 0};
-    ppf_item<BITS, MODE, false>(G.g, (const word *)G.in, (const word *)G.hist, po, s, f, chunk, G.spc, sm, ph,
-                                nullptr);
+    ppf_item<BITS, MODE, kTma>(G.g, (const word *)G.in, (const word *)G.hist, po, s, f, chunk, G.spc, sm, ph,
+                               kTma ? static_cast<const PpfMaps *>(G.maps) : nullptr);
   }
+  if (kTma && threadIdx.x % kHalf == 0) bulk_wait_all();
   __syncthreads();
   ppf_drain(sm.ctl);
 }
 
-template <int BITS, int MODE>
+template <int BITS, int MODE, bool kTma>
 cudaError_t launch_group_t(const PpfTable &T, long long total, unsigned long long *counter, int ctas,
                            cudaStream_t st) {
   const size_t smem = sizeof(PpfSmem<BITS>);
-  auto kern = ppf_group_kernel<BITS, MODE>;
+  auto kern = ppf_group_kernel<BITS, MODE, kTma>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
@@ -777,17 +786,47 @@ cudaError_t launch_ppf(const Geometry &g, int bits, const void *in, const void *
                     : launch_ppf_bits<8>(g, in, hist, chan, ct, ct16, st);
 }
 
-cudaError_t launch_ppf_group(int bits, int tc, const PpfGroup *h_groups, int ngrp, long long total,
+bool ppf_group_tma(const PpfGroup &G) {
+  if ((long long)G.g.S * G.g.F == 0 || G.g.M == 0) return false;
+  if (G.tc) return true;
+  return G.g.M % 2 == 0 && (reinterpret_cast<uintptr_t>(G.ct) & 15) == 0;
+}
+
+size_t ppf_group_maps_bytes() { return sizeof(PpfMaps); }
+
+cudaError_t ppf_group_maps(const PpfGroup &G, void *host_dst) {
+  if (!ppf_group_tma(G)) return cudaErrorInvalidValue;
+  PpfMaps m{};
+  const long long fc_rows = (long long)G.g.F * kN;
+  cudaError_t e;
+  if (G.tc) {
+    e = encode_ct16_store_map(&m.hi, G.ct16.hi, G.ct16.kpad, G.g.M, fc_rows);
+    if (e == cudaSuccess && G.ct16.lo) e = encode_ct16_store_map(&m.lo, G.ct16.lo, G.ct16.kpad, G.g.M, fc_rows);
+    m.has_lo = G.ct16.lo != nullptr;
+  } else {
+    e = encode_ct32_store_map(&m.ct, G.ct, G.g.S, G.g.M, fc_rows, kCtTma);
+  }
+  if (e == cudaSuccess) std::memcpy(host_dst, &m, sizeof(m));
+  return e;
+}
+
+cudaError_t launch_ppf_group(int bits, int tc, int tma, const PpfGroup *h_groups, int ngrp, long long total,
                              unsigned long long *counter, int ctas, cudaStream_t st) {
   if (total == 0) return cudaSuccess;
   if (ngrp < 1 || ngrp > kMaxGroups) return cudaErrorInvalidValue;
   PpfTable T;
   T.n = ngrp;
   for (int i = 0; i < ngrp; ++i) T.grp[i] = h_groups[i];
-  if (bits == 16) return tc ? launch_group_t<16, MODE_CT16>(T, total, counter, ctas, st)
-                            : launch_group_t<16, MODE_CT32>(T, total, counter, ctas, st);
-  return tc ? launch_group_t<8, MODE_CT16>(T, total, counter, ctas, st)
-            : launch_group_t<8, MODE_CT32>(T, total, counter, ctas, st);
+  if (tma) {
+    if (bits == 16) return tc ? launch_group_t<16, MODE_CT16, true>(T, total, counter, ctas, st)
+                              : launch_group_t<16, MODE_CT32, true>(T, total, counter, ctas, st);
+    return tc ? launch_group_t<8, MODE_CT16, true>(T, total, counter, ctas, st)
+              : launch_group_t<8, MODE_CT32, true>(T, total, counter, ctas, st);
+  }
+  if (bits == 16) return tc ? launch_group_t<16, MODE_CT16, false>(T, total, counter, ctas, st)
+                            : launch_group_t<16, MODE_CT32, false>(T, total, counter, ctas, st);
+  return tc ? launch_group_t<8, MODE_CT16, false>(T, total, counter, ctas, st)
+            : launch_group_t<8, MODE_CT32, false>(T, total, counter, ctas, st);
 }
 
 cudaError_t launch_hist_group(const PpfGroup *d_groups, int ngrp, long long total, cudaStream_t st) {

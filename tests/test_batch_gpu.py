@@ -18,7 +18,9 @@ def _specs():
     out = []
     for i, (S, F, B, outk, bits, T) in enumerate([(12, 3, 1, "I", 16, 40 * N), (20, 2, 17, "IQUV", 8, 64 * N),
                                                   (33, 1, 130, "I", 16, 48 * N), (8, 4, 6, "V", 16, 32 * N),
-                                                  (64, 1, 40, "IQUV", 8, 64 * N)]):
+                                                  (64, 1, 40, "IQUV", 8, 64 * N),
+                                                  # odd M: the FP32 corner turn without tensor stores
+                                                  (10, 2, 3, "V", 16, 41 * N)]):
         xyz = G.lofar_positions(rng, S // 2, S - S // 2)
         wl = G.Workload(f"b{i}", xyz, G.subband_centres(F, 130e6 + 5e6 * i), G.hex_beam_grid(B, 0.05), (0.3, 0.4),
                         T, 4 if outk != "V" else 1, outk, sample_bits=bits, sigma=32.0 if bits == 16 else 8.0,
@@ -91,7 +93,8 @@ def test_batch_with_tensor_core_plans_equals_separate_runs():
     torch.cuda.set_device(dev)
     wls = _specs()
     kinds = [dict(), dict(precision="fp16tc"), dict(precision="fp16tc", incoherent_beam=True),
-             dict(precision="fp16tc"), dict(precision="fp16tc2")]
+             dict(precision="fp16tc"), dict(precision="fp16tc2"), dict()]
+    assert len(kinds) == len(wls)
     solo = [Plan.from_workload(wl, **kw) for wl, kw in zip(wls, kinds)]
     grouped = [Plan.from_workload(wl, **kw) for wl, kw in zip(wls, kinds)]
     batch = Batch(grouped)
