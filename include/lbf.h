@@ -302,15 +302,19 @@ lbf_status lbf_trace_end(lbf_plan_t plan, lbf_trace *out);
  * Otherwise LBF_OK.  The error word is cleared. */
 lbf_status lbf_device_status(lbf_plan_t plan, int32_t *code);
 
-/* Failure-detection test hook for the bounded waits of the tensor-core beam former.  The next
- * tensor-core beam-former launch of this plan (lbf_run_block, lbf_run_block_ws,
- * lbf_run_block_host or lbf_beamform_stokes) issues no loads from work item `item` on, so the CTA
- * that owns that item waits on a barrier that nothing completes: the wait expires after a bounded
- * number of polls (well under a second), the CTA records the MMA role in the plan's error word,
- * lets its own copies and MMAs finish, frees its tensor memory and returns.  The launch's output
- * is then invalid; lbf_device_status reports LBF_ETIMEOUT and the context stays usable.  One-shot.
- * item: a work item index in [0, F * 256 * ceil(B / 128)) (an index past the end never stalls).
- * Errors: LBF_EUNSUPPORTED for an FP32 plan (its kernels have no spin waits), LBF_EINVAL, LBF_ESTATE. */
+/* Failure-detection test hook for the bounded device-side waits.  One-shot; the launch's output
+ * is invalid afterwards, lbf_device_status reports LBF_ETIMEOUT and the context stays usable.
+ *  - Tensor-core plan: the next tensor-core beam-former launch (lbf_run_block, lbf_run_block_ws,
+ *    lbf_run_block_host or lbf_beamform_stokes) issues no loads from work item `item` on, so the
+ *    CTA that owns that item waits on a barrier that nothing completes: the wait expires after a
+ *    bounded number of polls (well under a second), the CTA records the MMA role in the plan's
+ *    error word, lets its own copies and MMAs finish, frees its tensor memory and returns.
+ *    item: a work item index in [0, F * 256 * ceil(B / 128)).
+ *  - FP32 plan: in the next fused launch (lbf_run_block, lbf_run_block_ws, lbf_run_block_host),
+ *    filter-bank CTA `item` (stream s * F + f and spectrum chunk, in [0, S * F * chunks)) issues
+ *    none of its input copies; its waits for them expire, it records code 4 (the filter bank's
+ *    input) and returns.  An index past the end never stalls.
+ * Errors: LBF_EINVAL, LBF_ESTATE. */
 lbf_status lbf_debug_stall_next(lbf_plan_t plan, int64_t item);
 
 /* lbf_run_block without any device allocation, for callers that cannot call cudaMalloc (for

@@ -269,6 +269,8 @@ cudaError_t run_block_device(lbf_plan_t p, const void *d_in, void *d_out, void *
       return lbf::launch_bf_tc(g, p->out_kind, &maps[0], &maps[1], (float *)d_out, p->d_err, st, stall); });
   }
   float2 *ct = static_cast<float2 *>(ws);
+  g.ppf_stall = p->stall_item;   // failure-detection test hook (one-shot)
+  p->stall_item = -1;
   cudaError_t e = traced(p, K_PPF_CT, st, [&] { return lbf::launch_ppf(g, p->bits, d_in, h, nullptr, ct, st); });
   if (e == cudaSuccess) e = traced(p, K_HIST, st, [&] { return lbf::launch_hist_update(g, p->bits, d_in, h, nh, st); });
   if (e == cudaSuccess && input_read) e = cudaEventRecord(input_read, st);
@@ -730,7 +732,6 @@ lbf_status lbf_dedisperse(lbf_plan_t p, double dm, int32_t fft_len, const void *
 lbf_status lbf_debug_stall_next(lbf_plan_t p, int64_t item) {
   lbf_status s = check_call(p);
   if (s != LBF_OK) return s;
-  if (!p->tc) return LBF_EUNSUPPORTED;
   if (item < 0) return LBF_EINVAL;
   p->stall_item = item;
   return LBF_OK;

@@ -36,6 +36,7 @@ struct Geometry {
   int ct16_raw = 0;           // 1: the FP16 planes hold the filtered spectrum before the delay phase
                               // and bandpass, which the tensor-core weights then carry
   int *err = nullptr;                   // device error word: a bounded wait that gave up records here
+  long long ppf_stall = -1;             // failure-detection test: this filter-bank CTA issues no input copies
 };
 
 // Codes of the device error word (lbf_device_status): the role whose bounded wait expired.

@@ -249,7 +249,9 @@ __device__ __forceinline__ void ppf_drain(PpfCtl &c) {
 // [256 - kCtTma, 256)) in the tile's own buffer and one thread per half stores them with tensor
 // stores (maps), which drain while the next tile is filtered; otherwise every thread stores its
 // values directly.
-template <int BITS, int MODE, bool kTmaSt>
+// kStall: failure-detection test build, the item issues none of its input copies (its waits
+// expire); launched only when the test asks for it, so the production kernels are untouched.
+template <int BITS, int MODE, bool kTmaSt, bool kStall = false>
 __device__ __forceinline__ void ppf_item(const Geometry &g, const typename SampleIO<BITS>::word *__restrict__ in,
                                          const typename SampleIO<BITS>::word *__restrict__ hist, const PpfOut &po,
                                          int s, int f, int chunk, int spc, PpfSmem<BITS> &sm, uint32_t &ph,
@@ -280,7 +282,7 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
   // frames start at slot offset e0 mod kAlign.
   auto is_bulk = [&](int mt) { return in16 && (long long)mt * kN - dsh >= 0; };
   auto issue = [&](int t) {   // one thread
-    if (t >= ntiles) return;
+    if (t >= ntiles || kStall) return;
     const int mt = m0 + t * kTile;
     if (!is_bulk(mt)) return;
     const int nfr = min(kTile, m_end - mt);
@@ -589,7 +591,7 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
   if (kTmaSt && p == 0) bulk_wait_read();   // as above
 }
 
-template <int BITS, int MODE, bool kTma>
+template <int BITS, int MODE, bool kTma, bool kStall = false>
 __global__ void __launch_bounds__(kThreads, 1)
 ppf_kernel(Geometry g, const typename SampleIO<BITS>::word *__restrict__ in,
            const typename SampleIO<BITS>::word *__restrict__ hist, PpfOut po, int chunks, int spc,
@@ -619,7 +621,10 @@ ppf_kernel(Geometry g, const typename SampleIO<BITS>::word *__restrict__ in,
   }
   ppf_setup(sm.ctl);
   uint32_t ph = 0;
-  ppf_item<BITS, MODE, kTma>(g, in, hist, po, s, f, chunk, spc, sm, ph, &maps);
+  if (kStall && item == g.ppf_stall)
+    ppf_item<BITS, MODE, kTma, true>(g, in, hist, po, s, f, chunk, spc, sm, ph, &maps);
+  else
+    ppf_item<BITS, MODE, kTma>(g, in, hist, po, s, f, chunk, spc, sm, ph, &maps);
   // the tensor stores of the last tiles complete (read and written) before the CTA's shared
   // memory is released; only thread 0 of each half issued any
   if (kTma && threadIdx.x % kHalf == 0) bulk_wait_all();
@@ -737,11 +742,16 @@ cudaError_t launch_ppf_t(const Geometry &g, const void *in, const void *hist, Pp
   const long long ctas = streams * chunks;
   if (ctas == 0) return cudaSuccess;
   const size_t smem = sizeof(PpfSmem<BITS>);
-  auto kern = ppf_kernel<BITS, MODE, kTma>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  kern<<<(unsigned)ctas, kThreads, smem, st>>>(g, (const word *)in, (const word *)hist, po, chunks, spc, maps);
-  return cudaGetLastError();
+  auto go = [&](auto kern) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)ctas, kThreads, smem, st>>>(g, (const word *)in, (const word *)hist, po, chunks, spc, maps);
+    return cudaGetLastError();
+  };
+  // the failure-detection test build (FP32 corner turn only) when one CTA is to stall
+  if constexpr (MODE == MODE_CT32)
+    if (g.ppf_stall >= 0 && g.ppf_stall < ctas) return go(ppf_kernel<BITS, MODE, kTma, true>);
+  return go(ppf_kernel<BITS, MODE, kTma>);
 }
 
 template <int BITS>

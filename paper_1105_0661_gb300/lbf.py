@@ -365,7 +365,7 @@ class Plan:
 
     def device_status(self) -> int:
         """Synchronise and return the role code of a device-side wait that gave up since the last
-        call (0 = none; 1 loads, 2 MMA, 3 epilogue) and clear it.  A wait that gave up
+        call (0 = none; 1 loads, 2 MMA, 3 epilogue, 4 filter-bank input) and clear it.  A wait that gave up
         (LBF_ETIMEOUT) is reported through the code; other failures raise."""
         code = ctypes.c_int32(0)
         st = self._lib.lbf_device_status(self._h, ctypes.byref(code))
@@ -374,7 +374,8 @@ class Plan:
         return code.value
 
     def debug_stall_next(self, item: int = 0):
-        """Failure-detection test: the next tensor-core launch stops loading at work item `item`."""
+        """Failure-detection test: the next tensor-core launch stops loading at work item `item`; on an
+        FP32 plan, filter-bank CTA `item` of the next fused launch issues none of its input copies."""
         _check(self._lib.lbf_debug_stall_next(self._h, int(item)), "lbf_debug_stall_next")
 
     def trace_begin(self, max_launches: int = 4096):

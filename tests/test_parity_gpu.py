@@ -488,3 +488,33 @@ def test_input_not_16_byte_aligned_gives_the_same_block(dev, bits, prec):
         assert torch.equal(o_a, o_b), bi
     p_a.close()
     p_b.close()
+
+
+# ----------------------------------------------------------------------------- failure detection
+def test_filter_bank_bounded_wait_expires_reports_and_context_survives(dev):
+    """Failure detection without a GPU fault, FP32 path: one filter-bank CTA issues none of its
+    input copies, so its halves wait on ring barriers that nothing completes.  The waits expire,
+    the CTA records code 4 (the filter bank's input) and returns, lbf_device_status reports it and
+    clears it, and the next launch on the same plan and context matches the oracle."""
+    import time
+    wl = _wl(S=8, F=2, T=64 * N, B=5, Q=4)
+    p = _plan(wl)
+    ob = O.observation_from_workload(wl)
+    blk = G.make_block(wl, seed=4)
+    d_in = _to_dev(blk, dev)
+    o = torch.empty(p.shape("stokes"), dtype=torch.float32, device=dev)
+    assert p.device_status() == 0
+    p.debug_stall_next(1)               # filter-bank CTA 1 (a spectrum chunk of one stream) copies nothing
+    t0 = time.perf_counter()
+    p.run_block(d_in, o)
+    code = p.device_status()            # synchronises
+    elapsed = time.perf_counter() - t0
+    print(f"stalled filter bank: code {code}, {elapsed:.2f} s")
+    assert code == 4
+    assert elapsed < 30.0
+    assert p.device_status() == 0       # the error word was cleared
+    p.reset_state()                     # the stalled launch advanced the history
+    p.run_block(d_in, o)
+    assert p.device_status() == 0
+    _check_stokes(o.cpu().numpy().astype(np.float64), ob.run_block(blk))
+    p.close()
