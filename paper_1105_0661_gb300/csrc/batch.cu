@@ -4,7 +4,8 @@
 // beam group) items until all are done, so small observations do not leave the GPU idle and large
 // ones do not serialise the batch.  There is one launch per class of plans whose bodies need the
 // same registers and shared memory, so that each body runs as it does alone: the filter bank per
-// (sample width, FP32 or FP16-plane output), one history launch, the FP32 beam former per
+// (sample width, FP32 or FP16-plane output, tensor-store output or not -- each observation's
+// tensor maps sit in a device array its table entry points at), one history launch, the FP32 beam former per
 // (kernel variant, output kind, CTAs per SM), and one tensor-core launch per (output kind,
 // integration length), whose work items number the class's plans one after the other.
 //

@@ -23,19 +23,22 @@
 //    column p2 of spectrum m, a 16-point DFT over p1 in registers and the twiddle
 //    exp(-2 pi i p2 k1 / 256), and writes the results back over its own 16 points.  Pass 2:
 //    thread (m = p & 15, k1 = p >> 4) reads 16 contiguous values, a 16-point DFT over p2 gives
-//    X[k1 + 16 k2]; sixteen lanes then hold sixteen consecutive spectra of one channel, so the
-//    FP32 corner-turned output is written straight from registers as whole 128-byte runs, with
-//    the delay phasor and bandpass applied.  The FP16 planes are staged instead, in the tile's own
-//    (by then consumed) FIR buffer in the layout of a tensor-map box (16 spectra x the station's
-//    two K rows x 256 channels), and one thread per half writes them with two tensor stores that
-//    drain while the next tile is filtered: written from the lanes, the tile's 64 KB left each SM
-//    in one burst at the end of the tile and stalled its warps (a runtime switch that dropped the
-//    stores cut pass 2 from ~3.8k to ~2.6k cycles per tile).
-//  * Software pipeline over two tile buffers per half (FP32 outputs): the FIR of tile t + 1 runs
-//    inside the two FFT passes of tile t (half of its outputs in each), so FMA-bound and
-//    shared-memory-bound work are interleaved in every warp; two named barriers per tile.  The
-//    FP16 planes run FIR, pass 1 and pass 2 in sequence, with two more barriers around the
-//    staging; a tile's stores must have read its buffer before the FIR two tiles later refills it.
+//    X[k1 + 16 k2]; sixteen lanes then hold sixteen consecutive spectra of one channel (for the
+//    FP32 output the delay phasor and bandpass are applied there).  The output is staged in the
+//    tile's own (by then consumed) FIR buffer in the layout of a tensor-map box -- the FP32
+//    corner turn as [256 channels][16 spectra] float2, the FP16 planes as [256 channels][the
+//    station's two K rows][16 spectra] per plane -- and one thread per half writes it with tensor
+//    stores that drain while the next tile is filtered: written from the lanes, the tile's 64 KB
+//    left each SM in one burst at the end of the tile and stalled its warps (a runtime switch that
+//    dropped the stores cut the pass-2 phase from 3.2-3.9k to 1.7-2.6k cycles per tile).  The
+//    FP32 corner turn with odd M (no 16-byte strides for a tensor map) is written from the lanes
+//    as whole 128-byte runs.
+//  * Schedule over two tile buffers per half.  FP32 output: the whole FIR of tile t + 1 runs
+//    inside pass 2 of tile t (pass 1 alone in the other phase), so that FMA-bound and
+//    shared-memory-bound work are interleaved and the staged tile has a phase to drain before
+//    that FIR refills its buffer (with lane stores the FIR is split 8/8 over the two passes).
+//    FP16 planes: FIR, pass 1 and pass 2 in sequence; the stores of a tile must have read its
+//    buffer before the FIR two tiles later refills it.
 // Every wait on a copy is bounded: on expiry the CTA records DERR_PPF_INPUT in the device error
 // word, stops, waits (bounded) for its copies in flight and returns.
 #include <cuda.h>
@@ -115,7 +118,7 @@ struct PpfSmem {
   alignas(16) float4 gain[kN / 2];             // [k1][k2 / 2]: bandpass x delay phasor, pairs of k2
   alignas(16) float2 tw[kN];                   // [k1][p2] = exp(-2 pi i k1 p2 / 256)
   // per polarisation, two tiles of v_m[p] (132 KB); each tile buffer (258 x 128 bytes) also stages
-  // the FP16 planes of its tile for the tensor stores, so it starts on a 128-byte boundary
+  // its tile's output for the tensor stores, so it starts on a 128-byte boundary
   alignas(128) float2 w[kP][2][kTile][kRowV];
   alignas(16) word in[kStages][kSlot];         // input ring of dual-pol samples (64 KB int16, 32 KB int8)
 };
@@ -574,8 +577,8 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
       });
     else
       pass1(t);
-    // the tensor store of tile t - 1 has read its staging rows, which pass 2 below refills with
-    // FIR outputs of tile t + 1
+    // the tensor store of tile t - 1 has read its staging rows, which the FIR of tile t + 1 below
+    // (inside pass 2) refills
     if (kTmaSt && p == 0) bulk_wait_read();
     if (half_sync_any(bar_x, failed || aborted())) return;
     if (next)
