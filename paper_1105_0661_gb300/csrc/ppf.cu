@@ -409,7 +409,9 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
 
   // ---- FFT pass 2 of tile t: row segment k1 of spectrum m2, 16-point DFT over p2:
   // a[k2] = X[k1 + 16 k2], channel c = (k + N/2) mod N = k1 + 16 ((k2 + 8) & 15)
-  auto pass2 = [&](int t) {
+  // fullc (FP16 planes with tensor stores): a full tile, no spectrum past the block's end to zero
+  auto pass2 = [&](int t, auto fullc) {
+    constexpr bool kFullTile = decltype(fullc)::value;
     const int mt = m0 + t * kTile;
     float2 a[16];
     const float4 *src = reinterpret_cast<const float4 *>(&wbuf[t & 1][m2][16 * k1]);
@@ -484,15 +486,16 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
           for (int k2 = 0; k2 < 16; ++k2) {
             const float send = odd ? a[k2].x : a[k2].y;
             const float recv = __shfl_xor_sync(0xffffffffu, send, 1);
-            float x0 = odd ? recv : a[k2].x;
-            float x1 = odd ? a[k2].y : recv;
-            if (!v0) x0 = 0.f;
-            if (!v1) x1 = 0.f;
-            const __half2 h = __floats2half2_rn(x0, x1);
-            const float2 hf = __half22float2(h);
+            float2 x = make_float2(odd ? recv : a[k2].x, odd ? a[k2].y : recv);
+            if (!kFullTile) {
+              if (!v0) x.x = 0.f;
+              if (!v1) x.y = 0.f;
+            }
+            const __half2 h = __floats2half2_rn(x.x, x.y);
+            const float2 lo = sub2(x, __half22float2(h));   // exact: x - hi
             const int o = (k1 + 16 * ((k2 + 8) & 15)) * 64 + col;
             *reinterpret_cast<__half2 *>(stg + o) = h;
-            *reinterpret_cast<__half2 *>(stg + 16384 + o) = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+            *reinterpret_cast<__half2 *>(stg + 16384 + o) = __floats2half2_rn(lo.x, lo.y);
           }
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // staging visible to the tensor stores
           if (p == 0) bulk_wait_read();   // the previous tile's stores have read their staging
@@ -554,7 +557,8 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
       release_slot(t);
       pass1(t);
       half_sync(bar_y);
-      pass2(t);
+      if (m_end - (m0 + t * kTile) >= kTile) pass2(t, std::true_type());
+      else pass2(t, std::false_type());
     }
     // the last tile's stores have read their buffer before another item's FIR refills it
     if (kTmaSt && p == 0) bulk_wait_read();
@@ -583,11 +587,11 @@ __device__ __forceinline__ void ppf_item(const Geometry &g, const typename Sampl
     if (half_sync_any(bar_x, failed || aborted())) return;
     if (next)
       with_variant(t + 1, [&](auto full, auto direct) {
-        pass2(t);
+        pass2(t, std::false_type());
         fir(t + 1, IA(), I16(), full, direct);
       });
     else
-      pass2(t);
+      pass2(t, std::false_type());
     half_sync(bar_y);
     if (next) release_slot(t + 1);
   }
