@@ -195,18 +195,22 @@ def test_brute_force_tiny_filter_bank():
 
 
 # ----------------------------------------------------------------------------- delay, weights, beam
-def test_single_station_unit_weight_reproduces_channelised_input():
+def check_single_station_unit_weight_reproduces_channelised_input(cls=O.Observation):
     """S = 1 at the array origin, beam at the phase centre: the beam is the channelised input
-    times the bandpass (Sections 3, 4.3)."""
+    times the bandpass of its channel (Sections 3, 4.3)."""
     bp = G.bandpass_ripple(N)
     for bpv in (None, bp):
-        ob = _obs(pc=(0.3, 0.4), bp=bpv)
+        ob = _obs(cls, pc=(0.3, 0.4), bp=bpv)
         blk = G.make_block(G.Workload("t", np.zeros((1, 3)), np.array([150e6]), np.zeros((1, 2)),
                                       (0.3, 0.4), 8 * N, 1, "V"), seed=7)
         chan = ob.ppf(blk, advance=False)
         vol = ob.beamform(ob.delay_correct(chan))          # [B, F, N, P, M]
         exp = np.transpose(chan[:, 0], (0, 3, 1, 2)) * (1.0 if bpv is None else bp.astype(np.float64)[None, :, None, None])
         assert np.max(np.abs(vol[0] - exp)) <= 1e-12 * np.max(np.abs(exp))
+
+
+def test_single_station_unit_weight_reproduces_channelised_input():
+    check_single_station_unit_weight_reproduces_channelised_input()
 
 
 def test_zero_delay_beam_is_station_sum():
@@ -392,11 +396,19 @@ class _TapsTimeReversed(O.Observation):
         self.h = self.h[::-1].copy()
 
 
+class _BandpassByFftBin(O.Observation):
+    """The bandpass indexed by FFT bin k instead of channel c = (k + N/2) mod N."""
+    def __init__(self, *a, **k):
+        super().__init__(*a, **k)
+        self.bp = np.roll(self.bp, self.N // 2)
+
+
 @pytest.mark.parametrize("cls,check", [
     (_ResidualUsesFullDelay, check_tone_at_beam_gains_S_squared),
     (_ShiftWrongWay, check_identity_taps_reproduce_shifted_input),
     (_WeightsUseCentreFrequency, check_tone_at_beam_gains_S_squared),
     (_TapsTimeReversed, check_impulse_reproduces_taps),
+    (_BandpassByFftBin, check_single_station_unit_weight_reproduces_channelised_input),
 ])
 def test_pins_catch_planted_mistakes(cls, check):
     with pytest.raises(AssertionError):
