@@ -281,10 +281,10 @@ def test_noise_adds_incoherently():
 
 
 # ----------------------------------------------------------------------------- Stokes (Section 4.5)
-def test_stokes_closed_forms():
+def check_stokes_closed_forms(stokes=O.stokes_from_voltages):
     X = np.array([1.0 + 0j, 1 + 1j, 0j, 3 - 2j])
     Y = np.array([1j, 1.0 + 0j, 2.0 + 0j, 0.5 + 4j])
-    s = O.stokes_from_voltages(X, Y, "IQUV")
+    s = stokes(X, Y, "IQUV")
     exp = []
     for x, y in zip(X, Y):
         xx, yy = abs(x) ** 2, abs(y) ** 2
@@ -292,7 +292,11 @@ def test_stokes_closed_forms():
         exp.append([xx + yy, xx - yy, 2 * z.real, 2 * z.imag])
     assert np.allclose(s.T, np.array(exp))
     assert np.allclose(s[:, 0], [2.0, 0.0, 0.0, -2.0])   # X = 1, Y = i: V = 2 Im(1 * conj(i)) = -2
-    assert np.allclose(O.stokes_from_voltages(X, Y, "I")[0], s[0])
+    assert np.allclose(stokes(X, Y, "I")[0], s[0])
+
+
+def test_stokes_closed_forms():
+    check_stokes_closed_forms()
 
 
 def test_stokes_fully_polarised_identity():
@@ -396,6 +400,12 @@ class _TapsTimeReversed(O.Observation):
         self.h = self.h[::-1].copy()
 
 
+class _WeightsConjugated(O.Observation):
+    """Weights with the phase sign of the DFT (exp(-2 pi i f tau)) instead of the delay's."""
+    def weights(self, f, channels=None):
+        return np.conj(super().weights(f, channels))
+
+
 class _BandpassByFftBin(O.Observation):
     """The bandpass indexed by FFT bin k instead of channel c = (k + N/2) mod N."""
     def __init__(self, *a, **k):
@@ -409,10 +419,23 @@ class _BandpassByFftBin(O.Observation):
     (_WeightsUseCentreFrequency, check_tone_at_beam_gains_S_squared),
     (_TapsTimeReversed, check_impulse_reproduces_taps),
     (_BandpassByFftBin, check_single_station_unit_weight_reproduces_channelised_input),
+    (_WeightsConjugated, check_tone_at_beam_gains_S_squared),
 ])
 def test_pins_catch_planted_mistakes(cls, check):
     with pytest.raises(AssertionError):
         check(cls)
+
+
+def test_pins_catch_wrong_stokes_v_sign():
+    """V = 2 Im(X conj Y) as printed (Section 4.5); the conjugate convention -2 Im(X conj Y) fails."""
+    def flipped(X, Y, kind):
+        out = O.stokes_from_voltages(X, Y, kind)
+        if kind == "IQUV":
+            out = out.copy()
+            out[3] = -out[3]
+        return out
+    with pytest.raises(AssertionError):
+        check_stokes_closed_forms(flipped)
 
 
 def test_pins_catch_wrong_fft_sign(monkeypatch):
