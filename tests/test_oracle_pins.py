@@ -308,12 +308,17 @@ def test_stokes_fully_polarised_identity():
     assert np.allclose(I ** 2, Qs ** 2 + U ** 2 + V ** 2, rtol=1e-12)
 
 
-def test_integration_sums_consecutive_spectra():
+def check_integration_sums_consecutive_spectra(integrate=O.integrate):
     p = np.arange(2 * 32, dtype=np.float64).reshape(2, 32)
     for q in (1, 2, 4, 8, 16):
-        r = O.integrate(p, q)
+        r = integrate(p, q)
         assert r.shape == (2, 32 // q)
         assert r[1, 1] == sum(p[1, q + i] for i in range(q))
+
+
+def test_integration_sums_consecutive_spectra():
+    """Brute force: the integrated Stokes sample is the sum (not the mean) of Q consecutive spectra."""
+    check_integration_sums_consecutive_spectra()
 
 
 def test_run_block_stokes_matches_stokes_of_voltages_and_sampled_path():
@@ -406,6 +411,13 @@ class _WeightsConjugated(O.Observation):
         return np.conj(super().weights(f, channels))
 
 
+class _ChannelsInBinOrder(O.Observation):
+    """Channels left in FFT-bin order (no (k + N/2) mod N reorder to ascending frequency)."""
+    def __init__(self, *a, **k):
+        super().__init__(*a, **k)
+        self.k_of_c = np.arange(self.N)
+
+
 class _BandpassByFftBin(O.Observation):
     """The bandpass indexed by FFT bin k instead of channel c = (k + N/2) mod N."""
     def __init__(self, *a, **k):
@@ -420,6 +432,7 @@ class _BandpassByFftBin(O.Observation):
     (_TapsTimeReversed, check_impulse_reproduces_taps),
     (_BandpassByFftBin, check_single_station_unit_weight_reproduces_channelised_input),
     (_WeightsConjugated, check_tone_at_beam_gains_S_squared),
+    (_ChannelsInBinOrder, check_tone_lands_in_its_channel),
 ])
 def test_pins_catch_planted_mistakes(cls, check):
     with pytest.raises(AssertionError):
@@ -436,6 +449,11 @@ def test_pins_catch_wrong_stokes_v_sign():
         return out
     with pytest.raises(AssertionError):
         check_stokes_closed_forms(flipped)
+
+
+def test_pins_catch_integration_as_mean():
+    with pytest.raises(AssertionError):
+        check_integration_sums_consecutive_spectra(lambda p, q: O.integrate(p, q) / q)
 
 
 def test_pins_catch_wrong_fft_sign(monkeypatch):
